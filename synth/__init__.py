@@ -1,0 +1,199 @@
+"""Seeded synthetic inputs for the TDSE workloads.
+
+This module only *samples the problem data* -- the initial wavefunction u0,
+the static potential profile V0 and its time factor f(t) (so that
+V(x, t) = f(t) V0(x)), and the parameters of the vector-potential pulse A(t)
+-- on the spatial grid that the problem statement fixes.  It contains none of
+the solver's arithmetic (no transforms, no phases, no quadrature, no phi = int
+A); both the CPU oracle and the CUDA path receive exactly these arrays.
+
+Grids (problem definition):
+  * periodic, Sec. 2.1: x_j = -pi + 2 pi j / M, j = 0..M-1 on [-pi, pi]^d;
+  * free space, Sec. 3.3: x_j = -1 + 2 (j-1) / M, j = 1..M on [-1, 1]^d.
+
+Workloads (shapes/values follow the paper's 1D/2D examples, Sec. 7):
+  * ``periodic_1d_cosine``  -- 1D periodic, N=128, Gaussian packet, 4-mode
+    cosine potential with time factor 1 + 0.5 sin 2t, A = 0, T=1, dt=1e-2;
+  * ``periodic_2d_wells``   -- 2D periodic 512^2, three Gaussians, four
+    attractive Gaussian wells, pulse A(t) = 2 sin^2(pi t/2) sin(10 t) (1,0),
+    T=2, dt=1e-3;
+  * ``periodic_1d_batch_member`` -- one member of the uneven 1D batch
+    (N in {256..16384}), T=1, dt=1e-3.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable, Optional, Sequence
+
+import numpy as np
+
+PERIODIC = 0
+FREE = 1
+
+
+def periodic_grid(M: int) -> np.ndarray:
+    """x_j = -pi + 2 pi j / M, j = 0..M-1 (Sec. 2.1)."""
+    return -math.pi + 2.0 * math.pi * np.arange(M, dtype=np.float64) / M
+
+
+def free_grid(M: int) -> np.ndarray:
+    """x_j = -1 + 2 (j-1) / M, j = 1..M (Sec. 3.3)."""
+    return -1.0 + 2.0 * np.arange(M, dtype=np.float64) / M
+
+
+@dataclasses.dataclass(frozen=True)
+class Pulse:
+    """A(t) = A0 sin^2(pi t / T_pulse) sin(omega t) * direction.
+
+    The workload tables use sin(omega t); the paper's eq. (apulse) prints
+    cos(omega t).  Only the sampling of A is defined here.
+    """
+
+    A0: float
+    omega: float
+    T_pulse: float
+    direction: tuple
+
+    def A(self, t) -> np.ndarray:
+        t = np.asarray(t, dtype=np.float64)
+        amp = self.A0 * np.sin(math.pi * t / self.T_pulse) ** 2 * np.sin(self.omega * t)
+        return np.multiply.outer(amp, np.asarray(self.direction, dtype=np.float64))
+
+
+@dataclasses.dataclass
+class Instance:
+    """One TDSE problem: data on the grid plus time stepping parameters."""
+
+    bc: int
+    shape: tuple
+    u0: np.ndarray            # complex128, shape `shape`
+    V0: np.ndarray            # float64, shape `shape`
+    vfac: Callable            # f(t), vectorised; V(x,t) = f(t) V0(x)
+    pulse: Optional[Pulse]    # None means A = 0
+    dt: float
+    nsteps: int
+    name: str = ""
+
+    @property
+    def dim(self) -> int:
+        return len(self.shape)
+
+    @property
+    def t_max(self) -> float:
+        return self.nsteps * self.dt
+
+    def vfac_table(self, sub: int = 8) -> np.ndarray:
+        """f(t) sampled at t = m dt / sub, m = 0 .. sub*nsteps."""
+        m = np.arange(sub * self.nsteps + 1, dtype=np.float64)
+        return np.asarray(self.vfac(m * self.dt / sub), dtype=np.float64).reshape(-1)
+
+
+def _const_one(t):
+    return np.ones_like(np.asarray(t, dtype=np.float64))
+
+
+def _grid_norm(u: np.ndarray, h: float) -> float:
+    return math.sqrt(float(np.sum(np.abs(u) ** 2)) * h ** u.ndim)
+
+
+def _periodised_gaussian_2d(X, Y, cx, cy, sigma, images=3):
+    out = np.zeros_like(X)
+    L = 2.0 * math.pi
+    for mx in range(-images, images + 1):
+        for my in range(-images, images + 1):
+            out += np.exp(-((X - cx - L * mx) ** 2 + (Y - cy - L * my) ** 2) / (2.0 * sigma * sigma))
+    return out
+
+
+def periodic_1d_cosine(seed: int = 1, M: int = 128, dt: float = 1e-2, nsteps: int = 100,
+                       amp: float = 5.0) -> Instance:
+    """1D periodic workload: u0 = normalised exp(-x^2/(2*0.3^2)) e^{3ix};
+    V(x,t) = (1 + 0.5 sin 2t) sum_{m=1..4} a_m cos(m x), a_m ~ U[-amp, amp]."""
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(-amp, amp, size=4)
+    x = periodic_grid(M)
+    u0 = np.exp(-x ** 2 / (2.0 * 0.3 ** 2)) * np.exp(3j * x)
+    u0 = u0 / _grid_norm(u0, 2.0 * math.pi / M)
+    V0 = sum(a[m - 1] * np.cos(m * x) for m in range(1, 5))
+    return Instance(PERIODIC, (M,), u0.astype(np.complex128), V0.astype(np.float64),
+                    lambda t: 1.0 + 0.5 * np.sin(2.0 * np.asarray(t, dtype=np.float64)),
+                    None, dt, nsteps, name=f"periodic_1d_cosine_M{M}")
+
+
+def periodic_2d_wells(seed: int = 2, M: int = 512, dt: float = 1e-3, nsteps: int = 2000,
+                      T_pulse: Optional[float] = None, A0: float = 2.0, omega: float = 10.0) -> Instance:
+    """2D periodic workload on [-pi,pi]^2: u0 = normalised sum of 3 Gaussians
+    (sigma ~ U[0.2,0.4], centres ~ U[-1.5,1.5]^2, phases ~ U[0,2pi)); V0 = sum
+    of 4 attractive wells -depth exp(-|x-c|^2/(2 sigma^2)), depth ~ U[5,20],
+    sigma ~ U[0.3,0.6], centres ~ U[-1.5,1.5]^2; both summed over lattice
+    images |m|<=3 so that they are smooth and periodic.  A(t) = A0
+    sin^2(pi t/T_pulse) sin(omega t) (1,0) with T_pulse = nsteps*dt by default."""
+    rng = np.random.default_rng(seed)
+    x = periodic_grid(M)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    u0 = np.zeros((M, M), dtype=np.complex128)
+    for _ in range(3):
+        s = rng.uniform(0.2, 0.4)
+        cx, cy = rng.uniform(-1.5, 1.5, size=2)
+        ph = rng.uniform(0.0, 2.0 * math.pi)
+        u0 += np.exp(1j * ph) * _periodised_gaussian_2d(X, Y, cx, cy, s)
+    u0 = u0 / _grid_norm(u0, 2.0 * math.pi / M)
+    V0 = np.zeros((M, M), dtype=np.float64)
+    for _ in range(4):
+        depth = rng.uniform(5.0, 20.0)
+        s = rng.uniform(0.3, 0.6)
+        cx, cy = rng.uniform(-1.5, 1.5, size=2)
+        V0 -= depth * _periodised_gaussian_2d(X, Y, cx, cy, s)
+    Tp = nsteps * dt if T_pulse is None else T_pulse
+    pulse = Pulse(A0, omega, Tp, (1.0, 0.0))
+    return Instance(PERIODIC, (M, M), u0, V0, _const_one, pulse, dt, nsteps,
+                    name=f"periodic_2d_wells_M{M}")
+
+
+BATCH_SIZES = tuple(2 ** p for p in range(8, 15))   # 256 .. 16384
+
+
+def periodic_1d_batch_member(i: int, seed: int = 4, dt: float = 1e-3, nsteps: int = 1000,
+                             sizes: Sequence[int] = BATCH_SIZES) -> Instance:
+    """Member i of the uneven 1D batch: N drawn uniformly from `sizes`; V = 4
+    cosine modes with a_m ~ U[-10,10]; pulse amplitude A0 ~ U[0,3], omega=10;
+    u0 = Gaussian with sigma ~ U[0.2,0.4], centre ~ U[-1,1], k0 ~ U[-5,5]."""
+    rng = np.random.default_rng([seed, i])
+    M = int(sizes[int(rng.integers(0, len(sizes)))])
+    a = rng.uniform(-10.0, 10.0, size=4)
+    A0 = rng.uniform(0.0, 3.0)
+    s = rng.uniform(0.2, 0.4)
+    c = rng.uniform(-1.0, 1.0)
+    k0 = rng.uniform(-5.0, 5.0)
+    x = periodic_grid(M)
+    L = 2.0 * math.pi
+    g = sum(np.exp(-(x - c - L * m) ** 2 / (2.0 * s * s)) for m in range(-3, 4))
+    u0 = g * np.exp(1j * k0 * x)
+    u0 = u0 / _grid_norm(u0, L / M)
+    V0 = sum(a[m - 1] * np.cos(m * x) for m in range(1, 5))
+    pulse = Pulse(A0, 10.0, nsteps * dt, (1.0,))
+    return Instance(PERIODIC, (M,), u0.astype(np.complex128), V0.astype(np.float64), _const_one,
+                    pulse, dt, nsteps, name=f"periodic_1d_batch_{i}_M{M}")
+
+
+def random_periodic(shape, seed: int, dt: float, nsteps: int, vamp: float = 5.0,
+                    pulse: Optional[Pulse] = None, vfac: Optional[Callable] = None,
+                    nmodes: int = 3) -> Instance:
+    """Small smooth random periodic problem for parity tests: u0 and V0 are
+    random trigonometric polynomials of degree `nmodes` per dimension."""
+    rng = np.random.default_rng(seed)
+    d = len(shape)
+    grids = np.meshgrid(*[periodic_grid(M) for M in shape], indexing="ij")
+    u0 = np.zeros(shape, dtype=np.complex128)
+    V0 = np.zeros(shape, dtype=np.float64)
+    for idx in np.ndindex(*([2 * nmodes + 1] * d)):
+        k = [i - nmodes for i in idx]
+        ph = sum(kk * g for kk, g in zip(k, grids))
+        w = math.exp(-0.5 * sum(kk * kk for kk in k))
+        u0 += w * (rng.normal() + 1j * rng.normal()) * np.exp(1j * ph)
+        V0 += vamp * w * (rng.normal() * np.cos(ph) + rng.normal() * np.sin(ph))
+    h = 2.0 * math.pi / shape[0]
+    u0 = u0 / _grid_norm(u0, h)
+    return Instance(PERIODIC, tuple(shape), u0, V0, vfac or _const_one, pulse, dt, nsteps,
+                    name=f"random_periodic_{'x'.join(map(str, shape))}")

@@ -1,0 +1,242 @@
+"""Pins for the periodic oracle (Sec. 2): closed forms, library routines,
+brute-force references and convergence orders.  No GPU."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import fields
+from oracle.periodic import PeriodicOracle, dft_matrices, rel_l2, wavenumbers
+from tests import _refs
+
+
+def _phi(pulse, d):
+    return fields.phi_callable(pulse, d)
+
+
+def _const_A(a):
+    a = np.asarray(a, dtype=np.float64)
+    return (lambda t: a), (lambda t: a * t)
+
+
+# --------------------------------------------------------------------------- DFT
+@pytest.mark.parametrize("shape", [(8,), (16,), (12,), (8, 6)])
+def test_dft_pair_matches_numpy_fft(shape):
+    """eq. ftperdisc / utrapkdisc with k = -M/2..M/2-1 equal fftshift(fft)/M^d."""
+    rng = np.random.default_rng(0)
+    f = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+    orc = PeriodicOracle(shape, 0.1, np.zeros(shape), lambda t: 1.0, lambda t: np.zeros(len(shape)))
+    ref = np.fft.fftshift(np.fft.fftn(f)) / np.prod(shape)
+    assert np.allclose(orc.fwd(f), ref, rtol=0, atol=1e-14)
+    assert np.allclose(orc.inv(ref), f, rtol=0, atol=1e-13)
+
+
+def test_dft_of_grid_mode_has_alternating_sign():
+    """e^{i k0 x_j} with x_j = -pi + 2 pi j/M has DFT (-1)^{k0} at k0 (reading C10)."""
+    M = 16
+    x = _refs.grid(M)
+    F, _ = dft_matrices(M)
+    for k0 in (-8, -3, 0, 5, 7):
+        fh = F @ np.exp(1j * k0 * x)
+        e = np.zeros(M, dtype=complex)
+        e[k0 + M // 2] = (-1) ** abs(k0)
+        assert np.allclose(fh, e, atol=1e-14)
+
+
+def test_wavenumbers_nyquist_negative():
+    assert list(wavenumbers(6)) == [-3, -2, -1, 0, 1, 2]
+
+
+# --------------------------------------------------------------- V = 0 is exact
+@pytest.mark.parametrize("shape,pulse", [
+    ((16,), synth.Pulse(3.0, 10.0, 1.0, (1.0,))),
+    ((8, 8), synth.Pulse(2.0, 10.0, 1.0, (0.8, -0.6))),
+])
+def test_free_particle_with_advection_exact(shape, pulse):
+    """V = 0: eq. uhatkinteq is explicit and the scheme reproduces it exactly at
+    any dt, including the Nyquist mode k = -M/2 (reading C9)."""
+    rng = np.random.default_rng(3)
+    d = len(shape)
+    coeffs = {}
+    for idx in np.ndindex(*shape):
+        k = tuple(int(i) - M // 2 for i, M in zip(idx, shape))
+        coeffs[k] = (rng.normal() + 1j * rng.normal()) * math.exp(-0.05 * sum(kk * kk for kk in k))
+    phi = _phi(pulse, d)
+    u0 = _refs.exact_free(coeffs, shape, 0.0, np.zeros(d))
+    dt, n = 0.05, 20
+    orc = PeriodicOracle(shape, dt, np.zeros(shape), lambda t: 1.0, phi)
+    u = orc.solve(u0, n)
+    ref = _refs.exact_free(coeffs, shape, n * dt, phi(n * dt))
+    assert rel_l2(u, ref) < 2e-13
+
+
+# ------------------------------------------------------------- convergence orders
+def _problem_1d(M=16, seed=5, vamp=4.0):
+    inst = synth.random_periodic((M,), seed, 0.1, 1, vamp=vamp)
+    return inst.u0, inst.V0
+
+
+VFAC = lambda t: 1.0 + 0.5 * math.sin(2.0 * t)
+
+
+@pytest.mark.parametrize("order,expected", [(2, 2), (4, 4), (6, 6), (8, 8)])
+def test_time_order_vs_pseudospectral_ode(order, expected):
+    """Error against the semi-discrete ODE (DOP853) falls like dt^order
+    with time-dependent V and a pulse A (Sec. 2.2; Fig. pererrvdt)."""
+    u0, V0 = _problem_1d()
+    pulse = synth.Pulse(3.0, 10.0, 0.5, (1.0,))
+    T = 0.5
+    ref = _refs.ode_reference((16,), u0, V0, VFAC, pulse.A, T)
+    steps = {2: (64, 128), 4: (32, 64), 6: (32, 64), 8: (32, 64)}[order]
+    errs = []
+    for n in steps:
+        orc = PeriodicOracle((16,), T / n, V0, VFAC, _phi(pulse, 1), order=order)
+        errs.append(rel_l2(orc.solve(u0, n), ref))
+    rate = math.log2(errs[0] / errs[1])
+    assert abs(rate - expected) < 0.6, (errs, rate)
+
+
+def test_startup_step_local_order():
+    """One Richardson start-up step (order 8) has local error O(dt^9)."""
+    u0, V0 = _problem_1d()
+    pulse = synth.Pulse(3.0, 10.0, 0.5, (1.0,))
+    errs = []
+    for dt in (0.08, 0.04):
+        ref = _refs.ode_reference((16,), u0, V0, VFAC, pulse.A, dt)
+        orc = PeriodicOracle((16,), dt, V0, VFAC, _phi(pulse, 1), order=8)
+        errs.append(rel_l2(orc.solve(u0, 1), ref))
+    rate = math.log2(errs[0] / errs[1])
+    assert rate > 8.3, (errs, rate)
+
+
+def test_constant_potential_closed_form():
+    """V = c: every mode obeys i y' = (k^2 - k A + c) y, so
+    u^_k(t) = exp(-i (k^2 + c) t + i k phi(t)) u^_k(0); 8th order in dt."""
+    M, c = 16, 7.0
+    rng = np.random.default_rng(9)
+    coeffs = {(k,): (rng.normal() + 1j * rng.normal()) * math.exp(-0.1 * k * k) for k in range(-8, 8)}
+    pulse = synth.Pulse(2.5, 10.0, 1.0, (1.0,))
+    phi = _phi(pulse, 1)
+    u0 = _refs.exact_free(coeffs, (M,), 0.0, [0.0])
+    T = 1.0
+    ref = _refs.exact_free(coeffs, (M,), T, phi(T)) * np.exp(-1j * c * T)
+    errs = []
+    for n in (16, 32):
+        orc = PeriodicOracle((M,), T / n, np.full(M, c), lambda t: 1.0, phi)
+        errs.append(rel_l2(orc.solve(u0, n), ref))
+    rate = math.log2(errs[0] / errs[1])
+    assert abs(rate - 8) < 0.6, (errs, rate)
+    assert errs[1] < 1e-6
+
+
+def test_time_independent_dense_propagator():
+    """Time-independent V, A = 0: converges to exp(-i H T) u0 (eigh)."""
+    u0, V0 = _problem_1d(M=16, seed=11, vamp=6.0)
+    T = 0.6
+    ref = _refs.dense_propagator_1d(u0, V0, T)
+    orc = PeriodicOracle((16,), T / 120, V0, lambda t: 1.0, lambda t: np.zeros(1))
+    assert rel_l2(orc.solve(u0, 120), ref) < 1e-10
+
+
+def test_norm_conservation():
+    """The continuous problem is unitary (||u(t)|| = ||u0|| = 1); the scheme's
+    norm drift is a discretisation error that falls at 8th order in dt."""
+    drift = []
+    for n in (200, 400):
+        inst = synth.periodic_1d_cosine(M=64, nsteps=n, dt=1.0 / n)
+        orc = PeriodicOracle(inst.shape, inst.dt, inst.V0, inst.vfac, _phi(None, 1))
+        u = orc.solve(inst.u0, n)
+        h = 2 * math.pi / 64
+        drift.append(abs(math.sqrt(np.sum(np.abs(u) ** 2) * h) - 1.0))
+    assert drift[1] < 5e-9
+    assert math.log2(drift[0] / drift[1]) > 7.0, drift
+
+
+def test_2d_separable_product():
+    """V = V1(x) + V2(y), u0 = a(x) b(y), A = (A1, A2) constant: the PDE
+    separates, u = u1(x,t) u2(y,t).  The 2D oracle converges to the product of
+    two 1D references (pins the axis handling of the 2D transforms)."""
+    M = 8
+    rng = np.random.default_rng(21)
+    x = _refs.grid(M)
+    V1 = 3.0 * np.cos(x) + 1.0 * np.sin(2 * x)
+    V2 = -2.0 * np.cos(2 * x) + 0.5 * np.sin(x)
+    a = np.exp(np.cos(x)) * np.exp(1j * x)
+    b = np.exp(0.5 * np.sin(x)) * (1 + 0.3j * np.cos(x))
+    A = np.array([1.7, -0.9])
+    T = 0.4
+    r1 = _refs.ode_reference((M,), a, V1, lambda t: 1.0, lambda t: A[:1], T)
+    r2 = _refs.ode_reference((M,), b, V2, lambda t: 1.0, lambda t: A[1:], T)
+    ref = np.outer(r1, r2)
+    V = V1[:, None] + V2[None, :]
+    u0 = np.outer(a, b)
+    errs = []
+    for n in (32, 64):
+        orc = PeriodicOracle((M, M), T / n, V, lambda t: 1.0, lambda t: A * t)
+        errs.append(rel_l2(orc.solve(u0, n), ref))
+    assert errs[1] < 1e-9
+    assert math.log2(errs[0] / errs[1]) > 7.0, errs
+
+
+# ----------------------------------------------- the pins catch planted mistakes
+def _run_pins(monkeypatch_ctx):
+    """Return which of three cheap pins still pass under a planted mistake."""
+    out = {}
+    try:
+        test_free_particle_with_advection_exact((16,), synth.Pulse(3.0, 10.0, 1.0, (1.0,)))
+        out["free"] = True
+    except AssertionError:
+        out["free"] = False
+    try:
+        test_time_order_vs_pseudospectral_ode(8, 8)
+        out["order8"] = True
+    except AssertionError:
+        out["order8"] = False
+    try:
+        test_2d_separable_product()
+        out["sep2d"] = True
+    except AssertionError:
+        out["sep2d"] = False
+    return out
+
+
+@pytest.mark.parametrize("mistake", ["phi_sign", "drop_history", "nyquist_plus", "transpose_2d", "mu0"])
+def test_planted_mistakes_fail_a_pin(monkeypatch, mistake):
+    """Plant a plausible bug in the oracle (on the CPU) and check a pin fails."""
+    import oracle.periodic as P
+    if mistake == "phi_sign":
+        orig = P.PeriodicOracle.P
+
+        def bad(self, t, s):
+            return orig(self, t - s, -s)
+        monkeypatch.setattr(P.PeriodicOracle, "P", bad)
+    elif mistake == "drop_history":
+        orig_init = P.PeriodicOracle.__init__
+
+        def bad_init(self, *a, **k):
+            orig_init(self, *a, **k)
+            if self.order == 8:
+                self.mu = self.mu.copy()
+                self.mu[7] = 0.0
+        monkeypatch.setattr(P.PeriodicOracle, "__init__", bad_init)
+    elif mistake == "nyquist_plus":
+        monkeypatch.setattr(P, "wavenumbers", lambda M: np.arange(-M // 2 + 1, M // 2 + 1, dtype=np.float64))
+    elif mistake == "transpose_2d":
+        orig_init = P.PeriodicOracle.__init__
+
+        def bad_init(self, *a, **k):
+            orig_init(self, *a, **k)
+            if self.d == 2:
+                self.k = [kk.T.copy() for kk in self.k]     # k_x and k_y swapped
+        monkeypatch.setattr(P.PeriodicOracle, "__init__", bad_init)
+    elif mistake == "mu0":
+        orig_init = P.PeriodicOracle.__init__
+
+        def bad_init(self, *a, **k):
+            orig_init(self, *a, **k)
+            self.mu = self.mu.copy()
+            self.mu[0] = self.mu[1]
+        monkeypatch.setattr(P.PeriodicOracle, "__init__", bad_init)
+    res = _run_pins(None)
+    assert not all(res.values()), res
