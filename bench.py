@@ -1,0 +1,382 @@
+"""Benchmark: point-steps/s of the periodic TDSE solver on one GB300.
+
+Workload (one bench "step" = one whole solve): the 2D periodic wells problem
+on [-pi,pi]^2, 512x512 grid, T = 2, dt = 1e-3 (2000 steps: 7 Richardson
+start-up steps + 1993 8th-order Adams steps), pulse A(t) = 2 sin^2(pi t/2)
+sin(10 t) (1,0), replicated as a batch of independent seeded instances so that
+the per-step working set (~27 MB per instance in mixed precision) exceeds the
+129 MB L2.  Point-steps = instances x 512^2 x 2000.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+                    [--batch B] [--impl reference]
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+M = 512
+DT = 1e-3
+NSTEPS = 2000
+ORDER = 8
+STARTUP = ORDER - 1
+METRIC = "point-steps/s (2D periodic 512^2, 8th-order, T=2)"
+# Algorithmic HBM bytes per point-step of the step operator: read u^ (16) and
+# 7 history slots, write u^ (16) and one slot; V read once (real).
+ALGO_BYTES = {"fp64": 16 + 7 * 16 + 8 + 16 + 16, "mixed": 16 + 7 * 8 + 4 + 16 + 8}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def instances(rank: int, batch: int):
+    return [synth.periodic_2d_wells(seed=1000 * rank + 2 + i, M=M, dt=DT, nsteps=NSTEPS) for i in range(batch)]
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clock, max clock, reasons)."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------- GPU arm
+def launches_per_solve(dim: int) -> int:
+    per_op = 1 if dim == 1 else 3            # kernels per application of the step operator
+    L = ORDER // 2
+    sub = sum(2 ** c for c in range(L))      # trapezoid sub-steps per start-up step
+    startup = STARTUP * (L + sub * per_op + 1 + per_op)   # copy_slot per chain, sub-steps, combine, refresh
+    init = 1 if dim == 1 else 2
+    return init + startup + (NSTEPS - STARTUP) * per_op
+
+
+def run_gpu(args, ws, rank, local):
+    import torch
+    from paper_2001_06113_gb300 import Problem
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    insts = instances(rank, args.batch)
+    B = len(insts)
+    prob = Problem((M, M), DT, NSTEPS, order=ORDER, batch=B, precision=args.precision, stream=stream)
+    pinned_V = [torch.from_numpy(it.V0).pin_memory() for it in insts]
+    pinned_u = [torch.from_numpy(it.u0).pin_memory() for it in insts]
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def load_inputs():
+        for b, it in enumerate(insts):
+            prob.set_potential(pinned_V[b], None, instance=b)
+            p = it.pulse
+            prob.set_pulse(p.A0, p.omega, p.T_pulse, p.direction, instance=b)
+            prob.set_initial(pinned_u[b], instance=b)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    load_inputs()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            prob.set_initial(pinned_u[0], instance=0)
+            for b in range(1, B):
+                prob.set_initial(pinned_u[b], instance=b)
+            prob.step(NSTEPS)
+        stream.synchronize()
+
+    # ---- device-timed region: K whole solves, inputs resident, L2 flushed between solves
+    times = []
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                for b in range(B):
+                    prob.set_initial(pinned_u[b], instance=b)   # resets the run (H2D outside the events)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                prob.step(NSTEPS)
+                e1.record(stream)
+            stream.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        torch.cuda.synchronize()
+        barrier()
+    t_solve = float(np.mean(times))
+    if ws > 1:
+        tt = torch.tensor([t_solve], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_solve = float(tt.item())
+    points = M * M
+    value = ws * B * points * NSTEPS / t_solve
+
+    # ---- step-operator roofline: events around single Adams steps (3 pass kernels)
+    with torch.cuda.stream(stream):
+        for b in range(B):
+            prob.set_initial(pinned_u[b], instance=b)
+        prob.step(STARTUP + 8)
+        nmeas = 50
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(nmeas + 1)]
+        evs[0].record(stream)
+        for i in range(nmeas):
+            prob.step(1)
+            evs[i + 1].record(stream)
+    stream.synchronize()
+    dts = np.array([evs[i].elapsed_time(evs[i + 1]) / 1e3 for i in range(nmeas)])
+    t_step = float(np.mean(dts))
+    algo = ALGO_BYTES[args.precision] * B * points
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    achieved = algo / t_step / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", f"traffic_step2d_{args.precision}.json")
+    if os.path.exists(tpath):
+        try:
+            tr = json.load(open(tpath))
+            if tr.get("batch") and tr.get("bytes_per_step"):
+                traffic = tr["bytes_per_step"] * B / tr["batch"]
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_src,
+                "kernel": "2D step operator (col_begin + row_mid + col_end)",
+                "algorithmic_bytes_per_point_step": ALGO_BYTES[args.precision],
+                "step_ms_p50": round(float(np.percentile(dts, 50)) * 1e3, 4),
+                "step_ms_p99": round(float(np.percentile(dts, 99)) * 1e3, 4)}
+
+    # ---- accuracy of this configuration on a sample instance (vs the FP64 GPU path,
+    #      itself checked against the oracle by the test suite)
+    stated_err = None
+    if args.precision == "mixed" and rank == 0:
+        ref = Problem((M, M), DT, NSTEPS, order=ORDER, batch=1, precision="fp64", stream=stream)
+        it = insts[0]
+        ref.set_potential(it.V0)
+        p = it.pulse
+        ref.set_pulse(p.A0, p.omega, p.T_pulse, p.direction)
+        ref.set_initial(it.u0)
+        with torch.cuda.stream(stream):
+            ref.step(NSTEPS)
+            prob.set_initial(pinned_u[0], instance=0)
+            for b in range(1, B):
+                prob.set_initial(pinned_u[b], instance=b)
+            prob.step(NSTEPS)
+        u_ref = ref.read_u(0)
+        u_mix = prob.read_u(0)
+        stated_err = float(np.sqrt(np.sum(np.abs(u_mix - u_ref) ** 2) / np.sum(np.abs(u_ref) ** 2)))
+        ref.close()
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        out = torch.empty((B, M, M), dtype=torch.complex128).pin_memory()
+        e2e_times = []
+        with torch.cuda.stream(stream):
+            for _ in range(max(1, min(args.steps, 3))):
+                flush.zero_()
+                stream.synchronize()
+                barrier()
+                t0 = time.perf_counter()
+                load_inputs()
+                prob.step(NSTEPS)
+                prob.read_u(-1, out=out)
+                e2e_times.append(time.perf_counter() - t0)
+        te = float(np.mean(e2e_times))
+        if ws > 1:
+            tt = torch.tensor([te], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            te = float(tt.item())
+        h2d = B * (points * 8 + points * 16 + 2 * (8 * NSTEPS + 1) * 8)
+        e2e = {"value": ws * B * points * NSTEPS / te, "unit": "point-steps/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": B * points * 16}
+
+    prob.close()
+    return dict(value=value, t_solve=t_solve, roofline=roofline, e2e=e2e, clocks=clk.summary(),
+                stated_err=stated_err, B=B)
+
+
+# ---------------------------------------------------------------- CPU oracle arm
+def oracle_sample(nadams: int = 6, seed: int = 2):
+    """Time the CPU oracle (as it stands) on a bounded sample of the workload:
+    `nadams` 8th-order Adams steps of one 512^2 instance, history seeded with
+    (Vu)^ of u0 (same cost per step as a real run).  Returns point-steps/s."""
+    from oracle.periodic import oracle_for
+    it = synth.periodic_2d_wells(seed=seed, M=M, dt=DT, nsteps=NSTEPS)
+    orc = oracle_for(it)
+    u = it.u0
+    h0 = orc.fwd(orc.V(0.0) * u)
+    n0 = 100
+    hist = {n0 - j: h0 for j in range(1, ORDER)}
+    t0 = time.perf_counter()
+    for k in range(nadams):
+        n = n0 + k
+        t = n * DT
+        u = orc.adams_step(u, t, hist, n)
+        hist[n] = orc.fwd(orc.V(t) * u)
+        hist.pop(n - ORDER, None)
+    el = time.perf_counter() - t0
+    return M * M * nadams / el, el
+
+
+def cpu_cores() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        n = [d.get("num_threads") for d in info if d.get("internal_api") in ("openblas", "mkl", "blis")]
+        if n and n[0]:
+            return int(n[0])
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        vals = []
+        for _ in range(args.warmup):
+            oracle_sample(nadams=2)
+        for _ in range(args.steps):
+            v, _ = oracle_sample(nadams=20)
+            vals.append(v)
+        value = float(np.mean(vals))
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "point-steps/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * M * M * 20 / value, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "2D periodic wells 512x512, dt=1e-3, 8th-order Adams (CPU oracle sample)",
+                           "grid": [M, M], "dt": DT, "order": ORDER},
+                "cpu_baseline": {"value": value, "unit": "point-steps/s", "cores": cpu_cores(), "kind": "oracle",
+                                 "sample": "20 Adams steps of one 512^2 instance per bench step (direct O(M^2) DFT sums)"},
+                "e2e": {"value": value, "unit": "point-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    if ws > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    res = run_gpu(args, ws, rank, local)
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and ws == 1:
+            # spawn-free: the oracle runs in this process after all GPU work is done
+            v, el = oracle_sample(nadams=60)
+            cpu = {"value": v, "unit": "point-steps/s", "cores": cpu_cores(), "kind": "oracle",
+                   "sample": f"60 8th-order Adams steps of one 512^2 instance ({el:.1f} s; direct O(M^2) DFT sums, "
+                             "numpy/OpenBLAS)"}
+        line = {
+            "metric": METRIC, "value": res["value"], "unit": "point-steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["t_solve"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64+f64" if args.precision == "mixed" else "c128",
+            "data": "synthetic",
+            "config": {"workload": f"2D periodic wells 512x512, T=2, dt=1e-3 (2000 steps), 8th-order Adams, "
+                                   f"batch of {res['B']} seeded instances per GPU, {args.precision}",
+                       "grid": [M, M], "nsteps": NSTEPS, "dt": DT, "order": ORDER, "batch_per_gpu": res["B"],
+                       "precision": args.precision, "l2": "flushed (256 MB write) before each timed solve; "
+                                                         "per-step working set > L2",
+                       "step": "one whole solve (7 Richardson start-up + 1993 Adams steps) of the batch",
+                       "parallelism": f"replicas x{ws}"},
+            "rel_l2_vs_fp64": res["stated_err"],
+            "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
+            "gpu_launches": launches_per_solve(2) * args.steps,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,179 @@
+/*
+ * tdse.h -- C ABI of the GB300 (sm_103a) Volterra / spectral-recurrence solver
+ * for the time-dependent Schroedinger equation with potential V(x,t) and a
+ * uniform vector potential A(t):
+ *
+ *     i u_t = -Laplace(u) + V(x,t) u + i A(t).grad(u)              (eq. schrodfree)
+ *
+ * Method: Kaye, Barnett & Greengard, "A high-order integral equation-based
+ * solver for the time-dependent Schroedinger equation", arXiv:2001.06113.
+ * Each time step applies the history-dependent operator of Sec. 2: the mode
+ * coefficients are advanced by the exact one-step phase
+ *     exp(-i |k|^2 dt + i k.(phi(t) - phi(t-dt))),   phi(t) = int_0^t A    (eq. uhatkrecur)
+ * plus an n-th order implicit Adams quadrature of the history of (Vu)^
+ * (eq. uadamsk), the implicit step being diagonal in physical space.  The
+ * first steps use iterated Richardson extrapolation of the trapezoidal rule
+ * (eq. utrapkdisc, Sec. 2.2).
+ *
+ * Conventions (Sec. 2.1):
+ *   periodic grid  x_j = -pi + 2 pi j / M, j = 0..M-1, per dimension;
+ *   modes          k = -M/2 .. M/2-1 (stored in FFT order: index m holds k = m
+ *                  for m < M/2 and k = m - M otherwise);
+ *   forward DFT    f^_k = (1/M) sum_j e^{-2 pi i j k/M} f_j      (eq. ftperdisc)
+ *   inverse DFT    f_j  = sum_k e^{+2 pi i j k/M} f^_k.
+ *   2D arrays are row-major [n0][n1]; axis 0 is the first coordinate.
+ *   Complex arrays are interleaved (re, im) doubles.
+ *
+ * Memory: the library never allocates device memory.  The caller queries
+ * tdse_workspace_bytes() and passes one device buffer (e.g. a PyTorch uint8
+ * tensor) to tdse_bind_workspace(); all state, history, tables and scratch
+ * live in it.  The caller keeps that buffer alive until tdse_destroy().
+ * Host pointers passed to calls are only read/written during the call (the
+ * call synchronises the stream when it copies to or from host memory);
+ * device pointers must stay valid until the stream reaches the call's work.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  All device work of a call is enqueued on that stream, in order.
+ *
+ * Errors: every call returns a tdse_status; nothing else crosses the ABI.
+ * tdse_last_error() gives a message for the last failing call on a context.
+ * A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef TDSE_H
+#define TDSE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdse_ctx tdse_ctx;
+
+typedef enum {
+    TDSE_OK = 0,
+    TDSE_EINVAL = -1,        /* bad argument or configuration                  */
+    TDSE_ENOMEM = -2,        /* workspace too small / not bound                */
+    TDSE_ECUDA = -3,         /* a CUDA runtime call or kernel launch failed    */
+    TDSE_ETIMEOUT = -4,      /* a bounded device wait gave up                  */
+    TDSE_ENONFINITE = -5,    /* NaN/Inf found in the state                     */
+    TDSE_ESTATE = -6,        /* call out of order (e.g. step before inputs)    */
+    TDSE_EUNSUPPORTED = -7   /* valid for the method, not built in this library */
+} tdse_status;
+
+enum { TDSE_PERIODIC = 0, TDSE_FREE = 1 };
+enum { TDSE_FP64 = 0, TDSE_MIXED = 1 };
+enum { TDSE_HOST = 0, TDSE_DEVICE = 1 };
+
+/*
+ * Problem configuration (Sec. 2 periodic scheme).
+ *   dim        1 or 2.
+ *   bc         TDSE_PERIODIC (domain [-pi,pi]^dim).
+ *   n[2]       grid points per dimension (powers of two; 1D: 8..8192,
+ *              2D: 8..1024 per dimension).  n[1] is ignored for dim = 1.
+ *   batch      number of independent instances that share n, dt, nsteps,
+ *              order and precision; each has its own V, A and u0.  >= 1.
+ *   dt         time step.
+ *   nsteps     number of steps the precomputed tables cover (t_max = nsteps*dt).
+ *   order      implicit Adams order n: even, 2..8 (Table 1 is n = 8).
+ *   startup_steps  Richardson start-up steps; -1 selects order-1 (the paper's
+ *              "seven" for n = 8).  Must be >= order-2 and <= nsteps.
+ *   precision  TDSE_FP64: every stage in complex FP64.
+ *              TDSE_MIXED: transforms, pointwise product and history sum in
+ *              complex FP32; the mode state u^ and its phase recurrence, the
+ *              phase tables and the Adams weights in FP64.
+ */
+typedef struct {
+    int dim;
+    int bc;
+    int n[2];
+    int batch;
+    double dt;
+    int nsteps;
+    int order;
+    int startup_steps;
+    int precision;
+} tdse_config;
+
+/* Vector potential callback: writes A(t) (dim components) to A_out. */
+typedef void (*tdse_field_fn)(double t, double* A_out, void* user);
+
+/* Validate `cfg` and create a context (host only; no CUDA call).
+ * Errors: TDSE_EINVAL for an invalid configuration, TDSE_EUNSUPPORTED for a
+ * size this build does not instantiate, TDSE_ENOMEM if host allocation fails. */
+tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out);
+
+/* Bytes of device workspace the context needs (0 if ctx is NULL). */
+size_t tdse_workspace_bytes(const tdse_ctx* ctx);
+
+/* Bind caller-owned device memory of at least tdse_workspace_bytes() bytes,
+ * 256-byte aligned, and build the device tables (twiddles, Adams weights,
+ * kinetic phase tables) on `stream`.  Errors: TDSE_ENOMEM if too small,
+ * TDSE_EINVAL if misaligned, TDSE_ECUDA on a CUDA failure. */
+tdse_status tdse_bind_workspace(tdse_ctx* ctx, void* device_ptr, size_t bytes, void* stream);
+
+/* V(x,t) = f(t) V0(x) for instance `instance` (0-based; -1 = every instance).
+ *   V0           n0*n1 real values on the grid (host or device per `where`).
+ *   time_factor  NULL for f = 1, else HOST array of 8*nsteps+1 values
+ *                f(m dt/8), m = 0..8*nsteps (the step and Richardson sub-step
+ *                times).  Copied during the call. */
+tdse_status tdse_set_potential(tdse_ctx* ctx, int instance, const double* V0,
+                               const double* time_factor, int where, void* stream);
+
+/* A(t) for an instance (-1 = all) from a callback (NULL = A == 0).  The library
+ * computes phi(t) = int_0^t A (eq. phi) by 8-point Gauss-Legendre on each
+ * sub-interval of length dt/8, then the per-interval phase tables on `stream`.
+ * The callback is called only during this call. */
+tdse_status tdse_set_vector_potential(tdse_ctx* ctx, int instance, tdse_field_fn A,
+                                      void* user, void* stream);
+
+/* Built-in pulse A(t) = A0 sin^2(pi t / T_pulse) sin(omega t) * direction
+ * (direction: dim values).  Same integration as tdse_set_vector_potential. */
+tdse_status tdse_set_pulse(tdse_ctx* ctx, int instance, double A0, double omega,
+                           double T_pulse, const double* direction, void* stream);
+
+/* Initial wavefunction u0 (n0*n1 interleaved complex, host or device) for an
+ * instance (-1 = all instances get the same u0).  Resets the step counter of
+ * the whole context to 0. */
+tdse_status tdse_set_initial(tdse_ctx* ctx, int instance, const double* u0, int where,
+                             void* stream);
+
+/* Advance every instance by `nsteps` steps of dt (asynchronous on `stream`).
+ * The first call after tdse_set_initial transforms u0 and V(0)u0; the first
+ * startup_steps steps use Richardson start-up, later ones the Adams scheme.
+ * Errors: TDSE_ESTATE if an instance lacks V, A or u0 (A may be left unset:
+ * then A == 0), TDSE_EINVAL if the tables' nsteps would be exceeded. */
+tdse_status tdse_step(tdse_ctx* ctx, int nsteps, void* stream);
+
+/* Step until t >= T (T rounded to the nearest multiple of dt). */
+tdse_status tdse_solve_to(tdse_ctx* ctx, double T, void* stream);
+
+/* u(x, t_current) = inverse DFT of u^ in FP64, for one instance (or -1 = all,
+ * laid out [batch][n0*n1]), into u_out (interleaved complex, host or device).
+ * Host destinations are complete when the call returns. */
+tdse_status tdse_read_u(tdse_ctx* ctx, int instance, double* u_out, int where, void* stream);
+
+/* Scan the mode state of every instance for NaN/Inf (synchronises `stream`).
+ * Returns TDSE_ENONFINITE if any is found. */
+tdse_status tdse_check_finite(tdse_ctx* ctx, void* stream);
+
+/* Number of completed steps and the current time t = steps * dt. */
+int tdse_step_index(const tdse_ctx* ctx);
+double tdse_time(const tdse_ctx* ctx);
+
+/* The implicit Adams weights mu_0..mu_{order-1} this library uses
+ * (Sec. 2.2; Table 1 for order 8), written to mu_out. */
+tdse_status tdse_adams_weights(int order, double* mu_out);
+
+/* Message of the last failing call on `ctx` ("" if none; static string if
+ * ctx is NULL). */
+const char* tdse_last_error(const tdse_ctx* ctx);
+
+/* Release the context (host memory only; the caller frees the workspace). */
+void tdse_destroy(tdse_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDSE_H */

@@ -1,0 +1,197 @@
+"""GB300-native (sm_103a) solver for the time-dependent Schroedinger equation
+by the Volterra / spectral-recurrence method of Kaye, Barnett & Greengard
+(arXiv:2001.06113).
+
+Every step of the method runs in the CUDA kernels of ``libtdse_gb300.so``
+(C ABI in ``include/tdse.h``); this package only marshals arguments:
+PyTorch provides the device workspace and the stream.  There is no CPU
+fallback: if the library is not built, using it raises ImportError.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Callable, Optional, Sequence
+
+import numpy as np
+
+from . import _native
+from ._native import DEVICE, FP64, HOST, MIXED, PERIODIC, TdseError
+
+__all__ = ["Problem", "TdseError", "adams_weights", "FP64", "MIXED", "PERIODIC"]
+
+
+def _check(status: int, ctx=None):
+    if status != _native.TDSE_OK:
+        msg = ""
+        if ctx is not None:
+            raw = _native.lib().tdse_last_error(ctx)
+            msg = raw.decode() if raw else ""
+        raise TdseError(status, msg)
+
+
+def adams_weights(order: int) -> np.ndarray:
+    """The library's implicit Adams weights mu_0..mu_{order-1} (Sec. 2.2)."""
+    out = np.zeros(order, dtype=np.float64)
+    _check(_native.lib().tdse_adams_weights(order, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def _stream_handle(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _as_buffer(x, dtype):
+    """(pointer, where, keepalive) for a host numpy array or a torch tensor."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(x, torch.Tensor):
+        tdt = torch.complex128 if dtype == np.complex128 else torch.float64
+        t = x.detach()
+        if t.dtype != tdt:
+            t = t.to(tdt)
+        t = t.contiguous()
+        return ctypes.c_void_p(t.data_ptr()), (DEVICE if t.is_cuda else HOST), t
+    a = np.ascontiguousarray(np.asarray(x, dtype=dtype))
+    return ctypes.c_void_p(a.ctypes.data), HOST, a
+
+
+class Problem:
+    """A batch of periodic TDSE instances sharing grid, dt, step count and order.
+
+    Parameters mirror ``tdse_config``: ``shape`` (n,) or (n0, n1); ``dt``;
+    ``nsteps`` (steps the tables cover); ``order`` (Adams order, even <= 8);
+    ``batch``; ``precision`` ("fp64" or "mixed"); ``startup_steps`` (-1 =
+    order-1).  The device workspace is a torch uint8 tensor owned here.
+    """
+
+    def __init__(self, shape: Sequence[int], dt: float, nsteps: int, order: int = 8, batch: int = 1,
+                 precision: str = "fp64", startup_steps: int = -1, device=None, stream=None):
+        import torch
+        self._lib = _native.lib()
+        self.shape = tuple(int(s) for s in shape)
+        self.batch = int(batch)
+        self.dt = float(dt)
+        self.nsteps = int(nsteps)
+        cfg = _native.TdseConfig()
+        cfg.dim = len(self.shape)
+        cfg.bc = PERIODIC
+        cfg.n[0] = self.shape[0]
+        cfg.n[1] = self.shape[1] if len(self.shape) > 1 else 1
+        cfg.batch = self.batch
+        cfg.dt = self.dt
+        cfg.nsteps = self.nsteps
+        cfg.order = int(order)
+        cfg.startup_steps = int(startup_steps)
+        cfg.precision = {"fp64": FP64, "mixed": MIXED}[precision]
+        self.precision = precision
+        self._ctx = ctypes.c_void_p()
+        _check(self._lib.tdse_create(ctypes.byref(cfg), ctypes.byref(self._ctx)))
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.workspace_bytes = int(self._lib.tdse_workspace_bytes(self._ctx))
+        self._ws = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws.data_ptr()
+        aligned = (base + 255) & ~255
+        self._stream = stream
+        _check(self._lib.tdse_bind_workspace(self._ctx, ctypes.c_void_p(aligned), self.workspace_bytes,
+                                             _stream_handle(stream)), self._ctx)
+        self._callbacks = []
+
+    @property
+    def npoints(self) -> int:
+        return int(np.prod(self.shape))
+
+    def set_potential(self, V0, time_factor=None, instance: int = -1):
+        """V(x,t) = f(t) V0(x); time_factor = f(m dt/8), m = 0..8*nsteps (host array) or None."""
+        pv, where, keep = _as_buffer(V0, np.float64)
+        tf_ptr = None
+        if time_factor is not None:
+            tf = np.ascontiguousarray(np.asarray(time_factor, dtype=np.float64))
+            if tf.size != 8 * self.nsteps + 1:
+                raise ValueError("time_factor must have 8*nsteps+1 samples")
+            tf_ptr = ctypes.c_void_p(tf.ctypes.data)
+        _check(self._lib.tdse_set_potential(self._ctx, instance, pv, tf_ptr, where, _stream_handle(self._stream)),
+               self._ctx)
+        del keep
+
+    def set_pulse(self, A0: float, omega: float, T_pulse: float, direction, instance: int = -1):
+        d = (ctypes.c_double * 2)(*(list(direction) + [0.0, 0.0])[:2])
+        _check(self._lib.tdse_set_pulse(self._ctx, instance, A0, omega, T_pulse, d, _stream_handle(self._stream)),
+               self._ctx)
+
+    def set_vector_potential(self, A: Optional[Callable], instance: int = -1):
+        """A(t) -> sequence of len(shape) floats, or None for A = 0."""
+        dim = len(self.shape)
+        if A is None:
+            cb = _native.FIELD_FN()
+        else:
+            def _cb(t, out, user):
+                v = A(t)
+                for i in range(dim):
+                    out[i] = float(v[i])
+            cb = _native.FIELD_FN(_cb)
+        self._callbacks.append(cb)
+        _check(self._lib.tdse_set_vector_potential(self._ctx, instance, cb, None, _stream_handle(self._stream)),
+               self._ctx)
+
+    def set_initial(self, u0, instance: int = -1):
+        pu, where, keep = _as_buffer(u0, np.complex128)
+        _check(self._lib.tdse_set_initial(self._ctx, instance, pu, where, _stream_handle(self._stream)), self._ctx)
+        del keep
+
+    def step(self, n: int = 1):
+        _check(self._lib.tdse_step(self._ctx, int(n), _stream_handle(self._stream)), self._ctx)
+
+    def solve_to(self, T: float):
+        _check(self._lib.tdse_solve_to(self._ctx, float(T), _stream_handle(self._stream)), self._ctx)
+
+    def read_u(self, instance: int = -1, out=None):
+        """u on the grid: numpy complex128 (host) by default, or into `out`
+        (numpy array or torch tensor, host or cuda, complex128)."""
+        nb = self.batch if instance == -1 else 1
+        shape = ((nb,) if instance == -1 else ()) + self.shape
+        if out is None:
+            out = np.empty(shape, dtype=np.complex128)
+        try:
+            import torch
+            is_t = isinstance(out, torch.Tensor)
+        except ImportError:  # pragma: no cover
+            is_t = False
+        if is_t:
+            ptr, where = ctypes.c_void_p(out.data_ptr()), (DEVICE if out.is_cuda else HOST)
+        else:
+            ptr, where = ctypes.c_void_p(out.ctypes.data), HOST
+        _check(self._lib.tdse_read_u(self._ctx, instance, ptr, where, _stream_handle(self._stream)), self._ctx)
+        return out
+
+    def check_finite(self):
+        _check(self._lib.tdse_check_finite(self._ctx, _stream_handle(self._stream)), self._ctx)
+
+    @property
+    def step_index(self) -> int:
+        return int(self._lib.tdse_step_index(self._ctx))
+
+    @property
+    def time(self) -> float:
+        return float(self._lib.tdse_time(self._ctx))
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.tdse_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

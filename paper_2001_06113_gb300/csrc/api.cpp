@@ -1,0 +1,601 @@
+// C ABI of the periodic TDSE solver (see include/tdse.h): context, workspace
+// layout, host-side setup (Adams weights, phi(t), Richardson coefficients,
+// interval schedule) and the launch sequence of each time step.
+#include "tdse.h"
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kargs.h"
+
+using namespace tdse;
+
+namespace {
+
+constexpr int SUB = 8;   // fine time grid: t_m = m dt / 8 (Richardson sub-steps down to dt/8)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Implicit Adams weights (Sec. 2.2): mu_j = int_0^1 l_j(theta) dtheta, l_j the
+// Lagrange basis polynomial on the nodes theta = 0..n-1 (s = t - theta dt).
+// Exact integer arithmetic: l_j = N_j(theta) / D_j with integer coefficients,
+// int_0^1 theta^p = 1/(p+1) scaled by lcm(1..n).  The final quotient of two
+// exact integers is correctly rounded.
+bool adams_weights(int n, double* mu) {
+    if (n < 1 || n > 12) return false;
+    long long lcm = 1;
+    for (long long q = 2; q <= n; ++q) {
+        long long a = lcm, b = q;
+        while (b) { long long t = a % b; a = b; b = t; }
+        lcm = lcm / a * q;
+    }
+    for (int j = 0; j < n; ++j) {
+        std::vector<long long> c(1, 1);       // coefficients of prod_{m != j} (theta - m), ascending
+        long long D = 1;
+        for (int m = 0; m < n; ++m) {
+            if (m == j) continue;
+            std::vector<long long> nc(c.size() + 1, 0);
+            for (size_t p = 0; p < c.size(); ++p) {
+                nc[p + 1] += c[p];
+                nc[p] -= (long long)m * c[p];
+            }
+            c.swap(nc);
+            D *= (long long)(j - m);
+        }
+        long long num = 0;
+        for (size_t p = 0; p < c.size(); ++p) num += c[p] * (lcm / (long long)(p + 1));
+        mu[j] = (double)num / ((double)lcm * (double)D);
+    }
+    return true;
+}
+
+// q-point Gauss-Legendre nodes/weights on [-1,1] by Newton on P_q (long double).
+void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(q, 0.0);
+    w.assign(q, 0.0);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int i = 0; i < q; ++i) {
+        long double z = cosl(pi * (i + 0.75L) / (q + 0.5L));
+        long double dp = 0;
+        for (int it = 0; it < 100; ++it) {
+            long double p0 = 1, p1 = z;
+            for (int k = 2; k <= q; ++k) {
+                long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = q * (z * p1 - p0) / (z * z - 1);
+            long double dz = p1 / dp;
+            z -= dz;
+            if (fabsl(dz) < 1e-19L) break;
+        }
+        long double p0 = 1, p1 = z;
+        for (int k = 2; k <= q; ++k) {
+            long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = q * (z * p1 - p0) / (z * z - 1);
+        x[i] = (double)z;
+        w[i] = (double)(2.0L / ((1 - z * z) * dp * dp));
+    }
+}
+
+struct Pulse {
+    double A0, omega, Tp, dir[2];
+};
+
+void pulse_fn(double t, double* A, void* user) {
+    const Pulse* p = static_cast<const Pulse*>(user);
+    const double s = std::sin(M_PI * t / p->Tp);
+    const double amp = p->A0 * s * s * std::sin(p->omega * t);
+    A[0] = amp * p->dir[0];
+    A[1] = amp * p->dir[1];
+}
+
+}  // namespace
+
+struct tdse_ctx {
+    tdse_config cfg{};
+    int d = 1, n0 = 0, n1 = 1;
+    size_t NP = 0;
+    int B = 1, m = 8, L = 4, S = 7, S_eff = 7, RS = 7, ntf = 0, n_int = 0;
+    int nh = 1, nl = 1, lb = 0;
+    size_t rsz = 16;            // ring element bytes
+    double mu[8] = {0};
+    double rich[4] = {0};
+    std::vector<int2> intervals;
+    // workspace
+    char* ws = nullptr;
+    size_t ws_need = 0;
+    struct {
+        size_t uhat, ring, chain_uhat, chain_ring, aux, aux2, V0, V0f, tfac, phi, kin64, kin32, adv64, adv32,
+            q64, q32, tw64_0, tw32_0, tw64_1, tw32_1, iv, scratch, end;
+    } off{};
+    std::vector<char> have_V, have_u0;
+    int step = 0;
+    bool inited = false;
+    std::string err;
+
+    template <class T> T* P(size_t o) const { return reinterpret_cast<T*>(ws + o); }
+    tdse_status fail(tdse_status s, const std::string& msg) {
+        err = msg;
+        return s;
+    }
+};
+
+static tdse_status cuda_fail(tdse_ctx* c, cudaError_t e, const char* where) {
+    return c->fail(TDSE_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define TDSE_CK(ctx, expr)                                       \
+    do {                                                         \
+        cudaError_t e__ = (expr);                                \
+        if (e__ != cudaSuccess) return cuda_fail(ctx, e__, #expr); \
+    } while (0)
+
+static void plan_workspace(tdse_ctx* c) {
+    const size_t NP = c->NP, B = c->B;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
+    c->off.uhat = take(B * NP * 16);
+    c->off.ring = take(B * c->RS * NP * c->rsz);
+    c->off.chain_uhat = take((size_t)c->L * B * NP * 16);
+    c->off.chain_ring = take((size_t)c->L * B * NP * c->rsz);
+    c->off.aux = take(B * NP * 16);
+    c->off.aux2 = take(B * NP * 16);
+    c->off.V0 = take(B * NP * 8);
+    c->off.V0f = take(B * NP * 4);
+    c->off.tfac = take(B * (size_t)c->ntf * 8);
+    c->off.phi = take(B * (size_t)c->d * c->ntf * 8);
+    if (c->d == 1) {
+        c->off.kin64 = take((size_t)c->L * c->n0 * 16);
+        c->off.kin32 = take((size_t)c->L * c->n0 * 8);
+        c->off.adv64 = take(B * (size_t)c->n_int * (c->nh + c->nl) * 16);
+        c->off.adv32 = take(B * (size_t)c->n_int * (c->nh + c->nl) * 8);
+        c->off.q64 = c->off.q32 = 0;
+    } else {
+        c->off.q64 = take(B * (size_t)c->n_int * (c->n0 + c->n1) * 16);
+        c->off.q32 = take(B * (size_t)c->n_int * (c->n0 + c->n1) * 8);
+        c->off.kin64 = c->off.kin32 = c->off.adv64 = c->off.adv32 = 0;
+    }
+    c->off.tw64_0 = take((size_t)c->n0 * 16);
+    c->off.tw32_0 = take((size_t)c->n0 * 8);
+    c->off.tw64_1 = take((size_t)(c->d == 2 ? c->n1 : 1) * 16);
+    c->off.tw32_1 = take((size_t)(c->d == 2 ? c->n1 : 1) * 8);
+    c->off.iv = take((size_t)c->n_int * sizeof(int2));
+    c->off.scratch = take(256);
+    c->off.end = o;
+    c->ws_need = o;
+}
+
+static KArgs base_args(const tdse_ctx* c) {
+    KArgs a{};
+    a.B = c->B;
+    a.n0 = c->n0;
+    a.n1 = c->n1;
+    a.uhat = c->P<double2>(c->off.uhat);
+    a.ring = c->P<void>(c->off.ring);
+    a.ring_slots = c->RS;
+    a.aux = c->P<double2>(c->off.aux);
+    a.aux2 = c->P<double2>(c->off.aux2);
+    a.V0 = c->P<double>(c->off.V0);
+    a.V0f = c->P<float>(c->off.V0f);
+    a.tfac = c->P<double>(c->off.tfac);
+    a.ntf = c->ntf;
+    a.n_int = c->n_int;
+    if (c->d == 1) {
+        a.kin64 = c->P<double2>(c->off.kin64);
+        a.kin32 = c->P<float2>(c->off.kin32);
+        a.adv64 = c->P<double2>(c->off.adv64);
+        a.adv32 = c->P<float2>(c->off.adv32);
+        a.nh = c->nh;
+        a.nl = c->nl;
+        a.lb = c->lb;
+    } else {
+        a.q64 = c->P<double2>(c->off.q64);
+        a.q32 = c->P<float2>(c->off.q32);
+    }
+    a.tw64_0 = c->P<double2>(c->off.tw64_0);
+    a.tw32_0 = c->P<float2>(c->off.tw32_0);
+    a.tw64_1 = c->P<double2>(c->off.tw64_1);
+    a.tw32_1 = c->P<float2>(c->off.tw32_1);
+    return a;
+}
+
+static int step_combo(const tdse_ctx* c) { return c->cfg.precision == TDSE_MIXED ? COMBO_F32 : COMBO_F64; }
+static int f64_combo(const tdse_ctx* c) { return c->cfg.precision == TDSE_MIXED ? COMBO_F64_R32 : COMBO_F64; }
+
+static cudaError_t run(const tdse_ctx* c, const KArgs& a, int combo, cudaStream_t s) {
+    return c->d == 1 ? launch_periodic1d(a, combo, s) : launch_periodic2d(a, combo, s);
+}
+
+static int slot_of(const tdse_ctx* c, int n) { return ((n % c->RS) + c->RS) % c->RS; }
+
+// Interval ids: main step n (t_{n-1} -> t_n) is n-1; Richardson chain c >= 1 of
+// start-up step s, sub-step i, is nsteps + (s-1)(2^L - 2) + (2^c - 2) + i.
+static int startup_interval(const tdse_ctx* c, int s, int chain, int i) {
+    if (chain == 0) return s - 1;
+    return c->cfg.nsteps + (s - 1) * ((1 << c->L) - 2) + ((1 << chain) - 2) + i;
+}
+
+static tdse_status build_phase_tables(tdse_ctx* c, int b, cudaStream_t s) {
+    const int2* iv = c->P<int2>(c->off.iv);
+    const double* phi = c->P<double>(c->off.phi) + (size_t)b * c->d * c->ntf;
+    if (c->d == 1) {
+        const size_t per = (size_t)c->n_int * (c->nh + c->nl);
+        TDSE_CK(c, launch_adv1d(c->P<double2>(c->off.adv64) + b * per, c->P<float2>(c->off.adv32) + b * per, iv,
+                                c->n_int, phi, c->ntf, 1, c->n0, c->nh, c->nl, s));
+    } else {
+        const size_t per = (size_t)c->n_int * (c->n0 + c->n1);
+        TDSE_CK(c, launch_q2d(c->P<double2>(c->off.q64) + b * per, c->P<float2>(c->off.q32) + b * per, iv,
+                              c->n_int, phi, c->ntf, 1, c->n0, c->n1, c->cfg.dt, s));
+    }
+    return TDSE_OK;
+}
+
+static bool instance_range(const tdse_ctx* c, int instance, int& lo, int& hi) {
+    if (instance == -1) { lo = 0; hi = c->B; return true; }
+    if (instance < 0 || instance >= c->B) return false;
+    lo = instance;
+    hi = instance + 1;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+tdse_status tdse_adams_weights(int order, double* mu_out) {
+    if (!mu_out || order < 1 || order > 12) return TDSE_EINVAL;
+    return adams_weights(order, mu_out) ? TDSE_OK : TDSE_EINVAL;
+}
+
+tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
+    if (!cfg || !out) return TDSE_EINVAL;
+    *out = nullptr;
+    if (cfg->dim != 1 && cfg->dim != 2) return TDSE_EINVAL;
+    if (cfg->bc == TDSE_FREE) return TDSE_EUNSUPPORTED;
+    if (cfg->bc != TDSE_PERIODIC) return TDSE_EINVAL;
+    if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt) || cfg->nsteps < 1 || cfg->batch < 1) return TDSE_EINVAL;
+    if (cfg->order < 2 || cfg->order > 8 || cfg->order % 2) return TDSE_EINVAL;
+    if (cfg->precision != TDSE_FP64 && cfg->precision != TDSE_MIXED) return TDSE_EINVAL;
+    const int S = cfg->startup_steps < 0 ? cfg->order - 1 : cfg->startup_steps;
+    if (S < cfg->order - 2) return TDSE_EINVAL;
+    const int n0 = cfg->n[0], n1 = cfg->dim == 2 ? cfg->n[1] : 1;
+    if (!is_pow2(n0) || (cfg->dim == 2 && !is_pow2(n1))) return TDSE_EINVAL;
+    if (cfg->dim == 1 && !periodic1d_supported(n0)) return TDSE_EUNSUPPORTED;
+    if (cfg->dim == 2 && !periodic2d_supported(n0, n1)) return TDSE_EUNSUPPORTED;
+    if ((long long)cfg->nsteps * SUB + 1 > (1LL << 30)) return TDSE_EINVAL;
+
+    tdse_ctx* c = new (std::nothrow) tdse_ctx();
+    if (!c) return TDSE_ENOMEM;
+    c->cfg = *cfg;
+    c->cfg.startup_steps = S;
+    c->d = cfg->dim;
+    c->n0 = n0;
+    c->n1 = n1;
+    c->NP = (size_t)n0 * n1;
+    c->B = cfg->batch;
+    c->m = cfg->order;
+    c->L = cfg->order / 2;
+    c->S = S;
+    c->S_eff = S < cfg->nsteps ? S : cfg->nsteps;
+    c->RS = cfg->order - 1 > 1 ? cfg->order - 1 : 1;
+    c->ntf = cfg->nsteps * SUB + 1;
+    c->rsz = cfg->precision == TDSE_MIXED ? 8 : 16;
+    adams_weights(c->m, c->mu);
+    // Richardson: T[l][c] = (4^l T[l-1][c+1] - T[l-1][c]) / (4^l - 1); final T[L-1][0] = sum rich[c] T[0][c]
+    {
+        std::vector<std::vector<double>> T(c->L, std::vector<double>(c->L, 0.0));
+        for (int q = 0; q < c->L; ++q) T[q][q] = 1.0;   // T[c] as coefficient vectors
+        for (int lev = 1; lev < c->L; ++lev) {
+            const double f = std::pow(4.0, lev);
+            for (int q = 0; q + 1 < (int)T.size(); ++q)
+                for (int r = 0; r < c->L; ++r) T[q][r] = (f * T[q + 1][r] - T[q][r]) / (f - 1.0);
+            T.pop_back();
+        }
+        for (int r = 0; r < c->L; ++r) c->rich[r] = T[0][r];
+    }
+    // interval schedule
+    c->n_int = cfg->nsteps + c->S_eff * ((1 << c->L) - 2);
+    c->intervals.resize(c->n_int);
+    for (int n = 1; n <= cfg->nsteps; ++n) c->intervals[n - 1] = make_int2(SUB * (n - 1), SUB * n);
+    for (int s = 1; s <= c->S_eff; ++s)
+        for (int ch = 1; ch < c->L; ++ch) {
+            const int len = SUB >> ch;
+            for (int i = 0; i < (1 << ch); ++i)
+                c->intervals[startup_interval(c, s, ch, i)] =
+                    make_int2(SUB * (s - 1) + i * len, SUB * (s - 1) + (i + 1) * len);
+        }
+    if (c->d == 1) {
+        c->nl = n0 / 2 < 64 ? n0 / 2 : 64;
+        c->lb = 0;
+        while ((1 << c->lb) < c->nl) ++c->lb;
+        c->nh = n0 / c->nl;
+    }
+    c->have_V.assign(c->B, 0);
+    c->have_u0.assign(c->B, 0);
+    plan_workspace(c);
+    *out = c;
+    return TDSE_OK;
+}
+
+size_t tdse_workspace_bytes(const tdse_ctx* c) { return c ? c->ws_need : 0; }
+
+tdse_status tdse_bind_workspace(tdse_ctx* c, void* dev, size_t bytes, void* stream) {
+    if (!c || !dev) return TDSE_EINVAL;
+    if (bytes < c->ws_need) return c->fail(TDSE_ENOMEM, "workspace smaller than tdse_workspace_bytes()");
+    if (reinterpret_cast<uintptr_t>(dev) & 255) return c->fail(TDSE_EINVAL, "workspace not 256-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    c->ws = static_cast<char*>(dev);
+    TDSE_CK(c, cudaMemcpyAsync(c->P<int2>(c->off.iv), c->intervals.data(), c->intervals.size() * sizeof(int2),
+                               cudaMemcpyHostToDevice, s));
+    TDSE_CK(c, launch_twiddles(c->P<double2>(c->off.tw64_0), c->P<float2>(c->off.tw32_0), c->n0, s));
+    if (c->d == 2)
+        TDSE_CK(c, launch_twiddles(c->P<double2>(c->off.tw64_1), c->P<float2>(c->off.tw32_1), c->n1, s));
+    else
+        TDSE_CK(c, launch_kin1d(c->P<double2>(c->off.kin64), c->P<float2>(c->off.kin32), c->n0, c->L, c->cfg.dt, s));
+    // defaults: A == 0 (phi == 0), f(t) == 1
+    TDSE_CK(c, cudaMemsetAsync(c->P<double>(c->off.phi), 0, (size_t)c->B * c->d * c->ntf * 8, s));
+    std::vector<double> ones(c->ntf, 1.0);
+    for (int b = 0; b < c->B; ++b)
+        TDSE_CK(c, cudaMemcpyAsync(c->P<double>(c->off.tfac) + (size_t)b * c->ntf, ones.data(), c->ntf * 8,
+                                   cudaMemcpyHostToDevice, s));
+    for (int b = 0; b < c->B; ++b) {
+        tdse_status st = build_phase_tables(c, b, s);
+        if (st != TDSE_OK) return st;
+    }
+    TDSE_CK(c, cudaStreamSynchronize(s));
+    c->step = 0;
+    c->inited = false;
+    return TDSE_OK;
+}
+
+tdse_status tdse_set_potential(tdse_ctx* c, int instance, const double* V0, const double* tf, int where,
+                               void* stream) {
+    if (!c || !V0) return TDSE_EINVAL;
+    if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
+    int lo, hi;
+    if (!instance_range(c, instance, lo, hi)) return c->fail(TDSE_EINVAL, "instance out of range");
+    if (where != TDSE_HOST && where != TDSE_DEVICE) return TDSE_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const cudaMemcpyKind kind = where == TDSE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    for (int b = lo; b < hi; ++b) {
+        double* dV = c->P<double>(c->off.V0) + (size_t)b * c->NP;
+        TDSE_CK(c, cudaMemcpyAsync(dV, V0, c->NP * 8, kind, s));
+        TDSE_CK(c, launch_to_float(c->P<float>(c->off.V0f) + (size_t)b * c->NP, dV, c->NP, s));
+        if (tf) {
+            for (int i = 0; i < c->ntf; ++i)
+                if (!std::isfinite(tf[i])) return c->fail(TDSE_EINVAL, "non-finite time factor");
+            TDSE_CK(c, cudaMemcpyAsync(c->P<double>(c->off.tfac) + (size_t)b * c->ntf, tf, c->ntf * 8,
+                                       cudaMemcpyHostToDevice, s));
+        } else {
+            std::vector<double> ones(c->ntf, 1.0);
+            TDSE_CK(c, cudaMemcpyAsync(c->P<double>(c->off.tfac) + (size_t)b * c->ntf, ones.data(), c->ntf * 8,
+                                       cudaMemcpyHostToDevice, s));
+            TDSE_CK(c, cudaStreamSynchronize(s));
+        }
+        c->have_V[b] = 1;
+    }
+    if (where == TDSE_HOST || tf) TDSE_CK(c, cudaStreamSynchronize(s));
+    return TDSE_OK;
+}
+
+static tdse_status set_field(tdse_ctx* c, int instance, tdse_field_fn A, void* user, void* stream) {
+    if (!c) return TDSE_EINVAL;
+    if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
+    int lo, hi;
+    if (!instance_range(c, instance, lo, hi)) return c->fail(TDSE_EINVAL, "instance out of range");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // phi(t_m), t_m = m dt/8: 8-point Gauss-Legendre on each [t_m, t_{m+1}],
+    // accumulated in long double (eq. phi).
+    std::vector<double> phi((size_t)c->d * c->ntf, 0.0);
+    if (A) {
+        std::vector<double> gx, gw;
+        gauss_legendre(8, gx, gw);
+        const double hs = c->cfg.dt / SUB;
+        long double acc[2] = {0.0L, 0.0L};
+        double Av[2] = {0.0, 0.0};
+        for (int mm = 0; mm + 1 < c->ntf; ++mm) {
+            const double t0 = (double)mm * hs, t1 = (double)(mm + 1) * hs;
+            const double half = 0.5 * (t1 - t0), mid = 0.5 * (t0 + t1);
+            long double part[2] = {0.0L, 0.0L};
+            for (int q = 0; q < 8; ++q) {
+                A(mid + half * gx[q], Av, user);
+                for (int dd = 0; dd < c->d; ++dd) part[dd] += (long double)gw[q] * Av[dd];
+            }
+            for (int dd = 0; dd < c->d; ++dd) {
+                if (!std::isfinite((double)part[dd])) return c->fail(TDSE_EINVAL, "non-finite A(t)");
+                acc[dd] += part[dd] * half;
+                phi[(size_t)dd * c->ntf + mm + 1] = (double)acc[dd];
+            }
+        }
+    }
+    for (int b = lo; b < hi; ++b) {
+        TDSE_CK(c, cudaMemcpyAsync(c->P<double>(c->off.phi) + (size_t)b * c->d * c->ntf, phi.data(),
+                                   phi.size() * 8, cudaMemcpyHostToDevice, s));
+        tdse_status st = build_phase_tables(c, b, s);
+        if (st != TDSE_OK) return st;
+    }
+    TDSE_CK(c, cudaStreamSynchronize(s));
+    return TDSE_OK;
+}
+
+tdse_status tdse_set_vector_potential(tdse_ctx* c, int instance, tdse_field_fn A, void* user, void* stream) {
+    return set_field(c, instance, A, user, stream);
+}
+
+tdse_status tdse_set_pulse(tdse_ctx* c, int instance, double A0, double omega, double Tp, const double* dir,
+                           void* stream) {
+    if (!c || !dir || !(Tp > 0.0) || !std::isfinite(A0) || !std::isfinite(omega)) return TDSE_EINVAL;
+    Pulse p{A0, omega, Tp, {dir[0], c->d == 2 ? dir[1] : 0.0}};
+    return set_field(c, instance, pulse_fn, &p, stream);
+}
+
+tdse_status tdse_set_initial(tdse_ctx* c, int instance, const double* u0, int where, void* stream) {
+    if (!c || !u0) return TDSE_EINVAL;
+    if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
+    int lo, hi;
+    if (!instance_range(c, instance, lo, hi)) return c->fail(TDSE_EINVAL, "instance out of range");
+    if (where != TDSE_HOST && where != TDSE_DEVICE) return TDSE_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const cudaMemcpyKind kind = where == TDSE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    for (int b = lo; b < hi; ++b) {
+        TDSE_CK(c, cudaMemcpyAsync(c->P<double2>(c->off.uhat) + (size_t)b * c->NP, u0, c->NP * 16, kind, s));
+        c->have_u0[b] = 1;
+    }
+    if (where == TDSE_HOST) TDSE_CK(c, cudaStreamSynchronize(s));
+    c->step = 0;
+    c->inited = false;
+    return TDSE_OK;
+}
+
+static tdse_status do_init(tdse_ctx* c, cudaStream_t s) {
+    KArgs a = base_args(c);
+    a.mode = MODE_INIT;
+    a.out_slot = slot_of(c, 0);
+    a.tf = 0;
+    TDSE_CK(c, run(c, a, f64_combo(c), s));
+    c->inited = true;
+    return TDSE_OK;
+}
+
+static tdse_status startup_step(tdse_ctx* c, int n, cudaStream_t s) {
+    const size_t NPB = c->NP * c->B;
+    double2* chain_u = c->P<double2>(c->off.chain_uhat);
+    char* chain_r = c->P<char>(c->off.chain_ring);
+    for (int ch = 0; ch < c->L; ++ch) {
+        double2* cu = chain_u + (size_t)ch * NPB;
+        void* cr = chain_r + (size_t)ch * NPB * c->rsz;
+        TDSE_CK(c, cudaMemcpyAsync(cu, c->P<double2>(c->off.uhat), NPB * 16, cudaMemcpyDeviceToDevice, s));
+        TDSE_CK(c, launch_copy_slot(cr, c->P<void>(c->off.ring), c->RS, slot_of(c, n - 1), c->B, c->NP, c->rsz, s));
+        const int len = SUB >> ch;
+        for (int i = 0; i < (1 << ch); ++i) {
+            KArgs a = base_args(c);
+            a.mode = MODE_STEP;
+            a.uhat = cu;
+            a.ring = cr;
+            a.ring_slots = 1;
+            a.nhist = 1;
+            a.h = c->cfg.dt / (double)(1 << ch);
+            a.mu[0] = 0.5;
+            a.mu[1] = 0.5;
+            a.hist_slot[0] = 0;
+            a.out_slot = 0;
+            a.interval[0] = startup_interval(c, n, ch, i);
+            a.kin = ch;
+            a.tf = SUB * (n - 1) + (i + 1) * len;
+            TDSE_CK(c, run(c, a, step_combo(c), s));
+        }
+    }
+    TDSE_CK(c, launch_combine(c->P<double2>(c->off.uhat), chain_u, NPB, c->L, c->rich, NPB, s));
+    KArgs a = base_args(c);
+    a.mode = MODE_REFRESH;
+    a.out_slot = slot_of(c, n);
+    a.tf = SUB * n;
+    TDSE_CK(c, run(c, a, step_combo(c), s));
+    return TDSE_OK;
+}
+
+static tdse_status adams_step(tdse_ctx* c, int n, cudaStream_t s) {
+    KArgs a = base_args(c);
+    a.mode = MODE_STEP;
+    a.nhist = c->m - 1;
+    a.h = c->cfg.dt;
+    for (int j = 0; j < c->m; ++j) a.mu[j] = c->mu[j];
+    for (int j = 1; j <= a.nhist; ++j) a.hist_slot[j - 1] = slot_of(c, n - j);
+    a.out_slot = slot_of(c, n);
+    for (int i = 0; i < a.nhist; ++i) a.interval[i] = n - 1 - i;
+    a.kin = 0;
+    a.tf = SUB * n;
+    TDSE_CK(c, run(c, a, step_combo(c), s));
+    return TDSE_OK;
+}
+
+tdse_status tdse_step(tdse_ctx* c, int nsteps, void* stream) {
+    if (!c) return TDSE_EINVAL;
+    if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
+    if (nsteps < 0) return c->fail(TDSE_EINVAL, "negative step count");
+    if (c->step + nsteps > c->cfg.nsteps) return c->fail(TDSE_EINVAL, "beyond the nsteps the tables cover");
+    for (int b = 0; b < c->B; ++b)
+        if (!c->have_V[b] || !c->have_u0[b]) return c->fail(TDSE_ESTATE, "instance lacks V or u0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (nsteps == 0) return TDSE_OK;
+    if (!c->inited) {
+        tdse_status st = do_init(c, s);
+        if (st != TDSE_OK) return st;
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        const int n = c->step + 1;
+        tdse_status st = (n <= c->S) ? startup_step(c, n, s) : adams_step(c, n, s);
+        if (st != TDSE_OK) return st;
+        c->step = n;
+    }
+    return TDSE_OK;
+}
+
+tdse_status tdse_solve_to(tdse_ctx* c, double T, void* stream) {
+    if (!c || !std::isfinite(T) || T < 0) return TDSE_EINVAL;
+    const long long target = llround(T / c->cfg.dt);
+    if (target < c->step) return c->fail(TDSE_EINVAL, "T is before the current time");
+    if (target > c->cfg.nsteps) return c->fail(TDSE_EINVAL, "T beyond the nsteps the tables cover");
+    return tdse_step(c, (int)(target - c->step), stream);
+}
+
+tdse_status tdse_read_u(tdse_ctx* c, int instance, double* u_out, int where, void* stream) {
+    if (!c || !u_out) return TDSE_EINVAL;
+    if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
+    int lo, hi;
+    if (!instance_range(c, instance, lo, hi)) return c->fail(TDSE_EINVAL, "instance out of range");
+    if (where != TDSE_HOST && where != TDSE_DEVICE) return TDSE_EINVAL;
+    for (int b = lo; b < hi; ++b)
+        if (!c->have_u0[b]) return c->fail(TDSE_ESTATE, "instance has no initial state");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t nb = (size_t)(hi - lo);
+    const double2* src;
+    if (!c->inited) {
+        src = c->P<double2>(c->off.uhat) + (size_t)lo * c->NP;    // u0 still parked in physical form
+    } else {
+        KArgs a = base_args(c);
+        a.mode = MODE_READ;
+        a.B = (int)nb;
+        a.uhat = c->P<double2>(c->off.uhat) + (size_t)lo * c->NP;
+        TDSE_CK(c, run(c, a, f64_combo(c), s));
+        src = a.aux2;
+    }
+    const cudaMemcpyKind kind = where == TDSE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    TDSE_CK(c, cudaMemcpyAsync(u_out, src, nb * c->NP * 16, kind, s));
+    if (where == TDSE_HOST) TDSE_CK(c, cudaStreamSynchronize(s));
+    return TDSE_OK;
+}
+
+tdse_status tdse_check_finite(tdse_ctx* c, void* stream) {
+    if (!c) return TDSE_EINVAL;
+    if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int* cnt = c->P<int>(c->off.scratch);
+    TDSE_CK(c, cudaMemsetAsync(cnt, 0, sizeof(int), s));
+    TDSE_CK(c, launch_count_nonfinite(c->P<double>(c->off.uhat), c->NP * c->B * 2, cnt, s));
+    int h = 0;
+    TDSE_CK(c, cudaMemcpyAsync(&h, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TDSE_CK(c, cudaStreamSynchronize(s));
+    if (h) return c->fail(TDSE_ENONFINITE, "non-finite values in the mode state");
+    return TDSE_OK;
+}
+
+int tdse_step_index(const tdse_ctx* c) { return c ? c->step : -1; }
+double tdse_time(const tdse_ctx* c) { return c ? c->step * c->cfg.dt : 0.0; }
+
+const char* tdse_last_error(const tdse_ctx* c) {
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+void tdse_destroy(tdse_ctx* c) { delete c; }
+
+}  // extern "C"
