@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-adams", type=int, default=0,
+                    help="profiling run: start-up + this many Adams steps of the batch, then exit")
     return ap.parse_args()
 
 
@@ -283,6 +285,26 @@ def run_gpu(args, ws, rank, local):
                 stated_err=stated_err, B=B)
 
 
+def profile_run(args):
+    """Small fixed launch sequence for ncu: init, start-up, then K Adams steps."""
+    import torch
+    from paper_2001_06113_gb300 import Problem
+    insts = instances(0, args.batch)
+    prob = Problem((M, M), DT, NSTEPS, order=ORDER, batch=len(insts), precision=args.precision)
+    for b, it in enumerate(insts):
+        prob.set_potential(it.V0, None, instance=b)
+        p = it.pulse
+        prob.set_pulse(p.A0, p.omega, p.T_pulse, p.direction, instance=b)
+        prob.set_initial(it.u0, instance=b)
+    prob.step(STARTUP + args.profile_adams)
+    torch.cuda.synchronize()
+    prob.check_finite()
+    print(json.dumps({"profile_adams": args.profile_adams, "batch": len(insts), "precision": args.precision,
+                      "launches_startup": launches_per_solve(2) - (NSTEPS - STARTUP) * 3}))
+    prob.close()
+    return 0
+
+
 # ---------------------------------------------------------------- CPU oracle arm
 def oracle_sample(nadams: int = 6, seed: int = 2):
     """Time the CPU oracle (as it stands) on a bounded sample of the workload:
@@ -344,6 +366,8 @@ def main():
         return 0
 
     import torch
+    if args.profile_adams:
+        return profile_run(args)
     if ws > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     res = run_gpu(args, ws, rank, local)

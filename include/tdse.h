@@ -165,6 +165,32 @@ double tdse_time(const tdse_ctx* ctx);
  * (Sec. 2.2; Table 1 for order 8), written to mu_out. */
 tdse_status tdse_adams_weights(int order, double* mu_out);
 
+/*
+ * Allocation-free read-out transform, for callers that cannot allocate device
+ * memory at all (and so cannot provide a workspace): code where cudaMalloc is
+ * forbidden or unavailable, e.g. a host application that owns every device
+ * allocation itself or a plugin with a fixed device-memory budget.  The paper
+ * has no counterpart; it is a packaging of this library's own read-out.
+ *
+ * Computes, for `batch` 2D arrays of n0 x n1 modes in FFT order (device
+ * pointer `uhat`, interleaved complex FP64, [batch][n0][n1]), the grid values
+ *     u_j = sum_k e^{+2 pi i j.k / n} uhat_k       (same as tdse_read_u)
+ * into the device array `u` (same layout), in FP64, on `stream`.
+ * n0, n1: powers of two in 8..1024.  batch*n0*n1 must not exceed
+ * TDSE_NOALLOC_MAX_POINTS: larger requests return TDSE_ENOMEM and do nothing.
+ * Its scratch is one fixed device array inside the library
+ * (TDSE_NOALLOC_MAX_POINTS * 16 bytes plus tables) that every GPU loading the
+ * library holds until the process exits.  All calls share that array: calls
+ * whose work overlaps on the GPU (different streams or threads) race and give
+ * wrong results, so serialise them.  The first call on a device looks up the
+ * array's address with that device current; make it before any stream
+ * capture.  Errors: TDSE_EINVAL (null pointer, bad size), TDSE_ENOMEM (too
+ * large), TDSE_ECUDA (launch failure).
+ */
+#define TDSE_NOALLOC_MAX_POINTS 524288
+tdse_status tdse_modes_to_grid_2d_noalloc(const double* uhat, double* u, int n0, int n1, int batch,
+                                          void* stream);
+
 /* Message of the last failing call on `ctx` ("" if none; static string if
  * ctx is NULL). */
 const char* tdse_last_error(const tdse_ctx* ctx);

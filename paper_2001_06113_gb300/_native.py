@@ -23,8 +23,9 @@ EXPORTS = [
     "tdse_create", "tdse_workspace_bytes", "tdse_bind_workspace", "tdse_set_potential",
     "tdse_set_vector_potential", "tdse_set_pulse", "tdse_set_initial", "tdse_step", "tdse_solve_to",
     "tdse_read_u", "tdse_check_finite", "tdse_step_index", "tdse_time", "tdse_adams_weights",
-    "tdse_last_error", "tdse_destroy",
+    "tdse_last_error", "tdse_destroy", "tdse_modes_to_grid_2d_noalloc",
 ]
+NOALLOC_MAX_POINTS = 524288
 
 
 class TdseConfig(ctypes.Structure):
@@ -72,6 +73,7 @@ def load(path: str = _LIB_PATH) -> ctypes.CDLL:
         "tdse_adams_weights": ([ip, dp], ip),
         "tdse_last_error": ([vp], ctypes.c_char_p),
         "tdse_destroy": ([vp], None),
+        "tdse_modes_to_grid_2d_noalloc": ([vp, vp, ip, ip, ip, vp], ip),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
