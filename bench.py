@@ -126,13 +126,24 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------- GPU arm
-def launches_per_solve(dim: int) -> int:
-    per_op = 1 if dim == 1 else 3            # kernels per application of the step operator
+def launches_per_solve(dim: int, mixed: bool) -> int:
+    """Kernel launches of one tdse_step(NSTEPS) call (init, start-up, Adams)."""
     L = ORDER // 2
     sub = sum(2 ** c for c in range(L))      # trapezoid sub-steps per start-up step
+    per_op = 1 if dim == 1 else 3            # kernels per unfused application of the step operator
     startup = STARTUP * (L + sub * per_op + 1 + per_op)   # copy_slot per chain, sub-steps, combine, refresh
     init = 1 if dim == 1 else 2
-    return init + startup + (NSTEPS - STARTUP) * per_op
+    k = NSTEPS - STARTUP
+    adams = k if dim == 1 else 2 * k + 1     # 2D: col_begin, (row_mid, col_fused) x (k-1), row_mid, col_end
+    return init + startup + (1 if mixed else 0) + adams
+
+
+# DRAM bytes per point-step of the 2D step operator (k_row_mid + k_col_end<fused>)
+# from the ncu capture of the 512^2 mixed workload at batch 8 (summarised under
+# profiles/); traffic scales with the number of instances.  None = not captured
+# for the current kernels.
+TRAFFIC_BYTES_PER_POINT_STEP = {"mixed": (151.192064e6 + 31.29728e6 + 33.606144e6 + 0.041216e6) / (8 * 512 * 512),
+                                "fp64": None}
 
 
 def run_gpu(args, ws, rank, local):
@@ -196,19 +207,20 @@ def run_gpu(args, ws, rank, local):
     points = M * M
     value = ws * B * points * NSTEPS / t_solve
 
-    # ---- step-operator roofline: events around single Adams steps (3 pass kernels)
+    # ---- step-operator roofline: events around groups of consecutive Adams steps
+    #      (2D: per step one row pass + one fused column pass)
+    GROUP, NGROUPS = 10, 20
     with torch.cuda.stream(stream):
         for b in range(B):
             prob.set_initial(pinned_u[b], instance=b)
         prob.step(STARTUP + 8)
-        nmeas = 50
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(nmeas + 1)]
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(NGROUPS + 1)]
         evs[0].record(stream)
-        for i in range(nmeas):
-            prob.step(1)
+        for i in range(NGROUPS):
+            prob.step(GROUP)
             evs[i + 1].record(stream)
     stream.synchronize()
-    dts = np.array([evs[i].elapsed_time(evs[i + 1]) / 1e3 for i in range(nmeas)])
+    dts = np.array([evs[i].elapsed_time(evs[i + 1]) / 1e3 / GROUP for i in range(NGROUPS)])
     t_step = float(np.mean(dts))
     algo = ALGO_BYTES[args.precision] * B * points
     peaks = {}
@@ -219,18 +231,12 @@ def run_gpu(args, ws, rank, local):
     peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     achieved = algo / t_step / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", f"traffic_step2d_{args.precision}.json")
-    if os.path.exists(tpath):
-        try:
-            tr = json.load(open(tpath))
-            if tr.get("batch") and tr.get("bytes_per_step"):
-                traffic = tr["bytes_per_step"] * B / tr["batch"]
-        except Exception:
-            traffic = None
+    tb = TRAFFIC_BYTES_PER_POINT_STEP.get(args.precision)
+    traffic = None if tb is None else round(tb * B * points)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_src,
-                "kernel": "2D step operator (col_begin + row_mid + col_end)",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "traffic_unit": "bytes per step (all instances)",
+                "peak_source": peak_src,
+                "kernel": "2D Adams step operator (k_row_mid + k_col_end<fused>), timed over groups of 10 steps",
                 "algorithmic_bytes_per_point_step": ALGO_BYTES[args.precision],
                 "step_ms_p50": round(float(np.percentile(dts, 50)) * 1e3, 4),
                 "step_ms_p99": round(float(np.percentile(dts, 99)) * 1e3, 4)}
@@ -300,7 +306,8 @@ def profile_run(args):
     torch.cuda.synchronize()
     prob.check_finite()
     print(json.dumps({"profile_adams": args.profile_adams, "batch": len(insts), "precision": args.precision,
-                      "launches_startup": launches_per_solve(2) - (NSTEPS - STARTUP) * 3}))
+                      "launches_before_adams": launches_per_solve(2, args.precision == "mixed")
+                      - (2 * (NSTEPS - STARTUP) + 1)}))
     prob.close()
     return 0
 
@@ -394,7 +401,7 @@ def main():
                        "parallelism": f"replicas x{ws}"},
             "rel_l2_vs_fp64": res["stated_err"],
             "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
-            "gpu_launches": launches_per_solve(2) * args.steps,
+            "gpu_launches": launches_per_solve(2, args.precision == "mixed") * args.steps,
         }
         print(json.dumps(line))
     if ws > 1:

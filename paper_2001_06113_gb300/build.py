@@ -28,8 +28,9 @@ def nvcc() -> str:
 
 
 def _flags():
+    extra = os.environ.get("TDSE_NVCC_FLAGS", "").split()   # optional tuning defines
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-                   "-I", os.path.join(ROOT, "include"), "-I", CSRC, "--expt-relaxed-constexpr"]
+                   "-I", os.path.join(ROOT, "include"), "-I", CSRC, "--expt-relaxed-constexpr"] + extra
 
 
 def _deps_mtime() -> float:

@@ -104,18 +104,21 @@ struct tdse_ctx {
     tdse_config cfg{};
     int d = 1, n0 = 0, n1 = 1;
     size_t NP = 0;
-    int B = 1, m = 8, L = 4, S = 7, S_eff = 7, RS = 7, ntf = 0, n_int = 0;
+    int B = 1, m = 8, L = 4, S = 7, S_eff = 7, RS = 7, ntf = 0, n_int = 0, n_int_startup = 0, nhi = 1;
+    bool mixed = false;
+    bool ip = false;            // mixed mode: state and ring are in the interaction picture
     int nh = 1, nl = 1, lb = 0;
     size_t rsz = 16;            // ring element bytes
     double mu[8] = {0};
     double rich[4] = {0};
     std::vector<int2> intervals;
+    std::vector<float> zdither;   // [nsteps + 1][2]: FP32 ring dither z_n (interaction picture)
     // workspace
     char* ws = nullptr;
     size_t ws_need = 0;
     struct {
-        size_t uhat, ring, chain_uhat, chain_ring, aux, aux2, V0, V0f, tfac, phi, kin64, kin32, adv64, adv32,
-            q64, q32, tw64_0, tw32_0, tw64_1, tw32_1, iv, scratch, end;
+        size_t uhat, ring, chain_uhat, chain_ring, aux, aux2, V0, V0f, tfac, phi, kin64, kinff, adv64, advff,
+            q64, qff, e2d, k1lo, k1hi, a1d, tw64_0, tw32_0, tw64_1, tw32_1, tw32lo_0, tw32lo_1, iv, scratch, end;
     } off{};
     std::vector<char> have_V, have_u0;
     int step = 0;
@@ -143,6 +146,7 @@ static void plan_workspace(tdse_ctx* c) {
     const size_t NP = c->NP, B = c->B;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
+    c->off = {};
     c->off.uhat = take(B * NP * 16);
     c->off.ring = take(B * c->RS * NP * c->rsz);
     c->off.chain_uhat = take((size_t)c->L * B * NP * 16);
@@ -150,28 +154,46 @@ static void plan_workspace(tdse_ctx* c) {
     c->off.aux = take(B * NP * 16);
     c->off.aux2 = take(B * NP * 16);
     c->off.V0 = take(B * NP * 8);
-    c->off.V0f = take(B * NP * 4);
+    c->off.V0f = take(B * NP * 8);
     c->off.tfac = take(B * (size_t)c->ntf * 8);
     c->off.phi = take(B * (size_t)c->d * c->ntf * 8);
+    const size_t nsp1 = (size_t)c->cfg.nsteps + 1;
     if (c->d == 1) {
-        c->off.kin64 = take((size_t)c->L * c->n0 * 16);
-        c->off.kin32 = take((size_t)c->L * c->n0 * 8);
-        c->off.adv64 = take(B * (size_t)c->n_int * (c->nh + c->nl) * 16);
-        c->off.adv32 = take(B * (size_t)c->n_int * (c->nh + c->nl) * 8);
-        c->off.q64 = c->off.q32 = 0;
+        if (c->mixed) {
+            c->off.kinff = take((size_t)c->L * c->n0 * 16);
+            c->off.advff = take(B * (size_t)c->n_int * (c->nh + c->nl) * 16);
+            c->off.k1lo = take((size_t)E1D_NLO * c->n0 * 8);
+            c->off.k1hi = take((size_t)c->nhi * c->n0 * 8);
+            c->off.a1d = take(B * nsp1 * (c->nh + c->nl) * 8);
+        } else {
+            c->off.kin64 = take((size_t)c->L * c->n0 * 16);
+            c->off.adv64 = take(B * (size_t)c->n_int * (c->nh + c->nl) * 16);
+        }
     } else {
-        c->off.q64 = take(B * (size_t)c->n_int * (c->n0 + c->n1) * 16);
-        c->off.q32 = take(B * (size_t)c->n_int * (c->n0 + c->n1) * 8);
-        c->off.kin64 = c->off.kin32 = c->off.adv64 = c->off.adv32 = 0;
+        if (c->mixed) {
+            c->off.qff = take(B * (size_t)c->n_int * (c->n0 + c->n1) * 16);
+            c->off.e2d = take(B * nsp1 * (c->n0 + c->n1) * 8);
+        } else {
+            c->off.q64 = take(B * (size_t)c->n_int * (c->n0 + c->n1) * 16);
+        }
     }
     c->off.tw64_0 = take((size_t)c->n0 * 16);
     c->off.tw32_0 = take((size_t)c->n0 * 8);
     c->off.tw64_1 = take((size_t)(c->d == 2 ? c->n1 : 1) * 16);
     c->off.tw32_1 = take((size_t)(c->d == 2 ? c->n1 : 1) * 8);
+    c->off.tw32lo_0 = take((size_t)c->n0 * 8);
+    c->off.tw32lo_1 = take((size_t)(c->d == 2 ? c->n1 : 1) * 8);
     c->off.iv = take((size_t)c->n_int * sizeof(int2));
     c->off.scratch = take(256);
     c->off.end = o;
     c->ws_need = o;
+}
+
+template <class T> static T* opt(const tdse_ctx* c, size_t off) { return off ? c->P<T>(off) : nullptr; }
+
+static void split(double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
 }
 
 static KArgs base_args(const tdse_ctx* c) {
@@ -179,33 +201,49 @@ static KArgs base_args(const tdse_ctx* c) {
     a.B = c->B;
     a.n0 = c->n0;
     a.n1 = c->n1;
-    a.uhat = c->P<double2>(c->off.uhat);
+    a.uhat = c->P<void>(c->off.uhat);
     a.ring = c->P<void>(c->off.ring);
     a.ring_slots = c->RS;
     a.aux = c->P<double2>(c->off.aux);
     a.aux2 = c->P<double2>(c->off.aux2);
     a.V0 = c->P<double>(c->off.V0);
-    a.V0f = c->P<float>(c->off.V0f);
+    a.V0f = c->P<float2>(c->off.V0f);
     a.tfac = c->P<double>(c->off.tfac);
     a.ntf = c->ntf;
     a.n_int = c->n_int;
-    if (c->d == 1) {
-        a.kin64 = c->P<double2>(c->off.kin64);
-        a.kin32 = c->P<float2>(c->off.kin32);
-        a.adv64 = c->P<double2>(c->off.adv64);
-        a.adv32 = c->P<float2>(c->off.adv32);
-        a.nh = c->nh;
-        a.nl = c->nl;
-        a.lb = c->lb;
-    } else {
-        a.q64 = c->P<double2>(c->off.q64);
-        a.q32 = c->P<float2>(c->off.q32);
-    }
+    a.dt = c->cfg.dt;
+    a.phi = c->P<double>(c->off.phi);
+    a.kin64 = opt<double2>(c, c->off.kin64);
+    a.kinff = opt<float4>(c, c->off.kinff);
+    a.adv64 = opt<double2>(c, c->off.adv64);
+    a.advff = opt<float4>(c, c->off.advff);
+    a.nh = c->nh;
+    a.nl = c->nl;
+    a.lb = c->lb;
+    a.q64 = opt<double2>(c, c->off.q64);
+    a.qff = opt<float4>(c, c->off.qff);
+    a.e2d = opt<float2>(c, c->off.e2d);
+    a.k1d_lo = opt<float2>(c, c->off.k1lo);
+    a.k1d_hi = opt<float2>(c, c->off.k1hi);
+    a.a1d = opt<float2>(c, c->off.a1d);
     a.tw64_0 = c->P<double2>(c->off.tw64_0);
     a.tw32_0 = c->P<float2>(c->off.tw32_0);
     a.tw64_1 = c->P<double2>(c->off.tw64_1);
     a.tw32_1 = c->P<float2>(c->off.tw32_1);
+    a.tw32lo_0 = c->P<float2>(c->off.tw32lo_0);
+    a.tw32lo_1 = c->P<float2>(c->off.tw32lo_1);
     return a;
+}
+
+// per-step scalars: h, mu (and their hi/lo splits)
+static void set_weights(KArgs& a, double h, const double* mu, int nmu) {
+    a.h = h;
+    split(h, a.h_hi, a.h_lo);
+    for (int j = 0; j < nmu; ++j) {
+        a.mu[j] = mu[j];
+        split(mu[j], a.mu_hi[j], a.mu_lo[j]);
+    }
+    split(h * mu[0], a.hmu0_hi, a.hmu0_lo);
 }
 
 static int step_combo(const tdse_ctx* c) { return c->cfg.precision == TDSE_MIXED ? COMBO_F32 : COMBO_F64; }
@@ -217,24 +255,37 @@ static cudaError_t run(const tdse_ctx* c, const KArgs& a, int combo, cudaStream_
 
 static int slot_of(const tdse_ctx* c, int n) { return ((n % c->RS) + c->RS) % c->RS; }
 
-// Interval ids: main step n (t_{n-1} -> t_n) is n-1; Richardson chain c >= 1 of
-// start-up step s, sub-step i, is nsteps + (s-1)(2^L - 2) + (2^c - 2) + i.
+// Interval ids.  Start-up step s (1..S_eff) owns ids (s-1)(2^L - 1) .. s(2^L - 1) - 1:
+// chain c, sub-step i at (s-1)(2^L - 1) + (2^c - 1) + i (chain 0 is the main
+// interval t_{s-1} -> t_s).  Main intervals of later steps n follow from
+// n_int_startup (FP64 mode only: mixed Adams steps use absolute phases).
 static int startup_interval(const tdse_ctx* c, int s, int chain, int i) {
-    if (chain == 0) return s - 1;
-    return c->cfg.nsteps + (s - 1) * ((1 << c->L) - 2) + ((1 << chain) - 2) + i;
+    return (s - 1) * ((1 << c->L) - 1) + ((1 << chain) - 1) + i;
+}
+static int main_interval(const tdse_ctx* c, int n) {
+    return n <= c->S_eff ? startup_interval(c, n, 0, 0) : c->n_int_startup + (n - c->S_eff - 1);
 }
 
 static tdse_status build_phase_tables(tdse_ctx* c, int b, cudaStream_t s) {
     const int2* iv = c->P<int2>(c->off.iv);
     const double* phi = c->P<double>(c->off.phi) + (size_t)b * c->d * c->ntf;
+    const size_t nsp1 = (size_t)c->cfg.nsteps + 1;
     if (c->d == 1) {
         const size_t per = (size_t)c->n_int * (c->nh + c->nl);
-        TDSE_CK(c, launch_adv1d(c->P<double2>(c->off.adv64) + b * per, c->P<float2>(c->off.adv32) + b * per, iv,
-                                c->n_int, phi, c->ntf, 1, c->n0, c->nh, c->nl, s));
+        TDSE_CK(c, launch_adv1d(c->mixed ? nullptr : c->P<double2>(c->off.adv64) + b * per,
+                                c->mixed ? c->P<float4>(c->off.advff) + b * per : nullptr, iv, c->n_int, phi, c->ntf,
+                                c->n0, c->nh, c->nl, s));
+        if (c->mixed)
+            TDSE_CK(c, launch_a1d(c->P<float2>(c->off.a1d) + b * nsp1 * (c->nh + c->nl), phi, c->ntf, c->cfg.nsteps,
+                                  c->n0, c->nh, c->nl, s));
     } else {
         const size_t per = (size_t)c->n_int * (c->n0 + c->n1);
-        TDSE_CK(c, launch_q2d(c->P<double2>(c->off.q64) + b * per, c->P<float2>(c->off.q32) + b * per, iv,
-                              c->n_int, phi, c->ntf, 1, c->n0, c->n1, c->cfg.dt, s));
+        TDSE_CK(c, launch_q2d(c->mixed ? nullptr : c->P<double2>(c->off.q64) + b * per,
+                              c->mixed ? c->P<float4>(c->off.qff) + b * per : nullptr, iv, c->n_int, phi, c->ntf,
+                              c->n0, c->n1, c->cfg.dt, s));
+        if (c->mixed)
+            TDSE_CK(c, launch_e2d(c->P<float2>(c->off.e2d) + b * nsp1 * (c->n0 + c->n1), phi, c->ntf, c->cfg.nsteps,
+                                  c->n0, c->n1, c->cfg.dt, s));
     }
     return TDSE_OK;
 }
@@ -288,6 +339,7 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     c->RS = cfg->order - 1 > 1 ? cfg->order - 1 : 1;
     c->ntf = cfg->nsteps * SUB + 1;
     c->rsz = cfg->precision == TDSE_MIXED ? 8 : 16;
+    c->mixed = cfg->precision == TDSE_MIXED;
     adams_weights(c->m, c->mu);
     // Richardson: T[l][c] = (4^l T[l-1][c+1] - T[l-1][c]) / (4^l - 1); final T[L-1][0] = sum rich[c] T[0][c]
     {
@@ -301,17 +353,31 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
         }
         for (int r = 0; r < c->L; ++r) c->rich[r] = T[0][r];
     }
-    // interval schedule
-    c->n_int = cfg->nsteps + c->S_eff * ((1 << c->L) - 2);
+    // interval schedule (see startup_interval / main_interval)
+    c->n_int_startup = c->S_eff * ((1 << c->L) - 1);
+    const int n_main_rest = cfg->nsteps - c->S_eff;
+    c->n_int = c->n_int_startup + (c->mixed ? 0 : n_main_rest);
     c->intervals.resize(c->n_int);
-    for (int n = 1; n <= cfg->nsteps; ++n) c->intervals[n - 1] = make_int2(SUB * (n - 1), SUB * n);
     for (int s = 1; s <= c->S_eff; ++s)
-        for (int ch = 1; ch < c->L; ++ch) {
+        for (int ch = 0; ch < c->L; ++ch) {
             const int len = SUB >> ch;
             for (int i = 0; i < (1 << ch); ++i)
                 c->intervals[startup_interval(c, s, ch, i)] =
                     make_int2(SUB * (s - 1) + i * len, SUB * (s - 1) + (i + 1) * len);
         }
+    if (!c->mixed)
+        for (int n = c->S_eff + 1; n <= cfg->nsteps; ++n)
+            c->intervals[main_interval(c, n)] = make_int2(SUB * (n - 1), SUB * n);
+    c->nhi = cfg->nsteps / E1D_NLO + 1;
+    // Ring dither: r~_n = z_n r^_n with z_n = e^{i psi_n}, psi_n = 2 pi frac(n (sqrt2 - 1)),
+    // rounded to FP32 once; the history weights divide it out exactly (FP64).
+    c->zdither.resize(2 * ((size_t)cfg->nsteps + 1));
+    for (int n = 0; n <= cfg->nsteps; ++n) {
+        const double f = (double)n * 0.41421356237309504880;
+        const double psi = 6.28318530717958647692 * (f - std::floor(f));
+        c->zdither[2 * n] = (float)std::cos(psi);
+        c->zdither[2 * n + 1] = (float)std::sin(psi);
+    }
     if (c->d == 1) {
         c->nl = n0 / 2 < 64 ? n0 / 2 : 64;
         c->lb = 0;
@@ -335,11 +401,15 @@ tdse_status tdse_bind_workspace(tdse_ctx* c, void* dev, size_t bytes, void* stre
     c->ws = static_cast<char*>(dev);
     TDSE_CK(c, cudaMemcpyAsync(c->P<int2>(c->off.iv), c->intervals.data(), c->intervals.size() * sizeof(int2),
                                cudaMemcpyHostToDevice, s));
-    TDSE_CK(c, launch_twiddles(c->P<double2>(c->off.tw64_0), c->P<float2>(c->off.tw32_0), c->n0, s));
+    TDSE_CK(c, launch_twiddles(c->P<double2>(c->off.tw64_0), c->P<float2>(c->off.tw32_0),
+                               c->P<float2>(c->off.tw32lo_0), c->n0, s));
     if (c->d == 2)
-        TDSE_CK(c, launch_twiddles(c->P<double2>(c->off.tw64_1), c->P<float2>(c->off.tw32_1), c->n1, s));
+        TDSE_CK(c, launch_twiddles(c->P<double2>(c->off.tw64_1), c->P<float2>(c->off.tw32_1),
+                                   c->P<float2>(c->off.tw32lo_1), c->n1, s));
     else
-        TDSE_CK(c, launch_kin1d(c->P<double2>(c->off.kin64), c->P<float2>(c->off.kin32), c->n0, c->L, c->cfg.dt, s));
+        TDSE_CK(c, launch_kin1d(opt<double2>(c, c->off.kin64), opt<float4>(c, c->off.kinff), c->n0, c->L, c->cfg.dt, s));
+    if (c->d == 1 && c->mixed)
+        TDSE_CK(c, launch_k1d(c->P<float2>(c->off.k1lo), c->P<float2>(c->off.k1hi), c->nhi, c->n0, c->cfg.dt, s));
     // defaults: A == 0 (phi == 0), f(t) == 1
     TDSE_CK(c, cudaMemsetAsync(c->P<double>(c->off.phi), 0, (size_t)c->B * c->d * c->ntf * 8, s));
     std::vector<double> ones(c->ntf, 1.0);
@@ -353,6 +423,7 @@ tdse_status tdse_bind_workspace(tdse_ctx* c, void* dev, size_t bytes, void* stre
     TDSE_CK(c, cudaStreamSynchronize(s));
     c->step = 0;
     c->inited = false;
+    c->ip = false;
     return TDSE_OK;
 }
 
@@ -368,7 +439,7 @@ tdse_status tdse_set_potential(tdse_ctx* c, int instance, const double* V0, cons
     for (int b = lo; b < hi; ++b) {
         double* dV = c->P<double>(c->off.V0) + (size_t)b * c->NP;
         TDSE_CK(c, cudaMemcpyAsync(dV, V0, c->NP * 8, kind, s));
-        TDSE_CK(c, launch_to_float(c->P<float>(c->off.V0f) + (size_t)b * c->NP, dV, c->NP, s));
+        TDSE_CK(c, launch_split_float(c->P<float2>(c->off.V0f) + (size_t)b * c->NP, dV, c->NP, s));
         if (tf) {
             for (int i = 0; i < c->ntf; ++i)
                 if (!std::isfinite(tf[i])) return c->fail(TDSE_EINVAL, "non-finite time factor");
@@ -452,6 +523,7 @@ tdse_status tdse_set_initial(tdse_ctx* c, int instance, const double* u0, int wh
     if (where == TDSE_HOST) TDSE_CK(c, cudaStreamSynchronize(s));
     c->step = 0;
     c->inited = false;
+    c->ip = false;
     return TDSE_OK;
 }
 
@@ -467,12 +539,13 @@ static tdse_status do_init(tdse_ctx* c, cudaStream_t s) {
 
 static tdse_status startup_step(tdse_ctx* c, int n, cudaStream_t s) {
     const size_t NPB = c->NP * c->B;
-    double2* chain_u = c->P<double2>(c->off.chain_uhat);
+    char* chain_u = c->P<char>(c->off.chain_uhat);
     char* chain_r = c->P<char>(c->off.chain_ring);
+    const double half[2] = {0.5, 0.5};
     for (int ch = 0; ch < c->L; ++ch) {
-        double2* cu = chain_u + (size_t)ch * NPB;
+        void* cu = chain_u + (size_t)ch * NPB * 16;
         void* cr = chain_r + (size_t)ch * NPB * c->rsz;
-        TDSE_CK(c, cudaMemcpyAsync(cu, c->P<double2>(c->off.uhat), NPB * 16, cudaMemcpyDeviceToDevice, s));
+        TDSE_CK(c, cudaMemcpyAsync(cu, c->P<void>(c->off.uhat), NPB * 16, cudaMemcpyDeviceToDevice, s));
         TDSE_CK(c, launch_copy_slot(cr, c->P<void>(c->off.ring), c->RS, slot_of(c, n - 1), c->B, c->NP, c->rsz, s));
         const int len = SUB >> ch;
         for (int i = 0; i < (1 << ch); ++i) {
@@ -482,9 +555,7 @@ static tdse_status startup_step(tdse_ctx* c, int n, cudaStream_t s) {
             a.ring = cr;
             a.ring_slots = 1;
             a.nhist = 1;
-            a.h = c->cfg.dt / (double)(1 << ch);
-            a.mu[0] = 0.5;
-            a.mu[1] = 0.5;
+            set_weights(a, c->cfg.dt / (double)(1 << ch), half, 2);
             a.hist_slot[0] = 0;
             a.out_slot = 0;
             a.interval[0] = startup_interval(c, n, ch, i);
@@ -493,7 +564,7 @@ static tdse_status startup_step(tdse_ctx* c, int n, cudaStream_t s) {
             TDSE_CK(c, run(c, a, step_combo(c), s));
         }
     }
-    TDSE_CK(c, launch_combine(c->P<double2>(c->off.uhat), chain_u, NPB, c->L, c->rich, NPB, s));
+    TDSE_CK(c, launch_combine(c->P<void>(c->off.uhat), chain_u, NPB, c->L, c->rich, NPB, c->mixed, s));
     KArgs a = base_args(c);
     a.mode = MODE_REFRESH;
     a.out_slot = slot_of(c, n);
@@ -502,18 +573,76 @@ static tdse_status startup_step(tdse_ctx* c, int n, cudaStream_t s) {
     return TDSE_OK;
 }
 
-static tdse_status adams_step(tdse_ctx* c, int n, cudaStream_t s) {
+// Mixed mode: after the start-up, move the state and the ring to the
+// interaction picture (v^ = u^ / E_n, r^_j = R_j / E_j).
+static tdse_status enter_interaction(tdse_ctx* c, int n, cudaStream_t s) {
+    int steps[8];
+    float zs[16];
+    for (int q = 0; q < c->RS && q < 8; ++q) {
+        const int j = n - ((n - q) % c->RS + c->RS) % c->RS;
+        steps[q] = j >= 0 ? j : -1;
+        zs[2 * q] = j >= 0 ? c->zdither[2 * j] : 1.f;
+        zs[2 * q + 1] = j >= 0 ? c->zdither[2 * j + 1] : 0.f;
+    }
+    KArgs a = base_args(c);
+    TDSE_CK(c, launch_to_interaction(a, n, steps, zs, c->RS < 8 ? c->RS : 8, s));
+    c->ip = true;
+    return TDSE_OK;
+}
+
+// interaction-picture weights: c_j = mu_j / z_{nb - j} for the step nb being
+// begun, d = h mu_0 / z_ne for the step ne being finished, zr = z_ne.
+static void set_dither(const tdse_ctx* c, KArgs& a, int nb, int ne) {
+    auto zinv = [&](int m, double w, float* hi, float* lo) {
+        const double zx = c->zdither[2 * m], zy = c->zdither[2 * m + 1];
+        const double n2 = zx * zx + zy * zy;
+        split(w * zx / n2, hi[0], lo[0]);
+        split(-w * zy / n2, hi[1], lo[1]);
+    };
+    for (int j = 1; j < c->m; ++j) zinv(nb - j, c->mu[j], a.c_hi[j], a.c_lo[j]);
+    zinv(ne, c->cfg.dt * c->mu[0], a.d_hi, a.d_lo);
+    a.zr[0] = c->zdither[2 * ne];
+    a.zr[1] = c->zdither[2 * ne + 1];
+}
+
+static KArgs adams_args(const tdse_ctx* c, int n) {
     KArgs a = base_args(c);
     a.mode = MODE_STEP;
     a.nhist = c->m - 1;
-    a.h = c->cfg.dt;
-    for (int j = 0; j < c->m; ++j) a.mu[j] = c->mu[j];
+    set_weights(a, c->cfg.dt, c->mu, c->m);
     for (int j = 1; j <= a.nhist; ++j) a.hist_slot[j - 1] = slot_of(c, n - j);
     a.out_slot = slot_of(c, n);
-    for (int i = 0; i < a.nhist; ++i) a.interval[i] = n - 1 - i;
+    if (!c->mixed)
+        for (int i = 0; i < a.nhist; ++i) a.interval[i] = main_interval(c, n - i);
     a.kin = 0;
     a.tf = SUB * n;
-    TDSE_CK(c, run(c, a, step_combo(c), s));
+    a.ip = c->mixed ? 1 : 0;
+    a.e_step = n;
+    if (c->mixed) set_dither(c, a, n, n);
+    return a;
+}
+
+// k consecutive Adams steps n0+1 .. n0+k.  2D runs them as col_begin,
+// (row_mid, col_fused) x (k-1), row_mid, col_end.
+static tdse_status adams_steps(tdse_ctx* c, int n0, int k, cudaStream_t s) {
+    const int combo = step_combo(c);
+    if (c->d == 1 || k == 1) {
+        for (int n = n0 + 1; n <= n0 + k; ++n) TDSE_CK(c, run(c, adams_args(c, n), combo, s));
+        return TDSE_OK;
+    }
+    TDSE_CK(c, launch_periodic2d_part(adams_args(c, n0 + 1), combo, PART_COL_BEGIN, s));
+    for (int n = n0 + 1; n < n0 + k; ++n) {
+        TDSE_CK(c, launch_periodic2d_part(adams_args(c, n), combo, PART_ROW_MID, s));
+        KArgs f = adams_args(c, n + 1);     // history slots, intervals and E of the next step ...
+        f.out_slot = slot_of(c, n);         // ... ring slot and E of the step being finished
+        f.e_step = n;
+        f.e_next = n + 1;
+        if (c->mixed) set_dither(c, f, n + 1, n);
+        TDSE_CK(c, launch_periodic2d_part(f, combo, PART_COL_FUSED, s));
+    }
+    const KArgs last = adams_args(c, n0 + k);
+    TDSE_CK(c, launch_periodic2d_part(last, combo, PART_ROW_MID, s));
+    TDSE_CK(c, launch_periodic2d_part(last, combo, PART_COL_END, s));
     return TDSE_OK;
 }
 
@@ -530,11 +659,25 @@ tdse_status tdse_step(tdse_ctx* c, int nsteps, void* stream) {
         tdse_status st = do_init(c, s);
         if (st != TDSE_OK) return st;
     }
-    for (int k = 0; k < nsteps; ++k) {
+    int k = 0;
+    while (k < nsteps) {
         const int n = c->step + 1;
-        tdse_status st = (n <= c->S) ? startup_step(c, n, s) : adams_step(c, n, s);
+        if (n <= c->S) {
+            tdse_status st = startup_step(c, n, s);
+            if (st != TDSE_OK) return st;
+            c->step = n;
+            ++k;
+            continue;
+        }
+        if (c->mixed && !c->ip) {
+            tdse_status st = enter_interaction(c, c->step, s);
+            if (st != TDSE_OK) return st;
+        }
+        const int run_len = nsteps - k;
+        tdse_status st = adams_steps(c, c->step, run_len, s);
         if (st != TDSE_OK) return st;
-        c->step = n;
+        c->step += run_len;
+        k += run_len;
     }
     return TDSE_OK;
 }
@@ -564,7 +707,10 @@ tdse_status tdse_read_u(tdse_ctx* c, int instance, double* u_out, int where, voi
         KArgs a = base_args(c);
         a.mode = MODE_READ;
         a.B = (int)nb;
-        a.uhat = c->P<double2>(c->off.uhat) + (size_t)lo * c->NP;
+        a.uhat = c->P<char>(c->off.uhat) + (size_t)lo * c->NP * 16;
+        a.phi = c->P<double>(c->off.phi) + (size_t)lo * c->d * c->ntf;
+        a.ip = c->ip ? 1 : 0;
+        a.e_step = c->step;
         TDSE_CK(c, run(c, a, f64_combo(c), s));
         src = a.aux2;
     }
@@ -580,7 +726,7 @@ tdse_status tdse_check_finite(tdse_ctx* c, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int* cnt = c->P<int>(c->off.scratch);
     TDSE_CK(c, cudaMemsetAsync(cnt, 0, sizeof(int), s));
-    TDSE_CK(c, launch_count_nonfinite(c->P<double>(c->off.uhat), c->NP * c->B * 2, cnt, s));
+    TDSE_CK(c, launch_count_nonfinite(c->P<void>(c->off.uhat), c->NP * c->B * 2, c->mixed && c->inited, cnt, s));
     int h = 0;
     TDSE_CK(c, cudaMemcpyAsync(&h, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
     TDSE_CK(c, cudaStreamSynchronize(s));

@@ -1,17 +1,25 @@
 // Complex arithmetic on double2/float2 and a shared-memory Stockham FFT.
 //
-// The FFT computes, for each of LANES interleaved sequences of length N held in
-// shared memory at buf[pos * LS + lane],
+// The FFT computes, for each of L interleaved sequences of length N,
 //     forward:  X_k = sum_j x_j e^{-2 pi i j k / N}
 //     inverse:  x_j = sum_k X_k e^{+2 pi i j k / N}     (no 1/N)
-// in place, as a Stockham auto-sort sequence of radix-8 passes preceded by
-// one radix-2 or radix-4 pass when log2(N) is not a multiple of 3.  In pass s
-// with Ns = product of the earlier radices, butterfly j (0 <= j < N/R) reads
-// x[j + r N/R], twiddles by e^{-+2 pi i (j mod Ns) r / (Ns R)}, takes an R-point
-// DFT in registers and writes positions (j - j mod Ns) R + j mod Ns + r Ns.
-// Consecutive threads take consecutive lanes, so interleaved columns give
-// conflict-free shared-memory access.  Twiddles come from a global table
-// tw[m] = e^{-2 pi i m / N} (read through the read-only cache).
+// as a Stockham auto-sort sequence of passes.  In pass s with Ns = product of
+// the earlier radices, butterfly j (0 <= j < N/R) reads x[j + r N/R], twiddles
+// by e^{-+2 pi i (j mod Ns) r / (Ns R)}, takes an R-point DFT in registers and
+// writes positions (j - j mod Ns) R + j mod Ns + r Ns.  The passes are radix 8
+// plus one radix-2 or radix-4 pass when log2 N is not a multiple of 3 (second
+// of three or more passes; with two passes first for forward transforms, last
+// for inverse ones).  Then the last pass of a
+// transform writes exactly the positions j + r N/R that the first pass of the
+// next transform reads, so a transform's inputs and outputs stay in the
+// registers of the thread that owns them: the first pass starts from
+// registers, the last pass ends in registers, and the epilogue/prologue work of
+// the step (history sum, implicit solve, mode update) runs there.  Shared
+// memory holds element (pos, line) at buf[pos * PS + line], consecutive threads
+// taking consecutive lines (interleaved columns).  Twiddles come from a global table
+// tw[m] = e^{-2 pi i m / N} (read through the read-only cache); in FP32 a
+// second table twlo = e^{-2 pi i m/N} - tw holds the rounding residual, used
+// (v tw + v twlo) when TDSE_TWIDDLE_LO is set.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -53,14 +61,22 @@ template <bool INV, class C> __device__ __forceinline__ C rot90(C a) {
     return r;
 }
 
-// multiply by e^{-+ i pi/4} = (1 -+ i)/sqrt(2)
-template <bool INV, class C> __device__ __forceinline__ C rot45(C a) {
-    using R = typename cx_traits<C>::real;
-    const R s = (R)0.70710678118654752440;
-    C r;
+// multiply by e^{-+ i pi/4} = (1 -+ i)/sqrt(2).  In FP32 the constant is
+// applied as hi + lo so that the butterfly has no fixed rounding of 1/sqrt(2)
+// (a rounding repeated identically at every step would bias the transform).
+template <bool INV> __device__ __forceinline__ double2 rot45(double2 a) {
+    const double s = 0.70710678118654752440;
+    double2 r;
     if (INV) { r.x = (a.x - a.y) * s; r.y = (a.x + a.y) * s; }
     else     { r.x = (a.x + a.y) * s; r.y = (a.y - a.x) * s; }
     return r;
+}
+template <bool INV> __device__ __forceinline__ float2 rot45(float2 a) {
+    const float sh = 0.707106769084930419921875f;          // float(1/sqrt 2)
+    const float sl = 1.2101617485882343317e-08f;           // 1/sqrt 2 - sh
+    const float u = INV ? a.x - a.y : a.x + a.y;
+    const float v = INV ? a.x + a.y : a.y - a.x;
+    return make_float2(fmaf(u, sh, u * sl), fmaf(v, sh, v * sl));
 }
 
 template <bool INV, class C> __device__ __forceinline__ void dft2(C* v) {
@@ -94,60 +110,257 @@ template <int R, bool INV, class C> __device__ __forceinline__ void dft_r(C* v) 
 
 constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 
-template <class C, int R, int N, int LANES, int LS, int T, bool INV>
-__device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw, int Ns) {
-    constexpr int NB = N / R;
-    constexpr int ITEMS = NB * LANES;
-    constexpr int PER = (ITEMS + T - 1) / T;
-    C v[PER][R];
-#pragma unroll
-    for (int p = 0; p < PER; ++p) {
-        const int item = threadIdx.x + p * T;
-        if ((ITEMS % T == 0) || item < ITEMS) {
-            const int lane = item % LANES, j = item / LANES;
-#pragma unroll
-            for (int r = 0; r < R; ++r) v[p][r] = buf[(j + r * NB) * LS + lane];
-        }
+
+template <int N, bool INV> struct FftPlan {
+    static constexpr int P = ilog2(N);
+    static constexpr int RS = (P % 3 == 0) ? 8 : (1 << (P % 3));
+    static constexpr int NPASS = (P % 3 == 0) ? P / 3 : P / 3 + 1;
+    // Boundary passes are radix 8 whenever possible (small radix in the second
+    // pass), so that a thread owns 8 values per item at both ends; with only two
+    // passes the small radix goes first (forward) / last (inverse).
+    static constexpr int radix(int s) {
+        return RS == 8 ? 8 : (NPASS >= 3 ? (s == 1 ? RS : 8) : ((INV ? (s == NPASS - 1) : (s == 0)) ? RS : 8));
     }
-    __syncthreads();
-#pragma unroll
-    for (int p = 0; p < PER; ++p) {
-        const int item = threadIdx.x + p * T;
-        if ((ITEMS % T == 0) || item < ITEMS) {
-            const int lane = item % LANES, j = item / LANES;
-            const int k = j & (Ns - 1);
-            if (Ns > 1) {
-                const int stride = N / (Ns * R);
-#pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    C w = __ldg(&tw[k * r * stride]);
-                    if (INV) w.y = -w.y;
-                    v[p][r] = cmul(v[p][r], w);
-                }
-            }
-            dft_r<R, INV>(v[p]);
-            const int base = (j - k) * R + k;
-#pragma unroll
-            for (int r = 0; r < R; ++r) buf[(base + r * Ns) * LS + lane] = v[p][r];
-        }
+    static constexpr int ns(int s) { return s == 0 ? 1 : ns(s - 1) * radix(s - 1); }
+};
+
+// v * w (w from tw, conjugated for the inverse); FP32 adds the residual table.
+template <bool INV> __device__ __forceinline__ double2 twiddle(double2 v, const double2* __restrict__ tw,
+                                                               const double2*, int idx) {
+    double2 w = __ldg(&tw[idx]);
+    if (INV) w.y = -w.y;
+    return cmul(v, w);
+}
+// TDSE_TWIDDLE_LO = 1 applies the FP32 twiddle as hi + lo.  Off by default:
+// on the 512^2 mixed workload it lowers the 2000-step error from 5.1e-7 to
+// 4.4e-7 at a 7% cost in step time.
+#ifndef TDSE_TWIDDLE_LO
+#define TDSE_TWIDDLE_LO 0
+#endif
+template <bool INV> __device__ __forceinline__ float2 twiddle(float2 v, const float2* __restrict__ tw,
+                                                              const float2* __restrict__ twl, int idx) {
+    float2 w = __ldg(&tw[idx]);
+    if (!TDSE_TWIDDLE_LO) {
+        if (INV) w.y = -w.y;
+        return cmul(v, w);
     }
-    __syncthreads();
+    float2 wl = __ldg(&twl[idx]);
+    if (INV) { w.y = -w.y; wl.y = -wl.y; }
+    float2 t = cmul(v, w);
+    t.x = fmaf(v.x, wl.x, fmaf(-v.y, wl.y, t.x));
+    t.y = fmaf(v.x, wl.y, fmaf(v.y, wl.x, t.y));
+    return t;
 }
 
-// Full in-place FFT of LANES interleaved sequences; the caller must have
-// synchronised after writing buf.  Ends with a barrier.
-template <class C, int N, int LANES, int LS, int T, bool INV>
-__device__ __forceinline__ void fft_smem(C* buf, const C* __restrict__ tw) {
-    constexpr int P = ilog2(N);
-    constexpr int R0 = (P % 3 == 0) ? 8 : (1 << (P % 3));
-    constexpr int NREST = (P - ilog2(R0)) / 3;
-    stockham_pass<C, R0, N, LANES, LS, T, INV>(buf, tw, 1);
-    int Ns = R0;
-#pragma unroll 1
-    for (int s = 0; s < NREST; ++s) {
-        stockham_pass<C, 8, N, LANES, LS, T, INV>(buf, tw, Ns);
-        Ns *= 8;
+// L interleaved length-N transforms by T threads; element (pos, line) at
+// buf[pos * PS + line].  Item it of a pass with NB butterflies is butterfly
+// j = it / L of line it % L.
+template <class C, int N, int L, int PS, int T, bool INV>
+struct Fft {
+    using Plan = FftPlan<N, INV>;
+    static constexpr int NPASS = Plan::NPASS;
+    static constexpr int RF = Plan::radix(0);
+    static constexpr int RL = Plan::radix(NPASS - 1);
+    static constexpr int NBF = N / RF;           // first pass: item (j, line) owns positions j + r NBF
+    static constexpr int NBL = N / RL;           // last pass:  item (j, line) owns positions j + r NBL
+    static constexpr int PF = (NBF * L + T - 1) / T;
+    static constexpr int PL = (NBL * L + T - 1) / T;
+
+    __device__ static __forceinline__ bool item(int p, int NB, int& j, int& line) {
+        const int it = threadIdx.x + p * T;
+        line = it % L;
+        j = it / L;
+        return ((NB * L) % T == 0) || it < NB * L;
     }
-}
+
+    template <int S>
+    __device__ static __forceinline__ void mid_pass(C* buf, const C* __restrict__ tw, const C* __restrict__ twl) {
+        constexpr int R = Plan::radix(S);
+        constexpr int Ns = Plan::ns(S);
+        constexpr int NB = N / R;
+        constexpr int PER = (NB * L + T - 1) / T;
+        C v[PER][R];
+#pragma unroll
+        for (int p = 0; p < PER; ++p) {
+            int j, line;
+            if (item(p, NB, j, line)) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[p][r] = buf[(j + r * NB) * PS + line];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int p = 0; p < PER; ++p) {
+            int j, line;
+            if (item(p, NB, j, line)) {
+                const int k = j & (Ns - 1);
+                constexpr int stride = N / (Ns * R);
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[p][r] = twiddle<INV>(v[p][r], tw, twl, k * r * stride);
+                dft_r<R, INV>(v[p]);
+                const int base = (j - k) * R + k;
+#pragma unroll
+                for (int r = 0; r < R; ++r) buf[(base + r * Ns) * PS + line] = v[p][r];
+            }
+        }
+        __syncthreads();
+    }
+
+    template <int S>
+    __device__ static __forceinline__ void mids(C* buf, const C* __restrict__ tw, const C* __restrict__ twl) {
+        if constexpr (S <= NPASS - 2) {
+            mid_pass<S>(buf, tw, twl);
+            mids<S + 1>(buf, tw, twl);
+        }
+    }
+
+    // in[p][r]: value at position j + r NBF of the item (p); out[p][r]: result at
+    // position j + r NBL.  buf must not be in use by any thread on entry; the
+    // call ends with a barrier (buf free again).
+    __device__ static __forceinline__ void run(C (&in)[PF][RF], C (&out)[PL][RL], C* buf,
+                                               const C* __restrict__ tw, const C* __restrict__ twl) {
+        if constexpr (NPASS == 1) {
+#pragma unroll
+            for (int p = 0; p < PF; ++p) {
+                dft_r<RF, INV>(in[p]);
+#pragma unroll
+                for (int r = 0; r < RF; ++r) out[p][r] = in[p][r];
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < PF; ++p) {
+                int j, line;
+                if (item(p, NBF, j, line)) {
+                    dft_r<RF, INV>(in[p]);
+#pragma unroll
+                    for (int r = 0; r < RF; ++r) buf[(j * RF + r) * PS + line] = in[p][r];
+                }
+            }
+            __syncthreads();
+            mids<1>(buf, tw, twl);
+#pragma unroll
+            for (int p = 0; p < PL; ++p) {
+                int j, line;
+                if (item(p, NBL, j, line)) {
+#pragma unroll
+                    for (int r = 0; r < RL; ++r) out[p][r] = buf[(j + r * NBL) * PS + line];
+#pragma unroll
+                    for (int r = 1; r < RL; ++r) out[p][r] = twiddle<INV>(out[p][r], tw, twl, j * r);
+                    dft_r<RL, INV>(out[p]);
+                }
+            }
+            __syncthreads();
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// One length-N transform per warp on warp-private lines of shared memory:
+// element x at line[lpos(x)], lpos(x) = x + x/8 (one pad slot per 8 elements,
+// so that both the unit-stride reads and the stride-R writes of a pass are
+// free of bank conflicts).  Same Stockham passes and radix plan as Fft.  The
+// passes alternate between two lines (ping-pong), so each butterfly is read,
+// transformed and written before the next one: one butterfly's values live
+// in registers at a time, and only __syncwarp separates passes.  run() returns
+// the line holding the result (a or b).  On entry line a holds the input and
+// every lane of the warp must have finished writing it.
+__device__ __forceinline__ int lpos(int x) { return x + (x >> 3); }
+template <int N> constexpr int line_len() { return N + N / 8 + 1; }
+
+template <class C, int N, bool INV>
+struct WarpFft {
+    using Plan = FftPlan<N, INV>;
+    static constexpr bool RESULT_IN_B = (Plan::NPASS % 2) == 1;
+    template <int S>
+    __device__ static __forceinline__ C* pass(C* src, C* dst, const C* __restrict__ tw,
+                                              const C* __restrict__ twl, int lane) {
+        if constexpr (S < Plan::NPASS) {
+            constexpr int R = Plan::radix(S);
+            constexpr int Ns = Plan::ns(S);
+            constexpr int NB = N / R;
+            constexpr int PER = (NB + 31) / 32;
+#pragma unroll 1
+            for (int p = 0; p < PER; ++p) {
+                const int j = lane + 32 * p;
+                if (NB % 32 == 0 || j < NB) {
+                    C v[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[r] = src[lpos(j + r * NB)];
+                    const int k = j & (Ns - 1);
+                    constexpr int stride = N / (Ns * R);
+                    if (Ns > 1) {
+#pragma unroll
+                        for (int r = 1; r < R; ++r) v[r] = twiddle<INV>(v[r], tw, twl, k * r * stride);
+                    }
+                    dft_r<R, INV>(v);
+                    const int base = (j - k) * R + k;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) dst[lpos(base + r * Ns)] = v[r];
+                }
+            }
+            __syncwarp();
+            return pass<S + 1>(dst, src, tw, twl, lane);
+        } else {
+            return src;
+        }
+    }
+    __device__ static __forceinline__ C* run(C* a, C* b, const C* __restrict__ tw, const C* __restrict__ twl) {
+        return pass<0>(a, b, tw, twl, threadIdx.x & 31);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// L interleaved length-N transforms done in place by a whole CTA of T threads:
+// element (pos, line) at buf[pos * LS + line], consecutive threads taking
+// consecutive lines.  Each pass loads all butterflies of the thread into
+// registers, synchronises, then writes (in place).  The caller must have
+// synchronised after filling buf; the call ends with a barrier.
+template <class C, int N, int L, int LS, int T, bool INV>
+struct CtaFft {
+    using Plan = FftPlan<N, INV>;
+    template <int S>
+    __device__ static __forceinline__ void pass(C* buf, const C* __restrict__ tw, const C* __restrict__ twl) {
+        if constexpr (S < Plan::NPASS) {
+            constexpr int R = Plan::radix(S);
+            constexpr int Ns = Plan::ns(S);
+            constexpr int NB = N / R;
+            constexpr int ITEMS = NB * L;
+            constexpr int PER = (ITEMS + T - 1) / T;
+            C v[PER][R];
+#pragma unroll
+            for (int p = 0; p < PER; ++p) {
+                const int it = threadIdx.x + p * T;
+                if (ITEMS % T == 0 || it < ITEMS) {
+                    const int line = it % L, j = it / L;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[p][r] = buf[(j + r * NB) * LS + line];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int p = 0; p < PER; ++p) {
+                const int it = threadIdx.x + p * T;
+                if (ITEMS % T == 0 || it < ITEMS) {
+                    const int line = it % L, j = it / L;
+                    const int k = j & (Ns - 1);
+                    constexpr int stride = N / (Ns * R);
+                    if (Ns > 1) {
+#pragma unroll
+                        for (int r = 1; r < R; ++r) v[p][r] = twiddle<INV>(v[p][r], tw, twl, k * r * stride);
+                    }
+                    dft_r<R, INV>(v[p]);
+                    const int base = (j - k) * R + k;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) buf[(base + r * Ns) * LS + line] = v[p][r];
+                }
+            }
+            __syncthreads();
+            pass<S + 1>(buf, tw, twl);
+        }
+    }
+    __device__ static __forceinline__ void run(C* buf, const C* __restrict__ tw, const C* __restrict__ twl) {
+        pass<0>(buf, tw, twl);
+    }
+};
 
 }  // namespace tdse

@@ -1,5 +1,5 @@
 // Argument bundle shared by the host orchestrator (api.cpp) and the periodic
-// kernels (periodic1d.cu, periodic2d.cu, tables.cu).  Plain data only.
+// kernels (periodic1d.cu, periodic2d.cu, tables.cu, noalloc.cu).  Plain data.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstddef>
@@ -8,85 +8,119 @@ namespace tdse {
 
 // What one launch sequence of the step operator computes.
 enum Mode : int {
-    MODE_STEP = 0,      // W = p0 (u^ - i h S1);  u = IDFT(W)/(1 + i h mu0 V);  R = DFT(V u);
-                        // u^ <- W - i h mu0 R;  ring[out] <- R      (eq. uadamsk / utrapkdisc)
-    MODE_REFRESH = 1,   // R = DFT(V IDFT(u^)) -> ring[out]; u^ unchanged
-    MODE_INIT = 2,      // u^ <- DFT(u0) (u0 stored in u^'s buffer); ring[out] <- DFT(V u0)
-    MODE_READ = 3       // out <- IDFT(u^)
+    MODE_STEP = 0,      // one step of eq. uadamsk (or eq. utrapkdisc): see step_common.cuh
+    MODE_REFRESH = 1,   // R = DFT(V IDFT(u^)) -> ring[out]; state unchanged
+    MODE_INIT = 2,      // u^ <- DFT(u0) (u0 parked in the state slot); ring[out] <- DFT(V u0)
+    MODE_READ = 3       // out <- IDFT(u^)   (u^ = E_n v^ first when the state is in the interaction picture)
 };
 
 // Compute/storage precision combination of one kernel instantiation.
+//   C  = transform type, RT = ring element type, ST = state element type.
 enum Combo : int {
-    COMBO_F64 = 0,      // transforms complex FP64, ring complex FP64
-    COMBO_F32 = 1,      // transforms complex FP32, ring complex FP32
-    COMBO_F64_R32 = 2   // transforms complex FP64, ring complex FP32 (mixed-mode init/read)
+    COMBO_F64 = 0,      // C = double2, RT = double2, ST = double2  (FP64 mode)
+    COMBO_F32 = 1,      // C = float2,  RT = float2,  ST = float4 double-float (mixed steps)
+    COMBO_F64_R32 = 2   // C = double2, RT = float2,  ST = float4 (mixed-mode init / read-out)
 };
 
 constexpr int MAX_HIST = 7;
+constexpr int E1D_NLO = 32;    // 1D absolute kinetic phase: e^{-i k^2 n dt} = Khi[n / 32] Klo[n % 32]
 
 struct KArgs {
     int mode;
     int B;                    // instances in this launch
     int n0, n1;               // grid (n1 = 1 for 1D)
-    // step description
+    // ---- step description
     int nhist;                // history terms j = 1..nhist
     double h;                 // step size
     double mu[MAX_HIST + 1];  // mu_0 .. mu_nhist
+    float h_hi, h_lo;         // h split into two floats (double-float arithmetic)
+    float hmu0_hi, hmu0_lo;   // h mu_0 split
+    float mu_hi[MAX_HIST + 1], mu_lo[MAX_HIST + 1];
     int hist_slot[MAX_HIST];  // ring slot of lag j (index j-1)
     int out_slot;             // ring slot receiving the new (Vu)^
     int interval[MAX_HIST];   // interval id of the one-step phase p_i, i = 0..nhist-1
     int kin;                  // 1D kinetic table index (h = dt / 2^kin)
     int tf;                   // fine time index of the new time (t = tf * dt / 8)
-    // state
-    double2* uhat;            // [B][NP] FP64 modes (in/out)
-    void* ring;               // [B][ring_slots][NP] ring (double2 or float2)
+    int ip;                   // 1: interaction-picture step (state v^ = u^ / E_n, ring r~ = z_n R / E_n)
+    // interaction picture, mixed: the ring stores r~_n = z_n r^_n with a per-step
+    // dither z_n (|z| ~ 1); the history uses c_j = mu_j / z_{n-j} and the update
+    // d = h mu_0 / z_n, both split hi + lo (complex).
+    float zr[2];              // z_n of the ring value written by this launch
+    float c_hi[MAX_HIST + 1][2], c_lo[MAX_HIST + 1][2];
+    float d_hi[2], d_lo[2];
+    int e_step;               // n of E_n for an interaction-picture step / read-out
+    int e_next;               // fused column pass: n of the next step's E
+    // ---- state
+    void* uhat;               // [B][NP] state (ST)
+    void* ring;               // [B][ring_slots][NP] ring (RT)
     int ring_slots;
-    double2* aux;             // MODE_READ output / 2D intermediate T1 (16 B per element)
-    double2* aux2;            // 2D intermediate T2 (16 B per element)
-    // problem tables
+    double2* aux;             // 2D intermediate T1 (16 B per element)
+    double2* aux2;            // 2D intermediate T2 / read-out output (16 B per element)
+    // ---- problem tables
     const double* V0;         // [B][NP]
-    const float* V0f;         // [B][NP]
+    const float2* V0f;        // [B][NP] (float(V0), float(V0 - float(V0)))
     const double* tfac;       // [B][ntf]
     int ntf;
-    int n_int;                // number of phase intervals per instance
-    // 1D phase tables: p(k) = kin[c][m] * adv_hi[m >> lb] * adv_lo[m & (nl-1)]
+    int n_int;                // phase intervals per instance
+    double dt;
+    const double* phi;        // [B][d][ntf], phi at t = m dt / 8
+    // 1D relative phases p(k) = kin[c][m] * adv[hi] * adv[lo]
     const double2* kin64;     // [L][N]
-    const float2* kin32;
+    const float4* kinff;
     const double2* adv64;     // [B][n_int][nh + nl]
-    const float2* adv32;
+    const float4* advff;
     int nh, nl, lb;
-    // 2D phase tables: p(k0, k1) = q[int][m0] * q[int][n0 + m1]
+    // 2D relative phases p(k0,k1) = q[int][m0] * q[int][n0 + m1]
     const double2* q64;       // [B][n_int][n0 + n1]
-    const float2* q32;
+    const float4* qff;
+    // interaction-picture phases E_n(k) = exp(-i |k|^2 t_n + i k.phi(t_n)) in FP32
+    const float2* e2d;        // [B][nsteps + 1][n0 + n1]   (2D: separable)
+    const float2* k1d_lo;     // [E1D_NLO][N]               (1D: e^{-i k^2 n dt}, n < 32)
+    const float2* k1d_hi;     // [nhi][N]                   (1D: e^{-i k^2 32 q dt})
+    const float2* a1d;        // [B][nsteps + 1][nh + nl]   (1D: e^{i k phi(t_n)})
     // twiddles e^{-2 pi i m / n} for each axis length
     const double2* tw64_0;
     const double2* tw64_1;
     const float2* tw32_0;
     const float2* tw32_1;
+    const float2* tw32lo_0;   // e^{-2 pi i m / n} - tw32 (rounding residual)
+    const float2* tw32lo_1;
 };
 
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_periodic1d(const KArgs& a, int combo, cudaStream_t s);
+// 2D: launch_periodic2d runs the whole mode (MODE_STEP: col_begin, row_mid,
+// col_end); launch_periodic2d_part runs one pass kernel, which the host uses to
+// chain consecutive Adams steps as col_begin, (row_mid, col_fused)..., row_mid, col_end.
 cudaError_t launch_periodic2d(const KArgs& a, int combo, cudaStream_t s);
+cudaError_t launch_periodic2d_part(const KArgs& a, int combo, int part, cudaStream_t s);
+enum Part2D : int { PART_COL_BEGIN = 0, PART_ROW_MID = 1, PART_COL_END = 2, PART_COL_FUSED = 3 };
 bool periodic1d_supported(int n);
 bool periodic2d_supported(int n0, int n1);
 
 // Table builders (tables.cu).
-cudaError_t launch_twiddles(double2* tw64, float2* tw32, int n, cudaStream_t s);
-cudaError_t launch_kin1d(double2* kin64, float2* kin32, int n, int L, double dt, cudaStream_t s);
-// intervals: [n_int] pairs (a, b) of fine time indices; phi: [B][d][ntf]
-cudaError_t launch_adv1d(double2* adv64, float2* adv32, const int2* intervals, int n_int,
-                         const double* phi, int ntf, int B, int n, int nh, int nl, cudaStream_t s);
-cudaError_t launch_q2d(double2* q64, float2* q32, const int2* intervals, int n_int,
-                       const double* phi, int ntf, int B, int n0, int n1, double dt, cudaStream_t s);
-cudaError_t launch_to_float(float* dst, const double* src, size_t n, cudaStream_t s);
-// u^ <- sum_c coef[c] * chain[c] (chains laid out [L][B*NP])
-cudaError_t launch_combine(double2* uhat, const double2* chains, size_t chain_stride, int L,
-                           const double* coef, size_t n, cudaStream_t s);
-// copy ring slot src_slot of every instance into a 1-slot ring (same precision)
-cudaError_t launch_copy_slot(void* dst, const void* ring, int ring_slots, int slot, int B,
-                             size_t NP, size_t elem_bytes, cudaStream_t s);
-// count non-finite entries of x[0..n) into *count (device int, accumulated)
-cudaError_t launch_count_nonfinite(const double* x, size_t n, int* count, cudaStream_t s);
+cudaError_t launch_twiddles(double2* tw64, float2* tw32, float2* tw32lo, int n, cudaStream_t s);
+cudaError_t launch_kin1d(double2* kin64, float4* kinff, int n, int L, double dt, cudaStream_t s);
+cudaError_t launch_adv1d(double2* adv64, float4* advff, const int2* intervals, int n_int, const double* phi,
+                         int ntf, int n, int nh, int nl, cudaStream_t s);
+cudaError_t launch_q2d(double2* q64, float4* qff, const int2* intervals, int n_int, const double* phi, int ntf,
+                       int n0, int n1, double dt, cudaStream_t s);
+cudaError_t launch_e2d(float2* e, const double* phi, int ntf, int nsteps, int n0, int n1, double dt,
+                       cudaStream_t s);
+cudaError_t launch_k1d(float2* klo, float2* khi, int nhi, int n, double dt, cudaStream_t s);
+cudaError_t launch_a1d(float2* a1d, const double* phi, int ntf, int nsteps, int n, int nh, int nl,
+                       cudaStream_t s);
+cudaError_t launch_split_float(float2* hilo, const double* src, size_t n, cudaStream_t s);
+// state <- sum_c coef[c] * chain[c] (chains laid out [L][n]); ff = state is double-float
+cudaError_t launch_combine(void* state, const void* chains, size_t chain_stride, int L, const double* coef,
+                           size_t n, bool ff, cudaStream_t s);
+cudaError_t launch_copy_slot(void* dst, const void* ring, int ring_slots, int slot, int B, size_t NP,
+                             size_t elem_bytes, cudaStream_t s);
+// count non-finite doubles (ff = false) or floats (ff = true) in n 8-byte words
+cudaError_t launch_count_nonfinite(const void* x, size_t nwords, bool ff, int* count, cudaStream_t s);
+// Convert the double-float state at step n and the ring slots of steps
+// slot_steps[0..nslots) to the interaction picture (divide by E in FP64).
+cudaError_t launch_to_interaction(const KArgs& a, int n, const int* slot_steps, const float* slot_z, int nslots,
+                                  cudaStream_t s);
 
 }  // namespace tdse

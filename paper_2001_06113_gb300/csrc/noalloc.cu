@@ -25,8 +25,8 @@
 namespace tdse {
 
 constexpr size_t NOALLOC_T1_BYTES = (size_t)TDSE_NOALLOC_MAX_POINTS * 16;
-constexpr size_t NOALLOC_TW_OFF = NOALLOC_T1_BYTES;                 // 2 axes x 1024 x (16 + 8) bytes
-constexpr size_t NOALLOC_DUMMY_OFF = NOALLOC_TW_OFF + 2 * 1024 * 24;     // one double read by the row pass
+constexpr size_t NOALLOC_TW_OFF = NOALLOC_T1_BYTES;                 // 2 axes x 1024 x (16 + 8 + 8) bytes
+constexpr size_t NOALLOC_DUMMY_OFF = NOALLOC_TW_OFF + 2 * 1024 * 32;     // one double read by the row pass
 constexpr size_t NOALLOC_BYTES = NOALLOC_DUMMY_OFF + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
@@ -70,11 +70,13 @@ extern "C" tdse_status tdse_modes_to_grid_2d_noalloc(const double* uhat, double*
     double2* tw64_1 = tw64_0 + 1024;
     float2* tw32_0 = reinterpret_cast<float2*>(tw64_1 + 1024);
     float2* tw32_1 = tw32_0 + 1024;
+    float2* tw32lo_0 = tw32_1 + 1024;
+    float2* tw32lo_1 = tw32lo_0 + 1024;
     // The twiddles of this call's sizes are rewritten every call (stream-ordered
     // before the transform); the intermediate array needs no clearing because
     // every element is written before it is read.
-    if (launch_twiddles(tw64_0, tw32_0, n0, s) != cudaSuccess) return TDSE_ECUDA;
-    if (launch_twiddles(tw64_1, tw32_1, n1, s) != cudaSuccess) return TDSE_ECUDA;
+    if (launch_twiddles(tw64_0, tw32_0, tw32lo_0, n0, s) != cudaSuccess) return TDSE_ECUDA;
+    if (launch_twiddles(tw64_1, tw32_1, tw32lo_1, n1, s) != cudaSuccess) return TDSE_ECUDA;
     KArgs a{};
     a.mode = MODE_READ;
     a.B = batch;
@@ -87,6 +89,8 @@ extern "C" tdse_status tdse_modes_to_grid_2d_noalloc(const double* uhat, double*
     a.tw64_1 = tw64_1;
     a.tw32_0 = tw32_0;
     a.tw32_1 = tw32_1;
+    a.tw32lo_0 = tw32lo_0;
+    a.tw32lo_1 = tw32lo_1;
     a.tfac = reinterpret_cast<const double*>(b + NOALLOC_DUMMY_OFF);       // potential factor: unused on read-out
     a.ntf = 0;
     a.tf = 0;

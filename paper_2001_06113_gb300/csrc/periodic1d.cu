@@ -1,14 +1,15 @@
 // 1D periodic step: one CTA per instance, the whole transform in shared memory.
 //
 // MODE_STEP fuses, for an instance of N modes, in one launch:
-//   history Horner sum + one-step phase (eq. uadamsk)  ->  W          [registers/global]
-//   inverse DFT (no 1/N)                                ->  y          [shared memory]
-//   u = y / (1 + i h mu_0 V), Vu                        (diagonal implicit solve)
-//   forward DFT with 1/N                                ->  R = (Vu)^
-//   u^ <- W - i h mu_0 R,  ring[out] <- R
-// so that the mode arrays cross HBM once per step: read u^ and the history
-// slots, write u^ and one slot.  W stays in registers when each thread owns
-// at most 4 modes; otherwise it is parked in u^'s own slot (L2-resident).
+//   history sum + phase (eq. uadamsk, lab frame or interaction picture) -> W
+//   inverse DFT (no 1/N)                                                 -> y      [shared memory]
+//   u = y / (1 + i h mu_0 V), Vu                         (diagonal implicit solve)
+//   forward DFT with 1/N                                                 -> R = (Vu)^
+//   state update and ring write
+// so that the mode arrays cross HBM once per step: read the state and the
+// history slots, write the state and one slot.  The pre-FFT state value (W or
+// X) stays in registers when each thread owns at most 4 modes; otherwise it is
+// parked in the state's own slot (L2-resident) and read back.
 #include "step_common.cuh"
 
 namespace tdse {
@@ -18,107 +19,195 @@ constexpr int threads_1d(int N) { return N / 8 < 32 ? 32 : (N / 8 > 512 ? 512 : 
 template <class C, class RT, int N>
 __global__ void __launch_bounds__(threads_1d(N)) k_periodic1d(const KArgs a) {
     constexpr int T = threads_1d(N);
-    constexpr int PER = (N + T - 1) / T;
-    constexpr bool KEEP = PER <= 4;
+    using FI = Fft<C, N, 1, 1, T, true>;     // inverse transform (modes -> grid)
+    using FW = Fft<C, N, 1, 1, T, false>;    // forward transform (grid -> modes)
+    static_assert(FI::RL == FW::RF && FI::PL == FW::PF, "inverse output regs feed forward input regs");
+    static_assert(FW::RL == FI::RF && FW::PL == FI::PF, "forward output regs sit on the step's modes");
+    constexpr int PB = FI::PF, RB = FI::RF;  // a thread's modes: j + r FI::NBF (= j + r FW::NBL)
+    constexpr bool KEEP = PB * RB <= 8;
+    constexpr bool F64 = is_f64<C>::value;
+    constexpr bool FF = !is_f64<RT>::value;  // double-float state
+    using ST = state_t<RT>;
     using R = typename cx_traits<C>::real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
 
     const int b = blockIdx.x;
     const size_t NP = N;
-    double2* uh = a.uhat + (size_t)b * NP;
+    ST* st = reinterpret_cast<ST*>(a.uhat) + (size_t)b * NP;
     RT* ringb = reinterpret_cast<RT*>(a.ring) + (size_t)b * a.ring_slots * NP;
     const C* tw;
-    if constexpr (is_f64<C>::value) tw = a.tw64_0; else tw = a.tw32_0;
+    const C* twl;
+    if constexpr (F64) { tw = a.tw64_0; twl = tw; } else { tw = a.tw32_0; twl = a.tw32lo_0; }
     const double vfac = a.tfac[(size_t)b * a.ntf + a.tf];
     const double* V0 = a.V0 + (size_t)b * NP;
-    const float* V0f = a.V0f + (size_t)b * NP;
+    const float2* V0f = a.V0f + (size_t)b * NP;
     const R scale = (R)1 / (R)N;
+    const float fh = (float)vfac, fl = (float)(vfac - (double)fh);
 
-    auto Vat = [&](int j) -> R {
-        if constexpr (is_f64<C>::value) return vfac * V0[j];
-        else return (R)vfac * V0f[j];
+    // V(x_j, t) as hi + lo in the compute precision
+    auto Vat = [&](int j, R& hi, R& lo) {
+        if constexpr (F64) {
+            hi = vfac * V0[j];
+            lo = 0.0;
+        } else {
+            const float2 v2 = V0f[j];
+            hi = fh * v2.x;
+            lo = fmaf(fh, v2.x, -hi) + fmaf(fh, v2.y, fl * v2.x);
+        }
     };
 
     if (a.mode == MODE_INIT) {
-        // (V u0)^ -> ring[out]; u0 is read from u^'s slot, overwritten below.
+        // (V u0)^ -> ring[out]; u0 is parked as raw FP64 pairs in the state slot
+        // (overwritten below by the state in its own format).
+        const double2* u0 = reinterpret_cast<const double2*>(a.uhat) + (size_t)b * NP;
+        C in[FW::PF][FW::RF], out[FW::PL][FW::RL];
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
 #pragma unroll
-        for (int p = 0; p < PER; ++p) {
-            const int j = threadIdx.x + p * T;
-            if (N % T == 0 || j < N) buf[j] = cscale(cvt<C>(uh[j]), Vat(j));
-        }
-        __syncthreads();
-        fft_smem<C, N, 1, 1, T, false>(buf, tw);
+            for (int p = 0; p < FW::PF; ++p) {
+                int j, line;
+                if (FW::item(p, FW::NBF, j, line)) {
 #pragma unroll
-        for (int p = 0; p < PER; ++p) {
-            const int k = threadIdx.x + p * T;
-            if (N % T == 0 || k < N) {
-                ringb[(size_t)a.out_slot * NP + k] = cvt<RT>(cscale(buf[k], scale));
-                buf[k] = cvt<C>(uh[k]);
+                    for (int r = 0; r < FW::RF; ++r) {
+                        const int x = j + r * FW::NBF;
+                        const C u = cvt<C>(u0[x]);
+                        in[p][r] = pass == 0 ? cscale(u, (R)(vfac * V0[x])) : u;
+                    }
+                }
             }
-        }
-        __syncthreads();
-        fft_smem<C, N, 1, 1, T, false>(buf, tw);
+            FW::run(in, out, buf, tw, twl);
 #pragma unroll
-        for (int p = 0; p < PER; ++p) {
-            const int k = threadIdx.x + p * T;
-            if (N % T == 0 || k < N) uh[k] = cvt<double2>(cscale(buf[k], scale));
+            for (int p = 0; p < FW::PL; ++p) {
+                int j, line;
+                if (FW::item(p, FW::NBL, j, line)) {
+#pragma unroll
+                    for (int r = 0; r < FW::RL; ++r) {
+                        const int k = j + r * FW::NBL;
+                        const C v = cscale(out[p][r], scale);
+                        if (pass == 0) ringb[(size_t)a.out_slot * NP + k] = cvt<RT>(v);
+                    }
+                }
+            }
+            if (pass == 0) __syncthreads();   // every thread has read u0 before any state write
+        }
+        // the last forward result is still in registers: write the state
+#pragma unroll
+        for (int p = 0; p < FW::PL; ++p) {
+            int j, line;
+            if (FW::item(p, FW::NBL, j, line)) {
+#pragma unroll
+                for (int r = 0; r < FW::RL; ++r)
+                    st[j + r * FW::NBL] = d_to_st<ST>(cvt<double2>(cscale(out[p][r], scale)));
+            }
         }
         return;
     }
 
     if (a.mode == MODE_READ) {
+        C in[FI::PF][FI::RF], out[FI::PL][FI::RL];
 #pragma unroll
-        for (int p = 0; p < PER; ++p) {
-            const int k = threadIdx.x + p * T;
-            if (N % T == 0 || k < N) buf[k] = cvt<C>(uh[k]);
+        for (int p = 0; p < FI::PF; ++p) {
+            int j, line;
+            if (FI::item(p, FI::NBF, j, line)) {
+#pragma unroll
+                for (int r = 0; r < FI::RF; ++r) {
+                    const int k = j + r * FI::NBF;
+                    double2 v = st_to_d(st[k]);
+                    if (a.ip) v = cmul(e_exact(a, b, a.e_step, kmode(k, N), 0.0, 1), v);
+                    in[p][r] = cvt<C>(v);
+                }
+            }
         }
-        __syncthreads();
-        fft_smem<C, N, 1, 1, T, true>(buf, tw);
-        double2* out = a.aux2 + (size_t)b * NP;
+        FI::run(in, out, buf, tw, twl);
+        double2* outg = a.aux2 + (size_t)b * NP;
 #pragma unroll
-        for (int p = 0; p < PER; ++p) {
-            const int j = threadIdx.x + p * T;
-            if (N % T == 0 || j < N) out[j] = cvt<double2>(buf[j]);
+        for (int p = 0; p < FI::PL; ++p) {
+            int j, line;
+            if (FI::item(p, FI::NBL, j, line)) {
+#pragma unroll
+                for (int r = 0; r < FI::RL; ++r) outg[j + r * FI::NBL] = cvt<double2>(out[p][r]);
+            }
         }
         return;
     }
 
     const bool step = (a.mode == MODE_STEP);
-    double2 Wk[KEEP ? PER : 1];
+    ST Wk[KEEP ? PB : 1][KEEP ? RB : 1];
+    C in[PB][RB], mid[FI::PL][FI::RL], out[FW::PL][FW::RL];
 #pragma unroll
-    for (int p = 0; p < PER; ++p) {
-        const int k = threadIdx.x + p * T;
-        if (N % T == 0 || k < N) {
-            double2 W = uh[k];
-            if (step) {
-                Phase1D ph{a, b, k};
-                W = recurrence_W<C, RT>(a, W, ringb, NP, (size_t)k, ph);
-                if constexpr (KEEP) Wk[p]= W; else uh[k] = W;
+    for (int p = 0; p < PB; ++p) {
+        int j, line;
+        if (FI::item(p, FI::NBF, j, line)) {
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const int k = j + r * FI::NBF;
+                ST W = st[k];
+                C x;
+                if (step) {
+                    if constexpr (!FF) {
+                        Phase1D ph{a, b, k};
+                        W = horner_W64(a, W, reinterpret_cast<const double2*>(ringb), NP, (size_t)k, ph);
+                        x = cvt<C>(W);
+                    } else {
+                        if (a.ip) {
+                            W = ip_X(a, W, reinterpret_cast<const float2*>(ringb), NP, (size_t)k);
+                            x = cvt<C>(cmul(e_1d(a, b, a.e_step, k), make_float2(W.x, W.y)));
+                        } else {
+                            W = mixed_X(a, W, reinterpret_cast<const float2*>(ringb), NP, (size_t)k);
+                            Phase1D ph{a, b, k};
+                            W = ffc_mul(ph.pff(0), W);
+                            x = st_to_c<C>(W);
+                        }
+                    }
+                    if constexpr (KEEP) Wk[p][r] = W; else st[k] = W;
+                } else {
+                    x = st_to_c<C>(W);
+                }
+                in[p][r] = x;
             }
-            buf[k] = cvt<C>(W);
         }
     }
-    __syncthreads();
-    fft_smem<C, N, 1, 1, T, true>(buf, tw);
+    FI::run(in, mid, buf, tw, twl);
     const R hmu0 = step ? (R)(a.h * a.mu[0]) : (R)0;
 #pragma unroll
-    for (int p = 0; p < PER; ++p) {
-        const int j = threadIdx.x + p * T;
-        if (N % T == 0 || j < N) buf[j] = implicit_solve_times_V(buf[j], Vat(j), hmu0);
-    }
-    __syncthreads();
-    fft_smem<C, N, 1, 1, T, false>(buf, tw);
-    const double hmu0d = a.h * a.mu[0];
+    for (int p = 0; p < FI::PL; ++p) {
+        int j, line;
+        if (FI::item(p, FI::NBL, j, line)) {
 #pragma unroll
-    for (int p = 0; p < PER; ++p) {
-        const int k = threadIdx.x + p * T;
-        if (N % T == 0 || k < N) {
-            const RT r = cvt<RT>(cscale(buf[k], scale));
-            ringb[(size_t)a.out_slot * NP + k] = r;
-            if (step) {
-                const double2 W = KEEP ? Wk[p] : uh[k];
-                uh[k] = mode_update(W, cvt<double2>(r), hmu0d);
+            for (int r = 0; r < FI::RL; ++r) {
+                R vh, vl;
+                Vat(j + r * FI::NBL, vh, vl);
+                mid[p][r] = implicit_solve_times_V(mid[p][r], vh, vl, hmu0);
+            }
+        }
+    }
+    FW::run(mid, out, buf, tw, twl);
+#pragma unroll
+    for (int p = 0; p < FW::PL; ++p) {
+        int j, line;
+        if (FW::item(p, FW::NBL, j, line)) {
+#pragma unroll
+            for (int r = 0; r < FW::RL; ++r) {
+                const int k = j + r * FW::NBL;
+                RT rv = cvt<RT>(cscale(out[p][r], scale));
+                bool done = false;
+                if constexpr (FF) {
+                    if (step && a.ip) {
+                        rv = cmul(make_float2(a.zr[0], a.zr[1]), cmul(conjf2(e_1d(a, b, a.e_step, k)), rv));
+                        ringb[(size_t)a.out_slot * NP + k] = rv;
+                        st[k] = ip_update(a, KEEP ? Wk[p][r] : st[k], rv);
+                        done = true;
+                    }
+                }
+                if (!done) {
+                    ringb[(size_t)a.out_slot * NP + k] = rv;
+                    if (step) {
+                        const ST W = KEEP ? Wk[p][r] : st[k];
+                        if constexpr (FF) st[k] = update_ff(a, W, rv);
+                        else st[k] = update64(W, rv, a.h * a.mu[0]);
+                    }
+                }
             }
         }
     }
@@ -132,6 +221,9 @@ static cudaError_t launch_n(const KArgs& a, cudaStream_t s) {
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_periodic1d<C, RT, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_periodic1d<C, RT, N>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         configured = true;
     }

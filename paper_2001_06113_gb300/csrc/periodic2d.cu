@@ -1,59 +1,123 @@
-// 2D periodic step as three shared-memory pass kernels over [B][n0][n1]
-// (row-major, axis 1 contiguous).  Each pass holds LANES whole lines of the
-// 2D array in shared memory, interleaved so that consecutive threads touch
-// consecutive lanes:
+// 2D periodic step as shared-memory pass kernels over [B][n0][n1]
+// (row-major, axis 1 contiguous):
 //
-//   col_begin (axis 0, LANES columns per CTA):
-//       W = p_0 (u^ - i h S_1) per mode (eq. uadamsk), W -> u^'s slot,
-//       inverse DFT along axis 0                       -> T1 [i0][k1]
-//   row_mid   (axis 1, LANES rows per CTA):
-//       inverse DFT along axis 1 -> y; u = y/(1 + i h mu_0 V); Vu;
-//       forward DFT along axis 1 (1/n1)                 -> T2 [i0][k1]
+//   col_begin (axis 0, 8 columns per CTA):
+//       state -> W (lab frame) or X (interaction picture), stored back in the
+//       state slot; inverse DFT along axis 0 of W or E_n X    -> T1 [i0][k1]
+//   row_mid   (axis 1, 8 rows per CTA, one warp per row):
+//       inverse DFT along axis 1 -> y; u = y/(1 + i h mu_0 V); V u;
+//       forward DFT along axis 1 (1/n1)                        -> T2 [i0][k1]
 //   col_end   (axis 0):
-//       forward DFT along axis 0 (1/n0) -> R = (Vu)^; ring[out] <- R;
-//       u^ <- W - i h mu_0 R
+//       forward DFT along axis 0 (1/n0) -> R = (Vu)^; ring[out] <- R (lab
+//       frame) or z_n R / E_n (interaction picture); state update
+//   col_fused = col_end of step n followed by col_begin of step n+1 on the same
+//       column block: consecutive Adams steps cost two launches each
+//       (row_mid, col_fused), and the mode arrays cross HBM once per step.
 //
-// MODE_REFRESH runs the same passes with no phase/history and beta = 0;
+// Each CTA holds 8 whole lines (columns or rows) in shared memory, interleaved
+// so that consecutive threads touch consecutive lines, and transforms them
+// together (CtaFft).  The element phases read and write 8 consecutive columns
+// per row (one 64/128-byte segment); the per-mode history work is done one
+// mode at a time per thread with all of that mode's loads in flight.
+//
+// MODE_REFRESH runs the passes with no phase/history and beta = 0;
 // MODE_INIT runs row_mid (u0 -> T1 = F1 u0, T2 = F1 V u0) and col_end
-// (T1 -> u^, T2 -> ring[out]); MODE_READ runs col_begin (u^ -> T1) and
+// (T1 -> state, T2 -> ring[out]); MODE_READ runs col_begin (state -> T1, after
+// multiplying by E_n in FP64 if the state is in the interaction picture) and
 // row_mid (T1 -> u into aux2).
 #include "step_common.cuh"
 
 namespace tdse {
 
-constexpr int LANES2D = 8;
+constexpr int LANES2D = 8;     // columns per column-pass CTA = rows per row-pass CTA
 constexpr int T2D = 256;
+#ifndef TDSE_MINB2D
+#define TDSE_MINB2D 4          // resident CTAs per SM the register budget is sized for
+#endif
+
+// ------------------------------------------------------------ element helpers
+// Start of a step at mode (m0, m1): returns the inverse-DFT input and updates
+// the state slot (W or X) in MODE_STEP.
+template <class C, class RT>
+__device__ __forceinline__ C begin_elem(const KArgs& a, bool step, int b, state_t<RT>* st, const RT* ringb,
+                                        size_t NP, size_t idx, int m0, int m1, int n_e) {
+    using ST = state_t<RT>;
+    constexpr bool FF = !is_f64<RT>::value;
+    ST W = st[idx];
+    if (step) {
+        if constexpr (!FF) {
+            Phase2D ph{a, b, m0, m1};
+            W = horner_W64(a, W, ringb, NP, idx, ph);
+            st[idx] = W;
+            return cvt<C>(W);
+        } else {
+            if (a.ip) {
+                W = ip_X(a, W, ringb, NP, idx);
+                st[idx] = W;
+                return cvt<C>(cmul(e_2d(a, b, n_e, m0, m1), make_float2(W.x, W.y)));
+            }
+            W = mixed_X(a, W, ringb, NP, idx);
+            Phase2D ph{a, b, m0, m1};
+            W = ffc_mul(ph.pff(0), W);
+            st[idx] = W;
+            return st_to_c<C>(W);
+        }
+    }
+    if (a.mode == MODE_READ && a.ip) {
+        const double2 v = cmul(e_exact(a, b, a.e_step, kmode(m0, a.n0), kmode(m1, a.n1), 2), st_to_d(W));
+        return cvt<C>(v);
+    }
+    return st_to_c<C>(W);
+}
+
+// End of a step at mode (m0, m1) given R (already scaled): ring and state.
+template <class C, class RT>
+__device__ __forceinline__ void end_elem(const KArgs& a, bool step, int b, state_t<RT>* st, RT* ringb,
+                                         size_t NP, size_t idx, int m0, int m1, C Rc, int n_e) {
+    constexpr bool FF = !is_f64<RT>::value;
+    RT r = cvt<RT>(Rc);
+    if constexpr (FF) {
+        if (step && a.ip) {
+            r = cmul(make_float2(a.zr[0], a.zr[1]), cmul(conjf2(e_2d(a, b, n_e, m0, m1)), r));
+            ringb[(size_t)a.out_slot * NP + idx] = r;
+            st[idx] = ip_update(a, st[idx], r);
+            return;
+        }
+    }
+    ringb[(size_t)a.out_slot * NP + idx] = r;
+    if (step) {
+        if constexpr (FF) st[idx] = update_ff(a, st[idx], r);
+        else st[idx] = update64(st[idx], r, a.h * a.mu[0]);
+    }
+}
 
 // ---------------------------------------------------------------- col_begin
 template <class C, class RT, int N0>
-__global__ void __launch_bounds__(T2D) k_col_begin(const KArgs a) {
+__global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_begin(const KArgs a) {
     constexpr int L = LANES2D;
+    using FI = CtaFft<C, N0, L, L, T2D, true>;
+    using ST = state_t<RT>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int b = blockIdx.y;
     const int c0 = blockIdx.x * L;
     const int n1 = a.n1;
     const size_t NP = (size_t)N0 * n1;
-    double2* uh = a.uhat + (size_t)b * NP;
+    ST* st = reinterpret_cast<ST*>(a.uhat) + (size_t)b * NP;
     const RT* ringb = reinterpret_cast<const RT*>(a.ring) + (size_t)b * a.ring_slots * NP;
     const C* tw;
-    if constexpr (is_f64<C>::value) tw = a.tw64_0; else tw = a.tw32_0;
+    const C* twl;
+    if constexpr (is_f64<C>::value) { tw = a.tw64_0; twl = tw; } else { tw = a.tw32_0; twl = a.tw32lo_0; }
     const bool step = (a.mode == MODE_STEP);
 
+#pragma unroll 1
     for (int item = threadIdx.x; item < N0 * L; item += T2D) {
         const int lane = item % L, m0 = item / L;
         const int m1 = c0 + lane;
-        const size_t idx = (size_t)m0 * n1 + m1;
-        double2 W = uh[idx];
-        if (step) {
-            Phase2D ph{a, b, m0, m1};
-            W = recurrence_W<C, RT>(a, W, ringb, NP, idx, ph);
-            uh[idx] = W;
-        }
-        buf[m0 * L + lane] = cvt<C>(W);
+        buf[m0 * L + lane] = begin_elem<C, RT>(a, step, b, st, ringb, NP, (size_t)m0 * n1 + m1, m0, m1, a.e_step);
     }
     __syncthreads();
-    fft_smem<C, N0, L, L, T2D, true>(buf, tw);
+    FI::run(buf, tw, twl);
     C* T1 = reinterpret_cast<C*>(a.aux) + (size_t)b * NP;
     for (int item = threadIdx.x; item < N0 * L; item += T2D) {
         const int lane = item % L, i0 = item / L;
@@ -63,10 +127,13 @@ __global__ void __launch_bounds__(T2D) k_col_begin(const KArgs a) {
 
 // ------------------------------------------------------------------ row_mid
 template <class C, int N1>
-__global__ void __launch_bounds__(T2D) k_row_mid(const KArgs a) {
+__global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_row_mid(const KArgs a) {
     constexpr int L = LANES2D;
     constexpr int LS = L + 1;
+    using FI = CtaFft<C, N1, L, LS, T2D, true>;
+    using FW = CtaFft<C, N1, L, LS, T2D, false>;
     using R = typename cx_traits<C>::real;
+    constexpr bool F64 = is_f64<C>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int b = blockIdx.y;
@@ -74,19 +141,17 @@ __global__ void __launch_bounds__(T2D) k_row_mid(const KArgs a) {
     const int n0 = a.n0;
     const size_t NP = (size_t)n0 * N1;
     const C* tw;
-    if constexpr (is_f64<C>::value) tw = a.tw64_1; else tw = a.tw32_1;
+    const C* twl;
+    if constexpr (F64) { tw = a.tw64_1; twl = tw; } else { tw = a.tw32_1; twl = a.tw32lo_1; }
     const double vfac = a.tfac[(size_t)b * a.ntf + a.tf];
     const double* V0 = a.V0 + (size_t)b * NP;
-    const float* V0f = a.V0f + (size_t)b * NP;
-    auto Vat = [&](size_t idx) -> R {
-        if constexpr (is_f64<C>::value) return vfac * V0[idx];
-        else return (R)vfac * V0f[idx];
-    };
+    const float2* V0f = a.V0f + (size_t)b * NP;
+    const float fh = (float)vfac, fl = (float)(vfac - (double)fh);
     const R scale = (R)1 / (R)N1;
 
     if (a.mode == MODE_INIT) {
-        // T2 = F1 (V u0), then T1 = F1 u0 (u0 is parked in u^'s slot).
-        const double2* u0 = a.uhat + (size_t)b * NP;
+        // T2 = F1 (V u0), then T1 = F1 u0 (u0 is parked as raw FP64 pairs in the state slot).
+        const double2* u0 = reinterpret_cast<const double2*>(a.uhat) + (size_t)b * NP;
         C* T1 = reinterpret_cast<C*>(a.aux) + (size_t)b * NP;
         C* T2 = reinterpret_cast<C*>(a.aux2) + (size_t)b * NP;
 #pragma unroll 1
@@ -95,10 +160,10 @@ __global__ void __launch_bounds__(T2D) k_row_mid(const KArgs a) {
                 const int lane = item / N1, j1 = item % N1;
                 const size_t idx = (size_t)(r0 + lane) * N1 + j1;
                 const C u = cvt<C>(u0[idx]);
-                buf[j1 * LS + lane] = pass == 0 ? cscale(u, Vat(idx)) : u;
+                buf[j1 * LS + lane] = pass == 0 ? cscale(u, (R)(vfac * V0[idx])) : u;
             }
             __syncthreads();
-            fft_smem<C, N1, L, LS, T2D, false>(buf, tw);
+            FW::run(buf, tw, twl);
             C* dst = pass == 0 ? T2 : T1;
             for (int item = threadIdx.x; item < N1 * L; item += T2D) {
                 const int lane = item / N1, k1 = item % N1;
@@ -115,7 +180,7 @@ __global__ void __launch_bounds__(T2D) k_row_mid(const KArgs a) {
         buf[k1 * LS + lane] = T1[(size_t)(r0 + lane) * N1 + k1];
     }
     __syncthreads();
-    fft_smem<C, N1, L, LS, T2D, true>(buf, tw);
+    FI::run(buf, tw, twl);
 
     if (a.mode == MODE_READ) {
         double2* out = a.aux2 + (size_t)b * NP;
@@ -130,10 +195,19 @@ __global__ void __launch_bounds__(T2D) k_row_mid(const KArgs a) {
     for (int item = threadIdx.x; item < N1 * L; item += T2D) {
         const int lane = item / N1, j1 = item % N1;
         const size_t idx = (size_t)(r0 + lane) * N1 + j1;
-        buf[j1 * LS + lane] = implicit_solve_times_V(buf[j1 * LS + lane], Vat(idx), hmu0);
+        R vh, vl;
+        if constexpr (F64) {
+            vh = vfac * V0[idx];
+            vl = 0.0;
+        } else {
+            const float2 v2 = V0f[idx];
+            vh = fh * v2.x;
+            vl = fmaf(fh, v2.x, -vh) + fmaf(fh, v2.y, fl * v2.x);
+        }
+        buf[j1 * LS + lane] = implicit_solve_times_V(buf[j1 * LS + lane], vh, vl, hmu0);
     }
     __syncthreads();
-    fft_smem<C, N1, L, LS, T2D, false>(buf, tw);
+    FW::run(buf, tw, twl);
     C* T2 = reinterpret_cast<C*>(a.aux2) + (size_t)b * NP;
     for (int item = threadIdx.x; item < N1 * L; item += T2D) {
         const int lane = item / N1, k1 = item % N1;
@@ -141,51 +215,67 @@ __global__ void __launch_bounds__(T2D) k_row_mid(const KArgs a) {
     }
 }
 
-// ------------------------------------------------------------------ col_end
-template <class C, class RT, int N0>
-__global__ void __launch_bounds__(T2D) k_col_end(const KArgs a) {
+// ------------------------------------------------------ col_end / col_fused
+template <class C, class RT, int N0, bool FUSED>
+__global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_end(const KArgs a) {
     constexpr int L = LANES2D;
+    using FW = CtaFft<C, N0, L, L, T2D, false>;
+    using FI = CtaFft<C, N0, L, L, T2D, true>;
     using R = typename cx_traits<C>::real;
+    using ST = state_t<RT>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int b = blockIdx.y;
     const int c0 = blockIdx.x * L;
     const int n1 = a.n1;
     const size_t NP = (size_t)N0 * n1;
-    double2* uh = a.uhat + (size_t)b * NP;
+    ST* st = reinterpret_cast<ST*>(a.uhat) + (size_t)b * NP;
     RT* ringb = reinterpret_cast<RT*>(a.ring) + (size_t)b * a.ring_slots * NP;
     const C* tw;
-    if constexpr (is_f64<C>::value) tw = a.tw64_0; else tw = a.tw32_0;
+    const C* twl;
+    if constexpr (is_f64<C>::value) { tw = a.tw64_0; twl = tw; } else { tw = a.tw32_0; twl = a.tw32lo_0; }
     const R scale = (R)1 / (R)N0;
-    const C* T2 = reinterpret_cast<const C*>(a.aux2) + (size_t)b * NP;
 
-    for (int item = threadIdx.x; item < N0 * L; item += T2D) {
-        const int lane = item % L, i0 = item / L;
-        buf[i0 * L + lane] = T2[(size_t)i0 * n1 + c0 + lane];
-    }
-    __syncthreads();
-    fft_smem<C, N0, L, L, T2D, false>(buf, tw);
-    const bool step = (a.mode == MODE_STEP);
-    const double hmu0 = a.h * a.mu[0];
-    for (int item = threadIdx.x; item < N0 * L; item += T2D) {
-        const int lane = item % L, m0 = item / L;
-        const size_t idx = (size_t)m0 * n1 + c0 + lane;
-        const RT r = cvt<RT>(cscale(buf[m0 * L + lane], scale));
-        ringb[(size_t)a.out_slot * NP + idx] = r;
-        if (step) uh[idx] = mode_update(uh[idx], cvt<double2>(r), hmu0);
-    }
-    if (a.mode == MODE_INIT) {
-        __syncthreads();
-        const C* T1 = reinterpret_cast<const C*>(a.aux) + (size_t)b * NP;
+    auto load_tile = [&](const C* src) {
         for (int item = threadIdx.x; item < N0 * L; item += T2D) {
             const int lane = item % L, i0 = item / L;
-            buf[i0 * L + lane] = T1[(size_t)i0 * n1 + c0 + lane];
+            buf[i0 * L + lane] = src[(size_t)i0 * n1 + c0 + lane];
         }
         __syncthreads();
-        fft_smem<C, N0, L, L, T2D, false>(buf, tw);
+        FW::run(buf, tw, twl);
+    };
+    load_tile(reinterpret_cast<const C*>(a.aux2) + (size_t)b * NP);
+
+    if (a.mode == MODE_INIT) {
         for (int item = threadIdx.x; item < N0 * L; item += T2D) {
             const int lane = item % L, m0 = item / L;
-            uh[(size_t)m0 * n1 + c0 + lane] = cvt<double2>(cscale(buf[m0 * L + lane], scale));
+            ringb[(size_t)a.out_slot * NP + (size_t)m0 * n1 + c0 + lane] = cvt<RT>(cscale(buf[m0 * L + lane], scale));
+        }
+        __syncthreads();
+        load_tile(reinterpret_cast<const C*>(a.aux) + (size_t)b * NP);
+        for (int item = threadIdx.x; item < N0 * L; item += T2D) {
+            const int lane = item % L, m0 = item / L;
+            st[(size_t)m0 * n1 + c0 + lane] = d_to_st<ST>(cvt<double2>(cscale(buf[m0 * L + lane], scale)));
+        }
+        return;
+    }
+
+    const bool step = (a.mode == MODE_STEP);
+#pragma unroll 1
+    for (int item = threadIdx.x; item < N0 * L; item += T2D) {
+        const int lane = item % L, m0 = item / L;
+        const int m1 = c0 + lane;
+        const size_t idx = (size_t)m0 * n1 + m1;
+        end_elem<C, RT>(a, step, b, st, ringb, NP, idx, m0, m1, cscale(buf[m0 * L + lane], scale), a.e_step);
+        if constexpr (FUSED) buf[m0 * L + lane] = begin_elem<C, RT>(a, true, b, st, ringb, NP, idx, m0, m1, a.e_next);
+    }
+    if constexpr (FUSED) {
+        __syncthreads();
+        FI::run(buf, tw, twl);
+        C* T1 = reinterpret_cast<C*>(a.aux) + (size_t)b * NP;
+        for (int item = threadIdx.x; item < N0 * L; item += T2D) {
+            const int lane = item % L, i0 = item / L;
+            T1[(size_t)i0 * n1 + c0 + lane] = buf[i0 * L + lane];
         }
     }
 }
@@ -195,6 +285,8 @@ template <class K>
 static cudaError_t set_smem(K kern, size_t smem, bool& done) {
     if (done) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e == cudaSuccess) done = true;
     return e;
 }
@@ -209,13 +301,13 @@ static cudaError_t col_begin_n(const KArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <class C, class RT, int N0>
+template <class C, class RT, int N0, bool FUSED>
 static cudaError_t col_end_n(const KArgs& a, cudaStream_t s) {
     const size_t smem = (size_t)N0 * LANES2D * sizeof(C);
     static bool done = false;
-    cudaError_t e = set_smem(k_col_end<C, RT, N0>, smem, done);
+    cudaError_t e = set_smem(k_col_end<C, RT, N0, FUSED>, smem, done);
     if (e != cudaSuccess) return e;
-    k_col_end<C, RT, N0><<<dim3(a.n1 / LANES2D, a.B), T2D, smem, s>>>(a);
+    k_col_end<C, RT, N0, FUSED><<<dim3(a.n1 / LANES2D, a.B), T2D, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -229,22 +321,27 @@ static cudaError_t row_mid_n(const KArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-#define TDSE_SWITCH_N(n, FN, ...)                   \
-    switch (n) {                                    \
-        case 8: return FN<__VA_ARGS__, 8>(a, s);    \
-        case 16: return FN<__VA_ARGS__, 16>(a, s);  \
-        case 32: return FN<__VA_ARGS__, 32>(a, s);  \
-        case 64: return FN<__VA_ARGS__, 64>(a, s);  \
-        case 128: return FN<__VA_ARGS__, 128>(a, s); \
-        case 256: return FN<__VA_ARGS__, 256>(a, s); \
-        case 512: return FN<__VA_ARGS__, 512>(a, s); \
-        case 1024: return FN<__VA_ARGS__, 1024>(a, s); \
-        default: return cudaErrorInvalidValue;      \
+#define TDSE_SWITCH_N(n, ...)                                \
+    switch (n) {                                             \
+        case 8: return __VA_ARGS__(8)(a, s);                 \
+        case 16: return __VA_ARGS__(16)(a, s);               \
+        case 32: return __VA_ARGS__(32)(a, s);               \
+        case 64: return __VA_ARGS__(64)(a, s);               \
+        case 128: return __VA_ARGS__(128)(a, s);             \
+        case 256: return __VA_ARGS__(256)(a, s);             \
+        case 512: return __VA_ARGS__(512)(a, s);             \
+        case 1024: return __VA_ARGS__(1024)(a, s);           \
+        default: return cudaErrorInvalidValue;               \
     }
+#define TDSE_CB(n) col_begin_n<C, RT, n>
+#define TDSE_CE(n) col_end_n<C, RT, n, false>
+#define TDSE_CF(n) col_end_n<C, RT, n, true>
+#define TDSE_RM(n) row_mid_n<C, n>
 
-template <class C, class RT> static cudaError_t col_begin(const KArgs& a, cudaStream_t s) { TDSE_SWITCH_N(a.n0, col_begin_n, C, RT) }
-template <class C, class RT> static cudaError_t col_end(const KArgs& a, cudaStream_t s) { TDSE_SWITCH_N(a.n0, col_end_n, C, RT) }
-template <class C> static cudaError_t row_mid(const KArgs& a, cudaStream_t s) { TDSE_SWITCH_N(a.n1, row_mid_n, C) }
+template <class C, class RT> static cudaError_t col_begin(const KArgs& a, cudaStream_t s) { TDSE_SWITCH_N(a.n0, TDSE_CB) }
+template <class C, class RT> static cudaError_t col_end(const KArgs& a, cudaStream_t s) { TDSE_SWITCH_N(a.n0, TDSE_CE) }
+template <class C, class RT> static cudaError_t col_fused(const KArgs& a, cudaStream_t s) { TDSE_SWITCH_N(a.n0, TDSE_CF) }
+template <class C> static cudaError_t row_mid(const KArgs& a, cudaStream_t s) { TDSE_SWITCH_N(a.n1, TDSE_RM) }
 
 template <class C, class RT>
 static cudaError_t run2d(const KArgs& a, cudaStream_t s) {
@@ -266,6 +363,17 @@ static cudaError_t run2d(const KArgs& a, cudaStream_t s) {
     }
 }
 
+template <class C, class RT>
+static cudaError_t part2d(const KArgs& a, int part, cudaStream_t s) {
+    switch (part) {
+        case PART_COL_BEGIN: return col_begin<C, RT>(a, s);
+        case PART_ROW_MID: return row_mid<C>(a, s);
+        case PART_COL_END: return col_end<C, RT>(a, s);
+        case PART_COL_FUSED: return col_fused<C, RT>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 bool periodic2d_supported(int n0, int n1) {
     auto ok = [](int n) { return n >= 8 && n <= 1024 && (n & (n - 1)) == 0; };
     return ok(n0) && ok(n1);
@@ -277,6 +385,16 @@ cudaError_t launch_periodic2d(const KArgs& a, int combo, cudaStream_t s) {
         case COMBO_F64: return run2d<double2, double2>(a, s);
         case COMBO_F32: return run2d<float2, float2>(a, s);
         case COMBO_F64_R32: return run2d<double2, float2>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_periodic2d_part(const KArgs& a, int combo, int part, cudaStream_t s) {
+    if (!periodic2d_supported(a.n0, a.n1)) return cudaErrorInvalidValue;
+    switch (combo) {
+        case COMBO_F64: return part2d<double2, double2>(a, part, s);
+        case COMBO_F32: return part2d<float2, float2>(a, part, s);
+        case COMBO_F64_R32: return part2d<double2, float2>(a, part, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,34 +1,47 @@
-// Device tables for the periodic scheme, built once per problem in FP64.
+// Device tables for the periodic scheme, computed in FP64 once per problem.
 //
-//  * twiddles  tw[m] = e^{-2 pi i m / n}                      (FFT passes)
-//  * 1D kinetic factors  kin[c][m] = e^{-i k^2 h_c}, h_c = dt / 2^c, for the
-//    step sizes of the Richardson chains (Sec. 2.2) and the Adams step;
-//  * 1D advective factors per phase interval [t_a, t_b]:
-//        e^{i k (phi(t_b) - phi(t_a))} = hi[m >> lb] * lo[m & (nl - 1)]
-//    with k = m - n [m >= n/2] split as (m_hi nl - n [m_hi nl >= n/2]) + m_lo;
-//  * 2D separable one-step phases per interval and axis d:
-//        q_d[m] = e^{-i k_d^2 h + i k_d (phi_d(t_b) - phi_d(t_a))},
-//    so that exp(-i |k|^2 h + i k.(phi(t_b) - phi(t_a))) = q_0[m0] q_1[m1]
-//    (the one-step spectral Green's function of eq. uhatkrecur).
-// Every table is computed in FP64 (argument reduction of the large angles
-// k^2 h in double precision) and also stored rounded to FP32 for the
-// mixed-precision history sum.
-#include "kargs.h"
+//  * twiddles  tw[m] = e^{-2 pi i m / n}                              (FFT passes)
+//  * one-step (relative) phases of eq. uhatkrecur, lab-frame form:
+//      1D: kin[c][m] = e^{-i k^2 h_c}, h_c = dt / 2^c, and per interval
+//          [t_a, t_b] e^{i k (phi(t_b) - phi(t_a))} = adv[m >> lb] adv[nh + (m & (nl-1))],
+//          k = m - n [m >= n/2] split as (m_hi nl - n [m_hi nl >= n/2]) + m_lo;
+//      2D: q_d[m] = e^{-i k_d^2 h + i k_d (phi_d(t_b) - phi_d(t_a))} per interval/axis;
+//    stored as FP64 (FP64 mode) or double-float (mixed start-up);
+//  * absolute phases for the interaction picture, E_n = e^{-i |k|^2 t_n + i k.phi(t_n)}:
+//      2D: separable per axis, e_d[n][m];  1D: kinetic part split over n as
+//      e^{-i k^2 n dt} = khi[n / 32][m] klo[n % 32][m], advective part as above;
+//    arguments reduced in FP64, values rounded once to FP32.  Each step's E_n
+//    also carries a global phase e^{i theta_n} (theta_n = 2 pi frac(n g), g the
+//    golden ratio): a global phase commutes with the linear step operator and
+//    cancels between E_n (applied before the inverse transform) and conj(E_n)
+//    (applied after the forward transform), so the arithmetic is unchanged,
+//    but the FP32 rounding errors of the transforms no longer repeat from one
+//    step to the next (the grid data changes slowly between steps, so without
+//    it those errors add up coherently, linearly in the number of steps).
+#include "step_common.cuh"
 
 namespace tdse {
 
-__device__ __forceinline__ double kmode(int m, int n) { return (double)(m < n / 2 ? m : m - n); }
+__device__ __forceinline__ double dither_angle(int n) {
+    const double g = 0.61803398874989484820;
+    const double f = (double)n * g;
+    return 6.28318530717958647692 * (f - floor(f));
+}
 
-__global__ void k_twiddles(double2* tw64, float2* tw32, int n) {
+__device__ __forceinline__ float4 ff_from_cs(double c, double s) { return d_to_ffc(make_double2(c, s)); }
+
+__global__ void k_twiddles(double2* tw64, float2* tw32, float2* tw32lo, int n) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n) return;
     double s, c;
     sincospi(-2.0 * (double)m / (double)n, &s, &c);
     tw64[m] = make_double2(c, s);
-    tw32[m] = make_float2((float)c, (float)s);
+    const float ch = (float)c, sh = (float)s;
+    tw32[m] = make_float2(ch, sh);
+    tw32lo[m] = make_float2((float)(c - (double)ch), (float)(s - (double)sh));
 }
 
-__global__ void k_kin1d(double2* kin64, float2* kin32, int n, int L, double dt) {
+__global__ void k_kin1d(double2* kin64, float4* kinff, int n, int L, double dt) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     int c = blockIdx.y;
     if (m >= n || c >= L) return;
@@ -36,71 +49,111 @@ __global__ void k_kin1d(double2* kin64, float2* kin32, int n, int L, double dt) 
     const double h = dt / (double)(1 << c);
     double s, co;
     sincos(-(k * k) * h, &s, &co);
-    kin64[(size_t)c * n + m] = make_double2(co, s);
-    kin32[(size_t)c * n + m] = make_float2((float)co, (float)s);
+    if (kin64) kin64[(size_t)c * n + m] = make_double2(co, s);
+    if (kinff) kinff[(size_t)c * n + m] = ff_from_cs(co, s);
 }
 
-__global__ void k_adv1d(double2* adv64, float2* adv32, const int2* iv, int n_int, const double* phi,
-                        int ntf, int n, int nh, int nl) {
+__device__ __forceinline__ double split_k(int t, int n, int nh, int nl) {
+    if (t < nh) {
+        const int mh = t * nl;
+        return (double)(mh >= n / 2 ? mh - n : mh);
+    }
+    return (double)(t - nh);
+}
+
+__global__ void k_adv1d(double2* adv64, float4* advff, const int2* iv, int n_int, const double* phi, int ntf, int n,
+                        int nh, int nl) {
     const int i = blockIdx.x;
-    const int b = blockIdx.y;
     const int2 ab = iv[i];
-    const double dphi = phi[(size_t)b * ntf + ab.y] - phi[(size_t)b * ntf + ab.x];
-    const size_t base = ((size_t)b * n_int + i) * (size_t)(nh + nl);
+    const double dphi = phi[ab.y] - phi[ab.x];
+    const size_t base = (size_t)i * (size_t)(nh + nl);
     for (int t = threadIdx.x; t < nh + nl; t += blockDim.x) {
-        double k;
-        if (t < nh) {
-            const int mh = t * nl;
-            k = (double)(mh >= n / 2 ? mh - n : mh);
-        } else {
-            k = (double)(t - nh);
-        }
         double s, c;
-        sincos(k * dphi, &s, &c);
-        adv64[base + t] = make_double2(c, s);
-        adv32[base + t] = make_float2((float)c, (float)s);
+        sincos(split_k(t, n, nh, nl) * dphi, &s, &c);
+        if (adv64) adv64[base + t] = make_double2(c, s);
+        if (advff) advff[base + t] = ff_from_cs(c, s);
     }
 }
 
-__global__ void k_q2d(double2* q64, float2* q32, const int2* iv, int n_int, const double* phi, int ntf,
-                      int n0, int n1, double dt) {
+__global__ void k_q2d(double2* q64, float4* qff, const int2* iv, int n_int, const double* phi, int ntf, int n0,
+                      int n1, double dt) {
     const int i = blockIdx.x;
-    const int b = blockIdx.y;
     const int2 ab = iv[i];
     const double h = (double)(ab.y - ab.x) * (dt * 0.125);
-    const double* ph0 = phi + (size_t)b * 2 * ntf;
-    const double* ph1 = ph0 + ntf;
-    const double d0 = ph0[ab.y] - ph0[ab.x];
+    const double* ph1 = phi + ntf;
+    const double d0 = phi[ab.y] - phi[ab.x];
     const double d1 = ph1[ab.y] - ph1[ab.x];
-    const size_t base = ((size_t)b * n_int + i) * (size_t)(n0 + n1);
+    const size_t base = (size_t)i * (size_t)(n0 + n1);
     for (int t = threadIdx.x; t < n0 + n1; t += blockDim.x) {
         const bool ax0 = t < n0;
         const int m = ax0 ? t : t - n0;
         const double k = kmode(m, ax0 ? n0 : n1);
-        const double arg = -(k * k) * h + k * (ax0 ? d0 : d1);
         double s, c;
-        sincos(arg, &s, &c);
-        q64[base + t] = make_double2(c, s);
-        q32[base + t] = make_float2((float)c, (float)s);
+        sincos(-(k * k) * h + k * (ax0 ? d0 : d1), &s, &c);
+        if (q64) q64[base + t] = make_double2(c, s);
+        if (qff) qff[base + t] = ff_from_cs(c, s);
     }
 }
 
-__global__ void k_to_float(float* dst, const double* src, size_t n) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = (float)src[i];
+__global__ void k_e2d(float2* e, const double* phi, int ntf, int n0, int n1, double dt) {
+    const int n = blockIdx.x;
+    const double t = (double)n * dt;
+    const double p0 = phi[8 * (size_t)n], p1 = phi[ntf + 8 * (size_t)n];
+    const double th = dither_angle(n);
+    const size_t base = (size_t)n * (size_t)(n0 + n1);
+    for (int j = threadIdx.x; j < n0 + n1; j += blockDim.x) {
+        const bool ax0 = j < n0;
+        const double k = kmode(ax0 ? j : j - n0, ax0 ? n0 : n1);
+        double s, c;
+        sincos(-(k * k) * t + k * (ax0 ? p0 : p1) + (ax0 ? th : 0.0), &s, &c);
+        e[base + j] = make_float2((float)c, (float)s);
+    }
+}
+
+__global__ void k_k1d(float2* klo, float2* khi, int nhi, int n, double dt) {
+    const int r = blockIdx.y;                      // rows 0..31: klo; 32..: khi
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const double k = kmode(m, n);
+    // k^2 * steps is an exact integer below 2^53 for every supported size
+    const double steps = r < E1D_NLO ? (double)r : (double)(r - E1D_NLO) * E1D_NLO;
+    double s, c;
+    sincos(-(k * k * steps) * dt, &s, &c);
+    if (r < E1D_NLO) klo[(size_t)r * n + m] = make_float2((float)c, (float)s);
+    else if (r - E1D_NLO < nhi) khi[(size_t)(r - E1D_NLO) * n + m] = make_float2((float)c, (float)s);
+}
+
+__global__ void k_a1d(float2* a1d, const double* phi, int n, int nh, int nl) {
+    const int step = blockIdx.x;
+    const double p = phi[8 * (size_t)step];
+    const double th = dither_angle(step);
+    const size_t base = (size_t)step * (size_t)(nh + nl);
+    for (int t = threadIdx.x; t < nh + nl; t += blockDim.x) {
+        double s, c;
+        sincos(split_k(t, n, nh, nl) * p + (t < nh ? th : 0.0), &s, &c);
+        a1d[base + t] = make_float2((float)c, (float)s);
+    }
+}
+
+__global__ void k_split_float(float2* hilo, const double* src, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float h = (float)src[i];
+        hilo[i] = make_float2(h, (float)(src[i] - (double)h));
+    }
 }
 
 struct Coef4 { double c[4]; };
 
-__global__ void k_combine(double2* uhat, const double2* chains, size_t stride, int L, Coef4 co, size_t n) {
+template <class ST>
+__global__ void k_combine(ST* state, const ST* chains, size_t stride, int L, Coef4 co, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         double re = 0.0, im = 0.0;
         for (int c = 0; c < L; ++c) {
-            const double2 v = chains[c * stride + i];
+            const double2 v = st_to_d(chains[c * stride + i]);
             re = fma(co.c[c], v.x, re);
             im = fma(co.c[c], v.y, im);
         }
-        uhat[i] = make_double2(re, im);
+        state[i] = d_to_st<ST>(make_double2(re, im));
     }
 }
 
@@ -113,11 +166,48 @@ __global__ void k_copy_slot(char* dst, const char* ring, int ring_slots, int slo
         reinterpret_cast<int4*>(d)[i] = reinterpret_cast<const int4*>(src)[i];
 }
 
-__global__ void k_count_nonfinite(const double* x, size_t n, int* count) {
+__global__ void k_count_nonfinite(const double* x, size_t nwords, bool ff, int* count) {
     int local = 0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        local += isfinite(x[i]) ? 0 : 1;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nwords; i += (size_t)gridDim.x * blockDim.x) {
+        if (ff) {
+            const float2 f = reinterpret_cast<const float2*>(x)[i];
+            local += (isfinite(f.x) && isfinite(f.y)) ? 0 : 1;
+        } else {
+            local += isfinite(x[i]) ? 0 : 1;
+        }
+    }
     if (local) atomicAdd(count, local);
+}
+
+struct Steps8 { int s[8]; float z[8][2]; };
+
+// state (double-float, lab frame at step n) -> v^ = conj(E_n) u^, and ring slot
+// q (FP32, lab frame at step steps.s[q]) -> r~ = z_q conj(E) R; E in FP64.
+__global__ void k_to_interaction(float4* state, float2* ring, int ring_slots, const double* phi, int ntf, int d,
+                                 int n0, int n1, double dt, int n, Steps8 steps, int nslots) {
+    const int b = blockIdx.y;
+    const size_t NP = (size_t)n0 * n1;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < NP; idx += (size_t)gridDim.x * blockDim.x) {
+        const int m0 = (int)(idx / n1), m1 = (int)(idx % n1);
+        const double k0 = kmode(m0, n0), k1 = d == 2 ? kmode(m1, n1) : 0.0;
+        const double* ph = phi + (size_t)b * d * ntf;
+        auto E = [&](int step) {
+            double arg = -(k0 * k0 + k1 * k1) * ((double)step * dt) + k0 * ph[8 * (size_t)step];
+            if (d == 2) arg += k1 * ph[ntf + 8 * (size_t)step];
+            double s, c;
+            sincos(arg, &s, &c);
+            return make_double2(c, -s);     // conj(E)
+        };
+        float4* sv = state + (size_t)b * NP + idx;
+        *sv = d_to_ffc(cmul(E(n), ffc_to_d(*sv)));
+        for (int q = 0; q < nslots; ++q) {
+            if (steps.s[q] < 0) continue;
+            float2* r = ring + ((size_t)b * ring_slots + q) * NP + idx;
+            const double2 zq = make_double2(steps.z[q][0], steps.z[q][1]);
+            const double2 v = cmul(zq, cmul(E(steps.s[q]), make_double2(r->x, r->y)));
+            *r = make_float2((float)v.x, (float)v.y);
+        }
+    }
 }
 
 static int grid_for(size_t n, int threads) {
@@ -126,38 +216,61 @@ static int grid_for(size_t n, int threads) {
     return (int)(g ? g : 1);
 }
 
-cudaError_t launch_twiddles(double2* tw64, float2* tw32, int n, cudaStream_t s) {
-    k_twiddles<<<(n + 255) / 256, 256, 0, s>>>(tw64, tw32, n);
+cudaError_t launch_twiddles(double2* tw64, float2* tw32, float2* tw32lo, int n, cudaStream_t s) {
+    k_twiddles<<<(n + 255) / 256, 256, 0, s>>>(tw64, tw32, tw32lo, n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_kin1d(double2* kin64, float2* kin32, int n, int L, double dt, cudaStream_t s) {
-    k_kin1d<<<dim3((n + 255) / 256, L), 256, 0, s>>>(kin64, kin32, n, L, dt);
+cudaError_t launch_kin1d(double2* kin64, float4* kinff, int n, int L, double dt, cudaStream_t s) {
+    k_kin1d<<<dim3((n + 255) / 256, L), 256, 0, s>>>(kin64, kinff, n, L, dt);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adv1d(double2* adv64, float2* adv32, const int2* intervals, int n_int, const double* phi,
-                         int ntf, int B, int n, int nh, int nl, cudaStream_t s) {
-    k_adv1d<<<dim3(n_int, B), 128, 0, s>>>(adv64, adv32, intervals, n_int, phi, ntf, n, nh, nl);
+cudaError_t launch_adv1d(double2* adv64, float4* advff, const int2* intervals, int n_int, const double* phi, int ntf,
+                         int n, int nh, int nl, cudaStream_t s) {
+    if (n_int <= 0) return cudaSuccess;
+    k_adv1d<<<n_int, 128, 0, s>>>(adv64, advff, intervals, n_int, phi, ntf, n, nh, nl);
     return cudaGetLastError();
 }
 
-cudaError_t launch_q2d(double2* q64, float2* q32, const int2* intervals, int n_int, const double* phi, int ntf,
-                       int B, int n0, int n1, double dt, cudaStream_t s) {
-    k_q2d<<<dim3(n_int, B), 256, 0, s>>>(q64, q32, intervals, n_int, phi, ntf, n0, n1, dt);
+cudaError_t launch_q2d(double2* q64, float4* qff, const int2* intervals, int n_int, const double* phi, int ntf,
+                       int n0, int n1, double dt, cudaStream_t s) {
+    if (n_int <= 0) return cudaSuccess;
+    k_q2d<<<n_int, 256, 0, s>>>(q64, qff, intervals, n_int, phi, ntf, n0, n1, dt);
     return cudaGetLastError();
 }
 
-cudaError_t launch_to_float(float* dst, const double* src, size_t n, cudaStream_t s) {
-    k_to_float<<<grid_for(n, 256), 256, 0, s>>>(dst, src, n);
+cudaError_t launch_e2d(float2* e, const double* phi, int ntf, int nsteps, int n0, int n1, double dt, cudaStream_t s) {
+    k_e2d<<<nsteps + 1, 256, 0, s>>>(e, phi, ntf, n0, n1, dt);
     return cudaGetLastError();
 }
 
-cudaError_t launch_combine(double2* uhat, const double2* chains, size_t chain_stride, int L, const double* coef,
-                           size_t n, cudaStream_t s) {
+cudaError_t launch_k1d(float2* klo, float2* khi, int nhi, int n, double dt, cudaStream_t s) {
+    k_k1d<<<dim3((n + 255) / 256, E1D_NLO + nhi), 256, 0, s>>>(klo, khi, nhi, n, dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_a1d(float2* a1d, const double* phi, int ntf, int nsteps, int n, int nh, int nl, cudaStream_t s) {
+    (void)ntf;
+    k_a1d<<<nsteps + 1, 128, 0, s>>>(a1d, phi, n, nh, nl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_float(float2* hilo, const double* src, size_t n, cudaStream_t s) {
+    k_split_float<<<grid_for(n, 256), 256, 0, s>>>(hilo, src, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(void* state, const void* chains, size_t chain_stride, int L, const double* coef,
+                           size_t n, bool ff, cudaStream_t s) {
     Coef4 co{};
     for (int c = 0; c < L && c < 4; ++c) co.c[c] = coef[c];
-    k_combine<<<grid_for(n, 256), 256, 0, s>>>(uhat, chains, chain_stride, L, co, n);
+    if (ff)
+        k_combine<float4><<<grid_for(n, 256), 256, 0, s>>>((float4*)state, (const float4*)chains, chain_stride, L,
+                                                              co, n);
+    else
+        k_combine<double2><<<grid_for(n, 256), 256, 0, s>>>((double2*)state, (const double2*)chains, chain_stride,
+                                                               L, co, n);
     return cudaGetLastError();
 }
 
@@ -166,13 +279,29 @@ cudaError_t launch_copy_slot(void* dst, const void* ring, int ring_slots, int sl
     const size_t bytes = NP * elem_bytes;   // multiple of 16 (NP >= 8, elem 8 or 16)
     size_t gx = (bytes / 16 + 255) / 256;
     if (gx > 64) gx = 64;
-    k_copy_slot<<<dim3((unsigned)gx, B), 256, 0, s>>>(
-        (char*)dst, (const char*)ring, ring_slots, slot, bytes);
+    k_copy_slot<<<dim3((unsigned)gx, B), 256, 0, s>>>((char*)dst, (const char*)ring, ring_slots, slot, bytes);
     return cudaGetLastError();
 }
 
-cudaError_t launch_count_nonfinite(const double* x, size_t n, int* count, cudaStream_t s) {
-    k_count_nonfinite<<<grid_for(n, 256), 256, 0, s>>>(x, n, count);
+cudaError_t launch_count_nonfinite(const void* x, size_t nwords, bool ff, int* count, cudaStream_t s) {
+    k_count_nonfinite<<<grid_for(nwords, 256), 256, 0, s>>>((const double*)x, nwords, ff, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_interaction(const KArgs& a, int n, const int* slot_steps, const float* slot_z, int nslots,
+                                  cudaStream_t s) {
+    Steps8 st{};
+    for (int q = 0; q < 8; ++q) {
+        st.s[q] = q < nslots ? slot_steps[q] : -1;
+        st.z[q][0] = q < nslots ? slot_z[2 * q] : 1.f;
+        st.z[q][1] = q < nslots ? slot_z[2 * q + 1] : 0.f;
+    }
+    const size_t NP = (size_t)a.n0 * a.n1;
+    size_t gx = (NP + 255) / 256;
+    if (gx > 1024) gx = 1024;
+    k_to_interaction<<<dim3((unsigned)gx, a.B), 256, 0, s>>>((float4*)a.uhat, (float2*)a.ring, a.ring_slots, a.phi,
+                                                              a.ntf, a.n1 > 1 ? 2 : 1, a.n0, a.n1, a.dt, n, st,
+                                                              nslots);
     return cudaGetLastError();
 }
 
