@@ -66,11 +66,14 @@ enum { TDSE_FP64 = 0, TDSE_MIXED = 1 };
 enum { TDSE_HOST = 0, TDSE_DEVICE = 1 };
 
 /*
- * Problem configuration (Sec. 2 periodic scheme).
+ * Problem configuration.
  *   dim        1 or 2.
- *   bc         TDSE_PERIODIC (domain [-pi,pi]^dim).
- *   n[2]       grid points per dimension (powers of two; 1D: 8..8192,
- *              2D: 8..1024 per dimension).  n[1] is ignored for dim = 1.
+ *   bc         TDSE_PERIODIC: domain [-pi,pi]^dim, Fourier modes (Sec. 2).
+ *              TDSE_FREE: free space, data supported in [-1,1]^dim, modes on
+ *              the deformed contour Gamma (Sec. 3-4).
+ *   n[2]       grid points per dimension (powers of two; periodic 1D: 8..8192,
+ *              periodic 2D: 8..1024 per dimension; free space: 32..512).
+ *              n[1] is ignored for dim = 1.
  *   batch      number of independent instances that share n, dt, nsteps,
  *              order and precision; each has its own V, A and u0.  >= 1.
  *   dt         time step.
@@ -81,7 +84,20 @@ enum { TDSE_HOST = 0, TDSE_DEVICE = 1 };
  *   precision  TDSE_FP64: every stage in complex FP64.
  *              TDSE_MIXED: transforms, pointwise product and history sum in
  *              complex FP32; the mode state u^ and its phase recurrence, the
- *              phase tables and the Adams weights in FP64.
+ *              phase tables and the Adams weights in FP64 (periodic only).
+ * Free space only (ignored for TDSE_PERIODIC), Sec. 3.4 and 4.1:
+ *   nu[2]      length of the equispaced FFTs per dimension: nu = R n with
+ *              R in {4, 8, 16} and nu <= 4096.  The equispaced blocks then
+ *              have NE = nu/2 - 2 kappa + 1 nodes at spacing h = pi n / nu.
+ *   alpert_p   order of Alpert's endpoint correction: 8 (kappa = 7) or 4
+ *              (kappa = 4).
+ *   gauss_q    Gauss-Legendre points per panel of Gamma_2, 1..32.
+ *   n_r        dyadic refinement levels of the Gamma_2 panels toward 0, 0..4
+ *              (0: a single panel on [-H, H]; else 2 n_r panels).
+ *   H          contour offset, > 0 (tdse_free_choose_H gives the paper's
+ *              choice); truncation K = H + pi n / 2.
+ * Mode count per dimension N = 2 NE + 2 p + gauss_q * max(1, 2 n_r) (at most
+ * 2 NE + 128 dense modes).
  */
 typedef struct {
     int dim;
@@ -93,6 +109,12 @@ typedef struct {
     int order;
     int startup_steps;
     int precision;
+    /* free space only */
+    int nu[2];
+    int alpert_p;
+    int gauss_q;
+    int n_r;
+    double H;
 } tdse_config;
 
 /* Vector potential callback: writes A(t) (dim components) to A_out. */
@@ -148,10 +170,35 @@ tdse_status tdse_step(tdse_ctx* ctx, int nsteps, void* stream);
 /* Step until t >= T (T rounded to the nearest multiple of dt). */
 tdse_status tdse_solve_to(tdse_ctx* ctx, double T, void* stream);
 
-/* u(x, t_current) = inverse DFT of u^ in FP64, for one instance (or -1 = all,
- * laid out [batch][n0*n1]), into u_out (interleaved complex, host or device).
+/* u(x, t_current) on the grid for one instance (or -1 = all, laid out
+ * [batch][n0*n1]), into u_out (interleaved complex FP64, host or device).
+ * Periodic: the inverse DFT of u^ in FP64.  Free space: the grid values of the
+ * last implicit solve (or the Richardson combination of the start-up, or u0
+ * before the first step), which the scheme carries alongside u^ (u is not
+ * the inverse transform of u^ outside [-1,1]^dim).
  * Host destinations are complete when the call returns. */
 tdse_status tdse_read_u(tdse_ctx* ctx, int instance, double* u_out, int where, void* stream);
+
+/* The mode state u^(t_current) of one instance (or -1 = all) into u_out
+ * (interleaved complex FP64, host or device): periodic [n0][n1] in FFT order,
+ * free space [N0][N1] in the node order of tdse_free_rule.  TDSE_FP64 only
+ * (TDSE_EUNSUPPORTED for TDSE_MIXED, whose state is held in another
+ * representation); TDSE_ESTATE before the first step. */
+tdse_status tdse_read_modes(tdse_ctx* ctx, int instance, double* u_out, int where, void* stream);
+
+/* Free space: the contour rule of dimension `axis` (Sec. 3.4): *N receives
+ * the mode count; if zeta and w are not NULL they receive the N nodes zeta_m
+ * and weights w_m (interleaved complex, host) in the block order E1 (Gamma_1,
+ * equispaced), A1 (Alpert), C (Gauss panels on Gamma_2), A3 (Alpert), E3
+ * (Gamma_3, equispaced), each in ascending real part.  TDSE_EINVAL for a
+ * periodic context or a bad axis. */
+tdse_status tdse_free_rule(const tdse_ctx* ctx, int axis, int* N, double* zeta, double* w);
+
+/* The contour offset of Remark Hchoice:
+ *   H = log(eps / ((1 + vnorm) eps_m)) / (2 dim (1 + phimax)),  eps_m = 2^-52,
+ * vnorm = max_t ||V(., t)||_2 on [-1,1]^dim, phimax = max_t |phi(t)|.
+ * TDSE_EINVAL if the result is not positive and finite. */
+tdse_status tdse_free_choose_H(double eps, double vnorm, double phimax, int dim, double* H_out);
 
 /* Scan the mode state of every instance for NaN/Inf (synchronises `stream`).
  * Returns TDSE_ENONFINITE if any is found. */

@@ -117,6 +117,8 @@ class FreeSpaceOracle:
         return g - 1j * self.mu[0] * dt * vu, u, vu
 
     def solve(self, u0: np.ndarray, nsteps: int, keep=None):
+        """March nsteps steps from u0; returns u(t_n) (and {n: u} for n in keep).
+        The final mode state u^ is left in self.last_uhat."""
         u = np.asarray(u0, dtype=np.complex128)
         uh = self.fwd(u)
         hist = {0: self.fwd(self.V(0.0) * u)}
@@ -133,4 +135,5 @@ class FreeSpaceOracle:
             hist.pop(n - self.order, None)
             if keep is not None and n in keep:
                 kept[n] = u.copy()
+        self.last_uhat = uh
         return (u, kept) if keep is not None else u

@@ -15,9 +15,9 @@ from typing import Callable, Optional, Sequence
 import numpy as np
 
 from . import _native
-from ._native import DEVICE, FP64, HOST, MIXED, PERIODIC, TdseError
+from ._native import DEVICE, FP64, FREE, HOST, MIXED, PERIODIC, TdseError
 
-__all__ = ["Problem", "TdseError", "adams_weights", "FP64", "MIXED", "PERIODIC"]
+__all__ = ["Problem", "TdseError", "adams_weights", "free_choose_H", "FP64", "MIXED", "PERIODIC", "FREE"]
 
 
 def _check(status: int, ctx=None):
@@ -34,6 +34,13 @@ def adams_weights(order: int) -> np.ndarray:
     out = np.zeros(order, dtype=np.float64)
     _check(_native.lib().tdse_adams_weights(order, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out
+
+
+def free_choose_H(eps: float, vnorm: float, phimax: float, dim: int) -> float:
+    """Contour offset H of Remark Hchoice (library formula)."""
+    out = ctypes.c_double()
+    _check(_native.lib().tdse_free_choose_H(float(eps), float(vnorm), float(phimax), int(dim), ctypes.byref(out)))
+    return out.value
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -61,16 +68,21 @@ def _as_buffer(x, dtype):
 
 
 class Problem:
-    """A batch of periodic TDSE instances sharing grid, dt, step count and order.
+    """A batch of TDSE instances sharing grid, dt, step count and order.
 
     Parameters mirror ``tdse_config``: ``shape`` (n,) or (n0, n1); ``dt``;
     ``nsteps`` (steps the tables cover); ``order`` (Adams order, even <= 8);
     ``batch``; ``precision`` ("fp64" or "mixed"); ``startup_steps`` (-1 =
-    order-1).  The device workspace is a torch uint8 tensor owned here.
+    order-1); ``bc`` ("periodic" or "free").  Free space also takes ``nu``
+    (FFT length per dimension), ``H`` (contour offset), ``alpert_p``,
+    ``gauss_q`` and ``n_r``.  The device workspace is a torch uint8 tensor
+    owned here.
     """
 
     def __init__(self, shape: Sequence[int], dt: float, nsteps: int, order: int = 8, batch: int = 1,
-                 precision: str = "fp64", startup_steps: int = -1, device=None, stream=None):
+                 precision: str = "fp64", startup_steps: int = -1, device=None, stream=None, bc: str = "periodic",
+                 nu: Optional[Sequence[int]] = None, H: float = 0.0, alpert_p: int = 8, gauss_q: int = 10,
+                 n_r: int = 1):
         import torch
         self._lib = _native.lib()
         self.shape = tuple(int(s) for s in shape)
@@ -79,7 +91,16 @@ class Problem:
         self.nsteps = int(nsteps)
         cfg = _native.TdseConfig()
         cfg.dim = len(self.shape)
-        cfg.bc = PERIODIC
+        cfg.bc = {"periodic": PERIODIC, "free": FREE}[bc]
+        self.bc = bc
+        if bc == "free":
+            nus = list(nu) if nu is not None else [8 * s for s in self.shape]
+            cfg.nu[0] = int(nus[0])
+            cfg.nu[1] = int(nus[1]) if len(nus) > 1 else 0
+            cfg.alpert_p = int(alpert_p)
+            cfg.gauss_q = int(gauss_q)
+            cfg.n_r = int(n_r)
+            cfg.H = float(H)
         cfg.n[0] = self.shape[0]
         cfg.n[1] = self.shape[1] if len(self.shape) > 1 else 1
         cfg.batch = self.batch
@@ -167,6 +188,32 @@ class Problem:
             ptr, where = ctypes.c_void_p(out.ctypes.data), HOST
         _check(self._lib.tdse_read_u(self._ctx, instance, ptr, where, _stream_handle(self._stream)), self._ctx)
         return out
+
+    def read_modes(self, instance: int = -1) -> np.ndarray:
+        """The FP64 mode state u^ (periodic: FFT order; free space: node order
+        of ``free_rule``) as numpy complex128, [batch][...] for instance -1."""
+        shape = self.mode_shape
+        out = np.empty(((self.batch,) if instance == -1 else ()) + shape, dtype=np.complex128)
+        _check(self._lib.tdse_read_modes(self._ctx, instance, ctypes.c_void_p(out.ctypes.data), HOST,
+                                         _stream_handle(self._stream)), self._ctx)
+        return out
+
+    @property
+    def mode_shape(self):
+        if self.bc != "free":
+            return self.shape
+        return tuple(self.free_rule(a)[0].size for a in range(len(self.shape)))
+
+    def free_rule(self, axis: int):
+        """(zeta, w): nodes and weights of the contour rule of `axis` (free space)."""
+        n = ctypes.c_int()
+        _check(self._lib.tdse_free_rule(self._ctx, axis, ctypes.byref(n), None, None), self._ctx)
+        z = np.empty(n.value, dtype=np.complex128)
+        w = np.empty(n.value, dtype=np.complex128)
+        dp = ctypes.POINTER(ctypes.c_double)
+        _check(self._lib.tdse_free_rule(self._ctx, axis, ctypes.byref(n), z.ctypes.data_as(dp), w.ctypes.data_as(dp)),
+               self._ctx)
+        return z, w
 
     def check_finite(self):
         _check(self._lib.tdse_check_finite(self._ctx, _stream_handle(self._stream)), self._ctx)

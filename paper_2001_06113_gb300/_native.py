@@ -23,7 +23,8 @@ EXPORTS = [
     "tdse_create", "tdse_workspace_bytes", "tdse_bind_workspace", "tdse_set_potential",
     "tdse_set_vector_potential", "tdse_set_pulse", "tdse_set_initial", "tdse_step", "tdse_solve_to",
     "tdse_read_u", "tdse_check_finite", "tdse_step_index", "tdse_time", "tdse_adams_weights",
-    "tdse_last_error", "tdse_destroy", "tdse_modes_to_grid_2d_noalloc",
+    "tdse_last_error", "tdse_destroy", "tdse_modes_to_grid_2d_noalloc", "tdse_read_modes", "tdse_free_rule",
+    "tdse_free_choose_H",
 ]
 NOALLOC_MAX_POINTS = 524288
 
@@ -39,6 +40,11 @@ class TdseConfig(ctypes.Structure):
         ("order", ctypes.c_int),
         ("startup_steps", ctypes.c_int),
         ("precision", ctypes.c_int),
+        ("nu", ctypes.c_int * 2),
+        ("alpert_p", ctypes.c_int),
+        ("gauss_q", ctypes.c_int),
+        ("n_r", ctypes.c_int),
+        ("H", ctypes.c_double),
     ]
 
 
@@ -74,6 +80,9 @@ def load(path: str = _LIB_PATH) -> ctypes.CDLL:
         "tdse_last_error": ([vp], ctypes.c_char_p),
         "tdse_destroy": ([vp], None),
         "tdse_modes_to_grid_2d_noalloc": ([vp, vp, ip, ip, ip, vp], ip),
+        "tdse_read_modes": ([vp, ip, vp, ip, vp], ip),
+        "tdse_free_rule": ([vp, ip, ctypes.POINTER(ip), dp, dp], ip),
+        "tdse_free_choose_H": ([cd, cd, cd, ip, dp], ip),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -10,15 +10,13 @@
 #include <string>
 #include <vector>
 
+#include "ctx.h"
 #include "kargs.h"
 
 using namespace tdse;
 
 namespace {
 
-constexpr int SUB = 8;   // fine time grid: t_m = m dt / 8 (Richardson sub-steps down to dt/8)
-
-size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 // Implicit Adams weights (Sec. 2.2): mu_j = int_0^1 l_j(theta) dtheta, l_j the
@@ -54,8 +52,22 @@ bool adams_weights(int n, double* mu) {
     return true;
 }
 
+struct Pulse {
+    double A0, omega, Tp, dir[2];
+};
+
+void pulse_fn(double t, double* A, void* user) {
+    const Pulse* p = static_cast<const Pulse*>(user);
+    const double s = std::sin(M_PI * t / p->Tp);
+    const double amp = p->A0 * s * s * std::sin(p->omega * t);
+    A[0] = amp * p->dir[0];
+    A[1] = amp * p->dir[1];
+}
+
+}  // namespace
+
 // q-point Gauss-Legendre nodes/weights on [-1,1] by Newton on P_q (long double).
-void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
+void tdse::gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
     x.assign(q, 0.0);
     w.assign(q, 0.0);
     const long double pi = 3.141592653589793238462643383279502884L;
@@ -85,62 +97,6 @@ void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
         w[i] = (double)(2.0L / ((1 - z * z) * dp * dp));
     }
 }
-
-struct Pulse {
-    double A0, omega, Tp, dir[2];
-};
-
-void pulse_fn(double t, double* A, void* user) {
-    const Pulse* p = static_cast<const Pulse*>(user);
-    const double s = std::sin(M_PI * t / p->Tp);
-    const double amp = p->A0 * s * s * std::sin(p->omega * t);
-    A[0] = amp * p->dir[0];
-    A[1] = amp * p->dir[1];
-}
-
-}  // namespace
-
-struct tdse_ctx {
-    tdse_config cfg{};
-    int d = 1, n0 = 0, n1 = 1;
-    size_t NP = 0;
-    int B = 1, m = 8, L = 4, S = 7, S_eff = 7, RS = 7, ntf = 0, n_int = 0, n_int_startup = 0, nhi = 1;
-    bool mixed = false;
-    bool ip = false;            // mixed mode: state and ring are in the interaction picture
-    int nh = 1, nl = 1, lb = 0;
-    size_t rsz = 16;            // ring element bytes
-    double mu[8] = {0};
-    double rich[4] = {0};
-    std::vector<int2> intervals;
-    std::vector<float> zdither;   // [nsteps + 1][2]: FP32 ring dither z_n (interaction picture)
-    // workspace
-    char* ws = nullptr;
-    size_t ws_need = 0;
-    struct {
-        size_t uhat, ring, chain_uhat, chain_ring, aux, aux2, V0, V0f, tfac, phi, kin64, kinff, adv64, advff,
-            q64, qff, e2d, k1lo, k1hi, a1d, tw64_0, tw32_0, tw64_1, tw32_1, tw32lo_0, tw32lo_1, iv, scratch, end;
-    } off{};
-    std::vector<char> have_V, have_u0;
-    int step = 0;
-    bool inited = false;
-    std::string err;
-
-    template <class T> T* P(size_t o) const { return reinterpret_cast<T*>(ws + o); }
-    tdse_status fail(tdse_status s, const std::string& msg) {
-        err = msg;
-        return s;
-    }
-};
-
-static tdse_status cuda_fail(tdse_ctx* c, cudaError_t e, const char* where) {
-    return c->fail(TDSE_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
-}
-
-#define TDSE_CK(ctx, expr)                                       \
-    do {                                                         \
-        cudaError_t e__ = (expr);                                \
-        if (e__ != cudaSuccess) return cuda_fail(ctx, e__, #expr); \
-    } while (0)
 
 static void plan_workspace(tdse_ctx* c) {
     const size_t NP = c->NP, B = c->B;
@@ -253,20 +209,8 @@ static cudaError_t run(const tdse_ctx* c, const KArgs& a, int combo, cudaStream_
     return c->d == 1 ? launch_periodic1d(a, combo, s) : launch_periodic2d(a, combo, s);
 }
 
-static int slot_of(const tdse_ctx* c, int n) { return ((n % c->RS) + c->RS) % c->RS; }
-
-// Interval ids.  Start-up step s (1..S_eff) owns ids (s-1)(2^L - 1) .. s(2^L - 1) - 1:
-// chain c, sub-step i at (s-1)(2^L - 1) + (2^c - 1) + i (chain 0 is the main
-// interval t_{s-1} -> t_s).  Main intervals of later steps n follow from
-// n_int_startup (FP64 mode only: mixed Adams steps use absolute phases).
-static int startup_interval(const tdse_ctx* c, int s, int chain, int i) {
-    return (s - 1) * ((1 << c->L) - 1) + ((1 << chain) - 1) + i;
-}
-static int main_interval(const tdse_ctx* c, int n) {
-    return n <= c->S_eff ? startup_interval(c, n, 0, 0) : c->n_int_startup + (n - c->S_eff - 1);
-}
-
 static tdse_status build_phase_tables(tdse_ctx* c, int b, cudaStream_t s) {
+    if (c->fs) return fs_build_phase_tables(c, b, s);
     const int2* iv = c->P<int2>(c->off.iv);
     const double* phi = c->P<double>(c->off.phi) + (size_t)b * c->d * c->ntf;
     const size_t nsp1 = (size_t)c->cfg.nsteps + 1;
@@ -310,8 +254,8 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     if (!cfg || !out) return TDSE_EINVAL;
     *out = nullptr;
     if (cfg->dim != 1 && cfg->dim != 2) return TDSE_EINVAL;
-    if (cfg->bc == TDSE_FREE) return TDSE_EUNSUPPORTED;
-    if (cfg->bc != TDSE_PERIODIC) return TDSE_EINVAL;
+    if (cfg->bc != TDSE_PERIODIC && cfg->bc != TDSE_FREE) return TDSE_EINVAL;
+    const bool fs = cfg->bc == TDSE_FREE;
     if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt) || cfg->nsteps < 1 || cfg->batch < 1) return TDSE_EINVAL;
     if (cfg->order < 2 || cfg->order > 8 || cfg->order % 2) return TDSE_EINVAL;
     if (cfg->precision != TDSE_FP64 && cfg->precision != TDSE_MIXED) return TDSE_EINVAL;
@@ -319,8 +263,9 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     if (S < cfg->order - 2) return TDSE_EINVAL;
     const int n0 = cfg->n[0], n1 = cfg->dim == 2 ? cfg->n[1] : 1;
     if (!is_pow2(n0) || (cfg->dim == 2 && !is_pow2(n1))) return TDSE_EINVAL;
-    if (cfg->dim == 1 && !periodic1d_supported(n0)) return TDSE_EUNSUPPORTED;
-    if (cfg->dim == 2 && !periodic2d_supported(n0, n1)) return TDSE_EUNSUPPORTED;
+    if (!fs && cfg->dim == 1 && !periodic1d_supported(n0)) return TDSE_EUNSUPPORTED;
+    if (!fs && cfg->dim == 2 && !periodic2d_supported(n0, n1)) return TDSE_EUNSUPPORTED;
+    if (fs && cfg->precision != TDSE_FP64) return TDSE_EUNSUPPORTED;
     if ((long long)cfg->nsteps * SUB + 1 > (1LL << 30)) return TDSE_EINVAL;
 
     tdse_ctx* c = new (std::nothrow) tdse_ctx();
@@ -386,7 +331,16 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     }
     c->have_V.assign(c->B, 0);
     c->have_u0.assign(c->B, 0);
-    plan_workspace(c);
+    if (fs) {
+        c->fs = true;
+        const tdse_status st = fs_create(c);
+        if (st != TDSE_OK) {
+            delete c;
+            return st;
+        }
+    } else {
+        plan_workspace(c);
+    }
     *out = c;
     return TDSE_OK;
 }
@@ -401,6 +355,10 @@ tdse_status tdse_bind_workspace(tdse_ctx* c, void* dev, size_t bytes, void* stre
     c->ws = static_cast<char*>(dev);
     TDSE_CK(c, cudaMemcpyAsync(c->P<int2>(c->off.iv), c->intervals.data(), c->intervals.size() * sizeof(int2),
                                cudaMemcpyHostToDevice, s));
+    if (c->fs) {
+        tdse_status st = fs_bind(c, s);
+        if (st != TDSE_OK) return st;
+    } else {
     TDSE_CK(c, launch_twiddles(c->P<double2>(c->off.tw64_0), c->P<float2>(c->off.tw32_0),
                                c->P<float2>(c->off.tw32lo_0), c->n0, s));
     if (c->d == 2)
@@ -410,6 +368,7 @@ tdse_status tdse_bind_workspace(tdse_ctx* c, void* dev, size_t bytes, void* stre
         TDSE_CK(c, launch_kin1d(opt<double2>(c, c->off.kin64), opt<float4>(c, c->off.kinff), c->n0, c->L, c->cfg.dt, s));
     if (c->d == 1 && c->mixed)
         TDSE_CK(c, launch_k1d(c->P<float2>(c->off.k1lo), c->P<float2>(c->off.k1hi), c->nhi, c->n0, c->cfg.dt, s));
+    }
     // defaults: A == 0 (phi == 0), f(t) == 1
     TDSE_CK(c, cudaMemsetAsync(c->P<double>(c->off.phi), 0, (size_t)c->B * c->d * c->ntf * 8, s));
     std::vector<double> ones(c->ntf, 1.0);
@@ -517,7 +476,12 @@ tdse_status tdse_set_initial(tdse_ctx* c, int instance, const double* u0, int wh
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const cudaMemcpyKind kind = where == TDSE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     for (int b = lo; b < hi; ++b) {
-        TDSE_CK(c, cudaMemcpyAsync(c->P<double2>(c->off.uhat) + (size_t)b * c->NP, u0, c->NP * 16, kind, s));
+        if (c->fs) {
+            tdse_status st = fs_set_initial(c, b, u0, kind, s);
+            if (st != TDSE_OK) return st;
+        } else {
+            TDSE_CK(c, cudaMemcpyAsync(c->P<double2>(c->off.uhat) + (size_t)b * c->NP, u0, c->NP * 16, kind, s));
+        }
         c->have_u0[b] = 1;
     }
     if (where == TDSE_HOST) TDSE_CK(c, cudaStreamSynchronize(s));
@@ -655,6 +619,7 @@ tdse_status tdse_step(tdse_ctx* c, int nsteps, void* stream) {
         if (!c->have_V[b] || !c->have_u0[b]) return c->fail(TDSE_ESTATE, "instance lacks V or u0");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (nsteps == 0) return TDSE_OK;
+    if (c->fs) return fs_steps(c, nsteps, s);
     if (!c->inited) {
         tdse_status st = do_init(c, s);
         if (st != TDSE_OK) return st;
@@ -700,6 +665,13 @@ tdse_status tdse_read_u(tdse_ctx* c, int instance, double* u_out, int where, voi
         if (!c->have_u0[b]) return c->fail(TDSE_ESTATE, "instance has no initial state");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t nb = (size_t)(hi - lo);
+    if (c->fs) {
+        tdse_status st = fs_read_u(c, lo, hi, u_out, where == TDSE_HOST ? cudaMemcpyDeviceToHost
+                                                                      : cudaMemcpyDeviceToDevice, s);
+        if (st != TDSE_OK) return st;
+        if (where == TDSE_HOST) TDSE_CK(c, cudaStreamSynchronize(s));
+        return TDSE_OK;
+    }
     const double2* src;
     if (!c->inited) {
         src = c->P<double2>(c->off.uhat) + (size_t)lo * c->NP;    // u0 still parked in physical form
@@ -726,11 +698,29 @@ tdse_status tdse_check_finite(tdse_ctx* c, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int* cnt = c->P<int>(c->off.scratch);
     TDSE_CK(c, cudaMemsetAsync(cnt, 0, sizeof(int), s));
-    TDSE_CK(c, launch_count_nonfinite(c->P<void>(c->off.uhat), c->NP * c->B * 2, c->mixed && c->inited, cnt, s));
+    const size_t nmodes = c->fs ? c->F.NM : c->NP;
+    TDSE_CK(c, launch_count_nonfinite(c->P<void>(c->off.uhat), nmodes * c->B * 2, c->mixed && c->inited, cnt, s));
     int h = 0;
     TDSE_CK(c, cudaMemcpyAsync(&h, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
     TDSE_CK(c, cudaStreamSynchronize(s));
     if (h) return c->fail(TDSE_ENONFINITE, "non-finite values in the mode state");
+    return TDSE_OK;
+}
+
+tdse_status tdse_read_modes(tdse_ctx* c, int instance, double* u_out, int where, void* stream) {
+    if (!c || !u_out) return TDSE_EINVAL;
+    if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
+    if (c->mixed) return c->fail(TDSE_EUNSUPPORTED, "mode state is FP64 only in TDSE_FP64");
+    if (!c->inited) return c->fail(TDSE_ESTATE, "no step taken yet");
+    int lo, hi;
+    if (!instance_range(c, instance, lo, hi)) return c->fail(TDSE_EINVAL, "instance out of range");
+    if (where != TDSE_HOST && where != TDSE_DEVICE) return TDSE_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t nm = c->fs ? c->F.NM : c->NP;
+    const cudaMemcpyKind kind = where == TDSE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    TDSE_CK(c, cudaMemcpyAsync(u_out, c->P<double2>(c->off.uhat) + (size_t)lo * nm, (size_t)(hi - lo) * nm * 16,
+                               kind, s));
+    if (where == TDSE_HOST) TDSE_CK(c, cudaStreamSynchronize(s));
     return TDSE_OK;
 }
 

@@ -1,0 +1,106 @@
+// Private context of the C ABI (include/tdse.h), shared by the periodic
+// orchestrator (api.cpp) and the free-space one (fs_api.cpp).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "tdse.h"
+
+namespace tdse {
+
+constexpr int SUB = 8;   // fine time grid: t_m = m dt / 8 (Richardson sub-steps down to dt/8)
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// q-point Gauss-Legendre nodes/weights on [-1,1] (api.cpp).
+void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w);
+
+// One axis of the free-space contour rule (Sec. 3.4, 4.1), host copy.
+struct FsAxisHost {
+    int M = 0, nu = 0, R = 0, NE = 0, ND = 0, NC = 0, N = 0, p = 0, kappa = 0, q = 0, n_r = 0;
+    double H = 0, K = 0, h = 0;
+    std::vector<double> zeta;   // [N][2] nodes (complex)
+    std::vector<double> w;      // [N][2] weights (complex)
+};
+
+struct FsState {
+    FsAxisHost ax[2];
+    size_t NM = 0;   // modes per instance (N0 N1)
+    size_t NX = 0;   // grid points per instance (M0 M1)
+    struct {
+        size_t uhat, ring, chain_uhat, chain_ring, chain_u, u, Z, V0, tfac, phi, iv, scratch, end;
+        size_t zeta[2], preI[2], postI[2], preF[2], postF[2], Gd[2], Fd[2], tw[2], P[2];
+    } off{};
+};
+
+}  // namespace tdse
+
+struct tdse_ctx {
+    bool fs = false;            // free-space (bc = TDSE_FREE) context: state in F
+    tdse::FsState F;
+    tdse_config cfg{};
+    int d = 1, n0 = 0, n1 = 1;
+    size_t NP = 0;
+    int B = 1, m = 8, L = 4, S = 7, S_eff = 7, RS = 7, ntf = 0, n_int = 0, n_int_startup = 0, nhi = 1;
+    bool mixed = false;
+    bool ip = false;            // mixed mode: state and ring are in the interaction picture
+    int nh = 1, nl = 1, lb = 0;
+    size_t rsz = 16;            // ring element bytes
+    double mu[8] = {0};
+    double rich[4] = {0};
+    std::vector<int2> intervals;
+    std::vector<float> zdither;   // [nsteps + 1][2]: FP32 ring dither z_n (interaction picture)
+    // workspace
+    char* ws = nullptr;
+    size_t ws_need = 0;
+    struct {
+        size_t uhat, ring, chain_uhat, chain_ring, aux, aux2, V0, V0f, tfac, phi, kin64, kinff, adv64, advff,
+            q64, qff, e2d, k1lo, k1hi, a1d, tw64_0, tw32_0, tw64_1, tw32_1, tw32lo_0, tw32lo_1, iv, scratch, end;
+    } off{};
+    std::vector<char> have_V, have_u0;
+    int step = 0;
+    bool inited = false;
+    std::string err;
+
+    template <class T> T* P(size_t o) const { return reinterpret_cast<T*>(ws + o); }
+    tdse_status fail(tdse_status s, const std::string& msg) {
+        err = msg;
+        return s;
+    }
+};
+
+inline tdse_status cuda_fail(tdse_ctx* c, cudaError_t e, const char* where) {
+    return c->fail(TDSE_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define TDSE_CK(ctx, expr)                                       \
+    do {                                                         \
+        cudaError_t e__ = (expr);                                \
+        if (e__ != cudaSuccess) return cuda_fail(ctx, e__, #expr); \
+    } while (0)
+
+
+
+inline int slot_of(const tdse_ctx* c, int n) { return ((n % c->RS) + c->RS) % c->RS; }
+
+// Interval ids.  Start-up step s (1..S_eff) owns ids (s-1)(2^L - 1) .. s(2^L - 1) - 1:
+// chain c, sub-step i at (s-1)(2^L - 1) + (2^c - 1) + i (chain 0 is the main
+// interval t_{s-1} -> t_s).  Main intervals of later steps n follow from
+// n_int_startup (FP64 mode only: mixed Adams steps use absolute phases).
+inline int startup_interval(const tdse_ctx* c, int s, int chain, int i) {
+    return (s - 1) * ((1 << c->L) - 1) + ((1 << chain) - 1) + i;
+}
+inline int main_interval(const tdse_ctx* c, int n) {
+    return n <= c->S_eff ? startup_interval(c, n, 0, 0) : c->n_int_startup + (n - c->S_eff - 1);
+}
+
+// Free-space orchestration (fs_api.cpp), called by the entry points in api.cpp
+// once the common fields of the context are set.
+tdse_status fs_create(tdse_ctx* c);
+tdse_status fs_bind(tdse_ctx* c, cudaStream_t s);
+tdse_status fs_build_phase_tables(tdse_ctx* c, int b, cudaStream_t s);
+tdse_status fs_set_initial(tdse_ctx* c, int b, const double* u0, cudaMemcpyKind kind, cudaStream_t s);
+tdse_status fs_steps(tdse_ctx* c, int nsteps, cudaStream_t s);
+tdse_status fs_read_u(tdse_ctx* c, int lo, int hi, double* out, cudaMemcpyKind kind, cudaStream_t s);

@@ -1,0 +1,90 @@
+// Argument bundle of the free-space (complex contour) kernels, freespace.cu,
+// shared with the host orchestrator fs_api.cpp.  Plain data.
+//
+// Free-space discretisation (Sec. 3.3-3.4, 4.1), one axis:
+//   grid     x_j = -1 + 2 j / M, j = 0..M-1;
+//   modes    zeta_m on the contour Gamma in the block order
+//            E1 (NE equispaced, Gamma_1), A1 (p Alpert), C (Gauss panels on
+//            Gamma_2), A3 (p Alpert), E3 (NE equispaced, Gamma_3), N in all;
+//            the middle ND = 2p + NC modes are the "dense" block;
+//   forward  f^_m = (2/M) sum_j e^{-i zeta_m x_j} f_j                  (eq. fzdft)
+//   inverse  f_j  = (1/2pi) sum_m w_m e^{i zeta_m x_j} f^_m            (eq. uciftdisc)
+// In 2D both are tensor products (axis 0 then axis 1, row-major arrays).
+//
+// An equispaced block has zeta_i = zeta0 + i h, i = 0..NE-1, weight h, with
+// h = pi M / nu, so e^{i i h x_j} = e^{-i i h} e^{2 pi i i j / nu}: its sums are
+// length-nu DFTs with NE nonzero inputs (inverse) or M nonzero inputs
+// (forward), evaluated at M (resp. NE) points (eq. ssfftgen).  With nu = R M
+// and i = s + R q each is R interleaved M-point FFTs plus a twiddle
+// e^{+-2 pi i j s / nu}; the tables below fold that twiddle into the block's
+// pre/post factors.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace tdse {
+
+constexpr int FS_T = 256;         // threads per CTA of every free-space kernel
+constexpr int FS_MAX_ND = 128;    // dense (Alpert + Gauss) modes per axis
+constexpr int FS_MAX_HIST = 7;
+
+struct FsAxis {
+    int M;        // physical points
+    int R;        // nu / M
+    int nu;       // equispaced FFT length
+    int NE;       // modes per equispaced block
+    int ND;       // dense modes (A1, C, A3)
+    int N;        // all modes: 2 NE + ND
+    const double2* preI;   // [2][NE]    inverse, block b: (h / 2pi) e^{-i i h}
+    const double2* postI;  // [2][M][R]  inverse: e^{i zeta0_b x_j} e^{+2 pi i j s / nu}
+    const double2* preF;   // [2][M][R]  forward: (2/M) e^{-i zeta0_b x_j} e^{-2 pi i j s / nu}
+    const double2* postF;  // [2][NE]    forward: e^{+i i h}
+    const double2* Gd;     // [ND][M]    inverse dense: (w_d / 2pi) e^{i zeta_d x_j}
+    const double2* Fd;     // [ND][M]    forward dense: (2/M) e^{-i zeta_d x_j}
+    const double2* tw;     // [M]        e^{-2 pi i m / M}
+    const double2* P;      // [B][n_int][N] one-step phases e^{-i zeta^2 s + i zeta (phi(t1) - phi(t0))}
+};
+
+struct FsArgs {
+    int B;                 // instances in the launch
+    int d;                 // 1 or 2
+    FsAxis ax[2];
+    int n_int;             // phase intervals per instance
+    // ---- step description (eq. uadamsk with zeta for k; eq. utrapzfd for nhist = 1)
+    int nhist;             // history terms j = 1..nhist
+    double h;              // step size
+    double mu[FS_MAX_HIST + 1];
+    int hist_slot[FS_MAX_HIST];   // ring slot of lag j (index j-1)
+    int out_slot;          // ring slot receiving the new (Vu)^
+    int interval[FS_MAX_HIST];    // interval id of the one-step phase p_i, i = 0..nhist-1
+    int tf;                // fine time index of the new time (t = tf dt / 8)
+    // ---- buffers
+    double2* uhat;         // [B][N0 N1] mode state: u^ between steps, W inside a step
+    double2* ring;         // [B][ring_slots][N0 N1] history of (Vu)^
+    int ring_slots;
+    double2* Z;            // [B][N0][M1] 2D intermediate (axis-1 transformed rows)
+    double2* u;            // [B][M0 M1] physical state written by the implicit solve
+    const double2* usrc;   // forward-only source on the grid
+    double2* fdst;         // forward-only destination in mode space, instance b at fdst + b fdst_bstride
+    size_t fdst_bstride;
+    int mulV;              // forward-only: transform V(t) usrc instead of usrc
+    const double* V0;      // [B][M0 M1]
+    const double* tfac;    // [B][ntf]
+    int ntf;
+};
+
+// Row pass flags (2D) and 1D modes.
+enum FsRow : int { FS_ROW_END = 1, FS_ROW_BEGIN = 2, FS_ROW_FWD_ONLY = 4 };
+enum Fs1D : int { FS_1D_STEP = 0, FS_1D_FWD_ONLY = 1 };
+
+bool fs_supported(int M, int R);
+size_t fs_smem_bytes(int M, int R);
+// 2D: row pass over the N0 mode rows (axis 1), phys pass over the M1 grid columns (axis 0).
+cudaError_t launch_fs_row(const FsArgs& a, int flags, cudaStream_t s);
+cudaError_t launch_fs_phys(const FsArgs& a, int from_usrc, cudaStream_t s);
+cudaError_t launch_fs_1d(const FsArgs& a, int mode, cudaStream_t s);
+// P[iv][m] of one instance and axis: zeta [N] complex, phi_axis [ntf] = that
+// component of phi at t = m dt / 8.
+cudaError_t launch_fs_phase(double2* P, const double2* zeta, int N, const int2* intervals, int n_int,
+                            const double* phi_axis, double dt, cudaStream_t s);
+
+}  // namespace tdse

@@ -18,7 +18,12 @@ Workloads (shapes/values follow the paper's 1D/2D examples, Sec. 7):
     attractive Gaussian wells, pulse A(t) = 2 sin^2(pi t/2) sin(10 t) (1,0),
     T=2, dt=1e-3;
   * ``periodic_1d_batch_member`` -- one member of the uneven 1D batch
-    (N in {256..16384}), T=1, dt=1e-3.
+    (N in {256..16384}), T=1, dt=1e-3;
+  * ``free_bump_gaussians`` -- free space on [-1,1]^d (default 256^2):
+    Gaussians (sigma ~ U[0.08,0.15], centres ~ U[-0.4,0.4]^d) times the
+    C-infinity window exp(1 - 1/(1 - r^2)), r = |x| / 0.95, for u0 and for
+    four attractive wells of depth U[5,20]; pulse A0 = 2, omega = 10 along
+    (1,0), T = 1, dt = 5e-4.
 """
 from __future__ import annotations
 
@@ -197,3 +202,52 @@ def random_periodic(shape, seed: int, dt: float, nsteps: int, vamp: float = 5.0,
     u0 = u0 / _grid_norm(u0, h)
     return Instance(PERIODIC, tuple(shape), u0, V0, vfac or _const_one, pulse, dt, nsteps,
                     name=f"random_periodic_{'x'.join(map(str, shape))}")
+
+
+def bump_window(X: Sequence[np.ndarray], radius: float = 0.95) -> np.ndarray:
+    """exp(1 - 1/(1 - r^2)) for r = |x| / radius < 1, else 0 (C-infinity, compact)."""
+    r2 = sum(x * x for x in X) / (radius * radius)
+    out = np.zeros_like(r2)
+    inside = r2 < 1.0
+    out[inside] = np.exp(1.0 - 1.0 / (1.0 - r2[inside]))
+    return out
+
+
+def free_bump_gaussians(shape=(256, 256), seed: int = 3, dt: float = 5e-4, nsteps: int = 2000,
+                        T_pulse: Optional[float] = None, A0: float = 2.0, omega: float = 10.0,
+                        direction: Optional[Sequence[float]] = None, n_u: int = 3, n_v: int = 4,
+                        vfac: Optional[Callable] = None) -> Instance:
+    """Free-space workload on [-1,1]^d: u0 = normalised sum of n_u Gaussians
+    (sigma ~ U[0.08,0.15], centres ~ U[-0.4,0.4]^d, phases ~ U[0,2pi)) times
+    the bump window; V0 = -sum of n_v wells depth exp(-|x-c|^2/(2 sigma^2))
+    (depth ~ U[5,20], sigma ~ U[0.08,0.15], centres ~ U[-0.4,0.4]^d) times the
+    window.  A(t) = A0 sin^2(pi t / T_pulse) sin(omega t) along `direction`
+    (default (1, 0, ..)), T_pulse = nsteps dt by default."""
+    rng = np.random.default_rng(seed)
+    d = len(shape)
+    X = np.meshgrid(*[free_grid(M) for M in shape], indexing="ij")
+    win = bump_window(X)
+
+    def gauss(c, s):
+        return np.exp(-sum((x - cc) ** 2 for x, cc in zip(X, c)) / (2.0 * s * s))
+
+    u0 = np.zeros(tuple(shape), dtype=np.complex128)
+    for _ in range(n_u):
+        s = rng.uniform(0.08, 0.15)
+        c = rng.uniform(-0.4, 0.4, size=d)
+        ph = rng.uniform(0.0, 2.0 * math.pi)
+        u0 += np.exp(1j * ph) * gauss(c, s)
+    u0 *= win
+    u0 = u0 / _grid_norm(u0, 2.0 / shape[0])
+    V0 = np.zeros(tuple(shape), dtype=np.float64)
+    for _ in range(n_v):
+        depth = rng.uniform(5.0, 20.0)
+        s = rng.uniform(0.08, 0.15)
+        c = rng.uniform(-0.4, 0.4, size=d)
+        V0 -= depth * gauss(c, s)
+    V0 *= win
+    Tp = nsteps * dt if T_pulse is None else T_pulse
+    dirn = tuple(direction) if direction is not None else (1.0,) + (0.0,) * (d - 1)
+    pulse = Pulse(A0, omega, Tp, dirn) if A0 else None
+    return Instance(FREE, tuple(shape), u0, V0, vfac or _const_one, pulse, dt, nsteps,
+                    name=f"free_bump_gaussians_{'x'.join(map(str, shape))}")

@@ -24,7 +24,7 @@ def native():
 def _declared_symbols():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(tdse_[a-z_0-9]+)\s*\(", text)) - {"tdse_field_fn"})
+    return sorted(set(re.findall(r"\b(tdse_[A-Za-z_0-9]+)\s*\(", text)) - {"tdse_field_fn"})
 
 
 def test_header_declarations_listed(native):
@@ -52,6 +52,8 @@ def _cfg(native, **kw):
     for k, v in kw.items():
         if k == "n":
             c.n[0], c.n[1] = v
+        elif k == "nu":
+            c.nu[0], c.nu[1] = v
         else:
             setattr(c, k, v)
     return c
@@ -68,7 +70,17 @@ def _cfg(native, **kw):
     (dict(dt=0.0), -1),
     (dict(batch=0), -1),
     (dict(startup_steps=5), -1),       # fewer than order - 2
-    (dict(bc=1), -7),                  # free space: not built
+    (dict(bc=1), -1),                  # free space without nu / H
+    (dict(bc=1, nu=(512, 0), H=1.5, gauss_q=10, n_r=1), 0),
+    (dict(bc=1, dim=2, n=(64, 32), nu=(512, 256), H=1.5, gauss_q=10, n_r=1), 0),
+    (dict(bc=1, nu=(512, 0), H=1.5, gauss_q=10, n_r=1, precision=1), -7),   # free space: FP64 only
+    (dict(bc=1, n=(1024, 1), nu=(4096, 0), H=1.5, gauss_q=10, n_r=1), -7),  # n > 512
+    (dict(bc=1, nu=(500, 0), H=1.5, gauss_q=10, n_r=1), -1),                # nu not a multiple of n
+    (dict(bc=1, nu=(512, 0), H=0.0, gauss_q=10, n_r=1), -1),
+    (dict(bc=1, nu=(512, 0), H=1.5, gauss_q=10, n_r=1, alpert_p=5), -1),
+    (dict(bc=1, nu=(512, 0), H=1.5, gauss_q=10, n_r=5), -1),
+    (dict(bc=1, nu=(512, 0), H=1.5, gauss_q=0, n_r=1), -1),
+    (dict(bc=1, nu=(512, 0), H=1.5, gauss_q=32, n_r=4), -1),                # dense block > 128 modes
     (dict(precision=5), -1),
 ])
 def test_create_validates(native, kw, status):
@@ -93,3 +105,56 @@ def test_workspace_size_scales_with_batch(native):
         sizes.append(lib.tdse_workspace_bytes(ctx))
         lib.tdse_destroy(ctx)
     assert 3.5 * sizes[0] < sizes[1] < 4.5 * sizes[0]
+
+
+# ------------------------------------------------------------ free-space rule
+def _free_ctx(native, M=64, nu=512, H=1.7, p=8, q=10, n_r=2):
+    lib = native.lib()
+    ctx = ctypes.c_void_p()
+    cfg = _cfg(native, bc=1, n=(M, 1), nu=(nu, 0), H=H, gauss_q=q, n_r=n_r, alpert_p=p)
+    assert lib.tdse_create(ctypes.byref(cfg), ctypes.byref(ctx)) == 0
+    return lib, ctx
+
+
+@pytest.mark.parametrize("p,q,n_r", [(8, 10, 1), (8, 16, 2), (4, 6, 0), (8, 8, 3)])
+def test_free_rule_matches_oracle_rule(native, p, q, n_r):
+    """The library's contour rule (its own Gauss-Legendre and Alpert tables,
+    derived by a different algorithm) equals the oracle's GammaRule node by node."""
+    from oracle import gamma
+    M, nu, H = 64, 512, 1.7
+    lib, ctx = _free_ctx(native, M, nu, H, p, q, n_r)
+    n = ctypes.c_int()
+    assert lib.tdse_free_rule(ctx, 0, ctypes.byref(n), None, None) == 0
+    z = np.empty(n.value, dtype=np.complex128)
+    w = np.empty(n.value, dtype=np.complex128)
+    dp = ctypes.POINTER(ctypes.c_double)
+    assert lib.tdse_free_rule(ctx, 0, ctypes.byref(n), z.ctypes.data_as(dp), w.ctypes.data_as(dp)) == 0
+    assert lib.tdse_free_rule(ctx, 1, ctypes.byref(n), None, None) == -1      # 1D: no axis 1
+    lib.tdse_destroy(ctx)
+    r = gamma.GammaRule.for_nu(M, nu, H, p=p, q=q, n_r=n_r)
+    assert z.size == r.N
+    assert np.max(np.abs(z - r.zeta) / np.maximum(1.0, np.abs(r.zeta))) < 4e-16
+    assert np.max(np.abs(w - r.w)) < 2e-15      # Gauss-Legendre weights by two routes: a few ulps
+
+
+@pytest.mark.parametrize("eps,vnorm,phimax,dim", [(1e-10, 20.0, 0.3, 2), (1e-12, 0.0, 0.0, 1), (1e-8, 5.0, 1.0, 2)])
+def test_free_choose_H_matches_oracle(native, eps, vnorm, phimax, dim):
+    from oracle import gamma
+    from paper_2001_06113_gb300 import free_choose_H
+    assert abs(free_choose_H(eps, vnorm, phimax, dim) - gamma.choose_H(eps, vnorm, phimax, dim)) < 1e-15
+
+
+def test_free_choose_H_rejects_nonpositive(native):
+    from paper_2001_06113_gb300 import TdseError, free_choose_H
+    with pytest.raises(TdseError):
+        free_choose_H(1e-20, 100.0, 0.0, 1)         # eps below (1 + ||V||) eps_m: H < 0
+
+
+def test_alpert_header_is_generator_output():
+    """alpert_rules.h is exactly what its committed generator writes."""
+    pytest.importorskip("mpmath")
+    import subprocess
+    import sys
+    gen = os.path.join(ROOT, "paper_2001_06113_gb300", "csrc", "gen_alpert.py")
+    out = subprocess.run([sys.executable, gen], capture_output=True, text=True, check=True).stdout
+    assert out == open(os.path.join(ROOT, "paper_2001_06113_gb300", "csrc", "alpert_rules.h")).read()

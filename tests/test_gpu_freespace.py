@@ -1,0 +1,217 @@
+"""GPU parity of the free-space path (Sec. 3-4, Remark highorderfs) against
+the FP64 oracle, through the C ABI.
+
+Both sides march the same seeded problem with the same contour parameters
+(H, nu, p, q, n_r).  The bound is max(1e-12, eps) in relative L2 for u on the
+grid and for the mode state u^ on the contour, eps being the precision H was
+chosen for (Remark Hchoice): the transform pair amplifies rounding by
+e^{2 d H (1 + phi_max)} (1 + ||V||), which H makes equal to eps / eps_m, and
+the two sides round differently (FFT-based versus direct sums).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import fields, gamma
+from oracle.freespace import FreeSpaceOracle
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.sqrt(np.sum(np.abs(a - b) ** 2) / np.sum(np.abs(b) ** 2)))
+
+
+def _instance(shape, n, seed=11, dt=1e-3, A0=50.0, omega=200.0):
+    d = len(shape)
+    return synth.free_bump_gaussians(shape, seed=seed, dt=dt, nsteps=n, A0=A0, omega=omega,
+                                     direction=(1.0, -0.5)[:d],
+                                     vfac=lambda t: 1.0 + 0.3 * np.sin(40.0 * np.asarray(t, dtype=np.float64)))
+
+
+def _H(inst, eps):
+    phi = fields.phi_callable(inst.pulse, inst.dim)
+    phimax = max(float(np.max(np.abs(phi(t)))) for t in np.linspace(0.0, inst.t_max, 401))
+    vnorm = math.sqrt(float(np.sum(inst.V0 ** 2)) * (2.0 / inst.shape[0]) ** inst.dim)
+    vnorm *= float(np.max(np.abs(inst.vfac_table())))
+    return gamma.choose_H(eps, vnorm, phimax, inst.dim)
+
+
+def _gpu(inst, nu, H, n, q=10, n_r=1, p=8, order=8, startup=-1):
+    import torch
+    from paper_2001_06113_gb300 import Problem
+    pr = Problem(inst.shape, inst.dt, inst.nsteps, order=order, startup_steps=startup, bc="free", nu=nu, H=H,
+                 gauss_q=q, n_r=n_r, alpert_p=p)
+    pr.set_potential(inst.V0, inst.vfac_table())
+    if inst.pulse is not None:
+        pr.set_pulse(inst.pulse.A0, inst.pulse.omega, inst.pulse.T_pulse, inst.pulse.direction)
+    pr.set_initial(inst.u0)
+    pr.step(n)
+    torch.cuda.synchronize()
+    return pr.read_u(0), pr.read_modes(0), pr
+
+
+def _oracle(inst, nu, H, n, q=10, n_r=1, p=8, order=8, startup=None):
+    rules = [gamma.GammaRule.for_nu(M, v, H, p=p, q=q, n_r=n_r) for M, v in zip(inst.shape, nu)]
+    phi = fields.phi_callable(inst.pulse, inst.dim)
+    orc = FreeSpaceOracle(rules, inst.dt, inst.V0, inst.vfac, phi, order=order, n_startup=startup)
+    u = orc.solve(inst.u0, n)
+    return u, orc.last_uhat
+
+
+CASES_1D = [
+    # shape, nu, q, n_r, p, order, steps, eps
+    ((64,), (512,), 10, 1, 8, 8, 12, 1e-10),
+    ((32,), (512,), 8, 0, 4, 4, 9, 1e-10),
+    ((128,), (512,), 12, 2, 8, 6, 10, 1e-11),
+    ((256,), (1024,), 10, 1, 8, 8, 9, 1e-10),
+    ((512,), (2048,), 10, 1, 8, 8, 9, 1e-10),
+]
+
+
+@pytest.mark.parametrize("shape,nu,q,n_r,p,order,n,eps", CASES_1D)
+def test_free_1d_matches_oracle(shape, nu, q, n_r, p, order, n, eps):
+    inst = _instance(shape, n + 2)
+    H = _H(inst, eps)
+    u, uh, _ = _gpu(inst, nu, H, n, q, n_r, p, order)
+    uo, uho = _oracle(inst, nu, H, n, q, n_r, p, order)
+    tol = max(1e-12, eps)
+    assert rel(u, uo) < tol and rel(uh, uho) < tol, (rel(u, uo), rel(uh, uho))
+
+
+CASES_2D = [
+    ((64, 32), (512, 256), 10, 1, 8, 8, 10, 1e-10),
+    ((32, 64), (256, 1024), 8, 2, 8, 8, 9, 1e-10),
+    ((32, 32), (128, 512), 6, 0, 4, 4, 7, 1e-9),
+]
+
+
+@pytest.mark.parametrize("shape,nu,q,n_r,p,order,n,eps", CASES_2D)
+def test_free_2d_matches_oracle(shape, nu, q, n_r, p, order, n, eps):
+    inst = _instance(shape, n + 2)
+    H = _H(inst, eps)
+    u, uh, _ = _gpu(inst, nu, H, n, q, n_r, p, order)
+    uo, uho = _oracle(inst, nu, H, n, q, n_r, p, order)
+    tol = max(1e-12, eps)
+    assert rel(u, uo) < tol and rel(uh, uho) < tol, (rel(u, uo), rel(uh, uho))
+
+
+def test_free_2d_full_size_matches_oracle():
+    """The 256^2 free-space workload (nu = 2048, q = 10, n_r = 1, eps = 1e-10)
+    through the start-up and the first Adams step, in the launch sequence the
+    benchmark times."""
+    inst = synth.free_bump_gaussians((256, 256), seed=3, dt=5e-4, nsteps=2000, T_pulse=1.0)
+    n = 8
+    H = _H(inst, 1e-10)
+    u, uh, _ = _gpu(inst, (2048, 2048), H, n)
+    uo, uho = _oracle(inst, (2048, 2048), H, n)
+    assert rel(u, uo) < 1e-10 and rel(uh, uho) < 1e-10, (rel(u, uo), rel(uh, uho))
+
+
+def _wavepacket(x, t, sigma, phi=0.0):
+    a = sigma ** 2 + 2j * t
+    return (math.pi * sigma ** 2) ** -0.25 * sigma / np.sqrt(a) * np.exp(-(x + phi) ** 2 / (2 * a))
+
+
+@pytest.mark.parametrize("A0", [0.0, 3.0])
+def test_free_wavepacket_1d_closed_form(A0):
+    """V = 0: the scheme has no time error (Sec. 7 Example 2); the GPU solution
+    matches the closed form to the quadrature accuracy at every step."""
+    M, sigma, dt, n = 64, 0.1, 0.01, 10
+    pulse = synth.Pulse(A0, 20.0, 0.1, (1.0,)) if A0 else None
+    phi = fields.phi_callable(pulse, 1)
+    phimax = max(abs(phi(t)[0]) for t in np.linspace(0, 0.1, 101))
+    H = gamma.choose_H(1e-12, 0.0, phimax, 1)
+    x = synth.free_grid(M)
+    from paper_2001_06113_gb300 import Problem
+    pr = Problem((M,), dt, n, bc="free", nu=(512,), H=H, gauss_q=16, n_r=2)
+    pr.set_potential(np.zeros(M))
+    if pulse:
+        pr.set_pulse(A0, 20.0, 0.1, (1.0,))
+    pr.set_initial(_wavepacket(x, 0.0, sigma))
+    for k in range(1, n + 1):
+        pr.step(1)
+        u = pr.read_u(0)
+        ref = _wavepacket(x, k * dt, sigma, phi(k * dt)[0])
+        err = math.sqrt(np.sum(np.abs(u - ref) ** 2) * 2 / M)
+        assert err < 1e-12, (k, err)
+
+
+def test_free_wavepacket_2d_closed_form():
+    """2D, A = (A1, A2): u = u_1(x, t) u_2(y, t)."""
+    M, dt, n = (64, 64), 0.01, 6
+    s1, s2 = 0.1, 0.12
+    pulse = synth.Pulse(2.0, 20.0, 0.06, (1.0, -0.5))
+    phi = fields.phi_callable(pulse, 2)
+    H = gamma.choose_H(1e-12, 0.0, 0.1, 2)
+    x = synth.free_grid(M[0])
+    y = synth.free_grid(M[1])
+    u0 = np.outer(_wavepacket(x, 0.0, s1), _wavepacket(y, 0.0, s2))
+    from paper_2001_06113_gb300 import Problem
+    pr = Problem(M, dt, n, bc="free", nu=(512, 512), H=H, gauss_q=16, n_r=2)
+    pr.set_potential(np.zeros(M))
+    pr.set_pulse(2.0, 20.0, 0.06, (1.0, -0.5))
+    pr.set_initial(u0)
+    pr.step(n)
+    u = pr.read_u(0)
+    T = n * dt
+    ph = phi(T)
+    ref = np.outer(_wavepacket(x, T, s1, ph[0]), _wavepacket(y, T, s2, ph[1]))
+    assert rel(u, ref) < 1e-11
+
+
+def test_free_batch_members_equal_solo_runs():
+    """Instances in one batch (different u0, V, A) give bit-identical results
+    to the same instances run alone."""
+    import torch
+    from paper_2001_06113_gb300 import Problem
+    shape, nu, n = (64, 32), (512, 256), 9
+    insts = [_instance(shape, n + 2, seed=20 + i, A0=20.0 * i) for i in range(3)]
+    H = 2.5
+
+    def setup(pr, i, inst):
+        pr.set_potential(inst.V0, inst.vfac_table(), instance=i)
+        if inst.pulse is not None:
+            pr.set_pulse(inst.pulse.A0, inst.pulse.omega, inst.pulse.T_pulse, inst.pulse.direction, instance=i)
+        pr.set_initial(inst.u0, instance=i)
+
+    pb = Problem(shape, insts[0].dt, n + 2, batch=3, bc="free", nu=nu, H=H)
+    for i, inst in enumerate(insts):
+        setup(pb, i, inst)
+    pb.step(n)
+    torch.cuda.synchronize()
+    ub = pb.read_u()
+    mb = pb.read_modes()
+    for i, inst in enumerate(insts):
+        ps = Problem(shape, inst.dt, n + 2, bc="free", nu=nu, H=H)
+        setup(ps, 0, inst)
+        ps.step(n)
+        assert np.array_equal(ps.read_u(0), ub[i])
+        assert np.array_equal(ps.read_modes(0), mb[i])
+
+
+def test_free_read_u_before_and_across_calls():
+    """u0 is readable before stepping; k calls of step(1) equal one step(k)."""
+    from paper_2001_06113_gb300 import Problem, TdseError
+    inst = _instance((32, 32), 12)
+    H = 2.0
+    pr = Problem((32, 32), inst.dt, 12, bc="free", nu=(256, 256), H=H)
+    pr.set_potential(inst.V0, inst.vfac_table())
+    pr.set_pulse(inst.pulse.A0, inst.pulse.omega, inst.pulse.T_pulse, inst.pulse.direction)
+    pr.set_initial(inst.u0)
+    assert np.array_equal(pr.read_u(0), inst.u0)
+    with pytest.raises(TdseError):
+        pr.read_modes(0)
+    for _ in range(10):
+        pr.step(1)
+    pr.check_finite()
+    q = Problem((32, 32), inst.dt, 12, bc="free", nu=(256, 256), H=H)
+    q.set_potential(inst.V0, inst.vfac_table())
+    q.set_pulse(inst.pulse.A0, inst.pulse.omega, inst.pulse.T_pulse, inst.pulse.direction)
+    q.set_initial(inst.u0)
+    q.solve_to(10 * inst.dt)
+    assert q.step_index == 10
+    assert np.array_equal(pr.read_u(0), q.read_u(0))
+    assert np.array_equal(pr.read_modes(0), q.read_modes(0))
