@@ -295,19 +295,21 @@ __global__ void __launch_bounds__(FS_T) k_fs_phys(FsArgs a, int from_usrc) {
 
 // P[iv][m] = exp(-i zeta_m^2 s + i zeta_m (phi(t1) - phi(t0))), s = t1 - t0
 // (eq. uhatxirecur with zeta for k), one instance.
-__global__ void k_fs_phase(double2* P, const double2* zeta, int N, const int2* iv, const double* phi, double dt8) {
-    const int it = blockIdx.y;
-    const int2 q = iv[it];
-    const double s = (double)(q.y - q.x) * dt8;
-    const double dphi = phi[q.y] - phi[q.x];
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < N; m += gridDim.x * blockDim.x) {
-        const double2 z = zeta[m];
-        const double re = 2.0 * z.x * z.y * s - z.y * dphi;
-        const double im = -(z.x * z.x - z.y * z.y) * s + z.x * dphi;
-        double sn, cs;
-        sincos(im, &sn, &cs);
-        const double e = exp(re);
-        P[(size_t)it * N + m] = make_double2(e * cs, e * sn);
+__global__ void k_fs_phase(double2* P, const double2* zeta, int N, const int2* iv, int n_int, const double* phi,
+                           double dt8) {
+    for (int it = blockIdx.y; it < n_int; it += gridDim.y) {
+        const int2 q = iv[it];
+        const double s = (double)(q.y - q.x) * dt8;
+        const double dphi = phi[q.y] - phi[q.x];
+        for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < N; m += gridDim.x * blockDim.x) {
+            const double2 z = zeta[m];
+            const double re = 2.0 * z.x * z.y * s - z.y * dphi;
+            const double im = -(z.x * z.x - z.y * z.y) * s + z.x * dphi;
+            double sn, cs;
+            sincos(im, &sn, &cs);
+            const double e = exp(re);
+            P[(size_t)it * N + m] = make_double2(e * cs, e * sn);
+        }
     }
 }
 
@@ -374,7 +376,8 @@ cudaError_t launch_fs_phys(const FsArgs& a, int from_usrc, cudaStream_t s) {
 cudaError_t launch_fs_phase(double2* P, const double2* zeta, int N, const int2* intervals, int n_int,
                             const double* phi, double dt, cudaStream_t s) {
     if (n_int <= 0) return cudaSuccess;
-    k_fs_phase<<<dim3((N + 255) / 256, n_int), 256, 0, s>>>(P, zeta, N, intervals, phi, dt / 8.0);
+    const unsigned gy = n_int < 65535 ? (unsigned)n_int : 65535u;
+    k_fs_phase<<<dim3((N + 255) / 256, gy), 256, 0, s>>>(P, zeta, N, intervals, n_int, phi, dt / 8.0);
     return cudaGetLastError();
 }
 

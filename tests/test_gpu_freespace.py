@@ -2,11 +2,13 @@
 the FP64 oracle, through the C ABI.
 
 Both sides march the same seeded problem with the same contour parameters
-(H, nu, p, q, n_r).  The bound is max(1e-12, eps) in relative L2 for u on the
-grid and for the mode state u^ on the contour, eps being the precision H was
-chosen for (Remark Hchoice): the transform pair amplifies rounding by
-e^{2 d H (1 + phi_max)} (1 + ||V||), which H makes equal to eps / eps_m, and
-the two sides round differently (FFT-based versus direct sums).
+(H, nu, p, q, n_r).  The worst-case bound on the difference is eps, the
+precision H was chosen for (Remark Hchoice): the transform pair amplifies
+rounding by e^{2 d H (1 + phi_max)} (1 + ||V||), which H makes equal to
+eps / eps_m, and the two sides round differently (FFT-based versus direct
+sums).  The observed differences are 2e-15..3e-14 in relative L2, so the
+tests hold both u on the grid and the mode state u^ on the contour to
+1e-12, the FP64 bar of the periodic path.
 """
 import math
 
@@ -77,8 +79,7 @@ def test_free_1d_matches_oracle(shape, nu, q, n_r, p, order, n, eps):
     H = _H(inst, eps)
     u, uh, _ = _gpu(inst, nu, H, n, q, n_r, p, order)
     uo, uho = _oracle(inst, nu, H, n, q, n_r, p, order)
-    tol = max(1e-12, eps)
-    assert rel(u, uo) < tol and rel(uh, uho) < tol, (rel(u, uo), rel(uh, uho))
+    assert rel(u, uo) < 1e-12 and rel(uh, uho) < 1e-12, (rel(u, uo), rel(uh, uho))
 
 
 CASES_2D = [
@@ -94,8 +95,7 @@ def test_free_2d_matches_oracle(shape, nu, q, n_r, p, order, n, eps):
     H = _H(inst, eps)
     u, uh, _ = _gpu(inst, nu, H, n, q, n_r, p, order)
     uo, uho = _oracle(inst, nu, H, n, q, n_r, p, order)
-    tol = max(1e-12, eps)
-    assert rel(u, uo) < tol and rel(uh, uho) < tol, (rel(u, uo), rel(uh, uho))
+    assert rel(u, uo) < 1e-12 and rel(uh, uho) < 1e-12, (rel(u, uo), rel(uh, uho))
 
 
 def test_free_2d_full_size_matches_oracle():
@@ -107,7 +107,7 @@ def test_free_2d_full_size_matches_oracle():
     H = _H(inst, 1e-10)
     u, uh, _ = _gpu(inst, (2048, 2048), H, n)
     uo, uho = _oracle(inst, (2048, 2048), H, n)
-    assert rel(u, uo) < 1e-10 and rel(uh, uho) < 1e-10, (rel(u, uo), rel(uh, uho))
+    assert rel(u, uo) < 1e-12 and rel(uh, uho) < 1e-12, (rel(u, uo), rel(uh, uho))
 
 
 def _wavepacket(x, t, sigma, phi=0.0):
