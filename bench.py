@@ -8,10 +8,15 @@ the per-step working set (~27 MB per instance in mixed precision) exceeds the
 129 MB L2.  Point-steps = instances x 512^2 x 2000.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
-                    [--batch B] [--impl reference]
+                    [--batch B] [--impl reference] [--workload periodic2d|free2d]
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
 bounded sample of the same workload instead.
+
+`--workload free2d` measures the free-space scheme instead: bump-windowed
+Gaussians on [-1,1]^2, 256x256 grid, nu = 2048 per dimension (2058 contour
+modes per dimension), p = 8, q = 10, n_r = 1, H for eps = 1e-10, T = 1,
+dt = 5e-4 (2000 steps), FP64.
 """
 from __future__ import annotations
 
@@ -40,6 +45,9 @@ METRIC = "point-steps/s (2D periodic 512^2, 8th-order, T=2)"
 # Algorithmic HBM bytes per point-step of the step operator: read u^ (16) and
 # 7 history slots, write u^ (16) and one slot; V read once (real).
 ALGO_BYTES = {"fp64": 16 + 7 * 16 + 8 + 16 + 16, "mixed": 16 + 7 * 8 + 4 + 16 + 8}
+# FP64 FMA throughput of this GB300 pool (register-resident FMA chains, all
+# SMs), TFLOP/s: the peak of the FP64-bound free-space step.
+FP64_PEAK_TFLOPS = 1.25
 
 
 def parse():
@@ -48,10 +56,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=0, help="instances per GPU (default 16 periodic, 1 free space)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="periodic2d", choices=["periodic2d", "free2d"])
     ap.add_argument("--profile-adams", type=int, default=0,
                     help="profiling run: start-up + this many Adams steps of the batch, then exit")
     return ap.parse_args()
@@ -291,6 +300,197 @@ def run_gpu(args, ws, rank, local):
                 stated_err=stated_err, B=B)
 
 
+# ------------------------------------------------------------ free-space arm
+FS_M, FS_NU, FS_DT, FS_NSTEPS, FS_Q, FS_NR, FS_EPS = 256, 2048, 5e-4, 2000, 10, 1, 1e-10
+FS_METRIC = "point-steps/s (2D free space 256^2, nu=2048, 8th-order, T=1, eps=1e-10)"
+
+
+def free_instances(rank: int, batch: int):
+    return [synth.free_bump_gaussians((FS_M, FS_M), seed=1000 * rank + 3 + i, dt=FS_DT, nsteps=FS_NSTEPS,
+                                      T_pulse=1.0) for i in range(batch)]
+
+
+def free_H(insts) -> float:
+    """Remark Hchoice for the batch: ||V||_2 on the grid, max |phi| from the
+    sampled pulse (cumulative trapezoid on 20001 points), eps = 1e-10."""
+    from paper_2001_06113_gb300 import free_choose_H
+    vnorm = max(math.sqrt(float(np.sum(it.V0 ** 2))) * 2.0 / FS_M for it in insts)
+    phimax = 0.0
+    t = np.linspace(0.0, FS_NSTEPS * FS_DT, 20001)
+    for it in insts:
+        A = it.pulse.A(t)
+        phi = np.concatenate([np.zeros((1, A.shape[1])), np.cumsum(0.5 * (A[1:] + A[:-1]) * (t[1] - t[0]), axis=0)])
+        phimax = max(phimax, float(np.max(np.abs(phi))))
+    return free_choose_H(FS_EPS, vnorm, phimax, 2)
+
+
+def free_mode_count() -> int:
+    kappa = 7
+    ne = FS_NU // 2 - 2 * kappa + 1
+    return 2 * ne + 2 * 8 + FS_Q * max(1, 2 * FS_NR)
+
+
+def free_flops_per_step() -> float:
+    """Real FP64 flops of one 2D free-space Adams step, per instance (complex
+    mul 6, complex add 2, length-n FFT 5 n log2 n): the row pass over N0 mode
+    rows (forward along axis 1, update, Horner history of 7 terms with
+    separable phases, inverse along axis 1) plus the column pass over M1 grid
+    columns (inverse along axis 0, implicit solve, V u, forward along axis 0)."""
+    M, nu, N = FS_M, FS_NU, free_mode_count()
+    R = nu // M
+    ne = FS_NU // 2 - 13
+    nd = N - 2 * ne
+    fft = 2 * R * 5 * M * math.log2(M)
+    fwd = 2 * nu * 6 + fft + 2 * ne * 6 + nd * M * 8
+    inv = 2 * ne * 6 + fft + 2 * nu * 8 + nd * M * 8
+    horner = 7 * 2 + 6 * (6 + 6 + 2) + 6 + 6 + 4
+    row = fwd + inv + N * (4 + horner)
+    col = inv + fwd + M * 14
+    return N * row + M * col
+
+
+def run_free(args, ws, rank, local):
+    import torch
+    from paper_2001_06113_gb300 import Problem
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    insts = free_instances(rank, args.batch)
+    B = len(insts)
+    H = free_H(insts)
+    prob = Problem((FS_M, FS_M), FS_DT, FS_NSTEPS, order=ORDER, batch=B, precision="fp64", stream=stream, bc="free",
+                   nu=(FS_NU, FS_NU), H=H, gauss_q=FS_Q, n_r=FS_NR)
+    pinned_V = [torch.from_numpy(it.V0).pin_memory() for it in insts]
+    pinned_u = [torch.from_numpy(it.u0).pin_memory() for it in insts]
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def load_inputs():
+        for b, it in enumerate(insts):
+            prob.set_potential(pinned_V[b], None, instance=b)
+            p = it.pulse
+            prob.set_pulse(p.A0, p.omega, p.T_pulse, p.direction, instance=b)
+            prob.set_initial(pinned_u[b], instance=b)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    def reset():
+        for b in range(B):
+            prob.set_initial(pinned_u[b], instance=b)
+
+    load_inputs()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            reset()
+            prob.step(FS_NSTEPS)
+        stream.synchronize()
+    times = []
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                reset()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                prob.step(FS_NSTEPS)
+                e1.record(stream)
+            stream.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        torch.cuda.synchronize()
+        barrier()
+    t_solve = float(np.mean(times))
+    if ws > 1:
+        tt = torch.tensor([t_solve], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_solve = float(tt.item())
+    points = FS_M * FS_M
+    value = ws * B * points * FS_NSTEPS / t_solve
+
+    GROUP, NGROUPS = 10, 20
+    with torch.cuda.stream(stream):
+        reset()
+        prob.step(STARTUP + 8)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(NGROUPS + 1)]
+        evs[0].record(stream)
+        for i in range(NGROUPS):
+            prob.step(GROUP)
+            evs[i + 1].record(stream)
+    stream.synchronize()
+    dts = np.array([evs[i].elapsed_time(evs[i + 1]) / 1e3 / GROUP for i in range(NGROUPS)])
+    t_step = float(np.mean(dts))
+    flops = free_flops_per_step() * B
+    achieved = flops / t_step / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_source": "FP64 FMA rate of a register-resident microbenchmark on this GB300 pool "
+                               "(no FP64 figure in MEASURED_PEAKS.json)",
+                "kernel": "2D free-space Adams step (k_fs_row end+begin + k_fs_phys), timed over groups of 10 steps",
+                "algorithmic_flops_per_step": flops,
+                "step_ms_p50": round(float(np.percentile(dts, 50)) * 1e3, 4),
+                "step_ms_p99": round(float(np.percentile(dts, 99)) * 1e3, 4)}
+    e2e = None
+    if not args.no_e2e:
+        out = torch.empty((B, FS_M, FS_M), dtype=torch.complex128).pin_memory()
+        e2e_times = []
+        with torch.cuda.stream(stream):
+            for _ in range(max(1, min(args.steps, 2))):
+                flush.zero_()
+                stream.synchronize()
+                barrier()
+                t0 = time.perf_counter()
+                load_inputs()
+                prob.step(FS_NSTEPS)
+                prob.read_u(-1, out=out)
+                e2e_times.append(time.perf_counter() - t0)
+        te = float(np.mean(e2e_times))
+        if ws > 1:
+            tt = torch.tensor([te], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            te = float(tt.item())
+        h2d = B * (points * 8 + points * 16)
+        e2e = {"value": ws * B * points * FS_NSTEPS / te, "unit": "point-steps/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": B * points * 16}
+    prob.close()
+    return dict(value=value, t_solve=t_solve, roofline=roofline, e2e=e2e, clocks=clk.summary(), stated_err=None,
+                B=B, H=H)
+
+
+def free_launches_per_solve() -> int:
+    L = ORDER // 2
+    sub = sum(2 ** c for c in range(L))
+    startup = STARTUP * (L + sub * 3 + 2 + 2)   # copy_slot per chain, sub-steps, 2 combines, refresh (2)
+    init = 4
+    k = FS_NSTEPS - STARTUP
+    return init + startup + 2 * k + 1
+
+
+def free_oracle_sample(nadams: int = 2, seed: int = 3):
+    """The free-space oracle (as it stands) on `nadams` Adams steps of one
+    256^2 instance (direct transform sums); returns point-steps/s."""
+    from oracle import fields, gamma
+    from oracle.freespace import FreeSpaceOracle
+    it = synth.free_bump_gaussians((FS_M, FS_M), seed=seed, dt=FS_DT, nsteps=FS_NSTEPS, T_pulse=1.0)
+    H = 2.75
+    rules = [gamma.GammaRule.for_nu(FS_M, FS_NU, H, q=FS_Q, n_r=FS_NR) for _ in range(2)]
+    orc = FreeSpaceOracle(rules, FS_DT, it.V0, it.vfac, fields.phi_callable(it.pulse, 2))
+    uh = orc.fwd(it.u0)
+    h0 = orc.fwd(orc.V(0.0) * it.u0)
+    n0 = 100
+    hist = {n0 - j: h0 for j in range(1, ORDER)}
+    t0 = time.perf_counter()
+    for k in range(nadams):
+        n = n0 + k
+        uh, u, hist[n] = orc.adams_step(uh, n * FS_DT, hist, n)
+        hist.pop(n - ORDER, None)
+    el = time.perf_counter() - t0
+    return FS_M * FS_M * nadams / el, el
+
+
 def profile_run(args):
     """Small fixed launch sequence for ncu: init, start-up, then K Adams steps."""
     import torch
@@ -347,9 +547,87 @@ def cpu_cores() -> int:
     return os.cpu_count() or 1
 
 
+def free_profile_run(args):
+    """Small fixed launch sequence for ncu: init, start-up, then K Adams steps (free space)."""
+    import torch
+    from paper_2001_06113_gb300 import Problem
+    insts = free_instances(0, args.batch)
+    prob = Problem((FS_M, FS_M), FS_DT, FS_NSTEPS, order=ORDER, batch=len(insts), precision="fp64", bc="free",
+                   nu=(FS_NU, FS_NU), H=free_H(insts), gauss_q=FS_Q, n_r=FS_NR)
+    for b, it in enumerate(insts):
+        prob.set_potential(it.V0, None, instance=b)
+        p = it.pulse
+        prob.set_pulse(p.A0, p.omega, p.T_pulse, p.direction, instance=b)
+        prob.set_initial(it.u0, instance=b)
+    prob.step(STARTUP + args.profile_adams)
+    torch.cuda.synchronize()
+    prob.check_finite()
+    print(json.dumps({"profile_adams": args.profile_adams, "batch": len(insts), "workload": "free2d",
+                      "launches_before_adams": free_launches_per_solve() - (2 * (FS_NSTEPS - STARTUP) + 1)}))
+    prob.close()
+    return 0
+
+
+def main_free(args, ws, rank, local):
+    import torch
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        for _ in range(args.warmup):
+            free_oracle_sample(nadams=1)
+        vals = [free_oracle_sample(nadams=1)[0] for _ in range(args.steps)]
+        value = float(np.mean(vals))
+        line = {"impl": "reference", "metric": FS_METRIC, "value": value, "unit": "point-steps/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * FS_M * FS_M / value, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "2D free space 256x256, nu=2048, dt=5e-4, 8th-order Adams (CPU oracle sample)"},
+                "cpu_baseline": {"value": value, "unit": "point-steps/s", "cores": cpu_cores(), "kind": "oracle",
+                                 "sample": "1 Adams step of one 256^2 free-space instance per bench step "
+                                           "(direct transform sums)"},
+                "e2e": {"value": value, "unit": "point-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+    if args.profile_adams:
+        return free_profile_run(args)
+    if ws > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    res = run_free(args, ws, rank, local)
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and ws == 1:
+            v, el = free_oracle_sample(nadams=3)
+            cpu = {"value": v, "unit": "point-steps/s", "cores": cpu_cores(), "kind": "oracle",
+                   "sample": f"3 8th-order Adams steps of one 256^2 free-space instance ({el:.1f} s; direct "
+                             "transform sums, numpy/OpenBLAS)"}
+        line = {
+            "metric": FS_METRIC, "value": res["value"], "unit": "point-steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["t_solve"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": f"2D free space 256x256, nu=2048 (N=2058 modes/dim), p=8, q=10, n_r=1, "
+                                   f"H={res['H']:.4f} (eps=1e-10), T=1, dt=5e-4 (2000 steps), 8th-order Adams, "
+                                   f"batch of {res['B']} per GPU, fp64",
+                       "grid": [FS_M, FS_M], "nu": FS_NU, "nsteps": FS_NSTEPS, "dt": FS_DT, "order": ORDER,
+                       "batch_per_gpu": res["B"], "precision": "fp64",
+                       "l2": "flushed (256 MB write) before each timed solve; per-step working set > L2",
+                       "step": "one whole solve (7 Richardson start-up + 1993 Adams steps)",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
+            "gpu_launches": free_launches_per_solve() * args.steps,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
+    if args.batch <= 0:
+        args.batch = 1 if args.workload == "free2d" else 16
+    if args.workload == "free2d":
+        return main_free(args, ws, rank, local)
     if args.impl == "reference":
         if rank != 0:
             return 0

@@ -140,6 +140,32 @@ __device__ __forceinline__ double2 horner(const FsArgs& a, double2 uh, Lag lag, 
     return cmul(phase(0), uh + times_minus_i(S, a.h));
 }
 
+// c R + b S with one rounding per fused multiply-add (complex).
+__device__ __forceinline__ double2 cmul_add2(double2 c, double2 R, double2 b, double2 S) {
+    return make_double2(fma(c.x, R.x, fma(-c.y, R.y, fma(b.x, S.x, -b.y * S.y))),
+                        fma(c.x, R.y, fma(c.y, R.x, fma(b.x, S.y, b.y * S.x))));
+}
+
+// 2D form of the Horner recurrence with separable phases p_i = a_i b_i
+// (a_i of the row, b_i of the mode):  S_j = c_j R_j + b_j S_{j+1} with the
+// row constants c_j = mu_j a_1 .. a_{j-1}, so that S_1 equals the sum above;
+// then W = a_0 b_0 (u^ - i h S_1).
+template <class Lag, class PhaseB>
+__device__ __forceinline__ double2 horner_sep(const FsArgs& a, double2 uh, const double2 (&c)[FS_MAX_HIST + 1],
+                                              double2 a0, Lag lag, PhaseB phase_b) {
+    double2 S = zero2();
+#pragma unroll
+    for (int j = FS_MAX_HIST; j >= 1; --j) {
+        if (j <= a.nhist) {
+            if (j < FS_MAX_HIST && j < a.nhist)
+                S = cmul_add2(c[j], lag(j), phase_b(j), S);
+            else
+                S = cmul(c[j], lag(j));
+        }
+    }
+    return cmul(cmul(a0, phase_b(0)), uh + times_minus_i(S, a.h));
+}
+
 // u = y / (1 + i c)
 __device__ __forceinline__ double2 implicit_solve(double2 y, double c) {
     const double den = 1.0 + c * c;
@@ -221,10 +247,16 @@ __global__ void __launch_bounds__(FS_T) k_fs_row(FsArgs a, int flags) {
     }
     const double2* P0 = a.ax[0].P + (size_t)b * a.n_int * N0;
     const double2* P1 = ax.P + (size_t)b * a.n_int * N1;
-    double2 pa[FS_MAX_HIST];
+    double2 a0 = zero2(), cj[FS_MAX_HIST + 1];
+    if (begin) {
+        a0 = __ldg(&P0[(size_t)a.interval[0] * N0 + k0]);
+        double2 A = make_double2(1.0, 0.0);
 #pragma unroll
-    for (int i = 0; i < FS_MAX_HIST; ++i)
-        pa[i] = (begin && i < a.nhist) ? __ldg(&P0[(size_t)a.interval[i] * N0 + k0]) : zero2();
+        for (int j = 1; j <= FS_MAX_HIST; ++j) {
+            cj[j] = cscale(A, a.mu[j]);
+            if (j < FS_MAX_HIST && j < a.nhist) A = cmul(A, __ldg(&P0[(size_t)a.interval[j] * N0 + k0]));
+        }
+    }
     const double hm0 = a.h * a.mu[0];
     double2* ring = a.ring + (size_t)b * a.ring_slots * NPm + (size_t)k0 * N1;
     for (int m = threadIdx.x; m < N1; m += FS_T) {
@@ -238,13 +270,13 @@ __global__ void __launch_bounds__(FS_T) k_fs_row(FsArgs a, int flags) {
             uh = urow[m];
         }
         if (begin) {
-            const double2 W = horner(
-                a, uh,
+            const double2 W = horner_sep(
+                a, uh, cj, a0,
                 [&](int j) {
                     const int slot = a.hist_slot[j - 1];
                     return (end && slot == a.out_slot) ? F : ring[(size_t)slot * NPm + m];
                 },
-                [&](int i) { return cmul(pa[i], __ldg(&P1[(size_t)a.interval[i] * N1 + m])); });
+                [&](int i) { return __ldg(&P1[(size_t)a.interval[i] * N1 + m]); });
             urow[m] = W;
             Ln::stage_inv(m, W, E, dv, ax);
         }
