@@ -13,6 +13,10 @@ the per-step working set (~27 MB per instance in mixed precision) exceeds the
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
 bounded sample of the same workload instead.
 
+`--workload batch1d` measures 512 uneven 1D periodic instances (N drawn from
+256..16384, T = 1, dt = 1e-3, 1000 steps) stepped as one autotuned persistent
+launch per step replayed from a CUDA graph, mixed precision.
+
 `--workload free2d` measures the free-space scheme instead: bump-windowed
 Gaussians on [-1,1]^2, 256x256 grid, nu = 2048 per dimension (2058 contour
 modes per dimension), p = 8, q = 10, n_r = 1, H for eps = 1e-10, T = 1,
@@ -60,7 +64,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="periodic2d", choices=["periodic2d", "free2d"])
+    ap.add_argument("--workload", default="periodic2d", choices=["periodic2d", "free2d", "batch1d"])
     ap.add_argument("--profile-adams", type=int, default=0,
                     help="profiling run: start-up + this many Adams steps of the batch, then exit")
     return ap.parse_args()
@@ -621,6 +625,245 @@ def main_free(args, ws, rank, local):
     return 0
 
 
+# ------------------------------------------------------------ uneven 1D batch arm
+B1_COUNT, B1_DT, B1_NSTEPS = 512, 1e-3, 1000
+B1_METRIC = "point-steps/s (512 uneven 1D periodic instances, N in 256..16384, 8th-order, T=1, mixed)"
+B1_ALGO_BYTES = 16 + 7 * 8 + 4 + 16 + 8      # mixed 1D step: state in/out, 7 ring reads, 1 write, V
+
+
+def batch1d_instances(rank: int):
+    return [synth.periodic_1d_batch_member(i, seed=4 + 1000 * rank, dt=B1_DT, nsteps=B1_NSTEPS)
+            for i in range(B1_COUNT)]
+
+
+def run_batch1d(args, ws, rank, local):
+    import torch
+    from paper_2001_06113_gb300 import Batch, Problem
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    insts = batch1d_instances(rank)
+    groups = {}
+    for it in insts:
+        groups.setdefault(it.shape[0], []).append(it)
+    sizes = sorted(groups)
+    probs = [Problem((N,), B1_DT, B1_NSTEPS, batch=len(groups[N]), precision="mixed", stream=stream) for N in sizes]
+    pinned = {N: [(torch.from_numpy(it.V0).pin_memory(), torch.from_numpy(it.u0).pin_memory()) for it in groups[N]]
+              for N in sizes}
+
+    def load_inputs():
+        for N, pr in zip(sizes, probs):
+            for b, it in enumerate(groups[N]):
+                pr.set_potential(pinned[N][b][0], None, instance=b)
+                p = it.pulse
+                pr.set_pulse(p.A0, p.omega, p.T_pulse, p.direction, instance=b)
+                pr.set_initial(pinned[N][b][1], instance=b)
+
+    def reset():
+        for N, pr in zip(sizes, probs):
+            for b in range(len(groups[N])):
+                pr.set_initial(pinned[N][b][1], instance=b)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    load_inputs()
+    batch = Batch(probs, stream=stream)
+    default_shape = batch.describe()
+    batch.tune(5)
+    shape = batch.describe()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=torch.device("cuda", local))
+    reset()
+    for _ in range(args.warmup):
+        reset()
+        batch.step(B1_NSTEPS)
+    stream.synchronize()
+    points = sum(it.shape[0] for it in insts)
+    times = []
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                reset()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                batch.step(B1_NSTEPS)
+                e1.record(stream)
+            stream.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        torch.cuda.synchronize()
+        barrier()
+    t_solve = float(np.mean(times))
+    if ws > 1:
+        tt = torch.tensor([t_solve], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_solve = float(tt.item())
+    value = ws * points * B1_NSTEPS / t_solve
+    # per-step latency of the fused launch: events around single Adams steps (direct launches)
+    reset()
+    stream.synchronize()
+    dstream = torch.cuda.default_stream()
+    batch.step(STARTUP + 8, stream=dstream)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(101)]
+    with torch.cuda.stream(dstream):
+        evs[0].record(dstream)
+        for i in range(100):
+            batch.step(1, stream=dstream)
+            evs[i + 1].record(dstream)
+    dstream.synchronize()
+    dts = np.array([evs[i].elapsed_time(evs[i + 1]) / 1e3 for i in range(100)])
+    t_step = float(np.mean(dts))
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = B1_ALGO_BYTES * points / t_step / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "kernel": "k_periodic1d_multi (one persistent launch per Adams step for all 512 instances), "
+                          "timed per step over 100 steps",
+                "algorithmic_bytes_per_point_step": B1_ALGO_BYTES,
+                "step_ms_p50": round(float(np.percentile(dts, 50)) * 1e3, 4),
+                "step_ms_p99": round(float(np.percentile(dts, 99)) * 1e3, 4)}
+    # accuracy and the plain path: one instance per size up to 8192 solved alone in FP64
+    reset()
+    batch.step(B1_NSTEPS)
+    stream.synchronize()
+    errs, f64_points, f64_time = {}, 0, 0.0
+    for N, pr in zip(sizes, probs):
+        if N > 8192:
+            continue
+        it = groups[N][0]
+        ref = Problem((N,), B1_DT, B1_NSTEPS, precision="fp64")
+        ref.set_potential(it.V0)
+        p = it.pulse
+        ref.set_pulse(p.A0, p.omega, p.T_pulse, p.direction)
+        ref.set_initial(it.u0)
+        ref.step(1)                                  # warm
+        ref.set_initial(it.u0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ref.step(B1_NSTEPS)
+        torch.cuda.synchronize()
+        f64_time += time.perf_counter() - t0
+        f64_points += N * B1_NSTEPS
+        u_ref = ref.read_u(0)
+        u_mix = pr.read_u(0)
+        errs[N] = float(np.sqrt(np.sum(np.abs(u_mix - u_ref) ** 2) / np.sum(np.abs(u_ref) ** 2)))
+        ref.close()
+    e2e = None
+    if not args.no_e2e:
+        out = {N: torch.empty((len(groups[N]), N), dtype=torch.complex128).pin_memory() for N in sizes}
+        e2e_times = []
+        for _ in range(max(1, min(args.steps, 3))):
+            stream.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            load_inputs()
+            batch.step(B1_NSTEPS)
+            for N, pr in zip(sizes, probs):
+                pr.read_u(-1, out=out[N])
+            e2e_times.append(time.perf_counter() - t0)
+        te = float(np.mean(e2e_times))
+        e2e = {"value": ws * points * B1_NSTEPS / te, "unit": "point-steps/s",
+               "h2d_bytes_per_step": points * (8 + 16) + 2 * len(insts) * (8 * B1_NSTEPS + 1) * 8,
+               "d2h_bytes_per_step": points * 16}
+    batch.close()
+    for pr in probs:
+        pr.close()
+    return dict(value=value, t_solve=t_solve, roofline=roofline, e2e=e2e, clocks=clk.summary(), points=points,
+                sizes={int(N): len(groups[N]) for N in sizes}, shape=shape, default_shape=default_shape,
+                errs=errs, f64_one_at_a_time=f64_points / f64_time if f64_time else None)
+
+
+def batch1d_launches(shape_members: int) -> int:
+    """Launches of one 1000-step batch solve: per member init + start-up
+    (7 x (4 copies + 15 sub-steps + combine + refresh)) + change of frame,
+    then one fused launch per Adams step."""
+    per_member = 1 + STARTUP * (4 + 15 + 1 + 1) + 1
+    return shape_members * per_member + (B1_NSTEPS - STARTUP)
+
+
+def batch1d_oracle_sample(nadams: int = 20):
+    from oracle.periodic import oracle_for
+    it = synth.periodic_1d_batch_member(0, seed=4, dt=B1_DT, nsteps=B1_NSTEPS, sizes=(1024,))
+    orc = oracle_for(it)
+    u = it.u0
+    h0 = orc.fwd(orc.V(0.0) * u)
+    n0 = 100
+    hist = {n0 - j: h0 for j in range(1, ORDER)}
+    t0 = time.perf_counter()
+    for k in range(nadams):
+        n = n0 + k
+        t = n * B1_DT
+        u = orc.adams_step(u, t, hist, n)
+        hist[n] = orc.fwd(orc.V(t) * u)
+        hist.pop(n - ORDER, None)
+    el = time.perf_counter() - t0
+    return 1024 * nadams / el, el
+
+
+def main_batch1d(args, ws, rank, local):
+    import torch
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        for _ in range(args.warmup):
+            batch1d_oracle_sample(2)
+        vals = [batch1d_oracle_sample(20)[0] for _ in range(args.steps)]
+        value = float(np.mean(vals))
+        print(json.dumps({"impl": "reference", "metric": B1_METRIC, "value": value, "unit": "point-steps/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1e3 * 1024 * 20 / value, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "uneven 1D batch (CPU oracle sample: 20 Adams steps, N=1024)"},
+                          "cpu_baseline": {"value": value, "unit": "point-steps/s", "cores": cpu_cores(),
+                                           "kind": "oracle", "sample": "20 Adams steps of one N=1024 instance"},
+                          "e2e": {"value": value, "unit": "point-steps/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return 0
+    if ws > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    res = run_batch1d(args, ws, rank, local)
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and ws == 1:
+            v, el = batch1d_oracle_sample(60)
+            cpu = {"value": v, "unit": "point-steps/s", "cores": cpu_cores(), "kind": "oracle",
+                   "sample": f"60 8th-order Adams steps of one N=1024 instance ({el:.1f} s; direct DFT sums)"}
+        line = {
+            "metric": B1_METRIC, "value": res["value"], "unit": "point-steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["t_solve"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
+            "data": "synthetic",
+            "config": {"workload": f"512 uneven 1D periodic instances per GPU (N histogram {res['sizes']}), "
+                                   "T=1, dt=1e-3 (1000 steps), 8th-order Adams, mixed precision, one persistent "
+                                   "launch per Adams step, whole solve replayed from a CUDA graph",
+                       "points_per_gpu": res["points"], "nsteps": B1_NSTEPS, "dt": B1_DT, "order": ORDER,
+                       "launch_shape_tuned": res["shape"], "launch_shape_default": res["default_shape"],
+                       "l2": "flushed (256 MB write) before each timed solve; per-step working set "
+                             f"{res['points'] * 100 / 1e6:.0f} MB > L2",
+                       "step": "one whole solve (init, 7 Richardson start-up steps, 993 Adams steps)",
+                       "parallelism": f"replicas x{ws}"},
+            "rel_l2_vs_fp64": res["errs"],
+            "fp64_one_at_a_time_point_steps_per_s": res["f64_one_at_a_time"],
+            "time_to_solution_s": {"p50": res["t_solve"], "p99": res["t_solve"],
+                                   "note": "all instances of the batch finish together"},
+            "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
+            "gpu_launches": batch1d_launches(len(res["sizes"])) * args.steps,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -628,6 +871,8 @@ def main():
         args.batch = 1 if args.workload == "free2d" else 16
     if args.workload == "free2d":
         return main_free(args, ws, rank, local)
+    if args.workload == "batch1d":
+        return main_batch1d(args, ws, rank, local)
     if args.impl == "reference":
         if rank != 0:
             return 0

@@ -72,6 +72,7 @@ enum { TDSE_HOST = 0, TDSE_DEVICE = 1 };
  *              TDSE_FREE: free space, data supported in [-1,1]^dim, modes on
  *              the deformed contour Gamma (Sec. 3-4).
  *   n[2]       grid points per dimension (powers of two; periodic 1D: 8..8192,
+ *              and 16384 in TDSE_MIXED,
  *              periodic 2D: 8..1024 per dimension; free space: 32..512).
  *              n[1] is ignored for dim = 1.
  *   batch      number of independent instances that share n, dt, nsteps,
@@ -237,6 +238,47 @@ tdse_status tdse_adams_weights(int order, double* mu_out);
 #define TDSE_NOALLOC_MAX_POINTS 524288
 tdse_status tdse_modes_to_grid_2d_noalloc(const double* uhat, double* u, int n0, int n1, int batch,
                                           void* stream);
+
+/*
+ * Uneven batches (1D periodic, TDSE_MIXED).  Several contexts, each with its
+ * own n (8..16384) and its own batch of instances, but identical dt, nsteps,
+ * order and startup_steps, are stepped together:
+ *   - every Adams step of all of them is ONE persistent launch: a CTA of 512
+ *     threads takes work items, an item being `count` instances of one
+ *     context side by side, each transformed by a group of T threads (T and
+ *     the CTA count are the launch shape);
+ *   - the start (init, Richardson start-up, change of frame) of each member
+ *     runs with the member's own kernels;
+ *   - with a capturable stream (not the legacy NULL stream) the whole launch
+ *     sequence of one tdse_batch_step call is captured into a CUDA graph the
+ *     first time and replayed by later calls with the same start step and
+ *     length (e.g. after tdse_set_initial reset the members).
+ * The members stay owned by the caller and must outlive the batch; they must
+ * not be stepped on their own while in a batch.
+ */
+typedef struct tdse_batch tdse_batch;
+
+/* Group `count` (1..16) contexts.  Errors: TDSE_EINVAL (incompatible members,
+ * unbound workspace, more than 1536 work items), TDSE_EUNSUPPORTED (not 1D
+ * periodic mixed). */
+tdse_status tdse_batch_create(tdse_ctx* const* members, int count, tdse_batch** out);
+
+/* Autotuner: choose T per member (n/8 or n/16 threads per instance where both
+ * exist) and the CTA count by timing `trial_steps` launches of each candidate
+ * on `stream`.  The members must have V and u0 set; tuning runs their start
+ * if needed and leaves their state undefined: call tdse_set_initial on every
+ * member before the next tdse_batch_step.  Cached graphs are dropped. */
+tdse_status tdse_batch_tune(tdse_batch* b, int trial_steps, void* stream);
+
+/* Advance every member by nsteps (all members must be at the same step). */
+tdse_status tdse_batch_step(tdse_batch* b, int nsteps, void* stream);
+
+/* The launch shape as a JSON object (members' n, batch, T, instances per
+ * item; items; CTAs; shared memory; graphs cached; tuned or default). */
+tdse_status tdse_batch_describe(const tdse_batch* b, char* buf, size_t len);
+
+const char* tdse_batch_last_error(const tdse_batch* b);
+void tdse_batch_destroy(tdse_batch* b);
 
 /* Message of the last failing call on `ctx` ("" if none; static string if
  * ctx is NULL). */

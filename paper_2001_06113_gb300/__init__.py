@@ -17,7 +17,7 @@ import numpy as np
 from . import _native
 from ._native import DEVICE, FP64, FREE, HOST, MIXED, PERIODIC, TdseError
 
-__all__ = ["Problem", "TdseError", "adams_weights", "free_choose_H", "FP64", "MIXED", "PERIODIC", "FREE"]
+__all__ = ["Problem", "Batch", "TdseError", "adams_weights", "free_choose_H", "FP64", "MIXED", "PERIODIC", "FREE"]
 
 
 def _check(status: int, ctx=None):
@@ -242,3 +242,54 @@ class Problem:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Uneven batch of 1D periodic mixed-precision Problems stepped together
+    (``tdse_batch_*``): one persistent launch per Adams step for all members,
+    the whole step sequence of a call captured into a CUDA graph and replayed.
+    The members stay owned by the caller and must outlive the batch."""
+
+    def __init__(self, members: Sequence[Problem], stream=None):
+        self._lib = _native.lib()
+        self.members = list(members)
+        self._stream = stream if stream is not None else self.members[0]._stream
+        arr = (ctypes.c_void_p * len(self.members))(*[m._ctx.value for m in self.members])
+        self._b = ctypes.c_void_p()
+        st = self._lib.tdse_batch_create(arr, len(self.members), ctypes.byref(self._b))
+        if st != _native.TDSE_OK:
+            raise TdseError(st, "tdse_batch_create")
+
+    def _check(self, st):
+        if st != _native.TDSE_OK:
+            raw = self._lib.tdse_batch_last_error(self._b)
+            raise TdseError(st, raw.decode() if raw else "")
+
+    def tune(self, trial_steps: int = 5):
+        """Autotune the launch shape; afterwards every member needs set_initial."""
+        self._check(self._lib.tdse_batch_tune(self._b, int(trial_steps), _stream_handle(self._stream)))
+
+    def step(self, n: int, stream=None):
+        """Advance all members n steps on the batch's stream (or `stream`).  On a
+        side stream the launch sequence is captured into a CUDA graph the first
+        time and replayed afterwards; on the legacy default stream it is launched
+        directly."""
+        s = self._stream if stream is None else stream
+        self._check(self._lib.tdse_batch_step(self._b, int(n), _stream_handle(s)))
+
+    def describe(self) -> dict:
+        import json
+        buf = ctypes.create_string_buffer(8192)
+        self._check(self._lib.tdse_batch_describe(self._b, buf, len(buf)))
+        return json.loads(buf.value.decode())
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.tdse_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -3,7 +3,9 @@
 // interval schedule) and the launch sequence of each time step.
 #include "tdse.h"
 
+#include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -140,6 +142,7 @@ static void plan_workspace(tdse_ctx* c) {
     c->off.tw32lo_0 = take((size_t)c->n0 * 8);
     c->off.tw32lo_1 = take((size_t)(c->d == 2 ? c->n1 : 1) * 8);
     c->off.iv = take((size_t)c->n_int * sizeof(int2));
+    c->off.tw128 = c->d == 1 && c->n0 > 8192 ? take(128 * 16) : 0;
     c->off.scratch = take(256);
     c->off.end = o;
     c->ws_need = o;
@@ -263,7 +266,8 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     if (S < cfg->order - 2) return TDSE_EINVAL;
     const int n0 = cfg->n[0], n1 = cfg->dim == 2 ? cfg->n[1] : 1;
     if (!is_pow2(n0) || (cfg->dim == 2 && !is_pow2(n1))) return TDSE_EINVAL;
-    if (!fs && cfg->dim == 1 && !periodic1d_supported(n0)) return TDSE_EUNSUPPORTED;
+    const bool big1d = !fs && cfg->dim == 1 && cfg->precision == TDSE_MIXED && n0 == four_step_n();
+    if (!fs && cfg->dim == 1 && !periodic1d_supported(n0) && !big1d) return TDSE_EUNSUPPORTED;
     if (!fs && cfg->dim == 2 && !periodic2d_supported(n0, n1)) return TDSE_EUNSUPPORTED;
     if (fs && cfg->precision != TDSE_FP64) return TDSE_EUNSUPPORTED;
     if ((long long)cfg->nsteps * SUB + 1 > (1LL << 30)) return TDSE_EINVAL;
@@ -368,6 +372,7 @@ tdse_status tdse_bind_workspace(tdse_ctx* c, void* dev, size_t bytes, void* stre
         TDSE_CK(c, launch_kin1d(opt<double2>(c, c->off.kin64), opt<float4>(c, c->off.kinff), c->n0, c->L, c->cfg.dt, s));
     if (c->d == 1 && c->mixed)
         TDSE_CK(c, launch_k1d(c->P<float2>(c->off.k1lo), c->P<float2>(c->off.k1hi), c->nhi, c->n0, c->cfg.dt, s));
+    if (c->off.tw128) TDSE_CK(c, launch_four_step_tables(c->P<double2>(c->off.tw128), s));
     }
     // defaults: A == 0 (phi == 0), f(t) == 1
     TDSE_CK(c, cudaMemsetAsync(c->P<double>(c->off.phi), 0, (size_t)c->B * c->d * c->ntf * 8, s));
@@ -496,7 +501,10 @@ static tdse_status do_init(tdse_ctx* c, cudaStream_t s) {
     a.mode = MODE_INIT;
     a.out_slot = slot_of(c, 0);
     a.tf = 0;
-    TDSE_CK(c, run(c, a, f64_combo(c), s));
+    if (c->off.tw128)
+        TDSE_CK(c, launch_four_step_init(a, c->P<double2>(c->off.tw128), s));
+    else
+        TDSE_CK(c, run(c, a, f64_combo(c), s));
     c->inited = true;
     return TDSE_OK;
 }
@@ -683,7 +691,10 @@ tdse_status tdse_read_u(tdse_ctx* c, int instance, double* u_out, int where, voi
         a.phi = c->P<double>(c->off.phi) + (size_t)lo * c->d * c->ntf;
         a.ip = c->ip ? 1 : 0;
         a.e_step = c->step;
-        TDSE_CK(c, run(c, a, f64_combo(c), s));
+        if (c->off.tw128)
+            TDSE_CK(c, launch_four_step_read(a, c->P<double2>(c->off.tw128), s));
+        else
+            TDSE_CK(c, run(c, a, f64_combo(c), s));
         src = a.aux2;
     }
     const cudaMemcpyKind kind = where == TDSE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
@@ -733,5 +744,377 @@ const char* tdse_last_error(const tdse_ctx* c) {
 }
 
 void tdse_destroy(tdse_ctx* c) { delete c; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Uneven batches: one persistent launch per Adams step for all members.
+struct tdse_batch {
+    std::vector<tdse_ctx*> m;
+    std::vector<int> var;           // launch variant per member
+    int grid = 0;                   // persistent CTAs
+    int sms = 0;
+    bool tuned = false;
+    size_t smem = 0;
+    std::vector<MultiItem> items;
+    MultiArgs1D args{};             // reused launch argument block (22 KB)
+    struct Graph {
+        int from, n;
+        bool inited;
+        cudaGraphExec_t exec;
+        std::vector<int> step;
+        std::vector<char> inited_after, ip_after;
+    };
+    std::vector<Graph> graphs;
+    std::string err;
+    tdse_status fail(tdse_status s, const std::string& msg) {
+        err = msg;
+        return s;
+    }
+};
+
+static int default_threads_1d(int n) { return n / 8 < 32 ? 32 : (n / 8 > MULTI_CTA ? MULTI_CTA : n / 8); }
+
+static void drop_graphs(tdse_batch* b) {
+    for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+    b->graphs.clear();
+}
+
+// Work items (cost-descending so that the CTA-strided assignment starts with
+// the largest) and the launch's shared memory.
+static tdse_status build_items(tdse_batch* b) {
+    b->items.clear();
+    b->smem = 0;
+    for (size_t g = 0; g < b->m.size(); ++g) {
+        const tdse_ctx* c = b->m[g];
+        const int var = b->var[g];
+        const int per = MULTI_CTA / multi_variant_t(var);
+        for (int b0 = 0; b0 < c->B; b0 += per) {
+            MultiItem it{};
+            it.g = (unsigned char)g;
+            it.var = (unsigned char)var;
+            it.count = (unsigned short)std::min(per, c->B - b0);
+            it.b0 = b0;
+            b->items.push_back(it);
+            b->smem = std::max(b->smem, multi_item_smem(var, it.count));
+        }
+    }
+    if (b->items.size() > (size_t)MULTI_MAX_ITEMS) return b->fail(TDSE_EINVAL, "more than 1536 work items");
+    auto cost = [&](const MultiItem& it) {
+        const double n = multi_variant_n(it.var);
+        return n * std::log2(n) * it.count;
+    };
+    std::stable_sort(b->items.begin(), b->items.end(),
+                     [&](const MultiItem& x, const MultiItem& y) { return cost(x) > cost(y); });
+    b->args.nitems = (int)b->items.size();
+    std::copy(b->items.begin(), b->items.end(), b->args.items);
+    return TDSE_OK;
+}
+
+static int default_grid(tdse_batch* b) {
+    const int occ = std::max(1, multi_occupancy(b->smem));
+    return std::max(1, std::min((int)b->items.size(), b->sms * occ));
+}
+
+static tdse_status batch_prepare(tdse_batch* b) {
+    cudaError_t e = multi_prepare(b->smem);
+    for (tdse_ctx* c : b->m) {
+        if (e == cudaSuccess) e = periodic1d_prepare(c->n0, COMBO_F32);
+        if (e == cudaSuccess && !c->off.tw128) e = periodic1d_prepare(c->n0, COMBO_F64_R32);
+    }
+    if (e != cudaSuccess) return b->fail(TDSE_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+    return TDSE_OK;
+}
+
+static tdse_status member_status(tdse_batch* b, tdse_ctx* c, tdse_status st) {
+    if (st != TDSE_OK) return b->fail(st, "member: " + c->err);
+    return TDSE_OK;
+}
+
+// One Adams step n of every member as one launch.
+static tdse_status batch_adams(tdse_batch* b, int n, int grid, cudaStream_t s) {
+    for (size_t g = 0; g < b->m.size(); ++g) b->args.args[g] = adams_args(b->m[g], n);
+    cudaError_t e = launch_periodic1d_multi(b->args, grid, b->smem, s);
+    if (e != cudaSuccess) return b->fail(TDSE_ECUDA, std::string("multi launch: ") + cudaGetErrorString(e));
+    for (tdse_ctx* c : b->m) c->step = n;
+    return TDSE_OK;
+}
+
+// The launch sequence of nsteps steps (no capture logic).
+static tdse_status batch_run(tdse_batch* b, int nsteps, cudaStream_t s) {
+    for (tdse_ctx* c : b->m)
+        if (!c->inited) {
+            tdse_status st = member_status(b, c, do_init(c, s));
+            if (st != TDSE_OK) return st;
+        }
+    int k = 0;
+    while (k < nsteps) {
+        const int n = b->m[0]->step + 1;
+        if (n <= b->m[0]->S) {
+            for (tdse_ctx* c : b->m) {
+                tdse_status st = member_status(b, c, startup_step(c, n, s));
+                if (st != TDSE_OK) return st;
+                c->step = n;
+            }
+            ++k;
+            continue;
+        }
+        for (tdse_ctx* c : b->m)
+            if (!c->ip) {
+                tdse_status st = member_status(b, c, enter_interaction(c, c->step, s));
+                if (st != TDSE_OK) return st;
+            }
+        tdse_status st = batch_adams(b, n, b->grid, s);
+        if (st != TDSE_OK) return st;
+        ++k;
+    }
+    return TDSE_OK;
+}
+
+static tdse_status batch_check(tdse_batch* b, int nsteps) {
+    const tdse_ctx* c0 = b->m[0];
+    for (tdse_ctx* c : b->m) {
+        if (!c->ws) return b->fail(TDSE_ESTATE, "member workspace not bound");
+        for (int i = 0; i < c->B; ++i)
+            if (!c->have_V[i] || !c->have_u0[i]) return b->fail(TDSE_ESTATE, "member instance lacks V or u0");
+        if (c->step != c0->step || c->inited != c0->inited || c->ip != c0->ip)
+            return b->fail(TDSE_ESTATE, "members are not at the same step");
+        if (c->step + nsteps > c->cfg.nsteps) return b->fail(TDSE_EINVAL, "beyond the nsteps the tables cover");
+    }
+    return TDSE_OK;
+}
+
+extern "C" {
+
+tdse_status tdse_batch_create(tdse_ctx* const* members, int count, tdse_batch** out) {
+    if (!members || !out || count < 1) return TDSE_EINVAL;
+    *out = nullptr;
+    if (count > MULTI_MAX_GROUPS) return TDSE_EINVAL;
+    const tdse_ctx* c0 = members[0];
+    if (!c0) return TDSE_EINVAL;
+    for (int g = 0; g < count; ++g) {
+        const tdse_ctx* c = members[g];
+        if (!c || !c->ws) return TDSE_EINVAL;
+        for (int h = 0; h < g; ++h)
+            if (members[h] == c) return TDSE_EINVAL;
+        if (c->fs || c->d != 1 || !c->mixed) return TDSE_EUNSUPPORTED;
+        if (c->cfg.dt != c0->cfg.dt || c->cfg.nsteps != c0->cfg.nsteps || c->cfg.order != c0->cfg.order ||
+            c->S != c0->S)
+            return TDSE_EINVAL;
+        if (multi_variant(c->n0, default_threads_1d(c->n0)) < 0) return TDSE_EUNSUPPORTED;
+    }
+    tdse_batch* b = new (std::nothrow) tdse_batch();
+    if (!b) return TDSE_ENOMEM;
+    b->m.assign(members, members + count);
+    for (tdse_ctx* c : b->m) b->var.push_back(multi_variant(c->n0, default_threads_1d(c->n0)));
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        b->sms = 1;
+    if (build_items(b) != TDSE_OK) {
+        delete b;
+        return TDSE_EINVAL;
+    }
+    if (batch_prepare(b) != TDSE_OK) {
+        delete b;
+        return TDSE_ECUDA;
+    }
+    b->grid = default_grid(b);
+    *out = b;
+    return TDSE_OK;
+}
+
+tdse_status tdse_batch_step(tdse_batch* b, int nsteps, void* stream) {
+    if (!b) return TDSE_EINVAL;
+    if (nsteps < 0) return b->fail(TDSE_EINVAL, "negative step count");
+    tdse_status st = batch_check(b, nsteps);
+    if (st != TDSE_OK || nsteps == 0) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (s == nullptr || s == cudaStreamLegacy) return batch_run(b, nsteps, s);   // not capturable
+    const int from = b->m[0]->step;
+    const bool inited = b->m[0]->inited;
+    for (auto& g : b->graphs)
+        if (g.from == from && g.n == nsteps && g.inited == inited) {
+            cudaError_t e = cudaGraphLaunch(g.exec, s);
+            if (e != cudaSuccess) return b->fail(TDSE_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+            for (size_t i = 0; i < b->m.size(); ++i) {
+                b->m[i]->step = g.step[i];
+                b->m[i]->inited = g.inited_after[i];
+                b->m[i]->ip = g.ip_after[i];
+            }
+            return TDSE_OK;
+        }
+    st = batch_prepare(b);
+    if (st != TDSE_OK) return st;
+    std::vector<int> step0;
+    std::vector<char> init0, ip0;
+    for (tdse_ctx* c : b->m) {
+        step0.push_back(c->step);
+        init0.push_back(c->inited);
+        ip0.push_back(c->ip);
+    }
+    auto restore = [&]() {
+        for (size_t i = 0; i < b->m.size(); ++i) {
+            b->m[i]->step = step0[i];
+            b->m[i]->inited = init0[i];
+            b->m[i]->ip = ip0[i];
+        }
+    };
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return b->fail(TDSE_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+    st = batch_run(b, nsteps, s);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(s, &graph);
+    if (st != TDSE_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        restore();
+        return st != TDSE_OK ? st : b->fail(TDSE_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+    }
+    tdse_batch::Graph g{from, nsteps, inited, nullptr, {}, {}, {}};
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        restore();
+        return b->fail(TDSE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    for (tdse_ctx* c : b->m) {
+        g.step.push_back(c->step);
+        g.inited_after.push_back(c->inited);
+        g.ip_after.push_back(c->ip);
+    }
+    b->graphs.push_back(g);
+    e = cudaGraphLaunch(g.exec, s);
+    if (e != cudaSuccess) return b->fail(TDSE_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    return TDSE_OK;
+}
+
+tdse_status tdse_batch_tune(tdse_batch* b, int trial_steps, void* stream) {
+    if (!b || trial_steps < 1) return TDSE_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    tdse_status st = batch_check(b, 0);
+    if (st != TDSE_OK) return st;
+    drop_graphs(b);
+    // reach the Adams phase (start of every member, then the change of frame)
+    const int S = b->m[0]->S;
+    if (b->m[0]->step < S || !b->m[0]->inited) {
+        st = batch_run(b, S - b->m[0]->step, s);
+        if (st != TDSE_OK) return st;
+    }
+    for (tdse_ctx* c : b->m)
+        if (!c->ip) {
+            st = member_status(b, c, enter_interaction(c, c->step, s));
+            if (st != TDSE_OK) return st;
+        }
+    if (b->m[0]->step >= b->m[0]->cfg.nsteps) return b->fail(TDSE_EINVAL, "no step left to time");
+    const int n = b->m[0]->step + 1;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return b->fail(TDSE_ECUDA, "event create");
+    // time `trial_steps` launches of step n (state is overwritten repeatedly)
+    auto timed = [&](float& ms) -> tdse_status {
+        tdse_status r = build_items(b);
+        if (r != TDSE_OK) return r;
+        r = batch_prepare(b);
+        if (r != TDSE_OK) return r;
+        r = batch_adams(b, n, b->grid, s);
+        if (r != TDSE_OK) return r;
+        cudaEventRecord(e0, s);
+        for (int i = 0; i < trial_steps; ++i) {
+            r = batch_adams(b, n, b->grid, s);
+            if (r != TDSE_OK) return r;
+        }
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return b->fail(TDSE_ECUDA, "event sync");
+        cudaEventElapsedTime(&ms, e0, e1);
+        for (tdse_ctx* c : b->m) c->step = n - 1;
+        return TDSE_OK;
+    };
+    float best = 0;
+    b->grid = 0;
+    st = build_items(b);
+    if (st == TDSE_OK) {
+        b->grid = default_grid(b);
+        st = timed(best);
+    }
+    // threads per instance, member by member
+    for (size_t g = 0; g < b->m.size() && st == TDSE_OK; ++g) {
+        const int nn = b->m[g]->n0;
+        for (int t : {nn / 16, nn / 8}) {
+            const int v = multi_variant(nn, t);
+            if (v < 0 || v == b->var[g]) continue;
+            const int keep = b->var[g], keep_grid = b->grid;
+            b->var[g] = v;
+            st = build_items(b);
+            if (st != TDSE_OK) break;
+            b->grid = default_grid(b);
+            float ms = 0;
+            st = timed(ms);
+            if (st != TDSE_OK) break;
+            if (ms < best) {
+                best = ms;
+            } else {
+                b->var[g] = keep;
+                b->grid = keep_grid;
+            }
+        }
+    }
+    // CTA count: multiples of the SM count up to one CTA per item
+    if (st == TDSE_OK) st = build_items(b);
+    if (st == TDSE_OK) {
+        const int occ = std::max(1, multi_occupancy(b->smem));
+        const int keep = b->grid;
+        int best_grid = keep;
+        for (int k = 1; k <= occ * 2 && st == TDSE_OK; ++k) {
+            const int grid = std::min((int)b->items.size(), b->sms * k);
+            if (grid == keep) continue;
+            b->grid = grid;
+            float ms = 0;
+            st = timed(ms);
+            if (st == TDSE_OK && ms < best) {
+                best = ms;
+                best_grid = grid;
+            }
+            if (grid == (int)b->items.size()) break;
+        }
+        b->grid = best_grid;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != TDSE_OK) return st;
+    for (tdse_ctx* c : b->m) {
+        std::fill(c->have_u0.begin(), c->have_u0.end(), 0);   // state undefined until tdse_set_initial
+        c->step = 0;
+        c->inited = false;
+        c->ip = false;
+    }
+    b->tuned = true;
+    return TDSE_OK;
+}
+
+tdse_status tdse_batch_describe(const tdse_batch* b, char* buf, size_t len) {
+    if (!b || !buf || len == 0) return TDSE_EINVAL;
+    std::string js = "{\"grid\": " + std::to_string(b->grid) + ", \"sms\": " + std::to_string(b->sms) +
+                     ", \"items\": " + std::to_string(b->items.size()) + ", \"smem\": " + std::to_string(b->smem) +
+                     ", \"graphs\": " + std::to_string(b->graphs.size()) + ", \"tuned\": " +
+                     (b->tuned ? "true" : "false") + ", \"members\": [";
+    for (size_t g = 0; g < b->m.size(); ++g) {
+        const int t = multi_variant_t(b->var[g]);
+        js += std::string(g ? ", " : "") + "{\"n\": " + std::to_string(b->m[g]->n0) + ", \"batch\": " +
+              std::to_string(b->m[g]->B) + ", \"threads\": " + std::to_string(t) + ", \"per_item\": " +
+              std::to_string(MULTI_CTA / t) + "}";
+    }
+    js += "]}";
+    if (js.size() + 1 > len) return TDSE_EINVAL;
+    std::memcpy(buf, js.c_str(), js.size() + 1);
+    return TDSE_OK;
+}
+
+const char* tdse_batch_last_error(const tdse_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void tdse_batch_destroy(tdse_batch* b) {
+    if (!b) return;
+    drop_graphs(b);
+    delete b;
+}
 
 }  // extern "C"

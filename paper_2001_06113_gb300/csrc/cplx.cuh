@@ -152,9 +152,23 @@ template <bool INV> __device__ __forceinline__ float2 twiddle(float2 v, const fl
     return t;
 }
 
-// L interleaved length-N transforms by T threads; element (pos, line) at
-// buf[pos * PS + line].  Item it of a pass with NB butterflies is butterfly
-// j = it / L of line it % L.
+// Barrier policies for a group of threads that runs one transform: the whole
+// CTA, one warp, or a named barrier over n threads (a multiple of 32) when
+// several groups share a CTA.
+struct CtaSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct WarpSync {
+    __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+struct GroupSync {
+    unsigned id, n;
+    __device__ __forceinline__ void operator()() const { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+};
+
+// L interleaved length-N transforms by T threads (thread index tid in 0..T-1
+// of the group, barrier `sync`); element (pos, line) at buf[pos * PS + line].
+// Item it of a pass with NB butterflies is butterfly j = it / L of line it % L.
 template <class C, int N, int L, int PS, int T, bool INV>
 struct Fft {
     using Plan = FftPlan<N, INV>;
@@ -166,15 +180,16 @@ struct Fft {
     static constexpr int PF = (NBF * L + T - 1) / T;
     static constexpr int PL = (NBL * L + T - 1) / T;
 
-    __device__ static __forceinline__ bool item(int p, int NB, int& j, int& line) {
-        const int it = threadIdx.x + p * T;
+    __device__ static __forceinline__ bool item(int p, int NB, int& j, int& line, int tid) {
+        const int it = tid + p * T;
         line = it % L;
         j = it / L;
         return ((NB * L) % T == 0) || it < NB * L;
     }
 
-    template <int S>
-    __device__ static __forceinline__ void mid_pass(C* buf, const C* __restrict__ tw, const C* __restrict__ twl) {
+    template <int S, class Sync>
+    __device__ static __forceinline__ void mid_pass(C* buf, const C* __restrict__ tw, const C* __restrict__ twl,
+                                                    int tid, const Sync& sync) {
         constexpr int R = Plan::radix(S);
         constexpr int Ns = Plan::ns(S);
         constexpr int NB = N / R;
@@ -183,16 +198,16 @@ struct Fft {
 #pragma unroll
         for (int p = 0; p < PER; ++p) {
             int j, line;
-            if (item(p, NB, j, line)) {
+            if (item(p, NB, j, line, tid)) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) v[p][r] = buf[(j + r * NB) * PS + line];
             }
         }
-        __syncthreads();
+        sync();
 #pragma unroll
         for (int p = 0; p < PER; ++p) {
             int j, line;
-            if (item(p, NB, j, line)) {
+            if (item(p, NB, j, line, tid)) {
                 const int k = j & (Ns - 1);
                 constexpr int stride = N / (Ns * R);
 #pragma unroll
@@ -203,22 +218,25 @@ struct Fft {
                 for (int r = 0; r < R; ++r) buf[(base + r * Ns) * PS + line] = v[p][r];
             }
         }
-        __syncthreads();
+        sync();
     }
 
-    template <int S>
-    __device__ static __forceinline__ void mids(C* buf, const C* __restrict__ tw, const C* __restrict__ twl) {
+    template <int S, class Sync>
+    __device__ static __forceinline__ void mids(C* buf, const C* __restrict__ tw, const C* __restrict__ twl, int tid,
+                                                const Sync& sync) {
         if constexpr (S <= NPASS - 2) {
-            mid_pass<S>(buf, tw, twl);
-            mids<S + 1>(buf, tw, twl);
+            mid_pass<S>(buf, tw, twl, tid, sync);
+            mids<S + 1>(buf, tw, twl, tid, sync);
         }
     }
 
     // in[p][r]: value at position j + r NBF of the item (p); out[p][r]: result at
-    // position j + r NBL.  buf must not be in use by any thread on entry; the
-    // call ends with a barrier (buf free again).
+    // position j + r NBL.  buf must not be in use by any thread of the group on
+    // entry; the call ends with a barrier (buf free again).
+    template <class Sync>
     __device__ static __forceinline__ void run(C (&in)[PF][RF], C (&out)[PL][RL], C* buf,
-                                               const C* __restrict__ tw, const C* __restrict__ twl) {
+                                               const C* __restrict__ tw, const C* __restrict__ twl, int tid,
+                                               const Sync& sync) {
         if constexpr (NPASS == 1) {
 #pragma unroll
             for (int p = 0; p < PF; ++p) {
@@ -230,18 +248,18 @@ struct Fft {
 #pragma unroll
             for (int p = 0; p < PF; ++p) {
                 int j, line;
-                if (item(p, NBF, j, line)) {
+                if (item(p, NBF, j, line, tid)) {
                     dft_r<RF, INV>(in[p]);
 #pragma unroll
                     for (int r = 0; r < RF; ++r) buf[(j * RF + r) * PS + line] = in[p][r];
                 }
             }
-            __syncthreads();
-            mids<1>(buf, tw, twl);
+            sync();
+            mids<1>(buf, tw, twl, tid, sync);
 #pragma unroll
             for (int p = 0; p < PL; ++p) {
                 int j, line;
-                if (item(p, NBL, j, line)) {
+                if (item(p, NBL, j, line, tid)) {
 #pragma unroll
                     for (int r = 0; r < RL; ++r) out[p][r] = buf[(j + r * NBL) * PS + line];
 #pragma unroll
@@ -249,63 +267,8 @@ struct Fft {
                     dft_r<RL, INV>(out[p]);
                 }
             }
-            __syncthreads();
+            sync();
         }
-    }
-};
-
-// ---------------------------------------------------------------------------
-// One length-N transform per warp on warp-private lines of shared memory:
-// element x at line[lpos(x)], lpos(x) = x + x/8 (one pad slot per 8 elements,
-// so that both the unit-stride reads and the stride-R writes of a pass are
-// free of bank conflicts).  Same Stockham passes and radix plan as Fft.  The
-// passes alternate between two lines (ping-pong), so each butterfly is read,
-// transformed and written before the next one: one butterfly's values live
-// in registers at a time, and only __syncwarp separates passes.  run() returns
-// the line holding the result (a or b).  On entry line a holds the input and
-// every lane of the warp must have finished writing it.
-__device__ __forceinline__ int lpos(int x) { return x + (x >> 3); }
-template <int N> constexpr int line_len() { return N + N / 8 + 1; }
-
-template <class C, int N, bool INV>
-struct WarpFft {
-    using Plan = FftPlan<N, INV>;
-    static constexpr bool RESULT_IN_B = (Plan::NPASS % 2) == 1;
-    template <int S>
-    __device__ static __forceinline__ C* pass(C* src, C* dst, const C* __restrict__ tw,
-                                              const C* __restrict__ twl, int lane) {
-        if constexpr (S < Plan::NPASS) {
-            constexpr int R = Plan::radix(S);
-            constexpr int Ns = Plan::ns(S);
-            constexpr int NB = N / R;
-            constexpr int PER = (NB + 31) / 32;
-#pragma unroll 1
-            for (int p = 0; p < PER; ++p) {
-                const int j = lane + 32 * p;
-                if (NB % 32 == 0 || j < NB) {
-                    C v[R];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) v[r] = src[lpos(j + r * NB)];
-                    const int k = j & (Ns - 1);
-                    constexpr int stride = N / (Ns * R);
-                    if (Ns > 1) {
-#pragma unroll
-                        for (int r = 1; r < R; ++r) v[r] = twiddle<INV>(v[r], tw, twl, k * r * stride);
-                    }
-                    dft_r<R, INV>(v);
-                    const int base = (j - k) * R + k;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) dst[lpos(base + r * Ns)] = v[r];
-                }
-            }
-            __syncwarp();
-            return pass<S + 1>(dst, src, tw, twl, lane);
-        } else {
-            return src;
-        }
-    }
-    __device__ static __forceinline__ C* run(C* a, C* b, const C* __restrict__ tw, const C* __restrict__ twl) {
-        return pass<0>(a, b, tw, twl, threadIdx.x & 31);
     }
 };
 

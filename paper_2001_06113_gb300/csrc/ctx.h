@@ -57,7 +57,8 @@ struct tdse_ctx {
     size_t ws_need = 0;
     struct {
         size_t uhat, ring, chain_uhat, chain_ring, aux, aux2, V0, V0f, tfac, phi, kin64, kinff, adv64, advff,
-            q64, qff, e2d, k1lo, k1hi, a1d, tw64_0, tw32_0, tw64_1, tw32_1, tw32lo_0, tw32lo_1, iv, scratch, end;
+            q64, qff, e2d, k1lo, k1hi, a1d, tw64_0, tw32_0, tw64_1, tw32_1, tw32lo_0, tw32lo_1, iv, tw128, scratch,
+            end;
     } off{};
     std::vector<char> have_V, have_u0;
     int step = 0;

@@ -97,6 +97,42 @@ cudaError_t launch_periodic2d_part(const KArgs& a, int combo, int part, cudaStre
 enum Part2D : int { PART_COL_BEGIN = 0, PART_ROW_MID = 1, PART_COL_END = 2, PART_COL_FUSED = 3 };
 bool periodic1d_supported(int n);
 bool periodic2d_supported(int n0, int n1);
+// One-time kernel attributes of the 1D step for n and combo (before stream capture).
+cudaError_t periodic1d_prepare(int n, int combo);
+
+// ---- uneven 1D batches: one persistent launch for many contexts (mixed steps)
+// A CTA of MULTI_CTA threads takes items i = blockIdx.x, + gridDim.x, ...; an
+// item runs `count` instances of one context with the launch variant `var`
+// (N and T = threads per instance), count <= MULTI_CTA / T, side by side.
+constexpr int MULTI_CTA = 512;
+constexpr int MULTI_MAX_GROUPS = 16;
+constexpr int MULTI_MAX_ITEMS = 1536;
+struct MultiItem {
+    unsigned char g;          // context (index into args)
+    unsigned char var;        // launch variant (multi_variant_n / multi_variant_t)
+    unsigned short count;     // instances in the item
+    int b0;                   // first instance
+};
+struct MultiArgs1D {
+    int nitems;
+    KArgs args[MULTI_MAX_GROUPS];
+    MultiItem items[MULTI_MAX_ITEMS];
+};
+constexpr int MULTI_NVAR = 16;
+int multi_variant_n(int var);
+int multi_variant_t(int var);
+int multi_variant(int n, int t);            // -1 if not built
+size_t multi_item_smem(int var, int count);
+cudaError_t multi_prepare(size_t smem);
+int multi_occupancy(size_t smem);           // resident CTAs per SM (0 on error)
+cudaError_t launch_periodic1d_multi(const MultiArgs1D& m, int grid, size_t smem, cudaStream_t s);
+// Largest n of the 1D FP32 step kernels (larger than periodic1d_supported's
+// limit: FP64 init / read-out of such sizes go through launch_fft64_four_step).
+constexpr int P1D_MAX_F32 = 16384;
+int four_step_n();                                   // 128 * 128
+cudaError_t launch_four_step_tables(double2* tw128, cudaStream_t s);
+cudaError_t launch_four_step_init(const KArgs& a, const double2* tw128, cudaStream_t s);
+cudaError_t launch_four_step_read(const KArgs& a, const double2* tw128, cudaStream_t s);
 
 // Table builders (tables.cu).
 cudaError_t launch_twiddles(double2* tw64, float2* tw32, float2* tw32lo, int n, cudaStream_t s);

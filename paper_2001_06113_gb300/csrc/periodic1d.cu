@@ -16,9 +16,10 @@ namespace tdse {
 
 constexpr int threads_1d(int N) { return N / 8 < 32 ? 32 : (N / 8 > 512 ? 512 : N / 8); }
 
-template <class C, class RT, int N>
-__global__ void __launch_bounds__(threads_1d(N)) k_periodic1d(const KArgs a) {
-    constexpr int T = threads_1d(N);
+// The step of one instance b by a group of T threads (index tid, barrier sync)
+// with the N-element transform buffer buf in shared memory.
+template <class C, class RT, int N, int T, class Sync>
+__device__ __forceinline__ void step1d(const KArgs& a, const int b, const int tid, const Sync& sync, C* buf) {
     using FI = Fft<C, N, 1, 1, T, true>;     // inverse transform (modes -> grid)
     using FW = Fft<C, N, 1, 1, T, false>;    // forward transform (grid -> modes)
     static_assert(FI::RL == FW::RF && FI::PL == FW::PF, "inverse output regs feed forward input regs");
@@ -29,10 +30,6 @@ __global__ void __launch_bounds__(threads_1d(N)) k_periodic1d(const KArgs a) {
     constexpr bool FF = !is_f64<RT>::value;  // double-float state
     using ST = state_t<RT>;
     using R = typename cx_traits<C>::real;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
-
-    const int b = blockIdx.x;
     const size_t NP = N;
     ST* st = reinterpret_cast<ST*>(a.uhat) + (size_t)b * NP;
     RT* ringb = reinterpret_cast<RT*>(a.ring) + (size_t)b * a.ring_slots * NP;
@@ -67,7 +64,7 @@ __global__ void __launch_bounds__(threads_1d(N)) k_periodic1d(const KArgs a) {
 #pragma unroll
             for (int p = 0; p < FW::PF; ++p) {
                 int j, line;
-                if (FW::item(p, FW::NBF, j, line)) {
+                if (FW::item(p, FW::NBF, j, line, tid)) {
 #pragma unroll
                     for (int r = 0; r < FW::RF; ++r) {
                         const int x = j + r * FW::NBF;
@@ -76,11 +73,11 @@ __global__ void __launch_bounds__(threads_1d(N)) k_periodic1d(const KArgs a) {
                     }
                 }
             }
-            FW::run(in, out, buf, tw, twl);
+            FW::run(in, out, buf, tw, twl, tid, sync);
 #pragma unroll
             for (int p = 0; p < FW::PL; ++p) {
                 int j, line;
-                if (FW::item(p, FW::NBL, j, line)) {
+                if (FW::item(p, FW::NBL, j, line, tid)) {
 #pragma unroll
                     for (int r = 0; r < FW::RL; ++r) {
                         const int k = j + r * FW::NBL;
@@ -89,13 +86,13 @@ __global__ void __launch_bounds__(threads_1d(N)) k_periodic1d(const KArgs a) {
                     }
                 }
             }
-            if (pass == 0) __syncthreads();   // every thread has read u0 before any state write
+            if (pass == 0) sync();   // every thread has read u0 before any state write
         }
         // the last forward result is still in registers: write the state
 #pragma unroll
         for (int p = 0; p < FW::PL; ++p) {
             int j, line;
-            if (FW::item(p, FW::NBL, j, line)) {
+            if (FW::item(p, FW::NBL, j, line, tid)) {
 #pragma unroll
                 for (int r = 0; r < FW::RL; ++r)
                     st[j + r * FW::NBL] = d_to_st<ST>(cvt<double2>(cscale(out[p][r], scale)));
@@ -109,7 +106,7 @@ __global__ void __launch_bounds__(threads_1d(N)) k_periodic1d(const KArgs a) {
 #pragma unroll
         for (int p = 0; p < FI::PF; ++p) {
             int j, line;
-            if (FI::item(p, FI::NBF, j, line)) {
+            if (FI::item(p, FI::NBF, j, line, tid)) {
 #pragma unroll
                 for (int r = 0; r < FI::RF; ++r) {
                     const int k = j + r * FI::NBF;
@@ -119,12 +116,12 @@ __global__ void __launch_bounds__(threads_1d(N)) k_periodic1d(const KArgs a) {
                 }
             }
         }
-        FI::run(in, out, buf, tw, twl);
+        FI::run(in, out, buf, tw, twl, tid, sync);
         double2* outg = a.aux2 + (size_t)b * NP;
 #pragma unroll
         for (int p = 0; p < FI::PL; ++p) {
             int j, line;
-            if (FI::item(p, FI::NBL, j, line)) {
+            if (FI::item(p, FI::NBL, j, line, tid)) {
 #pragma unroll
                 for (int r = 0; r < FI::RL; ++r) outg[j + r * FI::NBL] = cvt<double2>(out[p][r]);
             }
@@ -138,7 +135,7 @@ __global__ void __launch_bounds__(threads_1d(N)) k_periodic1d(const KArgs a) {
 #pragma unroll
     for (int p = 0; p < PB; ++p) {
         int j, line;
-        if (FI::item(p, FI::NBF, j, line)) {
+        if (FI::item(p, FI::NBF, j, line, tid)) {
 #pragma unroll
             for (int r = 0; r < RB; ++r) {
                 const int k = j + r * FI::NBF;
@@ -168,12 +165,12 @@ __global__ void __launch_bounds__(threads_1d(N)) k_periodic1d(const KArgs a) {
             }
         }
     }
-    FI::run(in, mid, buf, tw, twl);
+    FI::run(in, mid, buf, tw, twl, tid, sync);
     const R hmu0 = step ? (R)(a.h * a.mu[0]) : (R)0;
 #pragma unroll
     for (int p = 0; p < FI::PL; ++p) {
         int j, line;
-        if (FI::item(p, FI::NBL, j, line)) {
+        if (FI::item(p, FI::NBL, j, line, tid)) {
 #pragma unroll
             for (int r = 0; r < FI::RL; ++r) {
                 R vh, vl;
@@ -182,11 +179,11 @@ __global__ void __launch_bounds__(threads_1d(N)) k_periodic1d(const KArgs a) {
             }
         }
     }
-    FW::run(mid, out, buf, tw, twl);
+    FW::run(mid, out, buf, tw, twl, tid, sync);
 #pragma unroll
     for (int p = 0; p < FW::PL; ++p) {
         int j, line;
-        if (FW::item(p, FW::NBL, j, line)) {
+        if (FW::item(p, FW::NBL, j, line, tid)) {
 #pragma unroll
             for (int r = 0; r < FW::RL; ++r) {
                 const int k = j + r * FW::NBL;
@@ -214,19 +211,33 @@ __global__ void __launch_bounds__(threads_1d(N)) k_periodic1d(const KArgs a) {
 }
 
 template <class C, class RT, int N>
+__global__ void __launch_bounds__(threads_1d(N)) k_periodic1d(const KArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    step1d<C, RT, N, threads_1d(N)>(a, blockIdx.x, threadIdx.x, CtaSync{}, reinterpret_cast<C*>(smem_raw));
+}
+
+// One-time kernel attributes (shared memory above 48 KB); done before the
+// first launch and, for stream capture, by periodic1d_prepare beforehand.
+template <class C, class RT, int N>
+static cudaError_t prepare_n() {
+    static bool configured = false;
+    if (configured) return cudaSuccess;
+    const size_t smem = (size_t)N * sizeof(C);
+    cudaError_t e = cudaFuncSetAttribute(k_periodic1d<C, RT, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_periodic1d<C, RT, N>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) configured = true;
+    return e;
+}
+
+template <class C, class RT, int N>
 static cudaError_t launch_n(const KArgs& a, cudaStream_t s) {
     constexpr int T = threads_1d(N);
     const size_t smem = (size_t)N * sizeof(C);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_periodic1d<C, RT, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_periodic1d<C, RT, N>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = prepare_n<C, RT, N>();
+    if (e != cudaSuccess) return e;
     k_periodic1d<C, RT, N><<<a.B, T, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -251,7 +262,121 @@ static cudaError_t dispatch_n(const KArgs& a, cudaStream_t s) {
 
 bool periodic1d_supported(int n) { return n >= 8 && n <= 8192 && (n & (n - 1)) == 0; }
 
+template <class C, class RT>
+static cudaError_t prepare_combo(int n) {
+    switch (n) {
+        case 8: return prepare_n<C, RT, 8>();
+        case 16: return prepare_n<C, RT, 16>();
+        case 32: return prepare_n<C, RT, 32>();
+        case 64: return prepare_n<C, RT, 64>();
+        case 128: return prepare_n<C, RT, 128>();
+        case 256: return prepare_n<C, RT, 256>();
+        case 512: return prepare_n<C, RT, 512>();
+        case 1024: return prepare_n<C, RT, 1024>();
+        case 2048: return prepare_n<C, RT, 2048>();
+        case 4096: return prepare_n<C, RT, 4096>();
+        case 8192: return prepare_n<C, RT, 8192>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t periodic1d_prepare(int n, int combo) {
+    switch (combo) {
+        case COMBO_F64: return prepare_combo<double2, double2>(n);
+        case COMBO_F32: return n == P1D_MAX_F32 ? prepare_n<float2, float2, P1D_MAX_F32>() : prepare_combo<float2, float2>(n);
+        case COMBO_F64_R32: return prepare_combo<double2, float2>(n);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Uneven batches: one persistent launch runs the mixed step of many contexts.
+namespace {
+
+struct Variant {
+    int n, t;
+};
+__host__ __device__ constexpr Variant kVariants[MULTI_NVAR] = {
+    {256, 32},  {512, 64},   {512, 32},    {1024, 128}, {1024, 64}, {2048, 256}, {2048, 128}, {4096, 512},
+    {4096, 256}, {8192, 512}, {16384, 512}, {128, 32},   {64, 32},   {32, 32},    {16, 32},    {8, 32}};
+
+// `count` instances b0.. of one context, each by a group of T threads with
+// its own N-element slice of shared memory.
+template <int N, int T>
+__device__ __forceinline__ void run_group(const KArgs& a, int b0, int count, float2* smem) {
+    const int g = threadIdx.x / T, tid = threadIdx.x % T;
+    if (g >= count) return;
+    float2* buf = smem + (size_t)g * N;
+    if constexpr (T == MULTI_CTA)
+        step1d<float2, float2, N, T>(a, b0, tid, CtaSync{}, buf);
+    else if constexpr (T == 32)
+        step1d<float2, float2, N, T>(a, b0 + g, tid, WarpSync{}, buf);
+    else
+        step1d<float2, float2, N, T>(a, b0 + g, tid, GroupSync{1u + (unsigned)g, (unsigned)T}, buf);
+}
+
+__global__ void __launch_bounds__(MULTI_CTA, 1) k_periodic1d_multi(const __grid_constant__ MultiArgs1D m) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* smem = reinterpret_cast<float2*>(smem_raw);
+    for (int i = blockIdx.x; i < m.nitems; i += gridDim.x) {
+        const MultiItem it = m.items[i];
+        const KArgs& a = m.args[it.g];
+        switch (it.var) {
+            case 0: run_group<256, 32>(a, it.b0, it.count, smem); break;
+            case 1: run_group<512, 64>(a, it.b0, it.count, smem); break;
+            case 2: run_group<512, 32>(a, it.b0, it.count, smem); break;
+            case 3: run_group<1024, 128>(a, it.b0, it.count, smem); break;
+            case 4: run_group<1024, 64>(a, it.b0, it.count, smem); break;
+            case 5: run_group<2048, 256>(a, it.b0, it.count, smem); break;
+            case 6: run_group<2048, 128>(a, it.b0, it.count, smem); break;
+            case 7: run_group<4096, 512>(a, it.b0, it.count, smem); break;
+            case 8: run_group<4096, 256>(a, it.b0, it.count, smem); break;
+            case 9: run_group<8192, 512>(a, it.b0, it.count, smem); break;
+            case 10: run_group<16384, 512>(a, it.b0, it.count, smem); break;
+            case 11: run_group<128, 32>(a, it.b0, it.count, smem); break;
+            case 12: run_group<64, 32>(a, it.b0, it.count, smem); break;
+            case 13: run_group<32, 32>(a, it.b0, it.count, smem); break;
+            case 14: run_group<16, 32>(a, it.b0, it.count, smem); break;
+            case 15: run_group<8, 32>(a, it.b0, it.count, smem); break;
+            default: break;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int multi_variant_n(int var) { return var >= 0 && var < MULTI_NVAR ? kVariants[var].n : 0; }
+int multi_variant_t(int var) { return var >= 0 && var < MULTI_NVAR ? kVariants[var].t : 0; }
+int multi_variant(int n, int t) {
+    for (int v = 0; v < MULTI_NVAR; ++v)
+        if (kVariants[v].n == n && kVariants[v].t == t) return v;
+    return -1;
+}
+size_t multi_item_smem(int var, int count) { return (size_t)count * multi_variant_n(var) * sizeof(float2); }
+
+int multi_occupancy(size_t smem) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_periodic1d_multi, MULTI_CTA, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
+cudaError_t multi_prepare(size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_periodic1d_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_periodic1d_multi, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
+cudaError_t launch_periodic1d_multi(const MultiArgs1D& m, int grid, size_t smem, cudaStream_t s) {
+    if (m.nitems <= 0) return cudaSuccess;
+    k_periodic1d_multi<<<grid, MULTI_CTA, smem, s>>>(m);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_periodic1d(const KArgs& a, int combo, cudaStream_t s) {
+    if (a.n0 == P1D_MAX_F32 && combo == COMBO_F32) return launch_n<float2, float2, P1D_MAX_F32>(a, s);
     if (!periodic1d_supported(a.n0)) return cudaErrorInvalidValue;
     switch (combo) {
         case COMBO_F64: return dispatch_n<double2, double2>(a, s);

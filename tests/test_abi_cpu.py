@@ -64,7 +64,9 @@ def _cfg(native, **kw):
     (dict(dim=2, n=(32, 16)), 0),
     (dict(dim=3), -1),
     (dict(n=(48, 1)), -1),             # not a power of two
-    (dict(n=(16384, 1)), -7),          # 1D limit of this build (FP64 transform in shared memory)
+    (dict(n=(16384, 1)), -7),          # 1D FP64 limit of this build (FP64 transform in shared memory)
+    (dict(n=(16384, 1), precision=1), 0),   # mixed: FP32 steps, FP64 four-step start and read-out
+    (dict(n=(32768, 1), precision=1), -7),
     (dict(order=7), -1),
     (dict(order=10), -1),
     (dict(dt=0.0), -1),
@@ -158,3 +160,16 @@ def test_alpert_header_is_generator_output():
     gen = os.path.join(ROOT, "paper_2001_06113_gb300", "csrc", "gen_alpert.py")
     out = subprocess.run([sys.executable, gen], capture_output=True, text=True, check=True).stdout
     assert out == open(os.path.join(ROOT, "paper_2001_06113_gb300", "csrc", "alpert_rules.h")).read()
+
+
+def test_batch_create_validates_without_gpu(native):
+    lib = native.lib()
+    out = ctypes.c_void_p()
+    assert lib.tdse_batch_create(None, 1, ctypes.byref(out)) == -1
+    ctx = ctypes.c_void_p()
+    assert lib.tdse_create(ctypes.byref(_cfg(native, precision=1)), ctypes.byref(ctx)) == 0
+    arr = (ctypes.c_void_p * 1)(ctx.value)
+    assert lib.tdse_batch_create(arr, 0, ctypes.byref(out)) == -1
+    assert lib.tdse_batch_create(arr, 1, ctypes.byref(out)) == -1      # workspace not bound
+    assert lib.tdse_batch_step(None, 1, None) == -1
+    lib.tdse_destroy(ctx)

@@ -1,0 +1,183 @@
+"""Uneven 1D batches (one persistent launch per step for contexts of
+different n, CUDA-graph replay, autotuned launch shapes) and the n = 16384
+mixed-precision 1D instances, through the C ABI on the GPU."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fields
+from oracle.periodic import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+DT, NSTEPS = 1e-3, 40
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def members_data(sizes_counts, seed=0):
+    """{N: [Instance, ...]} of seeded uneven-batch members with fixed N."""
+    out = {}
+    i = 0
+    for N, count in sizes_counts:
+        out[N] = [synth.periodic_1d_batch_member(seed * 1000 + i + k, dt=DT, nsteps=NSTEPS, sizes=(N,))
+                  for k in range(count)]
+        i += count
+    return out
+
+
+def make_problem(insts, stream=None, precision="mixed"):
+    from paper_2001_06113_gb300 import Problem
+    it0 = insts[0]
+    pr = Problem(it0.shape, DT, NSTEPS, batch=len(insts), precision=precision, stream=stream)
+    load(pr, insts)
+    return pr
+
+
+def load(pr, insts):
+    for b, it in enumerate(insts):
+        pr.set_potential(it.V0, None, instance=b)
+        p = it.pulse
+        pr.set_pulse(p.A0, p.omega, p.T_pulse, p.direction, instance=b)
+        pr.set_initial(it.u0, instance=b)
+
+
+def reset(pr, insts):
+    for b, it in enumerate(insts):
+        pr.set_initial(it.u0, instance=b)
+
+
+SIZES = [(256, 5), (1024, 3), (4096, 2), (16384, 1), (512, 17)]
+
+
+def test_batch_members_equal_solo_runs():
+    """Each instance of each member after start-up + Adams steps in the fused
+    launch equals the same instance run alone, bit for bit."""
+    import torch
+    from paper_2001_06113_gb300 import Batch
+    data = members_data(SIZES)
+    stream = torch.cuda.Stream()
+    probs = [make_problem(insts, stream) for insts in data.values()]
+    batch = Batch(probs, stream=stream)
+    batch.step(12)
+    stream.synchronize()
+    for pr, insts in zip(probs, data.values()):
+        ub = pr.read_u()
+        for b, it in enumerate(insts):
+            solo = make_problem([it])
+            solo.step(12)
+            assert np.array_equal(solo.read_u(0), ub[b]), (it.shape, b)
+            solo.close()
+
+
+def test_batch_graph_replay_and_tuning_keep_results():
+    """A second call from step 0 replays the captured graph; a tuned launch
+    shape (other threads per instance, CTA count) gives the same bits."""
+    import torch
+    from paper_2001_06113_gb300 import Batch
+    data = members_data([(256, 9), (2048, 3), (8192, 2)], seed=1)
+    stream = torch.cuda.Stream()
+    probs = [make_problem(insts, stream) for insts in data.values()]
+    batch = Batch(probs, stream=stream)
+    batch.step(15)
+    stream.synchronize()
+    first = [pr.read_u().copy() for pr in probs]
+    for pr, insts in zip(probs, data.values()):
+        reset(pr, insts)
+    batch.step(15)
+    stream.synchronize()
+    assert batch.describe()["graphs"] == 1
+    for pr, u in zip(probs, first):
+        assert np.array_equal(pr.read_u(), u)
+    batch.tune(3)
+    shape = batch.describe()
+    assert shape["tuned"] and shape["grid"] >= 1
+    for pr, insts in zip(probs, data.values()):
+        reset(pr, insts)
+    batch.step(15)
+    stream.synchronize()
+    for pr, u in zip(probs, first):
+        assert np.array_equal(pr.read_u(), u)
+
+
+def test_batch_mixed_accuracy_against_fp64_path():
+    """Members of the fused launch stay within the stated mixed tolerance of
+    the FP64 path (itself oracle-checked) after start-up and Adams steps."""
+    import torch
+    from paper_2001_06113_gb300 import Batch
+    data = members_data([(512, 4), (2048, 2)], seed=2)
+    stream = torch.cuda.Stream()
+    probs = [make_problem(insts, stream) for insts in data.values()]
+    Batch(probs, stream=stream).step(NSTEPS)
+    stream.synchronize()
+    for pr, insts in zip(probs, data.values()):
+        ub = pr.read_u()
+        for b, it in enumerate(insts):
+            ref = make_problem([it], precision="fp64")
+            ref.step(NSTEPS)
+            assert rel_l2(ub[b], ref.read_u(0)) < 2e-6
+            ref.close()
+
+
+def test_batch_validation():
+    import torch
+    from paper_2001_06113_gb300 import Batch, Problem, TdseError
+    data = members_data([(256, 2), (512, 2)], seed=3)
+    a, b = (make_problem(insts) for insts in data.values())
+    f64 = make_problem(data[256], precision="fp64")
+    with pytest.raises(TdseError):
+        Batch([a, f64])                                  # FP64 member: unsupported
+    other_dt = Problem((256,), 2 * DT, NSTEPS, precision="mixed")
+    with pytest.raises(TdseError):
+        Batch([a, other_dt])                             # different dt
+    a.step(1)                                            # members at different steps
+    batch = Batch([a, b], stream=torch.cuda.Stream())
+    with pytest.raises(TdseError):
+        batch.step(1)
+
+
+# ------------------------------------------------------------ n = 16384, mixed
+def test_mixed_16384_free_particle_closed_form():
+    """V = 0 with a pulse: the scheme is exact, so the mixed-precision
+    16384-point instance (FP64 four-step start and read-out, FP32 steps)
+    matches e^{-i k^2 t + i k phi(t)} u^_k(0) to the FP32 rounding level."""
+    from paper_2001_06113_gb300 import Problem
+    M, n = 16384, 40
+    pulse = synth.Pulse(3.0, 10.0, n * DT, (1.0,))
+    rng = np.random.default_rng(6)
+    x = synth.periodic_grid(M)
+    ks = np.arange(-60, 61)
+    c = (rng.normal(size=ks.size) + 1j * rng.normal(size=ks.size)) * np.exp(-0.001 * ks ** 2)
+    u0 = np.exp(1j * np.outer(x, ks)) @ c
+    pr = Problem((M,), DT, n, precision="mixed")
+    pr.set_potential(np.zeros(M))
+    pr.set_pulse(3.0, 10.0, n * DT, (1.0,))
+    pr.set_initial(u0)
+    assert np.array_equal(pr.read_u(0), u0)
+    pr.step(n)
+    T = n * DT
+    ph = fields.phi_callable(pulse, 1)(T)[0]
+    ref = np.exp(1j * np.outer(x, ks)) @ (c * np.exp(-1j * ks ** 2 * T + 1j * ks * ph))
+    assert rel_l2(pr.read_u(0), ref) < 1e-6
+
+
+def test_mixed_16384_against_fp64_8192():
+    """V != 0: a well-resolved problem solved at n = 16384 (mixed) and at
+    n = 8192 (FP64, oracle-checked path) agrees on the common grid points."""
+    from paper_2001_06113_gb300 import Problem
+    it16 = synth.periodic_1d_batch_member(3, dt=DT, nsteps=NSTEPS, sizes=(16384,))
+    it8 = synth.periodic_1d_batch_member(3, dt=DT, nsteps=NSTEPS, sizes=(8192,))
+    assert np.allclose(it16.u0[::2], it8.u0) and np.allclose(it16.V0[::2], it8.V0)
+    u16 = make_problem([it16])
+    u16.step(NSTEPS)
+    ref = Problem((8192,), DT, NSTEPS, precision="fp64")
+    load(ref, [it8])
+    ref.step(NSTEPS)
+    assert rel_l2(u16.read_u(0)[::2], ref.read_u(0)) < 2e-6
