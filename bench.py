@@ -809,6 +809,35 @@ def batch1d_oracle_sample(nadams: int = 20):
     return 1024 * nadams / el, el
 
 
+def batch1d_profile_run(args):
+    """ncu launch sequence: start-up + K fused Adams steps of the uneven batch
+    (direct launches), then K Adams steps of every member on its own kernel."""
+    import torch
+    from paper_2001_06113_gb300 import Batch, Problem
+    insts = batch1d_instances(0)
+    groups = {}
+    for it in insts:
+        groups.setdefault(it.shape[0], []).append(it)
+    sizes = sorted(groups)
+    probs = []
+    for N in sizes:
+        pr = Problem((N,), B1_DT, B1_NSTEPS, batch=len(groups[N]), precision="mixed")
+        for b, it in enumerate(groups[N]):
+            pr.set_potential(it.V0, None, instance=b)
+            p = it.pulse
+            pr.set_pulse(p.A0, p.omega, p.T_pulse, p.direction, instance=b)
+            pr.set_initial(it.u0, instance=b)
+        probs.append(pr)
+    batch = Batch(probs)
+    dstream = torch.cuda.default_stream()
+    batch.step(STARTUP + args.profile_adams, stream=dstream)
+    for pr in probs:
+        pr.step(args.profile_adams)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_adams": args.profile_adams, "workload": "batch1d", "shape": batch.describe()}))
+    return 0
+
+
 def main_batch1d(args, ws, rank, local):
     import torch
     if args.impl == "reference":
@@ -828,6 +857,8 @@ def main_batch1d(args, ws, rank, local):
                           "e2e": {"value": value, "unit": "point-steps/s", "h2d_bytes_per_step": 0,
                                   "d2h_bytes_per_step": 0}}))
         return 0
+    if args.profile_adams:
+        return batch1d_profile_run(args)
     if ws > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     res = run_batch1d(args, ws, rank, local)

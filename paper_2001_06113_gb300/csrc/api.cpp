@@ -807,6 +807,7 @@ static tdse_status build_items(tdse_batch* b) {
     std::stable_sort(b->items.begin(), b->items.end(),
                      [&](const MultiItem& x, const MultiItem& y) { return cost(x) > cost(y); });
     b->args.nitems = (int)b->items.size();
+    b->args.next = b->m[0]->P<int>(b->m[0]->off.scratch) + 1;   // word 0 is tdse_check_finite's counter
     std::copy(b->items.begin(), b->items.end(), b->args.items);
     return TDSE_OK;
 }

@@ -101,7 +101,7 @@ bool periodic2d_supported(int n0, int n1);
 cudaError_t periodic1d_prepare(int n, int combo);
 
 // ---- uneven 1D batches: one persistent launch for many contexts (mixed steps)
-// A CTA of MULTI_CTA threads takes items i = blockIdx.x, + gridDim.x, ...; an
+// A CTA of MULTI_CTA threads takes the next item from a global counter; an
 // item runs `count` instances of one context with the launch variant `var`
 // (N and T = threads per instance), count <= MULTI_CTA / T, side by side.
 constexpr int MULTI_CTA = 512;
@@ -115,6 +115,7 @@ struct MultiItem {
 };
 struct MultiArgs1D {
     int nitems;
+    int* next;                // work counter (zeroed before the launch): items are taken in order, as CTAs free up
     KArgs args[MULTI_MAX_GROUPS];
     MultiItem items[MULTI_MAX_ITEMS];
 };

@@ -317,8 +317,13 @@ __device__ __forceinline__ void run_group(const KArgs& a, int b0, int count, flo
 
 __global__ void __launch_bounds__(MULTI_CTA, 1) k_periodic1d_multi(const __grid_constant__ MultiArgs1D m) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int take;
     float2* smem = reinterpret_cast<float2*>(smem_raw);
-    for (int i = blockIdx.x; i < m.nitems; i += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) take = atomicAdd(m.next, 1);
+        __syncthreads();
+        const int i = take;
+        if (i >= m.nitems) break;
         const MultiItem it = m.items[i];
         const KArgs& a = m.args[it.g];
         switch (it.var) {
@@ -340,7 +345,7 @@ __global__ void __launch_bounds__(MULTI_CTA, 1) k_periodic1d_multi(const __grid_
             case 15: run_group<8, 32>(a, it.b0, it.count, smem); break;
             default: break;
         }
-        __syncthreads();
+        __syncthreads();   // shared memory and `take` free for the next item
     }
 }
 
@@ -371,6 +376,8 @@ cudaError_t multi_prepare(size_t smem) {
 
 cudaError_t launch_periodic1d_multi(const MultiArgs1D& m, int grid, size_t smem, cudaStream_t s) {
     if (m.nitems <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(m.next, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
     k_periodic1d_multi<<<grid, MULTI_CTA, smem, s>>>(m);
     return cudaGetLastError();
 }
