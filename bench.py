@@ -17,6 +17,13 @@ bounded sample of the same workload instead.
 256..16384, T = 1, dt = 1e-3, 1000 steps) stepped as one autotuned persistent
 launch per step replayed from a CUDA graph, mixed precision.
 
+`--workload serve` replays a seeded Poisson request stream (200 req/s for
+1 s; 1D periodic N 2^10..2^14, 2D periodic 2^7..2^10 per side, 2D free space
+2^6..2^8 per side, one third each; T ~ U[0.05, 0.2], dt log-uniform on
+[2e-4, 2e-3]) through the request loop (admission by a 64 GB HBM budget,
+solves overlapped on their own streams) and reports time-to-solution p50/p99
+and aggregate point-steps/s.
+
 `--workload free2d` measures the free-space scheme instead: bump-windowed
 Gaussians on [-1,1]^2, 256x256 grid, nu = 2048 per dimension (2058 contour
 modes per dimension), p = 8, q = 10, n_r = 1, H for eps = 1e-10, T = 1,
@@ -64,7 +71,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="periodic2d", choices=["periodic2d", "free2d", "batch1d"])
+    ap.add_argument("--workload", default="periodic2d", choices=["periodic2d", "free2d", "batch1d", "serve"])
     ap.add_argument("--profile-adams", type=int, default=0,
                     help="profiling run: start-up + this many Adams steps of the batch, then exit")
     return ap.parse_args()
@@ -895,6 +902,95 @@ def main_batch1d(args, ws, rank, local):
     return 0
 
 
+# ------------------------------------------------------------ request loop arm
+SV_RATE, SV_DURATION, SV_T, SV_BUDGET = 200.0, 1.0, (0.05, 0.2), 64 << 30
+SV_METRIC = "aggregate point-steps/s of a served request stream (1D/2D periodic mixed, 2D free space FP64)"
+
+
+def main_serve(args, ws, rank, local):
+    import torch
+    from paper_2001_06113_gb300.serve import Request, Server, TorchBackend, requests_from_trace
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        # the oracle on the 1D part of the stream: a bounded sample of Adams steps
+        for _ in range(args.warmup):
+            batch1d_oracle_sample(2)
+        vals = [batch1d_oracle_sample(20)[0] for _ in range(args.steps)]
+        value = float(np.mean(vals))
+        print(json.dumps({"impl": "reference", "metric": SV_METRIC, "value": value, "unit": "point-steps/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1e3 * 1024 * 20 / value, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "served stream (CPU oracle sample: 20 Adams steps, 1D N=1024)"},
+                          "cpu_baseline": {"value": value, "unit": "point-steps/s", "cores": cpu_cores(),
+                                           "kind": "oracle", "sample": "20 Adams steps of one N=1024 instance"},
+                          "e2e": {"value": value, "unit": "point-steps/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return 0
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    # warm-up: a short stream of small solves (kernel attributes, allocator)
+    warm = synth.serve_requests(seed=99, rate=100.0, duration=0.1, T_range=(0.005, 0.01), sizes_1d=(1024,),
+                                sizes_2d=(128,), sizes_free=(64,))
+    Server(TorchBackend(), SV_BUDGET).run(requests_from_trace(warm))
+    trace = synth.serve_requests(seed=5, rate=SV_RATE, duration=SV_DURATION, T_range=SV_T)
+    reqs = requests_from_trace(trace)
+    srv = Server(TorchBackend(), SV_BUDGET, max_active=64)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        st = srv.run(reqs)
+        torch.cuda.synchronize()
+    by_kind = {}
+    for (t, kind, inst), r in zip(trace, reqs):
+        d = by_kind.setdefault(kind, {"n": 0, "point_steps": 0.0, "lat": []})
+        d["n"] += 1
+        d["point_steps"] += r.points * r.nsteps
+        d["lat"].append(r.latency)
+    classes = {k: {"requests": v["n"], "point_steps": v["point_steps"],
+                   "p50_s": float(np.percentile(v["lat"], 50)), "p99_s": float(np.percentile(v["lat"], 99))}
+               for k, v in by_kind.items()}
+    # stated accuracy: mixed periodic results vs the FP64 path, solved alone (also timed: the plain path)
+    sample = [(r, kind) for r, (t, kind, inst) in zip(reqs, trace)
+              if kind == "2d" or (kind == "1d" and inst.shape[0] <= 8192)][:8]
+    errs, f64_work, f64_time = [], 0.0, 0.0
+    for r, kind in sample:
+        ref = Request(r.rid, 0.0, r.inst, precision="fp64")
+        be = TorchBackend()
+        h = be.prepare(ref)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        be.start(h)
+        torch.cuda.synchronize()
+        f64_time += time.perf_counter() - t0
+        f64_work += r.points * r.nsteps
+        u = be.finish(h)
+        errs.append(float(np.sqrt(np.sum(np.abs(r.result - u) ** 2) / np.sum(np.abs(u) ** 2))))
+    line = {
+        "metric": SV_METRIC, "value": st["point_steps_per_s"], "unit": "point-steps/s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": st["makespan_s"] * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64 (periodic), c128 (free space)",
+        "data": "synthetic",
+        "config": {"workload": f"Poisson stream {SV_RATE:.0f} req/s for {SV_DURATION:.1f} s ({len(reqs)} requests): "
+                               "1D periodic N 2^10..2^14, 2D periodic 2^7..2^10, 2D free space 2^6..2^8 (nu = 8n, "
+                               "eps = 1e-10), one third each; T ~ U[0.05, 0.2], dt log-uniform [2e-4, 2e-3]",
+                   "hbm_budget_bytes": SV_BUDGET, "max_active": 64,
+                   "step": "the whole stream from the first arrival to the last result on the host"},
+        "time_to_solution_s": {"p50": st["p50_s"], "p99": st["p99_s"], "mean": st["mean_s"]},
+        "classes": classes, "peak_active": st["peak_active"], "peak_workspace_bytes": st["peak_bytes"],
+        "rel_l2_vs_fp64_max": max(errs) if errs else None,
+        "fp64_one_at_a_time_point_steps_per_s": f64_work / f64_time if f64_time else None,
+        "roofline": None, "cpu_baseline": None,
+        "e2e": {"value": st["point_steps_per_s"], "unit": "point-steps/s",
+                "h2d_bytes_per_step": sum(r.points * 24 for r in reqs),
+                "d2h_bytes_per_step": sum(r.points * 16 for r in reqs)},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -904,6 +1000,8 @@ def main():
         return main_free(args, ws, rank, local)
     if args.workload == "batch1d":
         return main_batch1d(args, ws, rank, local)
+    if args.workload == "serve":
+        return main_serve(args, ws, rank, local)
     if args.impl == "reference":
         if rank != 0:
             return 0

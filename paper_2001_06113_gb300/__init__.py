@@ -43,6 +43,29 @@ def free_choose_H(eps: float, vnorm: float, phimax: float, dim: int) -> float:
     return out.value
 
 
+def _config(shape, dt, nsteps, order, batch, precision, startup_steps, bc, nu, H, alpert_p, gauss_q, n_r):
+    cfg = _native.TdseConfig()
+    cfg.dim = len(shape)
+    cfg.bc = {"periodic": PERIODIC, "free": FREE}[bc]
+    if bc == "free":
+        nus = list(nu) if nu is not None else [8 * s for s in shape]
+        cfg.nu[0] = int(nus[0])
+        cfg.nu[1] = int(nus[1]) if len(nus) > 1 else 0
+        cfg.alpert_p = int(alpert_p)
+        cfg.gauss_q = int(gauss_q)
+        cfg.n_r = int(n_r)
+        cfg.H = float(H)
+    cfg.n[0] = shape[0]
+    cfg.n[1] = shape[1] if len(shape) > 1 else 1
+    cfg.batch = int(batch)
+    cfg.dt = float(dt)
+    cfg.nsteps = int(nsteps)
+    cfg.order = int(order)
+    cfg.startup_steps = int(startup_steps)
+    cfg.precision = {"fp64": FP64, "mixed": MIXED}[precision]
+    return cfg
+
+
 def _stream_handle(stream) -> Optional[int]:
     import torch
     if stream is None:
@@ -89,27 +112,10 @@ class Problem:
         self.batch = int(batch)
         self.dt = float(dt)
         self.nsteps = int(nsteps)
-        cfg = _native.TdseConfig()
-        cfg.dim = len(self.shape)
-        cfg.bc = {"periodic": PERIODIC, "free": FREE}[bc]
         self.bc = bc
-        if bc == "free":
-            nus = list(nu) if nu is not None else [8 * s for s in self.shape]
-            cfg.nu[0] = int(nus[0])
-            cfg.nu[1] = int(nus[1]) if len(nus) > 1 else 0
-            cfg.alpert_p = int(alpert_p)
-            cfg.gauss_q = int(gauss_q)
-            cfg.n_r = int(n_r)
-            cfg.H = float(H)
-        cfg.n[0] = self.shape[0]
-        cfg.n[1] = self.shape[1] if len(self.shape) > 1 else 1
-        cfg.batch = self.batch
-        cfg.dt = self.dt
-        cfg.nsteps = self.nsteps
-        cfg.order = int(order)
-        cfg.startup_steps = int(startup_steps)
-        cfg.precision = {"fp64": FP64, "mixed": MIXED}[precision]
         self.precision = precision
+        cfg = _config(self.shape, dt, nsteps, order, batch, precision, startup_steps, bc, nu, H, alpert_p, gauss_q,
+                      n_r)
         self._ctx = ctypes.c_void_p()
         _check(self._lib.tdse_create(ctypes.byref(cfg), ctypes.byref(self._ctx)))
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
@@ -121,6 +127,21 @@ class Problem:
         _check(self._lib.tdse_bind_workspace(self._ctx, ctypes.c_void_p(aligned), self.workspace_bytes,
                                              _stream_handle(stream)), self._ctx)
         self._callbacks = []
+
+    @staticmethod
+    def workspace_bytes_for(shape: Sequence[int], dt: float, nsteps: int, order: int = 8, batch: int = 1,
+                            precision: str = "fp64", startup_steps: int = -1, bc: str = "periodic",
+                            nu: Optional[Sequence[int]] = None, H: float = 0.0, alpert_p: int = 8, gauss_q: int = 10,
+                            n_r: int = 1) -> int:
+        """Device workspace a Problem of this configuration needs (host-only query)."""
+        lib = _native.lib()
+        cfg = _config(tuple(int(s) for s in shape), dt, nsteps, order, batch, precision, startup_steps, bc, nu, H,
+                      alpert_p, gauss_q, n_r)
+        ctx = ctypes.c_void_p()
+        _check(lib.tdse_create(ctypes.byref(cfg), ctypes.byref(ctx)))
+        n = int(lib.tdse_workspace_bytes(ctx))
+        lib.tdse_destroy(ctx)
+        return n + 256
 
     @property
     def npoints(self) -> int:

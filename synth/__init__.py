@@ -251,3 +251,39 @@ def free_bump_gaussians(shape=(256, 256), seed: int = 3, dt: float = 5e-4, nstep
     pulse = Pulse(A0, omega, Tp, dirn) if A0 else None
     return Instance(FREE, tuple(shape), u0, V0, vfac or _const_one, pulse, dt, nsteps,
                     name=f"free_bump_gaussians_{'x'.join(map(str, shape))}")
+
+
+def serve_requests(seed: int = 5, rate: float = 200.0, duration: float = 10.0, T_range=(0.5, 2.0),
+                   dt_range=(2e-4, 2e-3), sizes_1d=tuple(2 ** p for p in range(10, 15)),
+                   sizes_2d=tuple(2 ** p for p in range(7, 11)), sizes_free=tuple(2 ** p for p in range(6, 9))):
+    """Seeded request stream: Poisson arrivals (mean `rate` per second over
+    `duration` s); each request is 1D periodic, 2D periodic or 2D free space
+    with probability 1/3 each, its size drawn uniformly from the class's
+    sizes, T ~ U[T_range], dt log-uniform on dt_range, nsteps = round(T/dt),
+    data as in the 1D batch, 2D wells and free-space workloads.  Returns
+    [(arrival, class, Instance)]."""
+    rng = np.random.default_rng(seed)
+    t, out, i = 0.0, [], 0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            return out
+        cls = int(rng.integers(0, 3))
+        T = rng.uniform(*T_range)
+        dt = float(math.exp(rng.uniform(math.log(dt_range[0]), math.log(dt_range[1]))))
+        n = max(8, int(round(T / dt)))
+        sub = 100000 * seed + i
+        if cls == 0:
+            M = int(sizes_1d[int(rng.integers(0, len(sizes_1d)))])
+            inst = periodic_1d_batch_member(sub, seed=seed, dt=dt, nsteps=n, sizes=(M,))
+            kind = "1d"
+        elif cls == 1:
+            M = int(sizes_2d[int(rng.integers(0, len(sizes_2d)))])
+            inst = periodic_2d_wells(seed=sub, M=M, dt=dt, nsteps=n)
+            kind = "2d"
+        else:
+            M = int(sizes_free[int(rng.integers(0, len(sizes_free)))])
+            inst = free_bump_gaussians((M, M), seed=sub, dt=dt, nsteps=n)
+            kind = "free"
+        out.append((t, kind, inst))
+        i += 1

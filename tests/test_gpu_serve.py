@@ -1,0 +1,64 @@
+"""The request loop on the GPU: a seeded trace of 1D periodic, 2D periodic
+and 2D free-space solves admitted by HBM budget and overlapped on the
+device; every result equals the same solve run alone, and the mixed
+periodic results stay within the stated tolerance of the FP64 path."""
+import numpy as np
+import pytest
+
+import synth
+from oracle.periodic import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _trace():
+    return synth.serve_requests(seed=7, rate=60.0, duration=0.4, T_range=(0.01, 0.03), sizes_1d=(1024, 4096),
+                                sizes_2d=(128, 256), sizes_free=(64,))
+
+
+def test_results_equal_alone_and_in_the_mix():
+    import torch
+    from paper_2001_06113_gb300.serve import Server, TorchBackend, requests_from_trace
+    reqs = requests_from_trace(_trace())
+    assert len({r.bc for r in reqs}) == 2 and len(reqs) >= 10
+    be = TorchBackend()
+    srv = Server(be, hbm_budget=4 << 30, max_active=32)
+    st = srv.run(reqs)
+    assert st["requests"] == len(reqs) and st["peak_active"] > 1
+    for r in reqs:
+        alone = TorchBackend()
+        h = alone.prepare(r)
+        alone.start(h)
+        torch.cuda.synchronize()
+        assert np.array_equal(alone.finish(h), r.result), (r.rid, r.bc, r.inst.shape)
+
+
+def test_mixed_results_within_tolerance_of_fp64():
+    from paper_2001_06113_gb300.serve import Request, Server, TorchBackend
+    trace = [(t, k, inst) for t, k, inst in _trace() if k != "free"][:6]
+    reqs = [Request(i, t, inst, precision="mixed") for i, (t, k, inst) in enumerate(trace)]
+    refs = [Request(i, 0.0, inst, precision="fp64") for i, (t, k, inst) in enumerate(trace)]
+    Server(TorchBackend(), hbm_budget=4 << 30).run(reqs)
+    Server(TorchBackend(), hbm_budget=4 << 30).run(refs)
+    for r, f in zip(reqs, refs):
+        assert rel_l2(r.result, f.result) < 1e-6, (r.inst.shape, r.nsteps)
+
+
+def test_budget_limits_concurrency():
+    from paper_2001_06113_gb300 import Problem
+    from paper_2001_06113_gb300.serve import Request, Server, TorchBackend
+    insts = [synth.periodic_2d_wells(seed=40 + i, M=256, dt=1e-3, nsteps=30) for i in range(6)]
+    need = Problem.workspace_bytes_for((256, 256), 1e-3, 30, precision="mixed")
+    reqs = [Request(i, 0.0, inst) for i, inst in enumerate(insts)]
+    srv = Server(TorchBackend(), hbm_budget=2 * need + need // 2)
+    srv.run(reqs)
+    assert srv.peak_active == 2 and srv.peak_bytes <= 2 * need + need // 2

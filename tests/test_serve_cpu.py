@@ -1,0 +1,95 @@
+"""Host logic of the request loop (admission by HBM budget, arrival order,
+completion handling, statistics) with a fake device backend; no GPU."""
+import numpy as np
+import pytest
+
+from paper_2001_06113_gb300.serve import Backend, Request, Server
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        self.t += 1e-3          # every clock read advances 1 ms
+        return self.t
+
+
+class FakeBackend(Backend):
+    """A solve takes `nsteps` polls after it starts; workspace = points * 10 bytes."""
+
+    def __init__(self):
+        self.log = []
+        self.live = 0
+        self.max_live_bytes = 0
+
+    def prepare(self, req):
+        return {"req": req, "left": None, "bytes": req.points * 10}
+
+    def workspace_bytes(self, h):
+        return h["bytes"]
+
+    def start(self, h):
+        h["left"] = h["req"].nsteps
+        self.live += h["bytes"]
+        self.max_live_bytes = max(self.max_live_bytes, self.live)
+        self.log.append(("start", h["req"].rid))
+
+    def done(self, h):
+        h["left"] -= 1
+        return h["left"] <= 0
+
+    def finish(self, h):
+        self.live -= h["bytes"]
+        self.log.append(("finish", h["req"].rid))
+        return np.full(3, h["req"].rid, dtype=np.complex128)
+
+
+class Inst:
+    def __init__(self, shape, nsteps):
+        self.shape = shape
+        self.nsteps = nsteps
+
+
+def _requests(n, seed=0):
+    rng = np.random.default_rng(seed)
+    out = []
+    t = 0.0
+    for i in range(n):
+        t += rng.exponential(0.005)
+        out.append(Request(i, t, Inst((int(rng.choice([64, 256, 1024])),), int(rng.integers(2, 20)))))
+    return out
+
+
+def test_admission_respects_budget_and_order():
+    reqs = _requests(60)
+    be = FakeBackend()
+    budget = 1024 * 10 * 3                      # at most three of the largest at once
+    srv = Server(be, budget, max_active=8, clock=FakeClock(), idle_sleep=0)
+    st = srv.run(reqs)
+    assert be.max_live_bytes <= budget and srv.peak_bytes <= budget
+    assert srv.peak_active <= 8
+    starts = [rid for kind, rid in be.log if kind == "start"]
+    assert starts == sorted(starts)             # admitted in arrival order
+    for r in reqs:
+        assert r.admitted >= r.arrival and r.finished > r.admitted
+        assert r.result[0] == r.rid
+    assert st["requests"] == 60 and st["p99_s"] >= st["p50_s"] > 0
+    assert st["point_steps"] == sum(r.points * r.nsteps for r in reqs)
+
+
+def test_requests_overlap_when_memory_allows():
+    reqs = [Request(i, 0.0, Inst((64,), 50)) for i in range(10)]
+    be = FakeBackend()
+    srv = Server(be, 10 ** 9, max_active=16, clock=FakeClock(), idle_sleep=0)
+    srv.run(reqs)
+    assert srv.peak_active == 10                # all in flight together
+    kinds = [k for k, _ in be.log]
+    assert kinds[:10] == ["start"] * 10
+
+
+def test_oversize_request_rejected():
+    be = FakeBackend()
+    srv = Server(be, 100, clock=FakeClock(), idle_sleep=0)
+    with pytest.raises(ValueError):
+        srv.run([Request(0, 0.0, Inst((64,), 3))])
