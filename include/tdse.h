@@ -201,6 +201,25 @@ tdse_status tdse_free_rule(const tdse_ctx* ctx, int axis, int* N, double* zeta, 
  * TDSE_EINVAL if the result is not positive and finite. */
 tdse_status tdse_free_choose_H(double eps, double vnorm, double phimax, int dim, double* H_out);
 
+/* FP64 residual check of the mixed-precision implicit step (TDSE_MIXED,
+ * periodic; 1D n <= 8192, 2D n <= 1024 per dimension).  After every
+ * `every`-th Adams step (0 = off) the library evaluates, in FP64 on the GPU,
+ * with u^_n and R_n = (Vu)^_n as stored (taken back to the lab frame):
+ *     W = u^_n + i mu_0 dt R_n,  R64 = DFT(V IDFT(W) / (1 + i mu_0 dt V)),
+ *     rho = mu_0 dt ||R64 - R_n||_2 / ||u^_n||_2          (per instance)
+ * i.e. the relative residual of the step's implicit equation (eq. uadamsk),
+ * and where rho > tol (or is not finite) redoes the step in FP64:
+ * u^_n <- W - i mu_0 dt R64, R_n <- R64.  The check and the redo stay on the
+ * device (no host synchronisation).  Errors: TDSE_EUNSUPPORTED outside the
+ * sizes above or for FP64 / free-space contexts (every > 0). */
+tdse_status tdse_set_residual_check(tdse_ctx* ctx, int every, double tol);
+
+/* Last checked residual rho per instance and the number of FP64 redos per
+ * instance (host arrays of batch entries, either may be NULL), and the number
+ * of checks run since tdse_set_initial.  Synchronises `stream`.
+ * TDSE_ENONFINITE if a checked residual is not finite. */
+tdse_status tdse_residual_report(tdse_ctx* ctx, double* rho, int* corrections, int* checks, void* stream);
+
 /* Scan the mode state of every instance for NaN/Inf (synchronises `stream`).
  * Returns TDSE_ENONFINITE if any is found. */
 tdse_status tdse_check_finite(tdse_ctx* ctx, void* stream);
@@ -263,9 +282,9 @@ typedef struct tdse_batch tdse_batch;
  * periodic mixed). */
 tdse_status tdse_batch_create(tdse_ctx* const* members, int count, tdse_batch** out);
 
-/* Autotuner: choose T per member (n/8 or n/16 threads per instance where both
- * exist) and the CTA count by timing `trial_steps` launches of each candidate
- * on `stream`.  The members must have V and u0 set; tuning runs their start
+/* Autotuner: choose the instances per work item of each member (all that fit
+ * the CTA, a half or a quarter) and the CTA count by timing `trial_steps`
+ * launches of each candidate on `stream`.  The members must have V and u0 set; tuning runs their start
  * if needed and leaves their state undefined: call tdse_set_initial on every
  * member before the next tdse_batch_step.  Cached graphs are dropped. */
 tdse_status tdse_batch_tune(tdse_batch* b, int trial_steps, void* stream);

@@ -236,6 +236,21 @@ class Problem:
                self._ctx)
         return z, w
 
+    def set_residual_check(self, every: int, tol: float = 1e-6):
+        """FP64 residual check of the mixed implicit step after every `every`-th
+        Adams step, with an FP64 redo where the residual exceeds `tol`."""
+        _check(self._lib.tdse_set_residual_check(self._ctx, int(every), float(tol)), self._ctx)
+
+    def residual_report(self):
+        """(rho per instance of the last check, FP64 redos per instance, checks run)."""
+        rho = np.zeros(self.batch, dtype=np.float64)
+        corr = np.zeros(self.batch, dtype=np.int32)
+        n = ctypes.c_int()
+        _check(self._lib.tdse_residual_report(self._ctx, rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                              corr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(n),
+                                              _stream_handle(self._stream)), self._ctx)
+        return rho, corr, n.value
+
     def check_finite(self):
         _check(self._lib.tdse_check_finite(self._ctx, _stream_handle(self._stream)), self._ctx)
 

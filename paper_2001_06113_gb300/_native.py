@@ -25,7 +25,7 @@ EXPORTS = [
     "tdse_read_u", "tdse_check_finite", "tdse_step_index", "tdse_time", "tdse_adams_weights",
     "tdse_last_error", "tdse_destroy", "tdse_modes_to_grid_2d_noalloc", "tdse_read_modes", "tdse_free_rule",
     "tdse_free_choose_H", "tdse_batch_create", "tdse_batch_tune", "tdse_batch_step", "tdse_batch_describe",
-    "tdse_batch_last_error", "tdse_batch_destroy",
+    "tdse_batch_last_error", "tdse_batch_destroy", "tdse_set_residual_check", "tdse_residual_report",
 ]
 NOALLOC_MAX_POINTS = 524288
 
@@ -90,6 +90,8 @@ def load(path: str = _LIB_PATH) -> ctypes.CDLL:
         "tdse_batch_describe": ([vp, ctypes.c_char_p, ctypes.c_size_t], ip),
         "tdse_batch_last_error": ([vp], ctypes.c_char_p),
         "tdse_batch_destroy": ([vp], None),
+        "tdse_set_residual_check": ([vp, ip, cd], ip),
+        "tdse_residual_report": ([vp, dp, ctypes.POINTER(ip), ctypes.POINTER(ip), vp], ip),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -15,6 +15,21 @@
 #include "ctx.h"
 #include "kargs.h"
 
+namespace tdse {
+struct ResArgs {
+    KArgs a;
+    int n;
+    int slot;
+    float z[2];
+    double hmu0;
+    double tol;
+    double* sums;
+    int* flags;
+    double* rho;
+    int* ncorr;
+};
+}  // namespace tdse
+
 using namespace tdse;
 
 namespace {
@@ -143,6 +158,12 @@ static void plan_workspace(tdse_ctx* c) {
     c->off.tw32lo_1 = take((size_t)(c->d == 2 ? c->n1 : 1) * 8);
     c->off.iv = take((size_t)c->n_int * sizeof(int2));
     c->off.tw128 = c->d == 1 && c->n0 > 8192 ? take(128 * 16) : 0;
+    if (c->mixed) {
+        c->off.res_sums = take(B * 16);
+        c->off.res_rho = take(B * 8);
+        c->off.res_flags = take(B * 4);
+        c->off.res_ncorr = take(B * 4);
+    }
     c->off.scratch = take(256);
     c->off.end = o;
     c->ws_need = o;
@@ -489,10 +510,15 @@ tdse_status tdse_set_initial(tdse_ctx* c, int instance, const double* u0, int wh
         }
         c->have_u0[b] = 1;
     }
+    if (c->mixed && c->off.res_ncorr) {
+        TDSE_CK(c, cudaMemsetAsync(c->P<int>(c->off.res_ncorr), 0, (size_t)c->B * 4, s));
+        TDSE_CK(c, cudaMemsetAsync(c->P<double>(c->off.res_rho), 0, (size_t)c->B * 8, s));
+    }
     if (where == TDSE_HOST) TDSE_CK(c, cudaStreamSynchronize(s));
     c->step = 0;
     c->inited = false;
     c->ip = false;
+    c->res_checks = 0;
     return TDSE_OK;
 }
 
@@ -618,6 +644,26 @@ static tdse_status adams_steps(tdse_ctx* c, int n0, int k, cudaStream_t s) {
     return TDSE_OK;
 }
 
+// FP64 residual of the implicit equation for the step just completed, and the
+// FP64 redo of that step where it exceeds the tolerance (resid.cu).
+static tdse_status residual_check(tdse_ctx* c, cudaStream_t s) {
+    ResArgs r{};
+    r.a = base_args(c);
+    r.n = c->step;
+    r.slot = slot_of(c, c->step);
+    r.z[0] = c->zdither[2 * c->step];
+    r.z[1] = c->zdither[2 * c->step + 1];
+    r.hmu0 = c->cfg.dt * c->mu[0];
+    r.tol = c->res_tol;
+    r.sums = c->P<double>(c->off.res_sums);
+    r.flags = c->P<int>(c->off.res_flags);
+    r.rho = c->P<double>(c->off.res_rho);
+    r.ncorr = c->P<int>(c->off.res_ncorr);
+    TDSE_CK(c, launch_residual_check(r, true, s));
+    ++c->res_checks;
+    return TDSE_OK;
+}
+
 tdse_status tdse_step(tdse_ctx* c, int nsteps, void* stream) {
     if (!c) return TDSE_EINVAL;
     if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
@@ -646,11 +692,19 @@ tdse_status tdse_step(tdse_ctx* c, int nsteps, void* stream) {
             tdse_status st = enter_interaction(c, c->step, s);
             if (st != TDSE_OK) return st;
         }
-        const int run_len = nsteps - k;
+        int run_len = nsteps - k;
+        if (c->mixed && c->res_every > 0) {   // stop at the next step to check
+            const int to_check = c->res_every - c->step % c->res_every;
+            if (to_check < run_len) run_len = to_check;
+        }
         tdse_status st = adams_steps(c, c->step, run_len, s);
         if (st != TDSE_OK) return st;
         c->step += run_len;
         k += run_len;
+        if (c->mixed && c->res_every > 0 && c->step % c->res_every == 0) {
+            st = residual_check(c, s);
+            if (st != TDSE_OK) return st;
+        }
     }
     return TDSE_OK;
 }
@@ -735,6 +789,34 @@ tdse_status tdse_read_modes(tdse_ctx* c, int instance, double* u_out, int where,
     return TDSE_OK;
 }
 
+tdse_status tdse_set_residual_check(tdse_ctx* c, int every, double tol) {
+    if (!c) return TDSE_EINVAL;
+    if (every < 0 || !(tol >= 0.0)) return c->fail(TDSE_EINVAL, "every >= 0 and tol >= 0 required");
+    if (every > 0 && (!c->mixed || c->fs)) return c->fail(TDSE_EUNSUPPORTED, "residual check: periodic TDSE_MIXED only");
+    if (every > 0 && !residual_supported(c->d, c->n0, c->n1))
+        return c->fail(TDSE_EUNSUPPORTED, "residual check: n up to 8192 (1D) or 1024 per dimension (2D)");
+    c->res_every = every;
+    c->res_tol = tol;
+    return TDSE_OK;
+}
+
+tdse_status tdse_residual_report(tdse_ctx* c, double* rho, int* corrections, int* checks, void* stream) {
+    if (!c) return TDSE_EINVAL;
+    if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
+    if (checks) *checks = c->res_checks;
+    if (!c->mixed) return TDSE_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (rho) TDSE_CK(c, cudaMemcpyAsync(rho, c->P<double>(c->off.res_rho), (size_t)c->B * 8, cudaMemcpyDeviceToHost, s));
+    if (corrections)
+        TDSE_CK(c, cudaMemcpyAsync(corrections, c->P<int>(c->off.res_ncorr), (size_t)c->B * 4, cudaMemcpyDeviceToHost,
+                                   s));
+    TDSE_CK(c, cudaStreamSynchronize(s));
+    if (rho && c->res_checks > 0)
+        for (int b = 0; b < c->B; ++b)
+            if (!std::isfinite(rho[b])) return c->fail(TDSE_ENONFINITE, "non-finite residual");
+    return TDSE_OK;
+}
+
 int tdse_step_index(const tdse_ctx* c) { return c ? c->step : -1; }
 double tdse_time(const tdse_ctx* c) { return c ? c->step * c->cfg.dt : 0.0; }
 
@@ -752,6 +834,7 @@ void tdse_destroy(tdse_ctx* c) { delete c; }
 struct tdse_batch {
     std::vector<tdse_ctx*> m;
     std::vector<int> var;           // launch variant per member
+    std::vector<int> per;           // instances per work item per member (<= MULTI_CTA / T)
     int grid = 0;                   // persistent CTAs
     int sms = 0;
     bool tuned = false;
@@ -788,7 +871,7 @@ static tdse_status build_items(tdse_batch* b) {
     for (size_t g = 0; g < b->m.size(); ++g) {
         const tdse_ctx* c = b->m[g];
         const int var = b->var[g];
-        const int per = MULTI_CTA / multi_variant_t(var);
+        const int per = b->per[g];
         for (int b0 = 0; b0 < c->B; b0 += per) {
             MultiItem it{};
             it.g = (unsigned char)g;
@@ -907,7 +990,10 @@ tdse_status tdse_batch_create(tdse_ctx* const* members, int count, tdse_batch** 
     tdse_batch* b = new (std::nothrow) tdse_batch();
     if (!b) return TDSE_ENOMEM;
     b->m.assign(members, members + count);
-    for (tdse_ctx* c : b->m) b->var.push_back(multi_variant(c->n0, default_threads_1d(c->n0)));
+    for (tdse_ctx* c : b->m) {
+        b->var.push_back(multi_variant(c->n0, default_threads_1d(c->n0)));
+        b->per.push_back(MULTI_CTA / default_threads_1d(c->n0));
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -1037,14 +1123,13 @@ tdse_status tdse_batch_tune(tdse_batch* b, int trial_steps, void* stream) {
         b->grid = default_grid(b);
         st = timed(best);
     }
-    // threads per instance, member by member
+    // instances per work item, member by member (fewer: more, smaller items)
     for (size_t g = 0; g < b->m.size() && st == TDSE_OK; ++g) {
-        const int nn = b->m[g]->n0;
-        for (int t : {nn / 16, nn / 8}) {
-            const int v = multi_variant(nn, t);
-            if (v < 0 || v == b->var[g]) continue;
-            const int keep = b->var[g], keep_grid = b->grid;
-            b->var[g] = v;
+        const int full = MULTI_CTA / multi_variant_t(b->var[g]);
+        for (int per : {full / 2, full / 4}) {
+            if (per < 1 || per == b->per[g]) continue;
+            const int keep = b->per[g], keep_grid = b->grid;
+            b->per[g] = per;
             st = build_items(b);
             if (st != TDSE_OK) break;
             b->grid = default_grid(b);
@@ -1054,7 +1139,7 @@ tdse_status tdse_batch_tune(tdse_batch* b, int trial_steps, void* stream) {
             if (ms < best) {
                 best = ms;
             } else {
-                b->var[g] = keep;
+                b->per[g] = keep;
                 b->grid = keep_grid;
             }
         }
@@ -1102,7 +1187,7 @@ tdse_status tdse_batch_describe(const tdse_batch* b, char* buf, size_t len) {
         const int t = multi_variant_t(b->var[g]);
         js += std::string(g ? ", " : "") + "{\"n\": " + std::to_string(b->m[g]->n0) + ", \"batch\": " +
               std::to_string(b->m[g]->B) + ", \"threads\": " + std::to_string(t) + ", \"per_item\": " +
-              std::to_string(MULTI_CTA / t) + "}";
+              std::to_string(b->per[g]) + "}";
     }
     js += "]}";
     if (js.size() + 1 > len) return TDSE_EINVAL;

@@ -57,10 +57,13 @@ struct tdse_ctx {
     size_t ws_need = 0;
     struct {
         size_t uhat, ring, chain_uhat, chain_ring, aux, aux2, V0, V0f, tfac, phi, kin64, kinff, adv64, advff,
-            q64, qff, e2d, k1lo, k1hi, a1d, tw64_0, tw32_0, tw64_1, tw32_1, tw32lo_0, tw32lo_1, iv, tw128, scratch,
-            end;
+            q64, qff, e2d, k1lo, k1hi, a1d, tw64_0, tw32_0, tw64_1, tw32_1, tw32lo_0, tw32lo_1, iv, tw128, res_sums,
+            res_rho, res_flags, res_ncorr, scratch, end;
     } off{};
     std::vector<char> have_V, have_u0;
+    int res_every = 0;          // FP64 residual check after every res_every-th Adams step (mixed; 0 = off)
+    double res_tol = 0.0;
+    int res_checks = 0;
     int step = 0;
     bool inited = false;
     std::string err;

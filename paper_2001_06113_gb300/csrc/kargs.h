@@ -119,7 +119,7 @@ struct MultiArgs1D {
     KArgs args[MULTI_MAX_GROUPS];
     MultiItem items[MULTI_MAX_ITEMS];
 };
-constexpr int MULTI_NVAR = 16;
+constexpr int MULTI_NVAR = 12;
 int multi_variant_n(int var);
 int multi_variant_t(int var);
 int multi_variant(int n, int t);            // -1 if not built
@@ -127,6 +127,11 @@ size_t multi_item_smem(int var, int count);
 cudaError_t multi_prepare(size_t smem);
 int multi_occupancy(size_t smem);           // resident CTAs per SM (0 on error)
 cudaError_t launch_periodic1d_multi(const MultiArgs1D& m, int grid, size_t smem, cudaStream_t s);
+// FP64 residual check of the mixed implicit step (resid.cu).
+struct ResArgs;
+bool residual_supported(int dim, int n0, int n1);
+cudaError_t launch_residual_check(const ResArgs& r, bool correct, cudaStream_t s);
+
 // Largest n of the 1D FP32 step kernels (larger than periodic1d_supported's
 // limit: FP64 init / read-out of such sizes go through launch_fft64_four_step).
 constexpr int P1D_MAX_F32 = 16384;

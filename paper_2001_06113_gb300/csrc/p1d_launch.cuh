@@ -1,0 +1,40 @@
+// One-CTA-per-instance 1D step kernel and its launch (templates shared by
+// the FP64 and FP32 translation units).
+#pragma once
+#include "step1d.cuh"
+
+namespace tdse {
+
+template <class C, class RT, int N>
+__global__ void __launch_bounds__(threads_1d(N)) k_periodic1d(const KArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    step1d<C, RT, N, threads_1d(N)>(a, blockIdx.x, threadIdx.x, CtaSync{}, reinterpret_cast<C*>(smem_raw));
+}
+
+// One-time kernel attributes (shared memory above 48 KB); done before the
+// first launch and, for stream capture, by periodic1d_prepare beforehand.
+template <class C, class RT, int N>
+static cudaError_t prepare_n() {
+    static bool configured = false;
+    if (configured) return cudaSuccess;
+    const size_t smem = (size_t)N * sizeof(C);
+    cudaError_t e = cudaFuncSetAttribute(k_periodic1d<C, RT, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_periodic1d<C, RT, N>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) configured = true;
+    return e;
+}
+
+template <class C, class RT, int N>
+static cudaError_t launch_n(const KArgs& a, cudaStream_t s) {
+    constexpr int T = threads_1d(N);
+    const size_t smem = (size_t)N * sizeof(C);
+    cudaError_t e = prepare_n<C, RT, N>();
+    if (e != cudaSuccess) return e;
+    k_periodic1d<C, RT, N><<<a.B, T, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace tdse
