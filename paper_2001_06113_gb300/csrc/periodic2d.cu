@@ -13,6 +13,8 @@
 //   col_fused = col_end of step n followed by col_begin of step n+1 on the same
 //       column block: consecutive Adams steps cost two launches each
 //       (row_mid, col_fused), and the mode arrays cross HBM once per step.
+//       For mixed interaction-picture steps (the hot path) k_col_fused_ip does
+//       the same with the state and history reads staged by cp.async.
 //
 // Each CTA holds 8 whole lines (columns or rows) in shared memory, interleaved
 // so that consecutive threads touch consecutive lines, and transforms them
@@ -25,6 +27,8 @@
 // (T1 -> state, T2 -> ring[out]); MODE_READ runs col_begin (state -> T1, after
 // multiplying by E_n in FP64 if the state is in the interaction picture) and
 // row_mid (T1 -> u into aux2).
+#include <type_traits>
+
 #include "step_common.cuh"
 
 namespace tdse {
@@ -34,6 +38,15 @@ constexpr int T2D = 256;
 #ifndef TDSE_MINB2D
 #define TDSE_MINB2D 4          // resident CTAs per SM the register budget is sized for
 #endif
+
+// 16-byte asynchronous global -> shared copies (no registers held while in flight)
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // ------------------------------------------------------------ element helpers
 // Start of a step at mode (m0, m1): returns the inverse-DFT input and updates
@@ -280,6 +293,114 @@ __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_end(const KArgs a) {
     }
 }
 
+// ------------------------------------- col_fused, mixed interaction-picture step
+// Same work as k_col_end<float2, float2, N0, true> for MODE_STEP with the state
+// in the interaction picture, with the mode-space reads staged: the state and
+// the history slots of lags 2..nhist of each chunk of PF_ROWS rows are copied
+// into shared memory with cp.async (16-byte copies, no registers held), two
+// chunks ahead, so that the DRAM reads of the step overlap the column FFT
+// and the element work of the previous chunk.  The intermediate v^_n is not
+// stored (the state slot receives X_{n+1} directly).
+#ifndef TDSE_PF_ROWS
+#define TDSE_PF_ROWS 32
+#endif
+constexpr int PF_ROWS = TDSE_PF_ROWS;
+
+template <int N0>
+__global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_fused_ip(const KArgs a) {
+    constexpr int L = LANES2D;
+    constexpr int RC = PF_ROWS < N0 ? PF_ROWS : N0;     // rows per chunk
+    constexpr int NCH = N0 / RC;
+    constexpr int NPF = MAX_HIST - 1;                  // lags 2..7 at most
+    using FW = CtaFft<float2, N0, L, L, T2D, false>;
+    using FI = CtaFft<float2, N0, L, L, T2D, true>;
+    struct Chunk {
+        float4 st[RC * L];
+        float2 ring[NPF][RC * L];
+    };
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    Chunk* pre = reinterpret_cast<Chunk*>(smem_raw + (size_t)N0 * L * sizeof(float2));
+    const int b = blockIdx.y;
+    const int c0 = blockIdx.x * L;
+    const int n1 = a.n1;
+    const size_t NP = (size_t)N0 * n1;
+    float4* st = reinterpret_cast<float4*>(a.uhat) + (size_t)b * NP;
+    float2* ringb = reinterpret_cast<float2*>(a.ring) + (size_t)b * a.ring_slots * NP;
+    const int npf = a.nhist - 1;                      // slots to stage (lag 1 is the value written here)
+
+    // stage chunk c into buffer c & 1: state rows (8 x 16 B) and ring rows (8 x 8 B) of the CTA's columns
+    auto stage = [&](int c) {
+        Chunk& ch = pre[c & 1];
+        for (int it = threadIdx.x; it < RC * L; it += T2D) {          // state: one float4 per copy
+            const int r = it / L, q = it % L;
+            cp_async16(&ch.st[r * L + q], st + (size_t)(c * RC + r) * n1 + c0 + q);
+        }
+#pragma unroll
+        for (int j = 0; j < NPF; ++j) {                                // lag j + 2: two float2 per copy
+            if (j < npf) {
+                const float2* src = ringb + (size_t)a.hist_slot[j + 1] * NP + c0;
+                for (int it = threadIdx.x; it < RC * (L / 2); it += T2D) {
+                    const int r = it / (L / 2), h = it % (L / 2);
+                    cp_async16(&ch.ring[j][r * L + 2 * h], src + (size_t)(c * RC + r) * n1 + 2 * h);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    stage(0);
+    if (NCH > 1) stage(1);
+
+    const float2* T2 = reinterpret_cast<const float2*>(a.aux2) + (size_t)b * NP;
+    for (int item = threadIdx.x; item < N0 * L; item += T2D) {
+        const int lane = item % L, i0 = item / L;
+        buf[i0 * L + lane] = T2[(size_t)i0 * n1 + c0 + lane];
+    }
+    __syncthreads();
+    FW::run(buf, a.tw32_0, a.tw32lo_0);
+    const float scale = 1.0f / (float)N0;
+    const float2 z = make_float2(a.zr[0], a.zr[1]);
+
+#pragma unroll 1
+    for (int c = 0; c < NCH; ++c) {
+        if (c + 1 < NCH) cp_async_wait<1>(); else cp_async_wait<0>();
+        __syncthreads();
+        const Chunk& ch = pre[c & 1];
+        for (int it = threadIdx.x; it < RC * L; it += T2D) {
+            const int lane = it % L, r = it / L;
+            const int m0 = c * RC + r, m1 = c0 + lane;
+            const size_t idx = (size_t)m0 * n1 + m1;
+            // end of step n: r~ = z_n R / E_n into the ring, v^_n
+            const float2 R = cscale(buf[m0 * L + lane], scale);
+            const float2 rv = cmul(z, cmul(conjf2(e_2d(a, b, a.e_step, m0, m1)), R));
+            ringb[(size_t)a.out_slot * NP + idx] = rv;
+            const float4 v = ip_update(a, ch.st[it], rv);
+            // begin of step n+1: X = v^_n - i h sum_j c_j r~_{n+1-j}
+            float2 S = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = MAX_HIST; j >= 1; --j) {        // same order and terms as history_sum_ip
+                const float2 q = j > a.nhist ? make_float2(0.f, 0.f) : (j == 1 ? rv : ch.ring[j - 2][it]);
+                const float hh = a.c_hi[j][0], hi = a.c_hi[j][1], lo = a.c_lo[j][0], li = a.c_lo[j][1];
+                S.x = fmaf(lo, q.x, fmaf(-li, q.y, S.x));
+                S.y = fmaf(lo, q.y, fmaf(li, q.x, S.y));
+                S.x = fmaf(hh, q.x, fmaf(-hi, q.y, S.x));
+                S.y = fmaf(hh, q.y, fmaf(hi, q.x, S.y));
+            }
+            const float4 X = ff_minus_i_times(v, a.h_hi, a.h_lo, S);
+            st[idx] = X;
+            buf[m0 * L + lane] = cmul(e_2d(a, b, a.e_next, m0, m1), make_float2(X.x, X.y));
+        }
+        __syncthreads();                               // buffer c & 1 free
+        if (c + 2 < NCH) stage(c + 2);
+    }
+    FI::run(buf, a.tw32_0, a.tw32lo_0);
+    float2* T1 = reinterpret_cast<float2*>(a.aux) + (size_t)b * NP;
+    for (int item = threadIdx.x; item < N0 * L; item += T2D) {
+        const int lane = item % L, i0 = item / L;
+        T1[(size_t)i0 * n1 + c0 + lane] = buf[i0 * L + lane];
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 template <class K>
 static cudaError_t set_smem(K kern, size_t smem, bool& done) {
@@ -308,6 +429,18 @@ static cudaError_t col_end_n(const KArgs& a, cudaStream_t s) {
     cudaError_t e = set_smem(k_col_end<C, RT, N0, FUSED>, smem, done);
     if (e != cudaSuccess) return e;
     k_col_end<C, RT, N0, FUSED><<<dim3(a.n1 / LANES2D, a.B), T2D, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int N0>
+static cudaError_t col_fused_ip_n(const KArgs& a, cudaStream_t s) {
+    constexpr int RC = PF_ROWS < N0 ? PF_ROWS : N0;
+    const size_t smem = (size_t)N0 * LANES2D * sizeof(float2) +
+                        2 * (size_t)RC * LANES2D * (sizeof(float4) + (MAX_HIST - 1) * sizeof(float2));
+    static bool done = false;
+    cudaError_t e = set_smem(k_col_fused_ip<N0>, smem, done);
+    if (e != cudaSuccess) return e;
+    k_col_fused_ip<N0><<<dim3(a.n1 / LANES2D, a.B), T2D, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -369,7 +502,15 @@ static cudaError_t part2d(const KArgs& a, int part, cudaStream_t s) {
         case PART_COL_BEGIN: return col_begin<C, RT>(a, s);
         case PART_ROW_MID: return row_mid<C>(a, s);
         case PART_COL_END: return col_end<C, RT>(a, s);
-        case PART_COL_FUSED: return col_fused<C, RT>(a, s);
+        case PART_COL_FUSED:
+            if constexpr (std::is_same<C, float2>::value && std::is_same<RT, float2>::value) {
+                if (a.mode == MODE_STEP && a.ip) {
+#define TDSE_CFI(n) col_fused_ip_n<n>
+                    TDSE_SWITCH_N(a.n0, TDSE_CFI)
+#undef TDSE_CFI
+                }
+            }
+            return col_fused<C, RT>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -242,3 +242,23 @@ def test_device_pointers_and_callback_field():
     err = rel_l2(out.cpu().numpy(), oracle_solve(inst))
     p.close()
     assert err <= FP64_TOL, err
+
+
+def test_mixed_2d_single_steps_equal_fused_sequence():
+    """Mixed 2D: k calls of step(1) (separate end and begin column passes)
+    and one step(k) (fused column passes with staged history reads) give the
+    same bits."""
+    from paper_2001_06113_gb300 import Problem
+    inst = synth.periodic_2d_wells(seed=9, M=64, dt=1e-3, nsteps=30)
+    out = []
+    for chunks in ([1] * 20, [20]):
+        pr = Problem((64, 64), inst.dt, inst.nsteps, precision="mixed")
+        pr.set_potential(inst.V0)
+        p = inst.pulse
+        pr.set_pulse(p.A0, p.omega, p.T_pulse, p.direction)
+        pr.set_initial(inst.u0)
+        for k in chunks:
+            pr.step(k)
+        out.append(pr.read_u(0))
+        pr.close()
+    assert np.array_equal(out[0], out[1])
