@@ -158,11 +158,11 @@ def launches_per_solve(dim: int, mixed: bool) -> int:
     return init + startup + (1 if mixed else 0) + adams
 
 
-# DRAM bytes per point-step of the 2D step operator (k_row_mid + k_col_end<fused>)
+# DRAM bytes per point-step of the 2D step operator (k_row_mid + k_col_fused_ip)
 # from the ncu capture of the 512^2 mixed workload at batch 8 (summarised under
 # profiles/); traffic scales with the number of instances.  None = not captured
 # for the current kernels.
-TRAFFIC_BYTES_PER_POINT_STEP = {"mixed": (151.192064e6 + 31.29728e6 + 33.606144e6 + 0.041216e6) / (8 * 512 * 512),
+TRAFFIC_BYTES_PER_POINT_STEP = {"mixed": (151.207424e6 + 29.253632e6 + 33.606144e6 + 26.88e6) / (8 * 512 * 512),
                                 "fp64": None}
 
 
@@ -256,7 +256,7 @@ def run_gpu(args, ws, rank, local):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "traffic_unit": "bytes per step (all instances)",
                 "peak_source": peak_src,
-                "kernel": "2D Adams step operator (k_row_mid + k_col_end<fused>), timed over groups of 10 steps",
+                "kernel": "2D Adams step operator (k_row_mid + k_col_fused_ip), timed over groups of 10 steps",
                 "algorithmic_bytes_per_point_step": ALGO_BYTES[args.precision],
                 "step_ms_p50": round(float(np.percentile(dts, 50)) * 1e3, 4),
                 "step_ms_p99": round(float(np.percentile(dts, 99)) * 1e3, 4)}
