@@ -77,6 +77,22 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    """The largest x over the ranks (all_reduce MAX; x itself on one rank)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, ws: int, t_max: float) -> float:
+    """Throughput of the whole job: every rank processed units_per_rank in at
+    most t_max seconds (weak scaling)."""
+    return ws * units_per_rank / t_max
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -220,10 +236,7 @@ def run_gpu(args, ws, rank, local):
         torch.cuda.synchronize()
         barrier()
     t_solve = float(np.mean(times))
-    if ws > 1:
-        tt = torch.tensor([t_solve], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_solve = float(tt.item())
+    t_solve = max_over_ranks(t_solve, ws, dev)
     points = M * M
     value = ws * B * points * NSTEPS / t_solve
 
@@ -298,10 +311,7 @@ def run_gpu(args, ws, rank, local):
                 prob.read_u(-1, out=out)
                 e2e_times.append(time.perf_counter() - t0)
         te = float(np.mean(e2e_times))
-        if ws > 1:
-            tt = torch.tensor([te], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            te = float(tt.item())
+        te = max_over_ranks(te, ws, dev)
         h2d = B * (points * 8 + points * 16 + 2 * (8 * NSTEPS + 1) * 8)
         e2e = {"value": ws * B * points * NSTEPS / te, "unit": "point-steps/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": B * points * 16}
@@ -415,10 +425,7 @@ def run_free(args, ws, rank, local):
         torch.cuda.synchronize()
         barrier()
     t_solve = float(np.mean(times))
-    if ws > 1:
-        tt = torch.tensor([t_solve], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_solve = float(tt.item())
+    t_solve = max_over_ranks(t_solve, ws, dev)
     points = FS_M * FS_M
     value = ws * B * points * FS_NSTEPS / t_solve
 
@@ -459,10 +466,7 @@ def run_free(args, ws, rank, local):
                 prob.read_u(-1, out=out)
                 e2e_times.append(time.perf_counter() - t0)
         te = float(np.mean(e2e_times))
-        if ws > 1:
-            tt = torch.tensor([te], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            te = float(tt.item())
+        te = max_over_ranks(te, ws, dev)
         h2d = B * (points * 8 + points * 16)
         e2e = {"value": ws * B * points * FS_NSTEPS / te, "unit": "point-steps/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": B * points * 16}
@@ -704,10 +708,7 @@ def run_batch1d(args, ws, rank, local):
         torch.cuda.synchronize()
         barrier()
     t_solve = float(np.mean(times))
-    if ws > 1:
-        tt = torch.tensor([t_solve], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_solve = float(tt.item())
+    t_solve = max_over_ranks(t_solve, ws, "cuda")
     value = ws * points * B1_NSTEPS / t_solve
     # per-step latency of the fused launch: events around single Adams steps (direct launches)
     reset()
