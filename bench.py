@@ -178,7 +178,7 @@ def launches_per_solve(dim: int, mixed: bool) -> int:
 # from the ncu capture of the 512^2 mixed workload at batch 8 (summarised under
 # profiles/); traffic scales with the number of instances.  None = not captured
 # for the current kernels.
-TRAFFIC_BYTES_PER_POINT_STEP = {"mixed": (151.207424e6 + 29.253632e6 + 33.606144e6 + 26.88e6) / (8 * 512 * 512),
+TRAFFIC_BYTES_PER_POINT_STEP = {"mixed": (151.20896e6 + 29.985792e6 + 33.609216e6 + 37.632e6) / (8 * 512 * 512),
                                 "fp64": None}
 
 
