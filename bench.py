@@ -3,12 +3,14 @@
 Workload (one bench "step" = one whole solve): the 2D periodic wells problem
 on [-pi,pi]^2, 512x512 grid, T = 2, dt = 1e-3 (2000 steps: 7 Richardson
 start-up steps + 1993 8th-order Adams steps), pulse A(t) = 2 sin^2(pi t/2)
-sin(10 t) (1,0), replicated as a batch of independent seeded instances so that
-the per-step working set (~27 MB per instance in mixed precision) exceeds the
-129 MB L2.  Point-steps = instances x 512^2 x 2000.
+sin(10 t) (1,0), replicated as a batch of independent seeded instances (64 in
+mixed precision, 4 in FP64 by default) so that the per-step working set
+(~27 MB per instance in mixed precision) exceeds the 129 MB L2 and the pass
+kernels' grids span many waves.  Point-steps = instances x 512^2 x 2000.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
-                    [--batch B] [--impl reference] [--workload periodic2d|free2d]
+                    [--batch B] [--impl reference]
+                    [--workload periodic2d|free2d|batch1d|serve]
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -67,7 +69,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--batch", type=int, default=0, help="instances per GPU (default 16 periodic, 1 free space)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="instances per GPU (default: 64 periodic mixed, 4 periodic fp64, 1 free space)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -996,7 +999,7 @@ def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.batch <= 0:
-        args.batch = 1 if args.workload == "free2d" else 16
+        args.batch = 1 if args.workload == "free2d" else (64 if args.precision == "mixed" else 4)
     if args.workload == "free2d":
         return main_free(args, ws, rank, local)
     if args.workload == "batch1d":
