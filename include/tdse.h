@@ -224,6 +224,19 @@ tdse_status tdse_residual_report(tdse_ctx* ctx, double* rho, int* corrections, i
  * Returns TDSE_ENONFINITE if any is found. */
 tdse_status tdse_check_finite(tdse_ctx* ctx, void* stream);
 
+/* Checkpoint of the whole solve state: the context's workspace (mode state,
+ * history ring, start-up buffers, V, A and phase tables) and its host step
+ * counters, into a host blob.  blob == NULL: *size receives the bytes needed
+ * (no workspace needed).  Otherwise *size is the blob's capacity and receives
+ * the bytes written.  Synchronises `stream`.  The paper has no checkpoint; a
+ * run resumed with tdse_load continues bit for bit like an uninterrupted one. */
+tdse_status tdse_save(tdse_ctx* ctx, void* blob, size_t* size, void* stream);
+
+/* Resume from a tdse_save blob into a bound context of the same
+ * configuration (TDSE_EINVAL for another configuration or a short blob).
+ * Synchronises `stream`. */
+tdse_status tdse_load(tdse_ctx* ctx, const void* blob, size_t size, void* stream);
+
 /* Number of completed steps and the current time t = steps * dt. */
 int tdse_step_index(const tdse_ctx* ctx);
 double tdse_time(const tdse_ctx* ctx);

@@ -251,6 +251,18 @@ class Problem:
                                               _stream_handle(self._stream)), self._ctx)
         return rho, corr, n.value
 
+    def save(self) -> bytes:
+        """Checkpoint of the whole solve state (workspace and step counters)."""
+        n = ctypes.c_size_t()
+        _check(self._lib.tdse_save(self._ctx, None, ctypes.byref(n), _stream_handle(self._stream)), self._ctx)
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self._lib.tdse_save(self._ctx, buf, ctypes.byref(n), _stream_handle(self._stream)), self._ctx)
+        return buf.raw[:n.value]
+
+    def load(self, blob: bytes):
+        """Resume from `save()` output of a Problem with the same configuration."""
+        _check(self._lib.tdse_load(self._ctx, blob, len(blob), _stream_handle(self._stream)), self._ctx)
+
     def check_finite(self):
         _check(self._lib.tdse_check_finite(self._ctx, _stream_handle(self._stream)), self._ctx)
 

@@ -26,6 +26,7 @@ EXPORTS = [
     "tdse_last_error", "tdse_destroy", "tdse_modes_to_grid_2d_noalloc", "tdse_read_modes", "tdse_free_rule",
     "tdse_free_choose_H", "tdse_batch_create", "tdse_batch_tune", "tdse_batch_step", "tdse_batch_describe",
     "tdse_batch_last_error", "tdse_batch_destroy", "tdse_set_residual_check", "tdse_residual_report",
+    "tdse_save", "tdse_load",
 ]
 NOALLOC_MAX_POINTS = 524288
 
@@ -92,6 +93,8 @@ def load(path: str = _LIB_PATH) -> ctypes.CDLL:
         "tdse_batch_destroy": ([vp], None),
         "tdse_set_residual_check": ([vp, ip, cd], ip),
         "tdse_residual_report": ([vp, dp, ctypes.POINTER(ip), ctypes.POINTER(ip), vp], ip),
+        "tdse_save": ([vp, vp, ctypes.POINTER(ctypes.c_size_t), vp], ip),
+        "tdse_load": ([vp, vp, ctypes.c_size_t, vp], ip),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -817,6 +817,90 @@ tdse_status tdse_residual_report(tdse_ctx* c, double* rho, int* corrections, int
     return TDSE_OK;
 }
 
+// ---- checkpoint: header, then the whole workspace
+namespace {
+constexpr char kCkptMagic[8] = {'T', 'D', 'S', 'E', 'C', 'K', 'P', '1'};
+struct CkptHeader {
+    char magic[8];
+    int dim, bc, n0, n1, batch, nsteps, order, startup, precision, nu0, nu1, alpert_p, gauss_q, n_r;
+    double dt, H;
+    unsigned long long ws_bytes;
+    int step, inited, ip, res_every, res_checks, pad;
+    double res_tol;
+};
+void fill_header(const tdse_ctx* c, CkptHeader& h) {
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kCkptMagic, 8);
+    const tdse_config& g = c->cfg;
+    h.dim = g.dim; h.bc = g.bc; h.n0 = g.n[0]; h.n1 = g.dim == 2 ? g.n[1] : 1; h.batch = g.batch;
+    h.nsteps = g.nsteps; h.order = g.order; h.startup = c->S; h.precision = g.precision;
+    if (g.bc == TDSE_FREE) {
+        h.nu0 = g.nu[0]; h.nu1 = g.dim == 2 ? g.nu[1] : 0; h.alpert_p = g.alpert_p; h.gauss_q = g.gauss_q;
+        h.n_r = g.n_r; h.H = g.H;
+    }
+    h.dt = g.dt;
+    h.ws_bytes = c->ws_need;
+    h.step = c->step; h.inited = c->inited; h.ip = c->ip;
+    h.res_every = c->res_every; h.res_checks = c->res_checks; h.res_tol = c->res_tol;
+}
+}  // namespace
+
+tdse_status tdse_save(tdse_ctx* c, void* blob, size_t* size, void* stream) {
+    if (!c || !size) return TDSE_EINVAL;
+    const size_t need = sizeof(CkptHeader) + 2 * (size_t)c->B + c->ws_need;
+    if (!blob) {
+        *size = need;
+        return TDSE_OK;
+    }
+    if (*size < need) return c->fail(TDSE_EINVAL, "checkpoint buffer smaller than the size tdse_save reports");
+    if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CkptHeader h;
+    fill_header(c, h);
+    char* out = static_cast<char*>(blob);
+    std::memcpy(out, &h, sizeof(h));
+    for (int b = 0; b < c->B; ++b) {
+        out[sizeof(h) + 2 * b] = c->have_V[b];
+        out[sizeof(h) + 2 * b + 1] = c->have_u0[b];
+    }
+    TDSE_CK(c, cudaMemcpyAsync(out + sizeof(h) + 2 * (size_t)c->B, c->ws, c->ws_need, cudaMemcpyDeviceToHost, s));
+    TDSE_CK(c, cudaStreamSynchronize(s));
+    *size = need;
+    return TDSE_OK;
+}
+
+tdse_status tdse_load(tdse_ctx* c, const void* blob, size_t size, void* stream) {
+    if (!c || !blob) return TDSE_EINVAL;
+    if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
+    const size_t need = sizeof(CkptHeader) + 2 * (size_t)c->B + c->ws_need;
+    if (size < need) return c->fail(TDSE_EINVAL, "checkpoint too short");
+    CkptHeader h, mine;
+    std::memcpy(&h, blob, sizeof(h));
+    fill_header(c, mine);
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0) return c->fail(TDSE_EINVAL, "not a checkpoint of this library");
+    const bool same = h.dim == mine.dim && h.bc == mine.bc && h.n0 == mine.n0 && h.n1 == mine.n1 &&
+                      h.batch == mine.batch && h.nsteps == mine.nsteps && h.order == mine.order &&
+                      h.startup == mine.startup && h.precision == mine.precision && h.nu0 == mine.nu0 &&
+                      h.nu1 == mine.nu1 && h.alpert_p == mine.alpert_p && h.gauss_q == mine.gauss_q &&
+                      h.n_r == mine.n_r && h.dt == mine.dt && h.H == mine.H && h.ws_bytes == mine.ws_bytes;
+    if (!same) return c->fail(TDSE_EINVAL, "checkpoint of a different configuration");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const char* in = static_cast<const char*>(blob);
+    TDSE_CK(c, cudaMemcpyAsync(c->ws, in + sizeof(h) + 2 * (size_t)c->B, c->ws_need, cudaMemcpyHostToDevice, s));
+    TDSE_CK(c, cudaStreamSynchronize(s));
+    for (int b = 0; b < c->B; ++b) {
+        c->have_V[b] = in[sizeof(h) + 2 * b];
+        c->have_u0[b] = in[sizeof(h) + 2 * b + 1];
+    }
+    c->step = h.step;
+    c->inited = h.inited != 0;
+    c->ip = h.ip != 0;
+    c->res_every = h.res_every;
+    c->res_checks = h.res_checks;
+    c->res_tol = h.res_tol;
+    return TDSE_OK;
+}
+
 int tdse_step_index(const tdse_ctx* c) { return c ? c->step : -1; }
 double tdse_time(const tdse_ctx* c) { return c ? c->step * c->cfg.dt : 0.0; }
 

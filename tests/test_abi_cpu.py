@@ -173,3 +173,16 @@ def test_batch_create_validates_without_gpu(native):
     assert lib.tdse_batch_create(arr, 1, ctypes.byref(out)) == -1      # workspace not bound
     assert lib.tdse_batch_step(None, 1, None) == -1
     lib.tdse_destroy(ctx)
+
+
+def test_checkpoint_size_query_without_gpu(native):
+    lib = native.lib()
+    ctx = ctypes.c_void_p()
+    assert lib.tdse_create(ctypes.byref(_cfg(native)), ctypes.byref(ctx)) == 0
+    n = ctypes.c_size_t()
+    assert lib.tdse_save(ctx, None, ctypes.byref(n), None) == 0
+    assert n.value > lib.tdse_workspace_bytes(ctx)
+    buf = ctypes.create_string_buffer(n.value)
+    assert lib.tdse_save(ctx, buf, ctypes.byref(n), None) == -6          # workspace not bound
+    assert lib.tdse_load(ctx, buf, n.value, None) == -6
+    lib.tdse_destroy(ctx)
