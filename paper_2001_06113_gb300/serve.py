@@ -14,6 +14,13 @@ step count).  The loop
     time-to-solution;
   * reports p50 / p99 time-to-solution and the aggregate point-steps/s.
 
+Failures stay with their request: a request whose set-up or start fails (e.g.
+no device memory), whose result is not finite, or which is cancelled
+(`cancel_after` seconds after its arrival) gets `error` set, its workspace
+released once nothing of it is left on the device, and the loop goes on with
+the others.  Kernels already enqueued cannot be stopped: a cancelled active
+solve runs to its end, and its result is dropped.
+
 Every step runs in the library's kernels through `Problem`; this module is
 host-side scheduling only.  The device operations are behind a small backend
 interface so that the scheduling logic is testable without a GPU.
@@ -40,9 +47,11 @@ class Request:
     precision: str = "mixed"
     free: Optional[dict] = None
     # filled in by the server
+    cancel_after: Optional[float] = None   # seconds after arrival
     admitted: Optional[float] = None
     finished: Optional[float] = None
     result: Optional[np.ndarray] = None
+    error: Optional[str] = None
 
     @property
     def points(self) -> int:
@@ -74,6 +83,9 @@ class Backend:
 
     def finish(self, handle) -> np.ndarray:          # read the result, release the workspace
         raise NotImplementedError
+
+    def release(self, handle):                       # drop a started solve (after done) or a failed start
+        pass
 
 
 class TorchBackend(Backend):
@@ -120,10 +132,17 @@ class TorchBackend(Backend):
 
     def finish(self, handle) -> np.ndarray:
         prob = handle["prob"]
-        u = prob.read_u(0)
-        prob.close()
-        handle["prob"] = None
-        return u
+        try:
+            prob.check_finite()
+            return prob.read_u(0)
+        finally:
+            self.release(handle)
+
+    def release(self, handle):
+        prob = handle.get("prob")
+        if prob is not None:
+            prob.close()
+            handle["prob"] = None
 
 
 class Server:
@@ -147,39 +166,73 @@ class Server:
         waiting = sorted(requests, key=lambda r: (r.arrival, r.rid))
         handles = {}
         for r in waiting:
-            handles[r.rid] = self.backend.prepare(r)
+            try:
+                handles[r.rid] = self.backend.prepare(r)
+            except Exception as e:                   # invalid request: reported, not served
+                r.error = f"prepare: {e}"
+                continue
             if self.backend.workspace_bytes(handles[r.rid]) > self.hbm_budget:
                 raise ValueError(f"request {r.rid} needs more than the HBM budget")
+        waiting = [r for r in waiting if r.error is None]
         active: List[Request] = []
         used = 0
         t0 = self.clock()
         qi = 0
+
+        def cancelled(r, now):
+            return r.cancel_after is not None and now >= r.arrival + r.cancel_after
+
         while qi < len(waiting) or active:
             now = self.clock() - t0
             progressed = False
             # completions first: they free memory for admissions
             for r in list(active):
                 h = handles[r.rid]
-                if self.backend.done(h):
-                    r.result = self.backend.finish(h)
-                    r.finished = self.clock() - t0
-                    used -= self.backend.workspace_bytes(h)
-                    active.remove(r)
-                    progressed = True
+                try:
+                    finished = self.backend.done(h)
+                except Exception as e:
+                    r.error, finished = f"done: {e}", True
+                if not finished:
+                    if cancelled(r, now) and r.error is None:
+                        r.error = "cancelled"            # dropped once its enqueued work ends
+                    continue
+                if r.error is None:
+                    try:
+                        r.result = self.backend.finish(h)
+                    except Exception as e:
+                        r.error = f"finish: {e}"
+                else:
+                    self.backend.release(h)
+                r.finished = self.clock() - t0
+                used -= self.backend.workspace_bytes(h)
+                active.remove(r)
+                progressed = True
             # admissions in arrival order (head-of-line: a large request waits for memory)
             while qi < len(waiting) and len(active) < self.max_active:
                 r = waiting[qi]
                 if r.arrival > now:
                     break
+                if cancelled(r, now):                    # cancelled while waiting
+                    r.error = "cancelled"
+                    r.finished = now
+                    qi += 1
+                    progressed = True
+                    continue
                 need = self.backend.workspace_bytes(handles[r.rid])
                 if used + need > self.hbm_budget:
                     break
                 r.admitted = self.clock() - t0
-                self.backend.start(handles[r.rid])
-                used += need
-                active.append(r)
                 qi += 1
                 progressed = True
+                try:
+                    self.backend.start(handles[r.rid])
+                except Exception as e:                   # e.g. no device memory: this request fails
+                    r.error = f"start: {e}"
+                    self.backend.release(handles[r.rid])
+                    r.finished = self.clock() - t0
+                    continue
+                used += need
+                active.append(r)
                 self.peak_bytes = max(self.peak_bytes, used)
                 self.peak_active = max(self.peak_active, len(active))
             if not progressed:
@@ -189,9 +242,12 @@ class Server:
         return self.stats(requests, makespan)
 
     def stats(self, requests: Sequence[Request], makespan: float) -> Dict:
-        lat = np.array([r.latency for r in requests], dtype=np.float64)
-        work = float(sum(r.points * r.nsteps for r in requests))
-        return {"requests": len(requests), "makespan_s": makespan,
+        ok = [r for r in requests if r.error is None]
+        lat = np.array([r.latency for r in ok] or [np.nan], dtype=np.float64)
+        work = float(sum(r.points * r.nsteps for r in ok))
+        return {"requests": len(requests), "completed": len(ok),
+                "failed": sum(1 for r in requests if r.error is not None and r.error != "cancelled"),
+                "cancelled": sum(1 for r in requests if r.error == "cancelled"), "makespan_s": makespan,
                 "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                 "mean_s": float(lat.mean()), "point_steps": work,
                 "point_steps_per_s": work / makespan if makespan > 0 else None,

@@ -62,3 +62,29 @@ def test_budget_limits_concurrency():
     srv = Server(TorchBackend(), hbm_budget=2 * need + need // 2)
     srv.run(reqs)
     assert srv.peak_active == 2 and srv.peak_bytes <= 2 * need + need // 2
+
+
+def test_bad_requests_fail_alone():
+    """A request with a NaN in V (non-finite result) and an invalid one (grid
+    not a power of two) fail with their own errors; the rest of the stream is
+    served and equals the same solves alone."""
+    import copy
+    import torch
+    from paper_2001_06113_gb300.serve import Request, Server, TorchBackend
+    insts = [synth.periodic_2d_wells(seed=60 + i, M=64, dt=1e-3, nsteps=20) for i in range(4)]
+    bad = copy.deepcopy(insts[1])
+    bad.V0 = bad.V0.copy()
+    bad.V0[3, 5] = np.nan
+    odd = synth.random_periodic((48,), 3, 1e-3, 12)
+    reqs = [Request(0, 0.0, insts[0]), Request(1, 0.0, bad), Request(2, 0.0, insts[2]), Request(3, 0.0, odd),
+            Request(4, 0.0, insts[3])]
+    st = Server(TorchBackend(), hbm_budget=2 << 30).run(reqs)
+    assert st["completed"] == 3 and st["failed"] == 2
+    assert reqs[1].error.startswith("finish") and "NONFINITE" in reqs[1].error
+    assert reqs[3].error.startswith("prepare")
+    for r in (reqs[0], reqs[2], reqs[4]):
+        be = TorchBackend()
+        h = be.prepare(r)
+        be.start(h)
+        torch.cuda.synchronize()
+        assert np.array_equal(be.finish(h), r.result)

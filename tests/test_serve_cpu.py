@@ -44,6 +44,10 @@ class FakeBackend(Backend):
         self.log.append(("finish", h["req"].rid))
         return np.full(3, h["req"].rid, dtype=np.complex128)
 
+    def release(self, h):
+        if h["left"] is not None:
+            self.live -= h["bytes"]
+
 
 class Inst:
     def __init__(self, shape, nsteps):
@@ -93,3 +97,53 @@ def test_oversize_request_rejected():
     srv = Server(be, 100, clock=FakeClock(), idle_sleep=0)
     with pytest.raises(ValueError):
         srv.run([Request(0, 0.0, Inst((64,), 3))])
+
+
+class FailingBackend(FakeBackend):
+    """Start fails for some requests (as a device allocation failure would);
+    the result of others is not finite."""
+
+    def __init__(self, fail_start=(), fail_finish=()):
+        super().__init__()
+        self.fail_start, self.fail_finish = set(fail_start), set(fail_finish)
+        self.released = []
+
+    def start(self, h):
+        if h["req"].rid in self.fail_start:
+            raise MemoryError("no device memory for the workspace")
+        super().start(h)
+
+    def finish(self, h):
+        if h["req"].rid in self.fail_finish:
+            self.live -= h["bytes"]
+            raise FloatingPointError("non-finite values in the mode state")
+        return super().finish(h)
+
+    def release(self, h):
+        self.released.append(h["req"].rid)
+        super().release(h)
+
+
+def test_failures_stay_with_their_request():
+    reqs = _requests(30, seed=1)
+    be = FailingBackend(fail_start={3, 7}, fail_finish={11})
+    srv = Server(be, 1024 * 10 * 4, max_active=8, clock=FakeClock(), idle_sleep=0)
+    st = srv.run(reqs)
+    assert st["failed"] == 3 and st["completed"] == 27 and st["cancelled"] == 0
+    assert reqs[3].error.startswith("start") and reqs[11].error.startswith("finish")
+    assert 3 in be.released and 7 in be.released
+    assert all(r.result is not None for r in reqs if r.error is None)
+    assert be.live == 0                               # every workspace given back
+
+
+def test_cancellation_waiting_and_active():
+    reqs = [Request(i, 0.0, Inst((1024,), 40)) for i in range(4)]
+    reqs[0].cancel_after = 0.005                      # active: runs out, result dropped
+    reqs[3].cancel_after = 0.0                        # still waiting (budget): never starts
+    be = FakeBackend()
+    srv = Server(be, 1024 * 10 * 2, max_active=8, clock=FakeClock(), idle_sleep=0)
+    st = srv.run(reqs)
+    assert st["cancelled"] == 2 and st["completed"] == 2
+    assert reqs[0].result is None and reqs[0].admitted is not None
+    assert reqs[3].admitted is None
+    assert ("start", 3) not in be.log and be.live == 0
