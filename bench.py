@@ -329,6 +329,9 @@ def run_gpu(args, ws, rank, local):
 # ------------------------------------------------------------ free-space arm
 FS_M, FS_NU, FS_DT, FS_NSTEPS, FS_Q, FS_NR, FS_EPS = 256, 2048, 5e-4, 2000, 10, 1, 1e-10
 FS_METRIC = "point-steps/s (2D free space 256^2, nu=2048, 8th-order, T=1, eps=1e-10)"
+# DRAM bytes of one fused k_fs_row launch (end + begin) of one 256^2 instance,
+# from the ncu capture summarised in profiles/step2d_free_256x256_fp64.md.
+FS_ROW_TRAFFIC = 484.806912e6 + 123.36256e6
 
 
 def free_instances(rank: int, batch: int):
@@ -449,7 +452,8 @@ def run_free(args, ws, rank, local):
     flops = free_flops_per_step() * B
     achieved = flops / t_step / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": FS_ROW_TRAFFIC * B,
+                "traffic_unit": "DRAM bytes per fused k_fs_row launch (ncu), per instance x instances",
                 "peak_source": "FP64 FMA rate of a register-resident microbenchmark on this GB300 pool "
                                "(no FP64 figure in MEASURED_PEAKS.json)",
                 "kernel": "2D free-space Adams step (k_fs_row end+begin + k_fs_phys), timed over groups of 10 steps",
@@ -645,6 +649,9 @@ def main_free(args, ws, rank, local):
 B1_COUNT, B1_DT, B1_NSTEPS = 512, 1e-3, 1000
 B1_METRIC = "point-steps/s (512 uneven 1D periodic instances, N in 256..16384, 8th-order, T=1, mixed)"
 B1_ALGO_BYTES = 16 + 7 * 8 + 4 + 16 + 8      # mixed 1D step: state in/out, 7 ring reads, 1 write, V
+# DRAM bytes of one k_periodic1d_multi launch over the 512 instances (ncu capture,
+# default launch shape; profiles/batch1d_512_uneven_mixed.md).
+B1_MULTI_TRAFFIC = 225.796096e6 + 51.56864e6
 
 
 def batch1d_instances(rank: int):
@@ -737,7 +744,8 @@ def run_batch1d(args, ws, rank, local):
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = B1_ALGO_BYTES * points / t_step / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4), "traffic": B1_MULTI_TRAFFIC,
+                "traffic_unit": "DRAM bytes per k_periodic1d_multi launch (ncu, default launch shape)",
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "kernel": "k_periodic1d_multi (one persistent launch per Adams step for all 512 instances), "
                           "timed per step over 100 steps",
