@@ -270,6 +270,38 @@ struct Fft {
             sync();
         }
     }
+
+    // The same transform split for callers that produce the inputs / consume
+    // the outputs one item at a time in a non-unrolled loop (NPASS > 1):
+    //   first_item(p, v)  for every p, then  middle(...),  then either
+    //   last_item(p, v)   for every p followed by  finish(sync)   (buf free again).
+    __device__ static __forceinline__ void first_item(int p, C (&v)[RF], C* buf, int tid) {
+        int j, line;
+        if (item(p, NBF, j, line, tid)) {
+            dft_r<RF, INV>(v);
+#pragma unroll
+            for (int r = 0; r < RF; ++r) buf[(j * RF + r) * PS + line] = v[r];
+        }
+    }
+    template <class Sync>
+    __device__ static __forceinline__ void middle(C* buf, const C* __restrict__ tw, const C* __restrict__ twl,
+                                                  int tid, const Sync& sync) {
+        sync();
+        mids<1>(buf, tw, twl, tid, sync);
+    }
+    __device__ static __forceinline__ bool last_item(int p, C (&v)[RL], const C* buf, const C* __restrict__ tw,
+                                                     const C* __restrict__ twl, int tid, int& j) {
+        int line;
+        if (!item(p, NBL, j, line, tid)) return false;
+#pragma unroll
+        for (int r = 0; r < RL; ++r) v[r] = buf[(j + r * NBL) * PS + line];
+#pragma unroll
+        for (int r = 1; r < RL; ++r) v[r] = twiddle<INV>(v[r], tw, twl, j * r);
+        dft_r<RL, INV>(v);
+        return true;
+    }
+    template <class Sync>
+    __device__ static __forceinline__ void finish(const Sync& sync) { sync(); }
 };
 
 // ---------------------------------------------------------------------------

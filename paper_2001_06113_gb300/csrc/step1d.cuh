@@ -121,80 +121,134 @@ __device__ __forceinline__ void step1d(const KArgs& a, const int b, const int ti
     }
 
     const bool step = (a.mode == MODE_STEP);
-    ST Wk[KEEP ? PB : 1][KEEP ? RB : 1];
-    C in[PB][RB], mid[FI::PL][FI::RL], out[FW::PL][FW::RL];
-#pragma unroll
-    for (int p = 0; p < PB; ++p) {
-        int j, line;
-        if (FI::item(p, FI::NBF, j, line, tid)) {
-#pragma unroll
-            for (int r = 0; r < RB; ++r) {
-                const int k = j + r * FI::NBF;
-                ST W = st[k];
-                C x;
-                if (step) {
-                    if constexpr (!FF) {
-                        Phase1D ph{a, b, k};
-                        W = horner_W64(a, W, reinterpret_cast<const double2*>(ringb), NP, (size_t)k, ph);
-                        x = cvt<C>(W);
-                    } else {
-                        if (a.ip) {
-                            W = ip_X(a, W, reinterpret_cast<const float2*>(ringb), NP, (size_t)k);
-                            x = cvt<C>(cmul(e_1d(a, b, a.e_step, k), make_float2(W.x, W.y)));
-                        } else {
-                            W = mixed_X(a, W, reinterpret_cast<const float2*>(ringb), NP, (size_t)k);
-                            Phase1D ph{a, b, k};
-                            W = ffc_mul(ph.pff(0), W);
-                            x = st_to_c<C>(W);
-                        }
-                    }
-                    if constexpr (KEEP) Wk[p][r] = W; else st[k] = W;
-                } else {
-                    x = st_to_c<C>(W);
-                }
-                in[p][r] = x;
+    // Start of the step at mode k: the inverse-transform input; W (or X) is
+    // returned for the update.
+    auto input_of = [&](int k, ST& W) -> C {
+        W = st[k];
+        if (!step) return st_to_c<C>(W);
+        if constexpr (!FF) {
+            Phase1D ph{a, b, k};
+            W = horner_W64(a, W, reinterpret_cast<const double2*>(ringb), NP, (size_t)k, ph);
+            return cvt<C>(W);
+        } else {
+            if (a.ip) {
+                W = ip_X(a, W, reinterpret_cast<const float2*>(ringb), NP, (size_t)k);
+                return cvt<C>(cmul(e_1d(a, b, a.e_step, k), make_float2(W.x, W.y)));
+            }
+            W = mixed_X(a, W, reinterpret_cast<const float2*>(ringb), NP, (size_t)k);
+            Phase1D ph{a, b, k};
+            W = ffc_mul(ph.pff(0), W);
+            return st_to_c<C>(W);
+        }
+    };
+    // End of the step at mode k from the forward-transform output o and W.
+    auto output_of = [&](int k, C o, const ST& W) {
+        RT rv = cvt<RT>(cscale(o, scale));
+        if constexpr (FF) {
+            if (step && a.ip) {
+                rv = cmul(make_float2(a.zr[0], a.zr[1]), cmul(conjf2(e_1d(a, b, a.e_step, k)), rv));
+                ringb[(size_t)a.out_slot * NP + k] = rv;
+                st[k] = ip_update(a, W, rv);
+                return;
             }
         }
-    }
-    FI::run(in, mid, buf, tw, twl, tid, sync);
+        ringb[(size_t)a.out_slot * NP + k] = rv;
+        if (step) {
+            if constexpr (FF) st[k] = update_ff(a, W, rv);
+            else st[k] = update64(W, rv, a.h * a.mu[0]);
+        }
+    };
     const R hmu0 = step ? (R)(a.h * a.mu[0]) : (R)0;
+    auto solve = [&](C (&m)[FI::PL][FI::RL]) {
 #pragma unroll
-    for (int p = 0; p < FI::PL; ++p) {
-        int j, line;
-        if (FI::item(p, FI::NBL, j, line, tid)) {
+        for (int p = 0; p < FI::PL; ++p) {
+            int j, line;
+            if (FI::item(p, FI::NBL, j, line, tid)) {
 #pragma unroll
-            for (int r = 0; r < FI::RL; ++r) {
-                R vh, vl;
-                Vat(j + r * FI::NBL, vh, vl);
-                mid[p][r] = implicit_solve_times_V(mid[p][r], vh, vl, hmu0);
+                for (int r = 0; r < FI::RL; ++r) {
+                    R vh, vl;
+                    Vat(j + r * FI::NBL, vh, vl);
+                    m[p][r] = implicit_solve_times_V(m[p][r], vh, vl, hmu0);
+                }
             }
         }
-    }
-    FW::run(mid, out, buf, tw, twl, tid, sync);
+    };
+
+    // Large n (several items per thread, W parked in the state slot): the
+    // element phases run one item at a time in a rolled loop, which keeps the
+    // kernel's code within the instruction cache.
+    constexpr bool ROLLED = !KEEP && PB > 1 && FI::NPASS > 1 && FW::NPASS > 1;
+    if constexpr (ROLLED) {
+#pragma unroll 1
+        for (int p = 0; p < PB; ++p) {
+            int j, line;
+            C x[RB];
+            if (FI::item(p, FI::NBF, j, line, tid)) {
 #pragma unroll
-    for (int p = 0; p < FW::PL; ++p) {
-        int j, line;
-        if (FW::item(p, FW::NBL, j, line, tid)) {
+                for (int r = 0; r < RB; ++r) {
+                    const int k = j + r * FI::NBF;
+                    ST W;
+                    x[r] = input_of(k, W);
+                    if (step) st[k] = W;
+                }
+            }
+            FI::first_item(p, x, buf, tid);
+        }
+        FI::middle(buf, tw, twl, tid, sync);
+        C mid[FI::PL][FI::RL];
 #pragma unroll
-            for (int r = 0; r < FW::RL; ++r) {
-                const int k = j + r * FW::NBL;
-                RT rv = cvt<RT>(cscale(out[p][r], scale));
-                bool done = false;
-                if constexpr (FF) {
-                    if (step && a.ip) {
-                        rv = cmul(make_float2(a.zr[0], a.zr[1]), cmul(conjf2(e_1d(a, b, a.e_step, k)), rv));
-                        ringb[(size_t)a.out_slot * NP + k] = rv;
-                        st[k] = ip_update(a, KEEP ? Wk[p][r] : st[k], rv);
-                        done = true;
+        for (int p = 0; p < FI::PL; ++p) {
+            int j;
+            FI::last_item(p, mid[p], buf, tw, twl, tid, j);
+        }
+        FI::finish(sync);
+        solve(mid);
+#pragma unroll
+        for (int p = 0; p < FW::PF; ++p) FW::first_item(p, mid[p], buf, tid);
+        FW::middle(buf, tw, twl, tid, sync);
+#pragma unroll 1
+        for (int p = 0; p < FW::PL; ++p) {
+            C o[FW::RL];
+            int j;
+            if (FW::last_item(p, o, buf, tw, twl, tid, j)) {
+#pragma unroll
+                for (int r = 0; r < FW::RL; ++r) {
+                    const int k = j + r * FW::NBL;
+                    output_of(k, o[r], st[k]);
+                }
+            }
+        }
+        FW::finish(sync);
+        return;
+    } else {
+        ST Wk[KEEP ? PB : 1][KEEP ? RB : 1];
+        C in[PB][RB], mid[FI::PL][FI::RL], out[FW::PL][FW::RL];
+#pragma unroll
+        for (int p = 0; p < PB; ++p) {
+            int j, line;
+            if (FI::item(p, FI::NBF, j, line, tid)) {
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    const int k = j + r * FI::NBF;
+                    ST W;
+                    in[p][r] = input_of(k, W);
+                    if (step) {
+                        if constexpr (KEEP) Wk[p][r] = W; else st[k] = W;
                     }
                 }
-                if (!done) {
-                    ringb[(size_t)a.out_slot * NP + k] = rv;
-                    if (step) {
-                        const ST W = KEEP ? Wk[p][r] : st[k];
-                        if constexpr (FF) st[k] = update_ff(a, W, rv);
-                        else st[k] = update64(W, rv, a.h * a.mu[0]);
-                    }
+            }
+        }
+        FI::run(in, mid, buf, tw, twl, tid, sync);
+        solve(mid);
+        FW::run(mid, out, buf, tw, twl, tid, sync);
+#pragma unroll
+        for (int p = 0; p < FW::PL; ++p) {
+            int j, line;
+            if (FW::item(p, FW::NBL, j, line, tid)) {
+#pragma unroll
+                for (int r = 0; r < FW::RL; ++r) {
+                    const int k = j + r * FW::NBL;
+                    output_of(k, out[p][r], KEEP ? Wk[p][r] : st[k]);
                 }
             }
         }
