@@ -68,7 +68,8 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default=None, choices=["mixed", "fp64"],
+                    help="default: mixed (periodic2d, batch1d, serve), fp64 (free2d)")
     ap.add_argument("--batch", type=int, default=0,
                     help="instances per GPU (default: 64 periodic mixed, 4 periodic fp64, 1 free space)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
@@ -259,13 +260,7 @@ def run_gpu(args, ws, rank, local):
     dts = np.array([evs[i].elapsed_time(evs[i + 1]) / 1e3 / GROUP for i in range(NGROUPS)])
     t_step = float(np.mean(dts))
     algo = ALGO_BYTES[args.precision] * B * points
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    peak = peaks.get("hbm_gbs", 6800.0)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    peak, peak_src = hbm_peak()
     achieved = algo / t_step / 1e9
     tb = TRAFFIC_BYTES_PER_POINT_STEP.get(args.precision)
     traffic = None if tb is None else round(tb * B * points)
@@ -327,11 +322,18 @@ def run_gpu(args, ws, rank, local):
 
 
 # ------------------------------------------------------------ free-space arm
-FS_M, FS_NU, FS_DT, FS_NSTEPS, FS_Q, FS_NR, FS_EPS = 256, 2048, 5e-4, 2000, 10, 1, 1e-10
-FS_METRIC = "point-steps/s (2D free space 256^2, nu=2048, 8th-order, T=1, eps=1e-10)"
+FS_M, FS_NU, FS_DT, FS_NSTEPS, FS_Q, FS_NR = 256, 2048, 5e-4, 2000, 10, 1
+# target precision eps of Remark Hchoice: FP64 sums (eps_m = 2^-52) and the
+# FP32-transform variant (eps_m = 2^-23)
+FS_EPS = {"fp64": 1e-10, "mixed": 1e-4}
+FS_METRICS = {"fp64": "point-steps/s (2D free space 256^2, nu=2048, 8th-order, T=1, eps=1e-10)",
+              "mixed": "point-steps/s (2D free space 256^2, nu=2048, 8th-order, T=1, FP32 transforms, eps=1e-4)"}
+FS_METRIC = FS_METRICS["fp64"]
 # DRAM bytes of one fused k_fs_row launch (end + begin) of one 256^2 instance,
 # from the ncu capture summarised in profiles/step2d_free_256x256_fp64.md.
-FS_ROW_TRAFFIC = 484.806912e6 + 123.36256e6
+FS_ROW_TRAFFIC = {"fp64": 484.806912e6 + 123.36256e6, "mixed": None}
+# FP32 FMA rate: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def free_instances(rank: int, batch: int):
@@ -339,9 +341,10 @@ def free_instances(rank: int, batch: int):
                                       T_pulse=1.0) for i in range(batch)]
 
 
-def free_H(insts) -> float:
+def free_H(insts, precision: str = "fp64") -> float:
     """Remark Hchoice for the batch: ||V||_2 on the grid, max |phi| from the
-    sampled pulse (cumulative trapezoid on 20001 points), eps = 1e-10."""
+    sampled pulse (cumulative trapezoid on 20001 points), eps of FS_EPS and
+    the machine epsilon of the precision the contour sums run in."""
     from paper_2001_06113_gb300 import free_choose_H
     vnorm = max(math.sqrt(float(np.sum(it.V0 ** 2))) * 2.0 / FS_M for it in insts)
     phimax = 0.0
@@ -350,7 +353,7 @@ def free_H(insts) -> float:
         A = it.pulse.A(t)
         phi = np.concatenate([np.zeros((1, A.shape[1])), np.cumsum(0.5 * (A[1:] + A[:-1]) * (t[1] - t[0]), axis=0)])
         phimax = max(phimax, float(np.max(np.abs(phi))))
-    return free_choose_H(FS_EPS, vnorm, phimax, 2)
+    return free_choose_H(FS_EPS[precision], vnorm, phimax, 2, precision=precision)
 
 
 def free_mode_count() -> int:
@@ -378,6 +381,27 @@ def free_flops_per_step() -> float:
     return N * row + M * col
 
 
+def hbm_peak():
+    """(GB/s, "measured" | "fallback"): the machine's measured copy bandwidth."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    return peaks.get("hbm_gbs", 6800.0), ("measured" if "hbm_gbs" in peaks else "fallback")
+
+
+def free_algo_bytes(precision: str) -> float:
+    """Algorithmic DRAM bytes of one 2D free-space Adams step, per instance:
+    per mode the state read and W written (FP64, 32 B), nhist - 1 = 6 ring
+    lags read and the new (Vu)^ written (ring element e = 16 B in FP64, 8 B
+    FP32); per intermediate value Z (N0 x M1) one write and one read in each
+    pass (4 e); per grid point V read (8 B) and u written (16 B)."""
+    N, M = free_mode_count(), FS_M
+    e = 16 if precision == "fp64" else 8
+    return N * N * (32 + 7 * e) + 4 * N * M * e + M * M * 24
+
+
 def run_free(args, ws, rank, local):
     import torch
     from paper_2001_06113_gb300 import Problem
@@ -387,8 +411,9 @@ def run_free(args, ws, rank, local):
     stream = torch.cuda.Stream(device=dev)
     insts = free_instances(rank, args.batch)
     B = len(insts)
-    H = free_H(insts)
-    prob = Problem((FS_M, FS_M), FS_DT, FS_NSTEPS, order=ORDER, batch=B, precision="fp64", stream=stream, bc="free",
+    prec = args.precision
+    H = free_H(insts, prec)
+    prob = Problem((FS_M, FS_M), FS_DT, FS_NSTEPS, order=ORDER, batch=B, precision=prec, stream=stream, bc="free",
                    nu=(FS_NU, FS_NU), H=H, gauss_q=FS_Q, n_r=FS_NR)
     pinned_V = [torch.from_numpy(it.V0).pin_memory() for it in insts]
     pinned_u = [torch.from_numpy(it.u0).pin_memory() for it in insts]
@@ -451,15 +476,32 @@ def run_free(args, ws, rank, local):
     t_step = float(np.mean(dts))
     flops = free_flops_per_step() * B
     achieved = flops / t_step / 1e12
-    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": FS_ROW_TRAFFIC * B,
-                "traffic_unit": "DRAM bytes per fused k_fs_row launch (ncu), per instance x instances",
-                "peak_source": "FP64 FMA rate of a register-resident microbenchmark on this GB300 pool "
-                               "(no FP64 figure in MEASURED_PEAKS.json)",
-                "kernel": "2D free-space Adams step (k_fs_row end+begin + k_fs_phys), timed over groups of 10 steps",
-                "algorithmic_flops_per_step": flops,
-                "step_ms_p50": round(float(np.percentile(dts, 50)) * 1e3, 4),
-                "step_ms_p99": round(float(np.percentile(dts, 99)) * 1e3, 4)}
+    traffic = FS_ROW_TRAFFIC[prec] * B if FS_ROW_TRAFFIC[prec] else None
+    timing = {"kernel": "2D free-space Adams step (k_fs_row end+begin + k_fs_phys), timed over groups of 10 steps",
+              "algorithmic_flops_per_step": flops,
+              "step_ms_p50": round(float(np.percentile(dts, 50)) * 1e3, 4),
+              "step_ms_p99": round(float(np.percentile(dts, 99)) * 1e3, 4)}
+    if prec == "fp64":
+        roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                    "traffic_unit": "DRAM bytes per fused k_fs_row launch (ncu), per instance x instances",
+                    "peak_source": "FP64 FMA rate of a register-resident microbenchmark on this GB300 pool "
+                                   "(no FP64 figure in MEASURED_PEAKS.json)", **timing}
+    else:
+        # FP32 transforms: both ceilings, the nearer one reported as the bound
+        algo = free_algo_bytes(prec) * B
+        gbs = algo / t_step / 1e9
+        alu = {"achieved": round(achieved, 4), "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
+               "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+               "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
+        hpk, hsrc = hbm_peak()
+        hbm = {"achieved": round(gbs, 1), "peak": hpk, "unit": "GB/s", "frac": round(gbs / hpk, 4),
+               "algorithmic_bytes_per_step": algo, "peak_source": hsrc}
+        top, other = ("hbm", "alu") if hbm["frac"] >= alu["frac"] else ("alu", "hbm")
+        pick = {"hbm": hbm, "alu": alu}
+        roofline = {"bound": top, **pick[top], "traffic": traffic,
+                    "traffic_unit": "DRAM bytes per fused k_fs_row launch (ncu), per instance x instances",
+                    "other_ceiling": {"bound": other, **pick[other]}, **timing}
     e2e = None
     if not args.no_e2e:
         out = torch.empty((B, FS_M, FS_M), dtype=torch.complex128).pin_memory()
@@ -479,8 +521,27 @@ def run_free(args, ws, rank, local):
         h2d = B * (points * 8 + points * 16)
         e2e = {"value": ws * B * points * FS_NSTEPS / te, "unit": "point-steps/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": B * points * 16}
+    stated_err = None
+    if prec == "mixed" and rank == 0:
+        # the FP32-transform variant against the FP64 path on the same contour
+        NCHK = 40
+        ref = Problem((FS_M, FS_M), FS_DT, FS_NSTEPS, order=ORDER, batch=1, precision="fp64", stream=stream,
+                      bc="free", nu=(FS_NU, FS_NU), H=H, gauss_q=FS_Q, n_r=FS_NR)
+        it = insts[0]
+        ref.set_potential(it.V0, None)
+        ref.set_pulse(it.pulse.A0, it.pulse.omega, it.pulse.T_pulse, it.pulse.direction)
+        ref.set_initial(it.u0)
+        with torch.cuda.stream(stream):
+            reset()
+            prob.step(NCHK)
+            ref.step(NCHK)
+        stream.synchronize()
+        um, ud = prob.read_u(0), ref.read_u(0)
+        stated_err = {"rel_l2_vs_fp64_same_contour": float(np.linalg.norm(um - ud) / np.linalg.norm(ud)),
+                      "after_steps": NCHK}
+        ref.close()
     prob.close()
-    return dict(value=value, t_solve=t_solve, roofline=roofline, e2e=e2e, clocks=clk.summary(), stated_err=None,
+    return dict(value=value, t_solve=t_solve, roofline=roofline, e2e=e2e, clocks=clk.summary(), stated_err=stated_err,
                 B=B, H=H)
 
 
@@ -576,8 +637,8 @@ def free_profile_run(args):
     import torch
     from paper_2001_06113_gb300 import Problem
     insts = free_instances(0, args.batch)
-    prob = Problem((FS_M, FS_M), FS_DT, FS_NSTEPS, order=ORDER, batch=len(insts), precision="fp64", bc="free",
-                   nu=(FS_NU, FS_NU), H=free_H(insts), gauss_q=FS_Q, n_r=FS_NR)
+    prob = Problem((FS_M, FS_M), FS_DT, FS_NSTEPS, order=ORDER, batch=len(insts), precision=args.precision,
+                   bc="free", nu=(FS_NU, FS_NU), H=free_H(insts, args.precision), gauss_q=FS_Q, n_r=FS_NR)
     for b, it in enumerate(insts):
         prob.set_potential(it.V0, None, instance=b)
         p = it.pulse
@@ -587,6 +648,7 @@ def free_profile_run(args):
     torch.cuda.synchronize()
     prob.check_finite()
     print(json.dumps({"profile_adams": args.profile_adams, "batch": len(insts), "workload": "free2d",
+                      "precision": args.precision,
                       "launches_before_adams": free_launches_per_solve() - (2 * (FS_NSTEPS - STARTUP) + 1)}))
     prob.close()
     return 0
@@ -624,18 +686,21 @@ def main_free(args, ws, rank, local):
             cpu = {"value": v, "unit": "point-steps/s", "cores": cpu_cores(), "kind": "oracle",
                    "sample": f"3 8th-order Adams steps of one 256^2 free-space instance ({el:.1f} s; direct "
                              "transform sums, numpy/OpenBLAS)"}
+        prec = args.precision
         line = {
-            "metric": FS_METRIC, "value": res["value"], "unit": "point-steps/s", "n_gpus": ws,
+            "metric": FS_METRICS[prec], "value": res["value"], "unit": "point-steps/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["t_solve"] * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128" if prec == "fp64" else "c64+c128", "data": "synthetic",
             "config": {"workload": f"2D free space 256x256, nu=2048 (N=2058 modes/dim), p=8, q=10, n_r=1, "
-                                   f"H={res['H']:.4f} (eps=1e-10), T=1, dt=5e-4 (2000 steps), 8th-order Adams, "
-                                   f"batch of {res['B']} per GPU, fp64",
+                                   f"H={res['H']:.4f} (eps={FS_EPS[prec]:g}), T=1, dt=5e-4 (2000 steps), "
+                                   f"8th-order Adams, batch of {res['B']} per GPU, {prec}",
                        "grid": [FS_M, FS_M], "nu": FS_NU, "nsteps": FS_NSTEPS, "dt": FS_DT, "order": ORDER,
-                       "batch_per_gpu": res["B"], "precision": "fp64",
+                       "batch_per_gpu": res["B"], "precision": prec,
                        "l2": "flushed (256 MB write) before each timed solve; per-step working set > L2",
                        "step": "one whole solve (7 Richardson start-up + 1993 Adams steps)",
                        "parallelism": f"replicas x{ws}"},
+            "stated_err": res["stated_err"],
             "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
             "gpu_launches": free_launches_per_solve() * args.steps,
         }
@@ -1009,6 +1074,8 @@ def main_serve(args, ws, rank, local):
 def main():
     args = parse()
     ws, rank, local = dist_env()
+    if args.precision is None:
+        args.precision = "fp64" if args.workload == "free2d" else "mixed"
     if args.batch <= 0:
         args.batch = 1 if args.workload == "free2d" else (64 if args.precision == "mixed" else 4)
     if args.workload == "free2d":

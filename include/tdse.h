@@ -85,7 +85,13 @@ enum { TDSE_HOST = 0, TDSE_DEVICE = 1 };
  *   precision  TDSE_FP64: every stage in complex FP64.
  *              TDSE_MIXED: transforms, pointwise product and history sum in
  *              complex FP32; the mode state u^ and its phase recurrence, the
- *              phase tables and the Adams weights in FP64 (periodic only).
+ *              phase tables and the Adams weights in FP64.  Free space: the
+ *              transforms (with their tables), V u, the history ring, the 2D
+ *              intermediate and the history sum in FP32; u^, the one-step
+ *              phase p_0, W = p_0 (u^ - i h S_1), the update and u in FP64.
+ *              The contour sums then carry FP32 rounding amplified by the
+ *              growth of e^{i zeta x} off the real axis, so H must be chosen
+ *              for FP32 (tdse_free_choose_H_prec).
  * Free space only (ignored for TDSE_PERIODIC), Sec. 3.4 and 4.1:
  *   nu[2]      length of the equispaced FFTs per dimension: nu = R n with
  *              R in {4, 8, 16} and nu <= 4096.  The equispaced blocks then
@@ -200,6 +206,13 @@ tdse_status tdse_free_rule(const tdse_ctx* ctx, int axis, int* N, double* zeta, 
  * vnorm = max_t ||V(., t)||_2 on [-1,1]^dim, phimax = max_t |phi(t)|.
  * TDSE_EINVAL if the result is not positive and finite. */
 tdse_status tdse_free_choose_H(double eps, double vnorm, double phimax, int dim, double* H_out);
+
+/* The same offset for the precision the contour sums are evaluated in:
+ * eps_m = 2^-52 for TDSE_FP64 and 2^-23 (FP32 machine epsilon) for
+ * TDSE_MIXED, whose free-space transforms run in FP32 (Remark Hchoice with
+ * eps_m the machine epsilon of those sums).  TDSE_EINVAL for another
+ * precision or a result that is not positive and finite. */
+tdse_status tdse_free_choose_H_prec(double eps, double vnorm, double phimax, int dim, int precision, double* H_out);
 
 /* FP64 residual check of the mixed-precision implicit step (TDSE_MIXED,
  * periodic; 1D n <= 8192, 2D n <= 1024 per dimension).  After every

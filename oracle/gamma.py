@@ -138,9 +138,10 @@ KAPPA_FOR_P = {8: 7}      # the paper's choice for p = 8 (Sec. 7, Example 2)
 
 
 # ----------------------------------------------------------------- Gamma rule
-def choose_H(eps: float, vnorm: float, phimax: float, d: int) -> float:
-    """Remark Hchoice."""
-    return math.log(eps / ((1.0 + vnorm) * EPS_M)) / (2.0 * d * (1.0 + phimax))
+def choose_H(eps: float, vnorm: float, phimax: float, d: int, eps_m: float = EPS_M) -> float:
+    """Remark Hchoice; eps_m is the machine epsilon of the arithmetic that
+    evaluates the contour sums (FP64 by default, 2^-23 for FP32 sums)."""
+    return math.log(eps / ((1.0 + vnorm) * eps_m)) / (2.0 * d * (1.0 + phimax))
 
 
 class GammaRule:

@@ -36,10 +36,13 @@ def adams_weights(order: int) -> np.ndarray:
     return out
 
 
-def free_choose_H(eps: float, vnorm: float, phimax: float, dim: int) -> float:
-    """Contour offset H of Remark Hchoice (library formula)."""
+def free_choose_H(eps: float, vnorm: float, phimax: float, dim: int, precision: str = "fp64") -> float:
+    """Contour offset H of Remark Hchoice (library formula), with the machine
+    epsilon of the precision the contour sums run in ("fp64" or "mixed")."""
     out = ctypes.c_double()
-    _check(_native.lib().tdse_free_choose_H(float(eps), float(vnorm), float(phimax), int(dim), ctypes.byref(out)))
+    prec = {"fp64": FP64, "mixed": MIXED}[precision]
+    _check(_native.lib().tdse_free_choose_H_prec(float(eps), float(vnorm), float(phimax), int(dim), prec,
+                                                 ctypes.byref(out)))
     return out.value
 
 

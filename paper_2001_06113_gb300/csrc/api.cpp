@@ -290,7 +290,6 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     const bool big1d = !fs && cfg->dim == 1 && cfg->precision == TDSE_MIXED && n0 == four_step_n();
     if (!fs && cfg->dim == 1 && !periodic1d_supported(n0) && !big1d) return TDSE_EUNSUPPORTED;
     if (!fs && cfg->dim == 2 && !periodic2d_supported(n0, n1)) return TDSE_EUNSUPPORTED;
-    if (fs && cfg->precision != TDSE_FP64) return TDSE_EUNSUPPORTED;
     if ((long long)cfg->nsteps * SUB + 1 > (1LL << 30)) return TDSE_EINVAL;
 
     tdse_ctx* c = new (std::nothrow) tdse_ctx();
@@ -326,7 +325,10 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     // interval schedule (see startup_interval / main_interval)
     c->n_int_startup = c->S_eff * ((1 << c->L) - 1);
     const int n_main_rest = cfg->nsteps - c->S_eff;
-    c->n_int = c->n_int_startup + (c->mixed ? 0 : n_main_rest);
+    // periodic TDSE_MIXED evaluates the main-step phases from closed forms; the
+    // free-space variant keeps tables for every step.
+    const bool main_tables = !c->mixed || fs;
+    c->n_int = c->n_int_startup + (main_tables ? n_main_rest : 0);
     c->intervals.resize(c->n_int);
     for (int s = 1; s <= c->S_eff; ++s)
         for (int ch = 0; ch < c->L; ++ch) {
@@ -335,7 +337,7 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
                 c->intervals[startup_interval(c, s, ch, i)] =
                     make_int2(SUB * (s - 1) + i * len, SUB * (s - 1) + (i + 1) * len);
         }
-    if (!c->mixed)
+    if (main_tables)
         for (int n = c->S_eff + 1; n <= cfg->nsteps; ++n)
             c->intervals[main_interval(c, n)] = make_int2(SUB * (n - 1), SUB * n);
     c->nhi = cfg->nsteps / E1D_NLO + 1;
@@ -764,7 +766,9 @@ tdse_status tdse_check_finite(tdse_ctx* c, void* stream) {
     int* cnt = c->P<int>(c->off.scratch);
     TDSE_CK(c, cudaMemsetAsync(cnt, 0, sizeof(int), s));
     const size_t nmodes = c->fs ? c->F.NM : c->NP;
-    TDSE_CK(c, launch_count_nonfinite(c->P<void>(c->off.uhat), nmodes * c->B * 2, c->mixed && c->inited, cnt, s));
+    // the free-space mode state is FP64 in both precisions
+    TDSE_CK(c, launch_count_nonfinite(c->P<void>(c->off.uhat), nmodes * c->B * 2, c->mixed && c->inited && !c->fs,
+                                      cnt, s));
     int h = 0;
     TDSE_CK(c, cudaMemcpyAsync(&h, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
     TDSE_CK(c, cudaStreamSynchronize(s));
@@ -775,7 +779,7 @@ tdse_status tdse_check_finite(tdse_ctx* c, void* stream) {
 tdse_status tdse_read_modes(tdse_ctx* c, int instance, double* u_out, int where, void* stream) {
     if (!c || !u_out) return TDSE_EINVAL;
     if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
-    if (c->mixed) return c->fail(TDSE_EUNSUPPORTED, "mode state is FP64 only in TDSE_FP64");
+    if (c->mixed && !c->fs) return c->fail(TDSE_EUNSUPPORTED, "periodic mode state is FP64 only in TDSE_FP64");
     if (!c->inited) return c->fail(TDSE_ESTATE, "no step taken yet");
     int lo, hi;
     if (!instance_range(c, instance, lo, hi)) return c->fail(TDSE_EINVAL, "instance out of range");
@@ -804,7 +808,7 @@ tdse_status tdse_residual_report(tdse_ctx* c, double* rho, int* corrections, int
     if (!c) return TDSE_EINVAL;
     if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
     if (checks) *checks = c->res_checks;
-    if (!c->mixed) return TDSE_OK;
+    if (!c->mixed || c->fs) return TDSE_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (rho) TDSE_CK(c, cudaMemcpyAsync(rho, c->P<double>(c->off.res_rho), (size_t)c->B * 8, cudaMemcpyDeviceToHost, s));
     if (corrections)

@@ -29,9 +29,12 @@ struct FsState {
     FsAxisHost ax[2];
     size_t NM = 0;   // modes per instance (N0 N1)
     size_t NX = 0;   // grid points per instance (M0 M1)
+    bool f32 = false;   // TDSE_MIXED: FP32 transforms, ring, intermediate and history sum
     struct {
         size_t uhat, ring, chain_uhat, chain_ring, chain_u, u, Z, V0, tfac, phi, iv, scratch, end;
         size_t zeta[2], preI[2], postI[2], preF[2], postF[2], Gd[2], Fd[2], tw[2], P[2];
+        // FP32 copies (f32 only; 0 otherwise)
+        size_t preI_f[2], postI_f[2], preF_f[2], postF_f[2], Gd_f[2], Fd_f[2], tw_f[2], P_f[2];
     } off{};
 };
 

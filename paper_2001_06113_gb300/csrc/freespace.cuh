@@ -1,0 +1,423 @@
+// Free-space time step (Sec. 3.4, Remark highorderfs), templated on the
+// transform type: complex FP64 (double2) or the FP32-transform variant
+// (float2: transforms, V u and the history sum in FP32; the mode state, its
+// one-step phase p_0 and the update in FP64).
+//
+// One step of eq. uadamsk on the contour modes, with zeta for k and
+// zeta.zeta for |k|^2 (eq. uhatxirecur):
+//   W   = p_0 (u^ - i h S_1),  S_j = mu_j R_j + p_j S_{j+1}       (mode space)
+//   u   = inverse(W) / (1 + i h mu_0 V)                          (grid)
+//   F   = forward(V u);   u^ <- W - i h mu_0 F;   ring <- F
+// The trapezoidal sub-steps of the start-up are the same with nhist = 1 and
+// mu = (1/2, 1/2) (eqs. utrapzfd, uhatzfd).
+//
+// Transforms (fsargs.h): each axis is split into the two equispaced blocks,
+// done as R interleaved M-point FFTs with folded twiddles (eq. ssfftgen), and
+// the dense block of Alpert and Gauss modes, done as a direct sum.  In shared
+// memory the E buffer holds both blocks as 2R lines of length M:
+// element (pos, line) at E[pos * LS + line], line = b R + s, LS = 2R + 1 (one
+// pad slot against bank conflicts).  The mode i = s + R q of block b sits at
+// pos q; the grid value j at pos j.
+//
+// Kernels:
+//   k_fs_1d   one CTA per instance: the whole 1D step;
+//   k_fs_row  (2D) one CTA per mode row k0: forward along axis 1 of the row
+//             of the intermediate Z, mode update and ring write (end of a
+//             step), then W of the next step and its inverse along axis 1
+//             back into Z (begin of a step);
+//   k_fs_phys (2D) one CTA per grid column j1: inverse along axis 0 of the
+//             column of Z, implicit solve and V u on the grid, forward along
+//             axis 0 back into the same column of Z.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "cplx.cuh"
+#include "fsargs.h"
+
+namespace tdse {
+namespace fs {
+
+__device__ __forceinline__ double2 zero2() { return make_double2(0.0, 0.0); }
+template <class C> __device__ __forceinline__ C zeroc() { return czero<C>(); }
+// v * (-i c)
+__device__ __forceinline__ double2 times_minus_i(double2 v, double c) { return make_double2(c * v.y, -c * v.x); }
+
+// Tables of an axis in the transform type C.
+template <class C> struct Tab;
+template <> struct Tab<double2> {
+    static __device__ __forceinline__ const double2* preI(const FsAxis& a) { return a.preI; }
+    static __device__ __forceinline__ const double2* postI(const FsAxis& a) { return a.postI; }
+    static __device__ __forceinline__ const double2* preF(const FsAxis& a) { return a.preF; }
+    static __device__ __forceinline__ const double2* postF(const FsAxis& a) { return a.postF; }
+    static __device__ __forceinline__ const double2* Gd(const FsAxis& a) { return a.Gd; }
+    static __device__ __forceinline__ const double2* Fd(const FsAxis& a) { return a.Fd; }
+    static __device__ __forceinline__ const double2* tw(const FsAxis& a) { return a.tw; }
+    static __device__ __forceinline__ const double2* P(const FsAxis& a) { return a.P; }
+};
+template <> struct Tab<float2> {
+    static __device__ __forceinline__ const float2* preI(const FsAxis& a) { return a.preI_f; }
+    static __device__ __forceinline__ const float2* postI(const FsAxis& a) { return a.postI_f; }
+    static __device__ __forceinline__ const float2* preF(const FsAxis& a) { return a.preF_f; }
+    static __device__ __forceinline__ const float2* postF(const FsAxis& a) { return a.postF_f; }
+    static __device__ __forceinline__ const float2* Gd(const FsAxis& a) { return a.Gd_f; }
+    static __device__ __forceinline__ const float2* Fd(const FsAxis& a) { return a.Fd_f; }
+    static __device__ __forceinline__ const float2* tw(const FsAxis& a) { return a.tw_f; }
+    static __device__ __forceinline__ const float2* P(const FsAxis& a) { return a.P_f; }
+};
+
+template <class C, int M, int R>
+struct FsLine {
+    using T = Tab<C>;
+    static constexpr int L = 2 * R;
+    static constexpr int LS = 2 * R + 1;
+    static constexpr int NU = M * R;
+    static constexpr int EBUF = M * LS;
+    using FftF = CtaFft<C, M, L, LS, FS_T, false>;
+    using FftI = CtaFft<C, M, L, LS, FS_T, true>;
+
+    __device__ static __forceinline__ int epos(int b, int i) { return (i / R) * LS + b * R + (i % R); }
+
+    // Forward transform of the M grid values f (shared, complete).  On return
+    // E holds the block sums at epos(b, i) (before the post factor) and dv the
+    // dense results.  Ends with a barrier.
+    __device__ static void forward(const C* f, C* E, C* dv, const FsAxis& ax) {
+        const C* preF = T::preF(ax);
+        for (int it = threadIdx.x; it < 2 * NU; it += FS_T) {
+            const int b = it / NU, r = it - b * NU;
+            const int j = r / R, s = r % R;
+            E[j * LS + b * R + s] = cmul(f[j], __ldg(&preF[it]));
+        }
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int dd = warp; dd < ax.ND; dd += FS_T / 32) {
+            C acc = zeroc<C>();
+            const C* row = T::Fd(ax) + (size_t)dd * M;
+            for (int j = lane; j < M; j += 32) acc = acc + cmul(__ldg(&row[j]), f[j]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+            }
+            if (lane == 0) dv[dd] = acc;
+        }
+        __syncthreads();
+        FftF::run(E, T::tw(ax), nullptr);
+    }
+
+    // Forward result for mode m after forward().
+    __device__ static __forceinline__ C fwd_value(int m, const C* E, const C* dv, const FsAxis& ax) {
+        const int NE = ax.NE, ND = ax.ND;
+        if (m < NE) return cmul(E[epos(0, m)], __ldg(&T::postF(ax)[m]));
+        if (m < NE + ND) return dv[m - NE];
+        const int i = m - NE - ND;
+        return cmul(E[epos(1, i)], __ldg(&T::postF(ax)[NE + i]));
+    }
+
+    // Place the mode value W_m as an input of the inverse transform.
+    __device__ static __forceinline__ void stage_inv(int m, C W, C* E, C* dv, const FsAxis& ax) {
+        const int NE = ax.NE, ND = ax.ND;
+        if (m < NE) {
+            E[epos(0, m)] = cmul(W, __ldg(&T::preI(ax)[m]));
+        } else if (m < NE + ND) {
+            dv[m - NE] = W;
+        } else {
+            const int i = m - NE - ND;
+            E[epos(1, i)] = cmul(W, __ldg(&T::preI(ax)[NE + i]));
+        }
+    }
+
+    // Zero the inputs NE..nu-1 of both blocks (the zero padding of eq. ssfftgen).
+    __device__ static void zero_pad(C* E, int NE) {
+        const int per = NU - NE;
+        for (int it = threadIdx.x; it < 2 * per; it += FS_T) {
+            const int b = it / per, i = NE + (it - b * per);
+            E[epos(b, i)] = zeroc<C>();
+        }
+    }
+
+    // Inverse transform of the staged inputs into y (M values, shared).
+    // Begins and ends with a barrier.
+    __device__ static void inverse(C* E, const C* dv, C* y, const FsAxis& ax) {
+        __syncthreads();
+        FftI::run(E, T::tw(ax), nullptr);
+        for (int j = threadIdx.x; j < M; j += FS_T) {
+            C acc = zeroc<C>();
+            const C* pj = T::postI(ax) + (size_t)j * R;
+#pragma unroll
+            for (int s = 0; s < R; ++s) acc = acc + cmul(E[j * LS + s], __ldg(&pj[s]));
+#pragma unroll
+            for (int s = 0; s < R; ++s) acc = acc + cmul(E[j * LS + R + s], __ldg(&pj[NU + s]));
+            const C* gd = T::Gd(ax);
+            for (int dd = 0; dd < ax.ND; ++dd) acc = acc + cmul(__ldg(&gd[(size_t)dd * M + j]), dv[dd]);
+            y[j] = acc;
+        }
+        __syncthreads();
+    }
+};
+
+// c R + b S with one rounding per fused multiply-add (complex).
+__device__ __forceinline__ double2 cmul_add2(double2 c, double2 R, double2 b, double2 S) {
+    return make_double2(fma(c.x, R.x, fma(-c.y, R.y, fma(b.x, S.x, -b.y * S.y))),
+                        fma(c.x, R.y, fma(c.y, R.x, fma(b.x, S.y, b.y * S.x))));
+}
+__device__ __forceinline__ float2 cmul_add2(float2 c, float2 R, float2 b, float2 S) {
+    return make_float2(fmaf(c.x, R.x, fmaf(-c.y, R.y, fmaf(b.x, S.x, -b.y * S.y))),
+                       fmaf(c.x, R.y, fmaf(c.y, R.x, fmaf(b.x, S.y, b.y * S.x))));
+}
+
+// History sum of eq. uadamsk in Horner form with separable phases p_i = a_i b_i
+// (a_i of the row, b_i of the mode; 1D: a_i = 1):  S_j = c_j R_j + b_j S_{j+1},
+// c_j = mu_j a_1 .. a_{j-1}, so that S_1 = sum_j mu_j p_1 .. p_{j-1} R_j.
+// In the transform type C (FP32 in the FP32-transform variant).
+template <class C, class Lag, class PhaseB>
+__device__ __forceinline__ C history_sep(const FsArgs& a, const C (&c)[FS_MAX_HIST + 1], Lag lag, PhaseB phase_b) {
+    C S = zeroc<C>();
+#pragma unroll
+    for (int j = FS_MAX_HIST; j >= 1; --j) {
+        if (j <= a.nhist) {
+            if (j < FS_MAX_HIST && j < a.nhist)
+                S = cmul_add2(c[j], lag(j), phase_b(j), S);
+            else
+                S = cmul(c[j], lag(j));
+        }
+    }
+    return S;
+}
+
+// W = p_0 (u^ - i h S_1) in FP64 (the state recurrence keeps FP64 in both variants).
+__device__ __forceinline__ double2 begin_W(const FsArgs& a, double2 uh, double2 p0, double2 S) {
+    return cmul(p0, uh + times_minus_i(S, a.h));
+}
+
+// u = y / (1 + i c)
+template <class C, class Rl>
+__device__ __forceinline__ C implicit_solve(C y, Rl c) {
+    const Rl den = (Rl)1 + c * c;
+    C u;
+    u.x = (y.x + c * y.y) / den;
+    u.y = (y.y - c * y.x) / den;
+    return u;
+}
+
+template <class C>
+__device__ __forceinline__ void store_fwd(const FsArgs& a, size_t idx, C F) {
+    if (a.fdst_ring) reinterpret_cast<C*>(a.fdst)[idx] = F;
+    else a.fdst[idx] = cvt<double2>(F);
+}
+
+template <class C, int M, int R>
+__global__ void __launch_bounds__(FS_T) k_fs_1d(FsArgs a, int mode) {
+    using Ln = FsLine<C, M, R>;
+    using Rl = typename cx_traits<C>::real;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* E = reinterpret_cast<C*>(sm_raw);
+    C* y = E + Ln::EBUF;
+    C* dv = y + M;
+    const FsAxis& ax = a.ax[0];
+    const int b = blockIdx.x, N = ax.N;
+    const double vf = a.tfac[(size_t)b * a.ntf + a.tf];
+    const double* V0 = a.V0 + (size_t)b * M;
+    if (mode == FS_1D_FWD_ONLY) {
+        for (int j = threadIdx.x; j < M; j += FS_T) {
+            const double2 u = a.usrc[(size_t)b * M + j];
+            y[j] = cvt<C>(a.mulV ? cscale(u, vf * V0[j]) : u);
+        }
+        __syncthreads();
+        Ln::forward(y, E, dv, ax);
+        for (int m = threadIdx.x; m < N; m += FS_T)
+            store_fwd(a, (size_t)b * a.fdst_bstride + m, Ln::fwd_value(m, E, dv, ax));
+        return;
+    }
+    double2* uh = a.uhat + (size_t)b * N;
+    C* ring = reinterpret_cast<C*>(a.ring) + (size_t)b * a.ring_slots * N;
+    const double2* P = ax.P + (size_t)b * a.n_int * N;
+    const C* Pc = Tab<C>::P(ax) + (size_t)b * a.n_int * N;
+    C cj[FS_MAX_HIST + 1];
+#pragma unroll
+    for (int j = 0; j <= FS_MAX_HIST; ++j) cj[j] = cvt<C>(make_double2(a.mu[j], 0.0));
+    for (int m = threadIdx.x; m < N; m += FS_T) {
+        const C S = history_sep<C>(
+            a, cj, [&](int j) { return ring[(size_t)a.hist_slot[j - 1] * N + m]; },
+            [&](int i) { return __ldg(&Pc[(size_t)a.interval[i] * N + m]); });
+        const double2 W = begin_W(a, uh[m], __ldg(&P[(size_t)a.interval[0] * N + m]), cvt<double2>(S));
+        uh[m] = W;
+        Ln::stage_inv(m, cvt<C>(W), E, dv, ax);
+    }
+    Ln::zero_pad(E, ax.NE);
+    Ln::inverse(E, dv, y, ax);
+    const double hm0 = a.h * a.mu[0];
+    for (int j = threadIdx.x; j < M; j += FS_T) {
+        const double V = vf * V0[j];
+        const C u = implicit_solve(y[j], (Rl)(hm0 * V));
+        a.u[(size_t)b * M + j] = cvt<double2>(u);
+        y[j] = cscale(u, (Rl)V);
+    }
+    __syncthreads();
+    Ln::forward(y, E, dv, ax);
+    for (int m = threadIdx.x; m < N; m += FS_T) {
+        const C F = Ln::fwd_value(m, E, dv, ax);
+        uh[m] = uh[m] + times_minus_i(cvt<double2>(F), hm0);
+        ring[(size_t)a.out_slot * N + m] = F;
+    }
+}
+
+template <class C, int M, int R>
+__global__ void __launch_bounds__(FS_T) k_fs_row(FsArgs a, int flags) {
+    using Ln = FsLine<C, M, R>;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* E = reinterpret_cast<C*>(sm_raw);
+    C* f = E + Ln::EBUF;
+    C* dv = f + M;
+    const FsAxis& ax = a.ax[1];
+    const int k0 = blockIdx.x, b = blockIdx.y;
+    const int N0 = a.ax[0].N, N1 = ax.N;
+    const size_t NPm = (size_t)N0 * N1;
+    double2* urow = a.uhat + (size_t)b * NPm + (size_t)k0 * N1;
+    C* zrow = reinterpret_cast<C*>(a.Z) + ((size_t)b * N0 + k0) * M;
+    const bool end = flags & FS_ROW_END, begin = flags & FS_ROW_BEGIN;
+    if (end || (flags & FS_ROW_FWD_ONLY)) {
+        for (int j = threadIdx.x; j < M; j += FS_T) f[j] = zrow[j];
+        __syncthreads();
+        Ln::forward(f, E, dv, ax);
+        if (flags & FS_ROW_FWD_ONLY) {
+            const size_t base = (size_t)b * a.fdst_bstride + (size_t)k0 * N1;
+            for (int m = threadIdx.x; m < N1; m += FS_T) store_fwd(a, base + m, Ln::fwd_value(m, E, dv, ax));
+            return;
+        }
+    }
+    const double2* P0 = a.ax[0].P + (size_t)b * a.n_int * N0;
+    const double2* P1 = ax.P + (size_t)b * a.n_int * N1;
+    const C* P1c = Tab<C>::P(ax) + (size_t)b * a.n_int * N1;
+    double2 a0 = zero2();
+    C cj[FS_MAX_HIST + 1];
+    if (begin) {
+        a0 = __ldg(&P0[(size_t)a.interval[0] * N0 + k0]);
+        double2 A = make_double2(1.0, 0.0);
+#pragma unroll
+        for (int j = 1; j <= FS_MAX_HIST; ++j) {
+            cj[j] = cvt<C>(cscale(A, a.mu[j]));
+            if (j < FS_MAX_HIST && j < a.nhist) A = cmul(A, __ldg(&P0[(size_t)a.interval[j] * N0 + k0]));
+        }
+    }
+    const double hm0 = a.h * a.mu[0];
+    C* ring = reinterpret_cast<C*>(a.ring) + (size_t)b * a.ring_slots * NPm + (size_t)k0 * N1;
+    for (int m = threadIdx.x; m < N1; m += FS_T) {
+        double2 uh;
+        C F = zeroc<C>();
+        if (end) {
+            F = Ln::fwd_value(m, E, dv, ax);
+            uh = urow[m] + times_minus_i(cvt<double2>(F), hm0);
+            ring[(size_t)a.out_slot * NPm + m] = F;
+            if (!begin) urow[m] = uh;
+        } else {
+            uh = urow[m];
+        }
+        if (begin) {
+            const C S = history_sep<C>(
+                a, cj,
+                [&](int j) {
+                    const int slot = a.hist_slot[j - 1];
+                    return (end && slot == a.out_slot) ? F : ring[(size_t)slot * NPm + m];
+                },
+                [&](int i) { return __ldg(&P1c[(size_t)a.interval[i] * N1 + m]); });
+            const double2 p0 = cmul(a0, __ldg(&P1[(size_t)a.interval[0] * N1 + m]));
+            const double2 W = begin_W(a, uh, p0, cvt<double2>(S));
+            urow[m] = W;
+            Ln::stage_inv(m, cvt<C>(W), E, dv, ax);
+        }
+    }
+    if (!begin) return;
+    Ln::zero_pad(E, ax.NE);
+    Ln::inverse(E, dv, f, ax);
+    for (int j = threadIdx.x; j < M; j += FS_T) zrow[j] = f[j];
+}
+
+template <class C, int M, int R>
+__global__ void __launch_bounds__(FS_T) k_fs_phys(FsArgs a, int from_usrc) {
+    using Ln = FsLine<C, M, R>;
+    using Rl = typename cx_traits<C>::real;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* E = reinterpret_cast<C*>(sm_raw);
+    C* y = E + Ln::EBUF;
+    C* dv = y + M;
+    const FsAxis& ax = a.ax[0];
+    const int j1 = blockIdx.x, b = blockIdx.y;
+    const int M1 = a.ax[1].M, N0 = ax.N;
+    C* zcol = reinterpret_cast<C*>(a.Z) + (size_t)b * N0 * M1 + j1;
+    const size_t NX = (size_t)M * M1;
+    const double vf = a.tfac[(size_t)b * a.ntf + a.tf];
+    const double* V0 = a.V0 + (size_t)b * NX;
+    if (!from_usrc) {
+        for (int m = threadIdx.x; m < N0; m += FS_T) Ln::stage_inv(m, zcol[(size_t)m * M1], E, dv, ax);
+        Ln::zero_pad(E, ax.NE);
+        Ln::inverse(E, dv, y, ax);
+        const double hm0 = a.h * a.mu[0];
+        for (int j0 = threadIdx.x; j0 < M; j0 += FS_T) {
+            const size_t g = (size_t)j0 * M1 + j1;
+            const double V = vf * V0[g];
+            const C u = implicit_solve(y[j0], (Rl)(hm0 * V));
+            a.u[(size_t)b * NX + g] = cvt<double2>(u);
+            y[j0] = cscale(u, (Rl)V);
+        }
+    } else {
+        for (int j0 = threadIdx.x; j0 < M; j0 += FS_T) {
+            const size_t g = (size_t)j0 * M1 + j1;
+            const double2 u = a.usrc[(size_t)b * NX + g];
+            y[j0] = cvt<C>(a.mulV ? cscale(u, vf * V0[g]) : u);
+        }
+    }
+    __syncthreads();
+    Ln::forward(y, E, dv, ax);
+    for (int m = threadIdx.x; m < N0; m += FS_T) zcol[(size_t)m * M1] = Ln::fwd_value(m, E, dv, ax);
+}
+
+template <class C, int M, int R>
+constexpr size_t smem_of() {
+    return (size_t)(FsLine<C, M, R>::EBUF + M + FS_MAX_ND) * sizeof(C);
+}
+
+template <class C, int M, int R>
+cudaError_t launch_mr(const FsArgs& a, int which, int flag, cudaStream_t s) {
+    constexpr size_t sm = smem_of<C, M, R>();
+    cudaError_t e;
+    if (which == 0) {
+        e = cudaFuncSetAttribute(k_fs_1d<C, M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_fs_1d<C, M, R><<<a.B, FS_T, sm, s>>>(a, flag);
+    } else if (which == 1) {
+        e = cudaFuncSetAttribute(k_fs_row<C, M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_fs_row<C, M, R><<<dim3(a.ax[0].N, a.B), FS_T, sm, s>>>(a, flag);
+    } else {
+        e = cudaFuncSetAttribute(k_fs_phys<C, M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_fs_phys<C, M, R><<<dim3(a.ax[1].M, a.B), FS_T, sm, s>>>(a, flag);
+    }
+    return cudaGetLastError();
+}
+
+// (M, R) pairs built: M = 32..512, R = 4, 8, 16, nu = M R <= 4096.
+template <class C>
+cudaError_t dispatch(const FsArgs& a, const FsAxis& ax, int which, int flag, cudaStream_t s) {
+#define FS_FOR_R(M_)                                                                               \
+    if (R == 4) return launch_mr<C, M_, 4>(a, which, flag, s);                                   \
+    if (R == 8) return launch_mr<C, M_, 8>(a, which, flag, s);                                   \
+    if (R == 16 && M_ * 16 <= 4096) return launch_mr<C, M_, (M_ * 16 <= 4096 ? 16 : 8)>(a, which, flag, s);
+    const int M = ax.M, R = ax.R;
+    switch (M) {
+        case 32: { FS_FOR_R(32) break; }
+        case 64: { FS_FOR_R(64) break; }
+        case 128: { FS_FOR_R(128) break; }
+        case 256: { FS_FOR_R(256) break; }
+        case 512: { FS_FOR_R(512) break; }
+        default: break;
+    }
+#undef FS_FOR_R
+    return cudaErrorInvalidValue;
+}
+
+inline const FsAxis& axis_of(const FsArgs& a, int which) { return which == 1 ? a.ax[1] : a.ax[0]; }
+
+}  // namespace fs
+}  // namespace tdse

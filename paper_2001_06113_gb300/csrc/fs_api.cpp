@@ -181,6 +181,16 @@ FsArgs fs_base(const tdse_ctx* c) {
         X.Fd = c->P<double2>(F.off.Fd[x]);
         X.tw = c->P<double2>(F.off.tw[x]);
         X.P = c->P<double2>(F.off.P[x]);
+        if (F.f32) {
+            X.preI_f = c->P<float2>(F.off.preI_f[x]);
+            X.postI_f = c->P<float2>(F.off.postI_f[x]);
+            X.preF_f = c->P<float2>(F.off.preF_f[x]);
+            X.postF_f = c->P<float2>(F.off.postF_f[x]);
+            X.Gd_f = c->P<float2>(F.off.Gd_f[x]);
+            X.Fd_f = c->P<float2>(F.off.Fd_f[x]);
+            X.tw_f = c->P<float2>(F.off.tw_f[x]);
+            X.P_f = c->P<float2>(F.off.P_f[x]);
+        }
     }
     a.n_int = c->n_int;
     a.uhat = c->P<double2>(F.off.uhat);
@@ -194,32 +204,42 @@ FsArgs fs_base(const tdse_ctx* c) {
     return a;
 }
 
-// Grid values usrc (times V(t_tf) if mulV) -> mode space at fdst (instance b at fdst + b bstride).
+// Ring slot `slot` of a ring with rsz-byte elements (as the kernels' double2* field).
+double2* ring_at(const tdse_ctx* c, size_t ring_off, size_t elems) {
+    return reinterpret_cast<double2*>(c->P<char>(ring_off) + elems * c->rsz);
+}
+
+// Grid values usrc (times V(t_tf) if mulV) -> mode space: into the FP64 state
+// (to_ring = 0) or a ring slot in the ring's element type (to_ring = 1), instance
+// b at fdst + b bstride elements.
 tdse_status forward_to(tdse_ctx* c, const double2* usrc, int mulV, int tf, double2* fdst, size_t bstride,
-                       cudaStream_t s) {
+                       int to_ring, cudaStream_t s) {
     FsArgs a = fs_base(c);
     a.usrc = usrc;
     a.mulV = mulV;
     a.tf = tf;
     a.fdst = fdst;
     a.fdst_bstride = bstride;
+    a.fdst_ring = to_ring;
+    const int f32 = c->F.f32 ? 1 : 0;
     if (c->d == 1) {
-        TDSE_CK(c, launch_fs_1d(a, FS_1D_FWD_ONLY, s));
+        TDSE_CK(c, launch_fs_1d(a, FS_1D_FWD_ONLY, f32, s));
     } else {
-        TDSE_CK(c, launch_fs_phys(a, 1, s));
-        TDSE_CK(c, launch_fs_row(a, FS_ROW_FWD_ONLY, s));
+        TDSE_CK(c, launch_fs_phys(a, 1, f32, s));
+        TDSE_CK(c, launch_fs_row(a, FS_ROW_FWD_ONLY, f32, s));
     }
     return TDSE_OK;
 }
 
 // One step with the description in a: 1D fused kernel, 2D begin / phys / end.
 tdse_status one_step(tdse_ctx* c, const FsArgs& a, cudaStream_t s) {
+    const int f32 = c->F.f32 ? 1 : 0;
     if (c->d == 1) {
-        TDSE_CK(c, launch_fs_1d(a, FS_1D_STEP, s));
+        TDSE_CK(c, launch_fs_1d(a, FS_1D_STEP, f32, s));
     } else {
-        TDSE_CK(c, launch_fs_row(a, FS_ROW_BEGIN, s));
-        TDSE_CK(c, launch_fs_phys(a, 0, s));
-        TDSE_CK(c, launch_fs_row(a, FS_ROW_END, s));
+        TDSE_CK(c, launch_fs_row(a, FS_ROW_BEGIN, f32, s));
+        TDSE_CK(c, launch_fs_phys(a, 0, f32, s));
+        TDSE_CK(c, launch_fs_row(a, FS_ROW_END, f32, s));
     }
     return TDSE_OK;
 }
@@ -227,9 +247,9 @@ tdse_status one_step(tdse_ctx* c, const FsArgs& a, cudaStream_t s) {
 tdse_status fs_init(tdse_ctx* c, cudaStream_t s) {
     const FsState& F = c->F;
     double2* u = c->P<double2>(F.off.u);
-    tdse_status st = forward_to(c, u, 0, 0, c->P<double2>(F.off.uhat), F.NM, s);
+    tdse_status st = forward_to(c, u, 0, 0, c->P<double2>(F.off.uhat), F.NM, 0, s);
     if (st != TDSE_OK) return st;
-    st = forward_to(c, u, 1, 0, c->P<double2>(F.off.ring) + (size_t)slot_of(c, 0) * F.NM, (size_t)c->RS * F.NM, s);
+    st = forward_to(c, u, 1, 0, ring_at(c, F.off.ring, (size_t)slot_of(c, 0) * F.NM), (size_t)c->RS * F.NM, 1, s);
     if (st != TDSE_OK) return st;
     c->inited = true;
     return TDSE_OK;
@@ -241,17 +261,16 @@ tdse_status fs_startup_step(tdse_ctx* c, int n, cudaStream_t s) {
     const FsState& F = c->F;
     const size_t BM = (size_t)c->B * F.NM, BX = (size_t)c->B * F.NX;
     double2* cu = c->P<double2>(F.off.chain_uhat);
-    double2* cr = c->P<double2>(F.off.chain_ring);
     double2* cx = c->P<double2>(F.off.chain_u);
     for (int ch = 0; ch < c->L; ++ch) {
+        double2* cr = ring_at(c, F.off.chain_ring, ch * BM);
         TDSE_CK(c, cudaMemcpyAsync(cu + ch * BM, c->P<double2>(F.off.uhat), BM * 16, cudaMemcpyDeviceToDevice, s));
-        TDSE_CK(c, launch_copy_slot(cr + ch * BM, c->P<double2>(F.off.ring), c->RS, slot_of(c, n - 1), c->B, F.NM,
-                                    16, s));
+        TDSE_CK(c, launch_copy_slot(cr, c->P<void>(F.off.ring), c->RS, slot_of(c, n - 1), c->B, F.NM, c->rsz, s));
         const int len = SUB >> ch;
         for (int i = 0; i < (1 << ch); ++i) {
             FsArgs a = fs_base(c);
             a.uhat = cu + ch * BM;
-            a.ring = cr + ch * BM;
+            a.ring = cr;
             a.ring_slots = 1;
             a.u = cx + ch * BX;
             a.nhist = 1;
@@ -268,8 +287,8 @@ tdse_status fs_startup_step(tdse_ctx* c, int n, cudaStream_t s) {
     }
     TDSE_CK(c, launch_combine(c->P<void>(F.off.uhat), cu, BM, c->L, c->rich, BM, false, s));
     TDSE_CK(c, launch_combine(c->P<void>(F.off.u), cx, BX, c->L, c->rich, BX, false, s));
-    return forward_to(c, c->P<double2>(F.off.u), 1, SUB * n, c->P<double2>(F.off.ring) + (size_t)slot_of(c, n) * F.NM,
-                      (size_t)c->RS * F.NM, s);
+    return forward_to(c, c->P<double2>(F.off.u), 1, SUB * n, ring_at(c, F.off.ring, (size_t)slot_of(c, n) * F.NM),
+                      (size_t)c->RS * F.NM, 1, s);
 }
 
 FsArgs adams_args(const tdse_ctx* c, int n) {
@@ -286,20 +305,21 @@ FsArgs adams_args(const tdse_ctx* c, int n) {
 
 // Adams steps n0+1 .. n0+k.  2D: row begin, (phys, row end+begin) x (k-1), phys, row end.
 tdse_status fs_adams(tdse_ctx* c, int n0, int k, cudaStream_t s) {
+    const int f32 = c->F.f32 ? 1 : 0;
     if (c->d == 1) {
-        for (int n = n0 + 1; n <= n0 + k; ++n) TDSE_CK(c, launch_fs_1d(adams_args(c, n), FS_1D_STEP, s));
+        for (int n = n0 + 1; n <= n0 + k; ++n) TDSE_CK(c, launch_fs_1d(adams_args(c, n), FS_1D_STEP, f32, s));
         return TDSE_OK;
     }
-    TDSE_CK(c, launch_fs_row(adams_args(c, n0 + 1), FS_ROW_BEGIN, s));
+    TDSE_CK(c, launch_fs_row(adams_args(c, n0 + 1), FS_ROW_BEGIN, f32, s));
     for (int n = n0 + 1; n < n0 + k; ++n) {
-        TDSE_CK(c, launch_fs_phys(adams_args(c, n), 0, s));
+        TDSE_CK(c, launch_fs_phys(adams_args(c, n), 0, f32, s));
         FsArgs f = adams_args(c, n + 1);
         f.out_slot = slot_of(c, n);
-        TDSE_CK(c, launch_fs_row(f, FS_ROW_END | FS_ROW_BEGIN, s));
+        TDSE_CK(c, launch_fs_row(f, FS_ROW_END | FS_ROW_BEGIN, f32, s));
     }
     const FsArgs last = adams_args(c, n0 + k);
-    TDSE_CK(c, launch_fs_phys(last, 0, s));
-    TDSE_CK(c, launch_fs_row(last, FS_ROW_END, s));
+    TDSE_CK(c, launch_fs_phys(last, 0, f32, s));
+    TDSE_CK(c, launch_fs_row(last, FS_ROW_END, f32, s));
     return TDSE_OK;
 }
 
@@ -313,7 +333,7 @@ tdse_status fs_create(tdse_ctx* c) {
     if (g.gauss_q < 1 || g.gauss_q > 32) return c->fail(TDSE_EINVAL, "gauss_q must be in 1..32");
     if (g.n_r < 0 || g.n_r > 4) return c->fail(TDSE_EINVAL, "n_r must be in 0..4");
     if (!(g.H > 0.0) || !std::isfinite(g.H)) return c->fail(TDSE_EINVAL, "H must be positive");
-    if (g.precision != TDSE_FP64) return c->fail(TDSE_EUNSUPPORTED, "free space is built in FP64 only");
+    F.f32 = g.precision == TDSE_MIXED;
     F.NM = 1;
     F.NX = 1;
     for (int x = 0; x < c->d; ++x) {
@@ -331,12 +351,12 @@ tdse_status fs_create(tdse_ctx* c) {
     auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
     F.off = {};
     F.off.uhat = take(B * F.NM * 16);
-    F.off.ring = take(B * c->RS * F.NM * 16);
+    F.off.ring = take(B * c->RS * F.NM * c->rsz);
     F.off.chain_uhat = take((size_t)c->L * B * F.NM * 16);
-    F.off.chain_ring = take((size_t)c->L * B * F.NM * 16);
+    F.off.chain_ring = take((size_t)c->L * B * F.NM * c->rsz);
     F.off.chain_u = take((size_t)c->L * B * F.NX * 16);
     F.off.u = take(B * F.NX * 16);
-    F.off.Z = c->d == 2 ? take(B * (size_t)F.ax[0].N * F.ax[1].M * 16) : 0;
+    F.off.Z = c->d == 2 ? take(B * (size_t)F.ax[0].N * F.ax[1].M * c->rsz) : 0;
     F.off.V0 = take(B * F.NX * 8);
     const size_t V0f = take(B * F.NX * 8);
     F.off.tfac = take(B * (size_t)c->ntf * 8);
@@ -353,6 +373,16 @@ tdse_status fs_create(tdse_ctx* c) {
         F.off.Fd[x] = take((size_t)A.ND * A.M * 16);
         F.off.tw[x] = take((size_t)A.M * 16);
         F.off.P[x] = take(B * (size_t)c->n_int * A.N * 16);
+        if (F.f32) {
+            F.off.preI_f[x] = take((size_t)2 * A.NE * 8);
+            F.off.postI_f[x] = take((size_t)2 * A.nu * 8);
+            F.off.preF_f[x] = take((size_t)2 * A.nu * 8);
+            F.off.postF_f[x] = take((size_t)2 * A.NE * 8);
+            F.off.Gd_f[x] = take((size_t)A.ND * A.M * 8);
+            F.off.Fd_f[x] = take((size_t)A.ND * A.M * 8);
+            F.off.tw_f[x] = take((size_t)A.M * 8);
+            F.off.P_f[x] = take(B * (size_t)c->n_int * A.N * 8);
+        }
     }
     F.off.scratch = take(256);
     F.off.end = o;
@@ -384,6 +414,22 @@ tdse_status fs_bind(tdse_ctx* c, cudaStream_t s) {
         TDSE_CK(c, up(F.off.Gd[x], T.Gd));
         TDSE_CK(c, up(F.off.Fd[x], T.Fd));
         TDSE_CK(c, up(F.off.tw[x], T.tw));
+        // FP32 copies: each complex value rounded from the FP64 table
+        std::vector<float> t32;
+        auto up32 = [&](size_t off, const std::vector<double>& v) -> cudaError_t {
+            t32.assign(v.begin(), v.end());
+            const cudaError_t e = cudaMemcpyAsync(c->P<float>(off), t32.data(), t32.size() * 4, cudaMemcpyHostToDevice, s);
+            return e != cudaSuccess ? e : cudaStreamSynchronize(s);   // t32 is reused
+        };
+        if (F.f32) {
+            TDSE_CK(c, up32(F.off.preI_f[x], T.preI));
+            TDSE_CK(c, up32(F.off.postI_f[x], T.postI));
+            TDSE_CK(c, up32(F.off.preF_f[x], T.preF));
+            TDSE_CK(c, up32(F.off.postF_f[x], T.postF));
+            TDSE_CK(c, up32(F.off.Gd_f[x], T.Gd));
+            TDSE_CK(c, up32(F.off.Fd_f[x], T.Fd));
+            TDSE_CK(c, up32(F.off.tw_f[x], T.tw));
+        }
         TDSE_CK(c, cudaStreamSynchronize(s));    // T goes out of scope
     }
     return TDSE_OK;
@@ -397,6 +443,9 @@ tdse_status fs_build_phase_tables(tdse_ctx* c, int b, cudaStream_t s) {
         double2* P = c->P<double2>(F.off.P[x]) + (size_t)b * c->n_int * A.N;
         const double* phi = c->P<double>(F.off.phi) + ((size_t)b * c->d + x) * c->ntf;
         TDSE_CK(c, launch_fs_phase(P, c->P<double2>(F.off.zeta[x]), A.N, iv, c->n_int, phi, c->cfg.dt, s));
+        if (F.f32)
+            TDSE_CK(c, launch_fs_to_f32(c->P<float2>(F.off.P_f[x]) + (size_t)b * c->n_int * A.N, P,
+                                        (size_t)c->n_int * A.N, s));
     }
     return TDSE_OK;
 }
@@ -447,11 +496,18 @@ extern "C" tdse_status tdse_free_rule(const tdse_ctx* c, int axis, int* N, doubl
     return TDSE_OK;
 }
 
-extern "C" tdse_status tdse_free_choose_H(double eps, double vnorm, double phimax, int dim, double* H_out) {
+extern "C" tdse_status tdse_free_choose_H_prec(double eps, double vnorm, double phimax, int dim, int precision,
+                                               double* H_out) {
     if (!H_out || (dim != 1 && dim != 2) || !(eps > 0.0) || !(vnorm >= 0.0) || !(phimax >= 0.0)) return TDSE_EINVAL;
-    const double eps_m = std::ldexp(1.0, -52);
+    if (precision != TDSE_FP64 && precision != TDSE_MIXED) return TDSE_EINVAL;
+    // machine epsilon of the arithmetic that evaluates the contour sums
+    const double eps_m = std::ldexp(1.0, precision == TDSE_FP64 ? -52 : -23);
     const double H = std::log(eps / ((1.0 + vnorm) * eps_m)) / (2.0 * dim * (1.0 + phimax));
     if (!(H > 0.0) || !std::isfinite(H)) return TDSE_EINVAL;
     *H_out = H;
     return TDSE_OK;
+}
+
+extern "C" tdse_status tdse_free_choose_H(double eps, double vnorm, double phimax, int dim, double* H_out) {
+    return tdse_free_choose_H_prec(eps, vnorm, phimax, dim, TDSE_FP64, H_out);
 }

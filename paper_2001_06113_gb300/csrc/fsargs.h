@@ -42,6 +42,15 @@ struct FsAxis {
     const double2* Fd;     // [ND][M]    forward dense: (2/M) e^{-i zeta_d x_j}
     const double2* tw;     // [M]        e^{-2 pi i m / M}
     const double2* P;      // [B][n_int][N] one-step phases e^{-i zeta^2 s + i zeta (phi(t1) - phi(t0))}
+    // FP32 copies for the FP32-transform variant (TDSE_MIXED), same layouts
+    const float2* preI_f;
+    const float2* postI_f;
+    const float2* preF_f;
+    const float2* postF_f;
+    const float2* Gd_f;
+    const float2* Fd_f;
+    const float2* tw_f;
+    const float2* P_f;
 };
 
 struct FsArgs {
@@ -58,14 +67,15 @@ struct FsArgs {
     int interval[FS_MAX_HIST];    // interval id of the one-step phase p_i, i = 0..nhist-1
     int tf;                // fine time index of the new time (t = tf dt / 8)
     // ---- buffers
-    double2* uhat;         // [B][N0 N1] mode state: u^ between steps, W inside a step
-    double2* ring;         // [B][ring_slots][N0 N1] history of (Vu)^
+    double2* uhat;         // [B][N0 N1] mode state: u^ between steps, W inside a step (FP64 in both variants)
+    double2* ring;         // [B][ring_slots][N0 N1] history of (Vu)^ (elements of the transform type)
     int ring_slots;
-    double2* Z;            // [B][N0][M1] 2D intermediate (axis-1 transformed rows)
+    double2* Z;            // [B][N0][M1] 2D intermediate (axis-1 transformed rows; transform type)
     double2* u;            // [B][M0 M1] physical state written by the implicit solve
     const double2* usrc;   // forward-only source on the grid
     double2* fdst;         // forward-only destination in mode space, instance b at fdst + b fdst_bstride
     size_t fdst_bstride;
+    int fdst_ring;         // destination is a ring slot (transform type) rather than the FP64 state
     int mulV;              // forward-only: transform V(t) usrc instead of usrc
     const double* V0;      // [B][M0 M1]
     const double* tfac;    // [B][ntf]
@@ -77,11 +87,14 @@ enum FsRow : int { FS_ROW_END = 1, FS_ROW_BEGIN = 2, FS_ROW_FWD_ONLY = 4 };
 enum Fs1D : int { FS_1D_STEP = 0, FS_1D_FWD_ONLY = 1 };
 
 bool fs_supported(int M, int R);
-size_t fs_smem_bytes(int M, int R);
 // 2D: row pass over the N0 mode rows (axis 1), phys pass over the M1 grid columns (axis 0).
-cudaError_t launch_fs_row(const FsArgs& a, int flags, cudaStream_t s);
-cudaError_t launch_fs_phys(const FsArgs& a, int from_usrc, cudaStream_t s);
-cudaError_t launch_fs_1d(const FsArgs& a, int mode, cudaStream_t s);
+// f32 = 1 selects the FP32-transform kernels (freespace_f32.cu).
+cudaError_t launch_fs_row(const FsArgs& a, int flags, int f32, cudaStream_t s);
+cudaError_t launch_fs_phys(const FsArgs& a, int from_usrc, int f32, cudaStream_t s);
+cudaError_t launch_fs_1d(const FsArgs& a, int mode, int f32, cudaStream_t s);
+cudaError_t launch_fs_f32(const FsArgs& a, int which, int flag, cudaStream_t s);   // freespace_f32.cu
+// FP32 copy of n complex values
+cudaError_t launch_fs_to_f32(float2* dst, const double2* src, size_t n, cudaStream_t s);
 // P[iv][m] of one instance and axis: zeta [N] complex, phi_axis [ntf] = that
 // component of phi at t = m dt / 8.
 cudaError_t launch_fs_phase(double2* P, const double2* zeta, int N, const int2* intervals, int n_int,

@@ -1,6 +1,7 @@
 """C-ABI checks that need no GPU: the library loads, exports every symbol
 include/tdse.h declares, and its host-only entry points validate input."""
 import ctypes
+import math
 import os
 import re
 from fractions import Fraction
@@ -75,7 +76,8 @@ def _cfg(native, **kw):
     (dict(bc=1), -1),                  # free space without nu / H
     (dict(bc=1, nu=(512, 0), H=1.5, gauss_q=10, n_r=1), 0),
     (dict(bc=1, dim=2, n=(64, 32), nu=(512, 256), H=1.5, gauss_q=10, n_r=1), 0),
-    (dict(bc=1, nu=(512, 0), H=1.5, gauss_q=10, n_r=1, precision=1), -7),   # free space: FP64 only
+    (dict(bc=1, nu=(512, 0), H=1.5, gauss_q=10, n_r=1, precision=1), 0),    # free space, FP32 transforms
+    (dict(bc=1, dim=2, n=(64, 64), nu=(512, 512), H=1.0, gauss_q=10, n_r=1, precision=1), 0),
     (dict(bc=1, n=(1024, 1), nu=(4096, 0), H=1.5, gauss_q=10, n_r=1), -7),  # n > 512
     (dict(bc=1, nu=(500, 0), H=1.5, gauss_q=10, n_r=1), -1),                # nu not a multiple of n
     (dict(bc=1, nu=(512, 0), H=0.0, gauss_q=10, n_r=1), -1),
@@ -139,11 +141,17 @@ def test_free_rule_matches_oracle_rule(native, p, q, n_r):
     assert np.max(np.abs(w - r.w)) < 2e-15      # Gauss-Legendre weights by two routes: a few ulps
 
 
-@pytest.mark.parametrize("eps,vnorm,phimax,dim", [(1e-10, 20.0, 0.3, 2), (1e-12, 0.0, 0.0, 1), (1e-8, 5.0, 1.0, 2)])
+@pytest.mark.parametrize("eps,vnorm,phimax,dim", [(1e-10, 20.0, 0.3, 2), (1e-12, 0.0, 0.0, 1), (1e-8, 5.0, 1.0, 2),
+                                                (1e-4, 5.0, 0.5, 2), (1e-3, 0.0, 0.0, 1)])
 def test_free_choose_H_matches_oracle(native, eps, vnorm, phimax, dim):
     from oracle import gamma
     from paper_2001_06113_gb300 import free_choose_H
     assert abs(free_choose_H(eps, vnorm, phimax, dim) - gamma.choose_H(eps, vnorm, phimax, dim)) < 1e-15
+    if eps > 1e-6:
+        # FP32 contour sums: eps_m = 2^-23, i.e. H smaller by log(2^29) / (2 d (1 + phimax))
+        Hm = free_choose_H(eps, vnorm, phimax, dim, precision="mixed")
+        assert abs(Hm - gamma.choose_H(eps, vnorm, phimax, dim, eps_m=2.0 ** -23)) < 1e-15
+        assert abs(free_choose_H(eps, vnorm, phimax, dim) - Hm - 29 * math.log(2.0) / (2 * dim * (1 + phimax))) < 1e-13
 
 
 def test_free_choose_H_rejects_nonpositive(native):

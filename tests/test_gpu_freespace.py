@@ -9,6 +9,14 @@ eps / eps_m, and the two sides round differently (FFT-based versus direct
 sums).  The observed differences are 2e-15..3e-14 in relative L2, so the
 tests hold both u on the grid and the mode state u^ on the contour to
 1e-12, the FP64 bar of the periodic path.
+
+The FP32-transform variant (precision "mixed": transforms, ring and
+history sum in FP32, mode state and update in FP64) takes H from the same
+remark with eps_m = 2^-23.  Against the FP64 oracle on the same contour the
+bound is again that eps; the observed differences are 1.5e-7..2.4e-7 on the
+grid and 4e-8..9e-8 on the contour (a few FP32 unit roundoffs, 2^-24 =
+6e-8), independent of eps in 1e-5..1e-3, so these tests hold 2e-6 on both,
+the mixed bar of the periodic path.
 """
 import math
 
@@ -33,19 +41,23 @@ def _instance(shape, n, seed=11, dt=1e-3, A0=50.0, omega=200.0):
                                      vfac=lambda t: 1.0 + 0.3 * np.sin(40.0 * np.asarray(t, dtype=np.float64)))
 
 
-def _H(inst, eps):
+MIXED_TOL = 2e-6
+EPS_M32 = 2.0 ** -23
+
+
+def _H(inst, eps, eps_m=gamma.EPS_M):
     phi = fields.phi_callable(inst.pulse, inst.dim)
     phimax = max(float(np.max(np.abs(phi(t)))) for t in np.linspace(0.0, inst.t_max, 401))
     vnorm = math.sqrt(float(np.sum(inst.V0 ** 2)) * (2.0 / inst.shape[0]) ** inst.dim)
     vnorm *= float(np.max(np.abs(inst.vfac_table())))
-    return gamma.choose_H(eps, vnorm, phimax, inst.dim)
+    return gamma.choose_H(eps, vnorm, phimax, inst.dim, eps_m=eps_m)
 
 
-def _gpu(inst, nu, H, n, q=10, n_r=1, p=8, order=8, startup=-1):
+def _gpu(inst, nu, H, n, q=10, n_r=1, p=8, order=8, startup=-1, precision="fp64"):
     import torch
     from paper_2001_06113_gb300 import Problem
     pr = Problem(inst.shape, inst.dt, inst.nsteps, order=order, startup_steps=startup, bc="free", nu=nu, H=H,
-                 gauss_q=q, n_r=n_r, alpert_p=p)
+                 gauss_q=q, n_r=n_r, alpert_p=p, precision=precision)
     pr.set_potential(inst.V0, inst.vfac_table())
     if inst.pulse is not None:
         pr.set_pulse(inst.pulse.A0, inst.pulse.omega, inst.pulse.T_pulse, inst.pulse.direction)
@@ -215,3 +227,96 @@ def test_free_read_u_before_and_across_calls():
     assert q.step_index == 10
     assert np.array_equal(pr.read_u(0), q.read_u(0))
     assert np.array_equal(pr.read_modes(0), q.read_modes(0))
+
+
+# ------------------------------------------------------------ FP32 transforms
+MIXED_CASES = [
+    # shape, nu, q, n_r, p, order, steps, eps (H for FP32 sums)
+    ((64,), (512,), 10, 1, 8, 8, 12, 1e-4),
+    ((256,), (1024,), 10, 1, 8, 8, 30, 1e-5),
+    ((128,), (512,), 8, 0, 4, 6, 10, 1e-3),
+    ((64, 64), (512, 512), 10, 1, 8, 8, 12, 1e-4),
+    ((32, 64), (256, 1024), 8, 2, 8, 8, 9, 1e-4),
+]
+
+
+@pytest.mark.parametrize("shape,nu,q,n_r,p,order,n,eps", MIXED_CASES)
+def test_free_mixed_matches_oracle(shape, nu, q, n_r, p, order, n, eps):
+    """FP32 transforms and history, FP64 state: u and u^ within the mixed
+    bar of the FP64 oracle on the same contour (H for eps_m = 2^-23)."""
+    inst = _instance(shape, n + 2)
+    H = _H(inst, eps, EPS_M32)
+    u, uh, pr = _gpu(inst, nu, H, n, q, n_r, p, order, precision="mixed")
+    pr.check_finite()
+    uo, uho = _oracle(inst, nu, H, n, q, n_r, p, order)
+    assert rel(u, uo) < MIXED_TOL and rel(uh, uho) < MIXED_TOL, (rel(u, uo), rel(uh, uho))
+
+
+def test_free_mixed_full_size_against_fp64_path():
+    """The 256^2 workload (nu = 2048) in the FP32-transform variant against
+    the FP64 path (oracle-checked above) on the same contour, through the
+    start-up and 32 Adams steps."""
+    inst = synth.free_bump_gaussians((256, 256), seed=3, dt=5e-4, nsteps=2000, T_pulse=1.0)
+    n = 40
+    H = _H(inst, 1e-4, EPS_M32)
+    um, mm, _ = _gpu(inst, (2048, 2048), H, n, precision="mixed")
+    ud, md, _ = _gpu(inst, (2048, 2048), H, n)
+    assert rel(um, ud) < MIXED_TOL and rel(mm, md) < MIXED_TOL, (rel(um, ud), rel(mm, md))
+
+
+def test_free_mixed_wavepacket_closed_form():
+    """V = 0 with a pulse: no time error, so the mixed variant matches the
+    closed form to its rounding level on the FP32 contour."""
+    M, sigma, dt, n = 128, 0.1, 0.01, 10
+    pulse = synth.Pulse(3.0, 20.0, 0.1, (1.0,))
+    phi = fields.phi_callable(pulse, 1)
+    phimax = max(abs(phi(t)[0]) for t in np.linspace(0, 0.1, 101))
+    H = gamma.choose_H(1e-4, 0.0, phimax, 1, eps_m=EPS_M32)
+    x = synth.free_grid(M)
+    from paper_2001_06113_gb300 import Problem
+    pr = Problem((M,), dt, n, bc="free", nu=(1024,), H=H, gauss_q=16, n_r=2, precision="mixed")
+    pr.set_potential(np.zeros(M))
+    pr.set_pulse(3.0, 20.0, 0.1, (1.0,))
+    pr.set_initial(_wavepacket(x, 0.0, sigma))
+    pr.step(n)
+    ref = _wavepacket(x, n * dt, sigma, phi(n * dt)[0])
+    assert rel(pr.read_u(0), ref) < MIXED_TOL
+
+
+def test_free_mixed_batch_and_checkpoint():
+    """Batched instances equal solo runs bit for bit; a checkpoint taken
+    mid-run restores the exact continuation."""
+    import torch
+    from paper_2001_06113_gb300 import Problem
+    shape, nu, n = (64, 32), (512, 256), 12
+    insts = [_instance(shape, n + 2, seed=40 + i, A0=20.0 * (i + 1)) for i in range(2)]
+    H = 1.2
+
+    def make(B):
+        return Problem(shape, insts[0].dt, n + 2, batch=B, bc="free", nu=nu, H=H, precision="mixed")
+
+    def setup(pr, i, inst):
+        pr.set_potential(inst.V0, inst.vfac_table(), instance=i)
+        pr.set_pulse(inst.pulse.A0, inst.pulse.omega, inst.pulse.T_pulse, inst.pulse.direction, instance=i)
+        pr.set_initial(inst.u0, instance=i)
+
+    pb = make(2)
+    for i, inst in enumerate(insts):
+        setup(pb, i, inst)
+    pb.step(5)
+    blob = pb.save()
+    pb.step(n - 5)
+    torch.cuda.synchronize()
+    ub = pb.read_u()
+    for i, inst in enumerate(insts):
+        ps = make(1)
+        setup(ps, 0, inst)
+        ps.step(n)
+        assert np.array_equal(ps.read_u(0), ub[i])
+    pc = make(2)
+    for i, inst in enumerate(insts):
+        setup(pc, i, inst)
+    pc.load(blob)
+    assert pc.step_index == 5
+    pc.step(n - 5)
+    assert np.array_equal(pc.read_u(), ub)
