@@ -328,7 +328,6 @@ FS_M, FS_NU, FS_DT, FS_NSTEPS, FS_Q, FS_NR = 256, 2048, 5e-4, 2000, 10, 1
 FS_EPS = {"fp64": 1e-10, "mixed": 1e-4}
 FS_METRICS = {"fp64": "point-steps/s (2D free space 256^2, nu=2048, 8th-order, T=1, eps=1e-10)",
               "mixed": "point-steps/s (2D free space 256^2, nu=2048, 8th-order, T=1, FP32 transforms, eps=1e-4)"}
-FS_METRIC = FS_METRICS["fp64"]
 # DRAM bytes of one fused k_fs_row launch (end + begin) of one 256^2 instance,
 # from the ncu capture summarised in profiles/step2d_free_256x256_fp64.md.
 FS_ROW_TRAFFIC = {"fp64": 484.806912e6 + 123.36256e6, "mixed": None}
@@ -663,7 +662,7 @@ def main_free(args, ws, rank, local):
             free_oracle_sample(nadams=1)
         vals = [free_oracle_sample(nadams=1)[0] for _ in range(args.steps)]
         value = float(np.mean(vals))
-        line = {"impl": "reference", "metric": FS_METRIC, "value": value, "unit": "point-steps/s",
+        line = {"impl": "reference", "metric": FS_METRICS[args.precision], "value": value, "unit": "point-steps/s",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * FS_M * FS_M / value, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -983,12 +982,16 @@ def main_batch1d(args, ws, rank, local):
 
 # ------------------------------------------------------------ request loop arm
 SV_RATE, SV_DURATION, SV_T, SV_BUDGET = 200.0, 1.0, (0.05, 0.2), 64 << 30
-SV_METRIC = "aggregate point-steps/s of a served request stream (1D/2D periodic mixed, 2D free space FP64)"
+SV_METRICS = {"fp64": "aggregate point-steps/s of a served request stream (1D/2D periodic mixed, 2D free space FP64)",
+              "mixed": "aggregate point-steps/s of a served request stream (1D/2D periodic mixed, 2D free space "
+                       "FP32 transforms)"}
 
 
 def main_serve(args, ws, rank, local):
     import torch
-    from paper_2001_06113_gb300.serve import Request, Server, TorchBackend, requests_from_trace
+    from paper_2001_06113_gb300.serve import (FREE_EPS, Request, Server, TorchBackend, free_contour_params,
+                                              requests_from_trace)
+    fprec = args.precision          # free-space requests: "mixed" (FP32 transforms) or "fp64"
     if args.impl == "reference":
         if rank != 0:
             return 0
@@ -997,7 +1000,7 @@ def main_serve(args, ws, rank, local):
             batch1d_oracle_sample(2)
         vals = [batch1d_oracle_sample(20)[0] for _ in range(args.steps)]
         value = float(np.mean(vals))
-        print(json.dumps({"impl": "reference", "metric": SV_METRIC, "value": value, "unit": "point-steps/s",
+        print(json.dumps({"impl": "reference", "metric": SV_METRICS[fprec], "value": value, "unit": "point-steps/s",
                           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                           "ms_per_step": 1e3 * 1024 * 20 / value, "higher_is_better": True, "scaling": "weak",
                           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -1013,9 +1016,9 @@ def main_serve(args, ws, rank, local):
     # warm-up: a short stream of small solves (kernel attributes, allocator)
     warm = synth.serve_requests(seed=99, rate=100.0, duration=0.1, T_range=(0.005, 0.01), sizes_1d=(1024,),
                                 sizes_2d=(128,), sizes_free=(64,))
-    Server(TorchBackend(), SV_BUDGET).run(requests_from_trace(warm))
+    Server(TorchBackend(), SV_BUDGET).run(requests_from_trace(warm, free_precision=fprec))
     trace = synth.serve_requests(seed=5, rate=SV_RATE, duration=SV_DURATION, T_range=SV_T)
-    reqs = requests_from_trace(trace)
+    reqs = requests_from_trace(trace, free_precision=fprec)
     srv = Server(TorchBackend(), SV_BUDGET, max_active=64)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -1030,12 +1033,18 @@ def main_serve(args, ws, rank, local):
     classes = {k: {"requests": v["n"], "point_steps": v["point_steps"],
                    "p50_s": float(np.percentile(v["lat"], 50)), "p99_s": float(np.percentile(v["lat"], 99))}
                for k, v in by_kind.items()}
-    # stated accuracy: mixed periodic results vs the FP64 path, solved alone (also timed: the plain path)
-    sample = [(r, kind) for r, (t, kind, inst) in zip(reqs, trace)
-              if kind == "2d" or (kind == "1d" and inst.shape[0] <= 8192)][:8]
-    errs, f64_work, f64_time = [], 0.0, 0.0
-    for r, kind in sample:
-        ref = Request(r.rid, 0.0, r.inst, precision="fp64")
+    # stated accuracy: mixed results vs the FP64 path, solved alone (also timed: the plain path);
+    # free space against FP64 on the eps = 1e-10 contour
+    per = [(r, kind) for r, (t, kind, inst) in zip(reqs, trace)
+           if kind == "2d" or (kind == "1d" and inst.shape[0] <= 8192)][:8]
+    fre = [(r, kind) for r, (t, kind, inst) in zip(reqs, trace) if kind == "free" and fprec == "mixed"][:4]
+    errs, ferrs, f64_work, f64_time = [], [], 0.0, 0.0
+    for r, kind in per + fre:
+        if kind == "free":
+            ref = Request(r.rid, 0.0, r.inst, bc="free", precision="fp64",
+                          free=free_contour_params(r.inst, FREE_EPS["fp64"]))
+        else:
+            ref = Request(r.rid, 0.0, r.inst, precision="fp64")
         be = TorchBackend()
         h = be.prepare(ref)
         torch.cuda.synchronize()
@@ -1045,21 +1054,25 @@ def main_serve(args, ws, rank, local):
         f64_time += time.perf_counter() - t0
         f64_work += r.points * r.nsteps
         u = be.finish(h)
-        errs.append(float(np.sqrt(np.sum(np.abs(r.result - u) ** 2) / np.sum(np.abs(u) ** 2))))
+        e = float(np.sqrt(np.sum(np.abs(r.result - u) ** 2) / np.sum(np.abs(u) ** 2)))
+        (ferrs if kind == "free" else errs).append(e)
     line = {
-        "metric": SV_METRIC, "value": st["point_steps_per_s"], "unit": "point-steps/s", "n_gpus": 1,
+        "metric": SV_METRICS[fprec], "value": st["point_steps_per_s"], "unit": "point-steps/s", "n_gpus": 1,
         "steps": 1, "warmup": 1, "ms_per_step": st["makespan_s"] * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64 (periodic), c128 (free space)",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64+f64 (periodic), " + ("c64+c128 (free space)" if fprec == "mixed" else "c128 (free space)"),
         "data": "synthetic",
         "config": {"workload": f"Poisson stream {SV_RATE:.0f} req/s for {SV_DURATION:.1f} s ({len(reqs)} requests): "
                                "1D periodic N 2^10..2^14, 2D periodic 2^7..2^10, 2D free space 2^6..2^8 (nu = 8n, "
-                               "eps = 1e-10), one third each; T ~ U[0.05, 0.2], dt log-uniform [2e-4, 2e-3]",
+                               f"{'FP32 transforms, eps = 1e-4' if fprec == 'mixed' else 'FP64, eps = 1e-10'}), "
+                               "one third each; T ~ U[0.05, 0.2], dt log-uniform [2e-4, 2e-3]",
                    "hbm_budget_bytes": SV_BUDGET, "max_active": 64,
                    "step": "the whole stream from the first arrival to the last result on the host"},
         "time_to_solution_s": {"p50": st["p50_s"], "p99": st["p99_s"], "mean": st["mean_s"]},
         "classes": classes, "peak_active": st["peak_active"], "peak_workspace_bytes": st["peak_bytes"],
         "completed": st["completed"], "failed": st["failed"],
         "rel_l2_vs_fp64_max": max(errs) if errs else None,
+        "free_rel_l2_vs_fp64_eps1e-10_max": max(ferrs) if ferrs else None,
         "fp64_one_at_a_time_point_steps_per_s": f64_work / f64_time if f64_time else None,
         "roofline": None, "cpu_baseline": None,
         "e2e": {"value": st["point_steps_per_s"], "unit": "point-steps/s",

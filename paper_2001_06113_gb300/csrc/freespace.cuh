@@ -39,6 +39,16 @@
 namespace tdse {
 namespace fs {
 
+// Resident CTAs per SM the register allocation is sized for: the FP64
+// kernels are bound by the FP64 pipe at one or two CTAs; the FP32 ones wait on
+// memory latency and need more warps in flight (4 CTAs: 64 registers, a few
+// words spilled; 0.41 ms against 0.45 ms per 256^2 step at 2 or 3 CTAs).
+#ifndef FS_MINB32
+#define FS_MINB32 4
+#endif
+template <class C> struct MinBlocks { static constexpr int value = 1; };
+template <> struct MinBlocks<float2> { static constexpr int value = FS_MINB32; };
+
 __device__ __forceinline__ double2 zero2() { return make_double2(0.0, 0.0); }
 template <class C> __device__ __forceinline__ C zeroc() { return czero<C>(); }
 // v * (-i c)
@@ -207,7 +217,7 @@ __device__ __forceinline__ void store_fwd(const FsArgs& a, size_t idx, C F) {
 }
 
 template <class C, int M, int R>
-__global__ void __launch_bounds__(FS_T) k_fs_1d(FsArgs a, int mode) {
+__global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_1d(FsArgs a, int mode) {
     using Ln = FsLine<C, M, R>;
     using Rl = typename cx_traits<C>::real;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -263,7 +273,7 @@ __global__ void __launch_bounds__(FS_T) k_fs_1d(FsArgs a, int mode) {
 }
 
 template <class C, int M, int R>
-__global__ void __launch_bounds__(FS_T) k_fs_row(FsArgs a, int flags) {
+__global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_row(FsArgs a, int flags) {
     using Ln = FsLine<C, M, R>;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     C* E = reinterpret_cast<C*>(sm_raw);
@@ -334,7 +344,7 @@ __global__ void __launch_bounds__(FS_T) k_fs_row(FsArgs a, int flags) {
 }
 
 template <class C, int M, int R>
-__global__ void __launch_bounds__(FS_T) k_fs_phys(FsArgs a, int from_usrc) {
+__global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_phys(FsArgs a, int from_usrc) {
     using Ln = FsLine<C, M, R>;
     using Rl = typename cx_traits<C>::real;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -377,21 +387,28 @@ constexpr size_t smem_of() {
     return (size_t)(FsLine<C, M, R>::EBUF + M + FS_MAX_ND) * sizeof(C);
 }
 
+// Dynamic shared memory of the kernel and, for the FP32 kernels, the largest
+// shared-memory carve-out (several CTAs per SM).
+template <class C, class K>
+cudaError_t prepare(K kernel, size_t sm) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess && MinBlocks<C>::value > 1)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
+}
+
 template <class C, int M, int R>
 cudaError_t launch_mr(const FsArgs& a, int which, int flag, cudaStream_t s) {
     constexpr size_t sm = smem_of<C, M, R>();
     cudaError_t e;
     if (which == 0) {
-        e = cudaFuncSetAttribute(k_fs_1d<C, M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
+        if ((e = prepare<C>(k_fs_1d<C, M, R>, sm)) != cudaSuccess) return e;
         k_fs_1d<C, M, R><<<a.B, FS_T, sm, s>>>(a, flag);
     } else if (which == 1) {
-        e = cudaFuncSetAttribute(k_fs_row<C, M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
+        if ((e = prepare<C>(k_fs_row<C, M, R>, sm)) != cudaSuccess) return e;
         k_fs_row<C, M, R><<<dim3(a.ax[0].N, a.B), FS_T, sm, s>>>(a, flag);
     } else {
-        e = cudaFuncSetAttribute(k_fs_phys<C, M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
+        if ((e = prepare<C>(k_fs_phys<C, M, R>, sm)) != cudaSuccess) return e;
         k_fs_phys<C, M, R><<<dim3(a.ax[1].M, a.B), FS_T, sm, s>>>(a, flag);
     }
     return cudaGetLastError();

@@ -255,10 +255,12 @@ class Server:
 
 
 
-def free_contour_params(inst, eps: float = 1e-10, R: int = 8, gauss_q: int = 10, n_r: int = 1) -> dict:
+def free_contour_params(inst, eps: float = 1e-10, R: int = 8, gauss_q: int = 10, n_r: int = 1,
+                        precision: str = "fp64") -> dict:
     """Contour parameters of a free-space request: nu = R n per axis and H of
     Remark Hchoice from ||V||_2 on the grid and max |phi| (phi integrated from
-    the sampled pulse by the trapezoid rule on 4001 points)."""
+    the sampled pulse by the trapezoid rule on 4001 points), with the machine
+    epsilon of `precision` ("mixed": FP32 contour sums)."""
     from . import free_choose_H
     d = len(inst.shape)
     vnorm = float(np.sqrt(np.sum(inst.V0 ** 2) * (2.0 / inst.shape[0]) ** d))
@@ -269,17 +271,24 @@ def free_contour_params(inst, eps: float = 1e-10, R: int = 8, gauss_q: int = 10,
         A = inst.pulse.A(t)
         phi = np.cumsum(0.5 * (A[1:] + A[:-1]) * (t[1] - t[0]), axis=0)
         phimax = float(np.max(np.abs(phi)))
-    return {"nu": [R * n for n in inst.shape], "H": free_choose_H(eps, vnorm, phimax, d), "gauss_q": gauss_q,
-            "n_r": n_r}
+    return {"nu": [R * n for n in inst.shape], "H": free_choose_H(eps, vnorm, phimax, d, precision=precision),
+            "gauss_q": gauss_q, "n_r": n_r}
 
 
-def requests_from_trace(trace, free_eps: float = 1e-10):
+FREE_EPS = {"fp64": 1e-10, "mixed": 1e-4}
+
+
+def requests_from_trace(trace, free_eps: Optional[float] = None, free_precision: str = "fp64"):
     """Requests of a synth.serve_requests trace: periodic classes in mixed
-    precision, free space in FP64 with its contour parameters."""
+    precision, free space in `free_precision` ("fp64", or "mixed" = FP32
+    transforms) on the contour chosen for free_eps (default 1e-10 in FP64,
+    1e-4 with FP32 sums)."""
+    eps = FREE_EPS[free_precision] if free_eps is None else free_eps
     out = []
     for i, (t, kind, inst) in enumerate(trace):
         if kind == "free":
-            out.append(Request(i, t, inst, bc="free", precision="fp64", free=free_contour_params(inst, free_eps)))
+            out.append(Request(i, t, inst, bc="free", precision=free_precision,
+                               free=free_contour_params(inst, eps, precision=free_precision)))
         else:
             out.append(Request(i, t, inst, precision="mixed"))
     return out

@@ -53,6 +53,33 @@ def test_mixed_results_within_tolerance_of_fp64():
         assert rel_l2(r.result, f.result) < 1e-6, (r.inst.shape, r.nsteps)
 
 
+def test_free_space_fp32_requests_within_tolerance():
+    """Free-space requests routed to the FP32-transform variant (contour for
+    eps = 1e-4 with FP32 sums) stay within the mixed bar of FP64 solves on
+    the eps = 1e-10 contour, and equal the same solves run alone."""
+    import torch
+    from paper_2001_06113_gb300.serve import (Request, Server, TorchBackend, free_contour_params,
+                                              requests_from_trace)
+    trace = synth.serve_requests(seed=8, rate=60.0, duration=0.5, T_range=(0.01, 0.03), sizes_1d=(1024,),
+                                 sizes_2d=(128,), sizes_free=(64, 128))
+    reqs = requests_from_trace(trace, free_precision="mixed")
+    free = [r for r in reqs if r.bc == "free"]
+    assert free and all(r.precision == "mixed" for r in free)
+    Server(TorchBackend(), hbm_budget=4 << 30, max_active=16).run(reqs)
+    for r in free:
+        ref = Request(r.rid, 0.0, r.inst, bc="free", precision="fp64", free=free_contour_params(r.inst, 1e-10))
+        be = TorchBackend()
+        h = be.prepare(ref)
+        be.start(h)
+        torch.cuda.synchronize()
+        assert rel_l2(r.result, be.finish(h)) < 2e-6, (r.inst.shape, r.nsteps)
+        alone = TorchBackend()
+        h = alone.prepare(r)
+        alone.start(h)
+        torch.cuda.synchronize()
+        assert np.array_equal(alone.finish(h), r.result)
+
+
 def test_budget_limits_concurrency():
     from paper_2001_06113_gb300 import Problem
     from paper_2001_06113_gb300.serve import Request, Server, TorchBackend
