@@ -64,6 +64,7 @@ typedef enum {
 enum { TDSE_PERIODIC = 0, TDSE_FREE = 1 };
 enum { TDSE_FP64 = 0, TDSE_MIXED = 1 };
 enum { TDSE_HOST = 0, TDSE_DEVICE = 1 };
+enum { TDSE_V_SEPARABLE = 0, TDSE_V_TABLE = 1, TDSE_V_TABLE_SHARED = 2 };
 
 /*
  * Problem configuration.
@@ -105,6 +106,14 @@ enum { TDSE_HOST = 0, TDSE_DEVICE = 1 };
  *              choice); truncation K = H + pi n / 2.
  * Mode count per dimension N = 2 NE + 2 p + gauss_q * max(1, 2 n_r) (at most
  * 2 NE + 128 dense modes).
+ * Both boundary conditions:
+ *   potential  TDSE_V_SEPARABLE (0): V(x,t) = f(t) V0(x), tdse_set_potential.
+ *              TDSE_V_TABLE (1): a general real V(x,t) (Sec. 1: any potential),
+ *              given on the grid at the times the scheme evaluates it
+ *              (tdse_potential_times) by tdse_set_potential_table; the
+ *              workspace then holds 16 bytes per grid point and time.
+ *              TDSE_V_TABLE_SHARED (2): as TDSE_V_TABLE with one table read
+ *              by every instance (instances differ in u0 and A only).
  */
 typedef struct {
     int dim;
@@ -122,6 +131,8 @@ typedef struct {
     int gauss_q;
     int n_r;
     double H;
+    /* potential form (both boundary conditions), appended last */
+    int potential;
 } tdse_config;
 
 /* Vector potential callback: writes A(t) (dim components) to A_out. */
@@ -148,6 +159,23 @@ tdse_status tdse_bind_workspace(tdse_ctx* ctx, void* device_ptr, size_t bytes, v
  *                times).  Copied during the call. */
 tdse_status tdse_set_potential(tdse_ctx* ctx, int instance, const double* V0,
                                const double* time_factor, int where, void* stream);
+
+/* TDSE_V_TABLE contexts: the times t_r at which the scheme evaluates V
+ * (eq. uadamsk at t_n = n dt; the trapezoid sub-steps of the Richardson
+ * start-up, Sec. 2.2, at every m dt/8 of the first startup_steps steps):
+ * t_r = r dt/8 for r = 0..8 S, then t = n dt for n = S+1..nsteps
+ * (S = min(startup_steps, nsteps)).  Returns the count R = 8 S + 1 +
+ * nsteps - S and writes the times to t_out (host, R doubles) if not NULL;
+ * -1 for a NULL or separable context. */
+int tdse_potential_times(const tdse_ctx* ctx, double* t_out);
+
+/* TDSE_V_TABLE contexts: V(x, t_r) for instance `instance` (-1 = every
+ * instance): R x n0*n1 real values, row r = V on the grid at t_r
+ * (tdse_potential_times), host or device per `where`; copied during the
+ * call (a host source is synchronised before return).  TDSE_ESTATE for a
+ * separable context (and tdse_set_potential for a table context);
+ * TDSE_EINVAL for instance != -1 in a TDSE_V_TABLE_SHARED context. */
+tdse_status tdse_set_potential_table(tdse_ctx* ctx, int instance, const double* V, int where, void* stream);
 
 /* A(t) for an instance (-1 = all) from a callback (NULL = A == 0).  The library
  * computes phi(t) = int_0^t A (eq. phi) by 8-point Gauss-Legendre on each

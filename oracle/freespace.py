@@ -35,7 +35,8 @@ def free_grid(M: int) -> np.ndarray:
 class FreeSpaceOracle:
     """Direct implementation of the free-space scheme for d = 1 or 2.
 
-    rules: one GammaRule per dimension.  V(x,t) = vfac(t) V0(x); phi(t) -> (d,).
+    rules: one GammaRule per dimension.  V(x,t) = vfac(t) V0(x), or V0 a
+    callable t -> V(., t) on the grid (general V, vfac unused); phi(t) -> (d,).
     """
 
     def __init__(self, rules: Sequence[GammaRule], dt: float, V0: np.ndarray, vfac: Callable, phi: Callable,
@@ -43,7 +44,8 @@ class FreeSpaceOracle:
         self.rules = list(rules)
         self.d = len(self.rules)
         self.dt = float(dt)
-        self.V0 = np.asarray(V0, dtype=np.float64)
+        self.Vt = V0 if callable(V0) else None
+        self.V0 = None if callable(V0) else np.asarray(V0, dtype=np.float64)
         self.vfac = vfac
         self.phi = phi
         self.order = order
@@ -74,6 +76,8 @@ class FreeSpaceOracle:
         return self._apply(self.G, fh)
 
     def V(self, t: float) -> np.ndarray:
+        if self.Vt is not None:
+            return np.asarray(self.Vt(t), dtype=np.float64)
         return float(self.vfac(t)) * self.V0
 
     def P(self, t: float, s: float) -> np.ndarray:

@@ -64,7 +64,9 @@ class PeriodicOracle:
     ----------
     shape : grid points per dimension (each even).
     dt    : time step.
-    V0, vfac : V(x, t) = vfac(t) * V0(x) (real).
+    V0, vfac : V(x, t) = vfac(t) * V0(x) (real); or V0 a callable t -> V(., t)
+               on the grid (any real potential, the problem of Sec. 1 with
+               general V(x, t)), vfac then unused.
     phi   : callable t -> array(d), phi(t) = int_0^t A.
     order : Adams order n (even, >= 2).
     n_startup : number of Richardson start-up steps (default n - 1).
@@ -77,7 +79,8 @@ class PeriodicOracle:
         if order < 2 or order % 2:
             raise ValueError("order must be even and >= 2")
         self.dt = float(dt)
-        self.V0 = np.asarray(V0, dtype=np.float64)
+        self.Vt = V0 if callable(V0) else None
+        self.V0 = None if callable(V0) else np.asarray(V0, dtype=np.float64)
         self.vfac = vfac
         self.phi = phi
         self.order = order
@@ -109,6 +112,8 @@ class PeriodicOracle:
 
     # -- problem data ---------------------------------------------------------
     def V(self, t: float) -> np.ndarray:
+        if self.Vt is not None:
+            return np.asarray(self.Vt(t), dtype=np.float64)
         return float(self.vfac(t)) * self.V0
 
     def P(self, t: float, s: float) -> np.ndarray:

@@ -46,8 +46,11 @@ def free_choose_H(eps: float, vnorm: float, phimax: float, dim: int, precision: 
     return out.value
 
 
-def _config(shape, dt, nsteps, order, batch, precision, startup_steps, bc, nu, H, alpert_p, gauss_q, n_r):
+def _config(shape, dt, nsteps, order, batch, precision, startup_steps, bc, nu, H, alpert_p, gauss_q, n_r,
+            potential="separable"):
     cfg = _native.TdseConfig()
+    cfg.potential = {"separable": _native.TDSE_V_SEPARABLE, "table": _native.TDSE_V_TABLE,
+                     "shared_table": _native.TDSE_V_TABLE_SHARED}[potential]
     cfg.dim = len(shape)
     cfg.bc = {"periodic": PERIODIC, "free": FREE}[bc]
     if bc == "free":
@@ -101,14 +104,17 @@ class Problem:
     ``batch``; ``precision`` ("fp64" or "mixed"); ``startup_steps`` (-1 =
     order-1); ``bc`` ("periodic" or "free").  Free space also takes ``nu``
     (FFT length per dimension), ``H`` (contour offset), ``alpert_p``,
-    ``gauss_q`` and ``n_r``.  The device workspace is a torch uint8 tensor
-    owned here.
+    ``gauss_q`` and ``n_r``.  ``potential``: "separable" (V = f(t) V0(x),
+    ``set_potential``), "table" (general V(x, t) per instance, given at
+    ``potential_times()``, ``set_potential_table`` / ``set_potential_fn``) or
+    "shared_table" (one such table for every instance, instance = -1).
+    The device workspace is a torch uint8 tensor owned here.
     """
 
     def __init__(self, shape: Sequence[int], dt: float, nsteps: int, order: int = 8, batch: int = 1,
                  precision: str = "fp64", startup_steps: int = -1, device=None, stream=None, bc: str = "periodic",
                  nu: Optional[Sequence[int]] = None, H: float = 0.0, alpert_p: int = 8, gauss_q: int = 10,
-                 n_r: int = 1):
+                 n_r: int = 1, potential: str = "separable"):
         import torch
         self._lib = _native.lib()
         self.shape = tuple(int(s) for s in shape)
@@ -117,8 +123,9 @@ class Problem:
         self.nsteps = int(nsteps)
         self.bc = bc
         self.precision = precision
+        self.potential = potential
         cfg = _config(self.shape, dt, nsteps, order, batch, precision, startup_steps, bc, nu, H, alpert_p, gauss_q,
-                      n_r)
+                      n_r, potential)
         self._ctx = ctypes.c_void_p()
         _check(self._lib.tdse_create(ctypes.byref(cfg), ctypes.byref(self._ctx)))
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
@@ -135,11 +142,11 @@ class Problem:
     def workspace_bytes_for(shape: Sequence[int], dt: float, nsteps: int, order: int = 8, batch: int = 1,
                             precision: str = "fp64", startup_steps: int = -1, bc: str = "periodic",
                             nu: Optional[Sequence[int]] = None, H: float = 0.0, alpert_p: int = 8, gauss_q: int = 10,
-                            n_r: int = 1) -> int:
+                            n_r: int = 1, potential: str = "separable") -> int:
         """Device workspace a Problem of this configuration needs (host-only query)."""
         lib = _native.lib()
         cfg = _config(tuple(int(s) for s in shape), dt, nsteps, order, batch, precision, startup_steps, bc, nu, H,
-                      alpert_p, gauss_q, n_r)
+                      alpert_p, gauss_q, n_r, potential)
         ctx = ctypes.c_void_p()
         _check(lib.tdse_create(ctypes.byref(cfg), ctypes.byref(ctx)))
         n = int(lib.tdse_workspace_bytes(ctx))
@@ -162,6 +169,29 @@ class Problem:
         _check(self._lib.tdse_set_potential(self._ctx, instance, pv, tf_ptr, where, _stream_handle(self._stream)),
                self._ctx)
         del keep
+
+    def potential_times(self) -> np.ndarray:
+        """Times at which a potential-table Problem evaluates V (every dt/8 of
+        the start-up steps, then every step)."""
+        n = int(self._lib.tdse_potential_times(self._ctx, None))
+        if n < 0:
+            raise TdseError(_native.TDSE_ESTATE, "not a potential-table Problem")
+        t = np.empty(n, dtype=np.float64)
+        self._lib.tdse_potential_times(self._ctx, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return t
+
+    def set_potential_table(self, V, instance: int = -1):
+        """V(x, t_r) for every t_r of potential_times(): array [R] + shape
+        (numpy or torch, host or cuda)."""
+        pv, where, keep = _as_buffer(V, np.float64)
+        _check(self._lib.tdse_set_potential_table(self._ctx, instance, pv, where, _stream_handle(self._stream)),
+               self._ctx)
+        del keep
+
+    def set_potential_fn(self, Vt: Callable, instance: int = -1):
+        """V from a callable t -> V(x, t) on the grid, sampled at potential_times()."""
+        t = self.potential_times()
+        self.set_potential_table(np.stack([np.asarray(Vt(float(tt)), dtype=np.float64) for tt in t]), instance)
 
     def set_pulse(self, A0: float, omega: float, T_pulse: float, direction, instance: int = -1):
         d = (ctypes.c_double * 2)(*(list(direction) + [0.0, 0.0])[:2])

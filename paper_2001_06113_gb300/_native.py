@@ -17,6 +17,8 @@ STATUS_NAMES = {0: "TDSE_OK", -1: "TDSE_EINVAL", -2: "TDSE_ENOMEM", -3: "TDSE_EC
 PERIODIC, FREE = 0, 1
 FP64, MIXED = 0, 1
 HOST, DEVICE = 0, 1
+TDSE_V_SEPARABLE, TDSE_V_TABLE, TDSE_V_TABLE_SHARED = 0, 1, 2
+TDSE_ESTATE = -6
 
 # Every symbol include/tdse.h declares (checked by the CPU test suite).
 EXPORTS = [
@@ -24,7 +26,7 @@ EXPORTS = [
     "tdse_set_vector_potential", "tdse_set_pulse", "tdse_set_initial", "tdse_step", "tdse_solve_to",
     "tdse_read_u", "tdse_check_finite", "tdse_step_index", "tdse_time", "tdse_adams_weights",
     "tdse_last_error", "tdse_destroy", "tdse_modes_to_grid_2d_noalloc", "tdse_read_modes", "tdse_free_rule",
-    "tdse_free_choose_H", "tdse_free_choose_H_prec", "tdse_batch_create", "tdse_batch_tune", "tdse_batch_step", "tdse_batch_describe",
+    "tdse_free_choose_H", "tdse_free_choose_H_prec", "tdse_potential_times", "tdse_set_potential_table", "tdse_batch_create", "tdse_batch_tune", "tdse_batch_step", "tdse_batch_describe",
     "tdse_batch_last_error", "tdse_batch_destroy", "tdse_set_residual_check", "tdse_residual_report",
     "tdse_save", "tdse_load",
 ]
@@ -47,6 +49,7 @@ class TdseConfig(ctypes.Structure):
         ("gauss_q", ctypes.c_int),
         ("n_r", ctypes.c_int),
         ("H", ctypes.c_double),
+        ("potential", ctypes.c_int),
     ]
 
 
@@ -95,6 +98,8 @@ def load(path: str = _LIB_PATH) -> ctypes.CDLL:
         "tdse_set_residual_check": ([vp, ip, cd], ip),
         "tdse_residual_report": ([vp, dp, ctypes.POINTER(ip), ctypes.POINTER(ip), vp], ip),
         "tdse_save": ([vp, vp, ctypes.POINTER(ctypes.c_size_t), vp], ip),
+        "tdse_potential_times": ([vp, dp], ip),
+        "tdse_set_potential_table": ([vp, ip, vp, ip, vp], ip),
         "tdse_load": ([vp, vp, ctypes.c_size_t, vp], ip),
     }
     for name, (args, res) in sig.items():

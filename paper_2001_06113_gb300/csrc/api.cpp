@@ -126,8 +126,9 @@ static void plan_workspace(tdse_ctx* c) {
     c->off.chain_ring = take((size_t)c->L * B * NP * c->rsz);
     c->off.aux = take(B * NP * 16);
     c->off.aux2 = take(B * NP * 16);
-    c->off.V0 = take(B * NP * 8);
-    c->off.V0f = take(B * NP * 8);
+    const size_t vcopies = c->vshared ? 1 : B;
+    c->off.V0 = take(vcopies * c->vrows * NP * 8);
+    c->off.V0f = take(vcopies * c->vrows * NP * 8);
     c->off.tfac = take(B * (size_t)c->ntf * 8);
     c->off.phi = take(B * (size_t)c->d * c->ntf * 8);
     const size_t nsp1 = (size_t)c->cfg.nsteps + 1;
@@ -188,6 +189,7 @@ static KArgs base_args(const tdse_ctx* c) {
     a.aux2 = c->P<double2>(c->off.aux2);
     a.V0 = c->P<double>(c->off.V0);
     a.V0f = c->P<float2>(c->off.V0f);
+    a.vstride = c->vshared ? 0 : (size_t)c->vrows * c->NP;
     a.tfac = c->P<double>(c->off.tfac);
     a.ntf = c->ntf;
     a.n_int = c->n_int;
@@ -216,6 +218,15 @@ static KArgs base_args(const tdse_ctx* c) {
 }
 
 // per-step scalars: h, mu (and their hi/lo splits)
+// The launch evaluates V at t = tf dt / 8: with a potential table, point V0 /
+// V0f at that time's row.
+static void set_time(const tdse_ctx* c, KArgs& a, int tf) {
+    a.tf = tf;
+    const size_t off = vrow(c, tf) * c->NP;
+    a.V0 = c->P<double>(c->off.V0) + off;
+    a.V0f = c->P<float2>(c->off.V0f) + off;
+}
+
 static void set_weights(KArgs& a, double h, const double* mu, int nmu) {
     a.h = h;
     split(h, a.h_hi, a.h_lo);
@@ -291,6 +302,9 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     if (!fs && cfg->dim == 1 && !periodic1d_supported(n0) && !big1d) return TDSE_EUNSUPPORTED;
     if (!fs && cfg->dim == 2 && !periodic2d_supported(n0, n1)) return TDSE_EUNSUPPORTED;
     if ((long long)cfg->nsteps * SUB + 1 > (1LL << 30)) return TDSE_EINVAL;
+    if (cfg->potential != TDSE_V_SEPARABLE && cfg->potential != TDSE_V_TABLE &&
+        cfg->potential != TDSE_V_TABLE_SHARED)
+        return TDSE_EINVAL;
 
     tdse_ctx* c = new (std::nothrow) tdse_ctx();
     if (!c) return TDSE_ENOMEM;
@@ -358,6 +372,9 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     }
     c->have_V.assign(c->B, 0);
     c->have_u0.assign(c->B, 0);
+    c->vtable = cfg->potential != TDSE_V_SEPARABLE;
+    c->vshared = cfg->potential == TDSE_V_TABLE_SHARED;
+    c->vrows = c->vtable ? SUB * c->S_eff + 1 + (cfg->nsteps - c->S_eff) : 1;
     if (fs) {
         c->fs = true;
         const tdse_status st = fs_create(c);
@@ -418,6 +435,7 @@ tdse_status tdse_set_potential(tdse_ctx* c, int instance, const double* V0, cons
                                void* stream) {
     if (!c || !V0) return TDSE_EINVAL;
     if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
+    if (c->vtable) return c->fail(TDSE_ESTATE, "potential-table context: use tdse_set_potential_table");
     int lo, hi;
     if (!instance_range(c, instance, lo, hi)) return c->fail(TDSE_EINVAL, "instance out of range");
     if (where != TDSE_HOST && where != TDSE_DEVICE) return TDSE_EINVAL;
@@ -441,6 +459,44 @@ tdse_status tdse_set_potential(tdse_ctx* c, int instance, const double* V0, cons
         c->have_V[b] = 1;
     }
     if (where == TDSE_HOST || tf) TDSE_CK(c, cudaStreamSynchronize(s));
+    return TDSE_OK;
+}
+
+int tdse_potential_times(const tdse_ctx* c, double* t_out) {
+    if (!c || !c->vtable) return -1;
+    if (t_out) {
+        const int fine = SUB * c->S_eff;
+        for (int r = 0; r < c->vrows; ++r) {
+            const int tf = r <= fine ? r : SUB * (c->S_eff + (r - fine));
+            t_out[r] = (double)tf * c->cfg.dt / SUB;
+        }
+    }
+    return c->vrows;
+}
+
+tdse_status tdse_set_potential_table(tdse_ctx* c, int instance, const double* V, int where, void* stream) {
+    if (!c || !V) return TDSE_EINVAL;
+    if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
+    if (!c->vtable) return c->fail(TDSE_ESTATE, "separable-potential context: use tdse_set_potential");
+    int lo, hi;
+    if (!instance_range(c, instance, lo, hi)) return c->fail(TDSE_EINVAL, "instance out of range");
+    if (c->vshared && instance != -1) return c->fail(TDSE_EINVAL, "shared potential table: instance must be -1");
+    if (where != TDSE_HOST && where != TDSE_DEVICE) return TDSE_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const cudaMemcpyKind kind = where == TDSE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const size_t per = (size_t)c->vrows * c->NP;
+    std::vector<double> ones(c->ntf, 1.0);
+    for (int b = lo; b < hi; ++b) {
+        if (!c->vshared || b == lo) {
+            double* dV = c->P<double>(c->off.V0) + (size_t)b * per;
+            TDSE_CK(c, cudaMemcpyAsync(dV, V, per * 8, kind, s));
+            TDSE_CK(c, launch_split_float(c->P<float2>(c->off.V0f) + (size_t)b * per, dV, per, s));
+        }
+        TDSE_CK(c, cudaMemcpyAsync(c->P<double>(c->off.tfac) + (size_t)b * c->ntf, ones.data(), c->ntf * 8,
+                                   cudaMemcpyHostToDevice, s));
+        c->have_V[b] = 1;
+    }
+    TDSE_CK(c, cudaStreamSynchronize(s));   // host sources and `ones` are released on return
     return TDSE_OK;
 }
 
@@ -528,7 +584,7 @@ static tdse_status do_init(tdse_ctx* c, cudaStream_t s) {
     KArgs a = base_args(c);
     a.mode = MODE_INIT;
     a.out_slot = slot_of(c, 0);
-    a.tf = 0;
+    set_time(c, a, 0);
     if (c->off.tw128)
         TDSE_CK(c, launch_four_step_init(a, c->P<double2>(c->off.tw128), s));
     else
@@ -560,7 +616,7 @@ static tdse_status startup_step(tdse_ctx* c, int n, cudaStream_t s) {
             a.out_slot = 0;
             a.interval[0] = startup_interval(c, n, ch, i);
             a.kin = ch;
-            a.tf = SUB * (n - 1) + (i + 1) * len;
+            set_time(c, a, SUB * (n - 1) + (i + 1) * len);
             TDSE_CK(c, run(c, a, step_combo(c), s));
         }
     }
@@ -568,7 +624,7 @@ static tdse_status startup_step(tdse_ctx* c, int n, cudaStream_t s) {
     KArgs a = base_args(c);
     a.mode = MODE_REFRESH;
     a.out_slot = slot_of(c, n);
-    a.tf = SUB * n;
+    set_time(c, a, SUB * n);
     TDSE_CK(c, run(c, a, step_combo(c), s));
     return TDSE_OK;
 }
@@ -615,7 +671,7 @@ static KArgs adams_args(const tdse_ctx* c, int n) {
     if (!c->mixed)
         for (int i = 0; i < a.nhist; ++i) a.interval[i] = main_interval(c, n - i);
     a.kin = 0;
-    a.tf = SUB * n;
+    set_time(c, a, SUB * n);
     a.ip = c->mixed ? 1 : 0;
     a.e_step = n;
     if (c->mixed) set_dither(c, a, n, n);
@@ -651,6 +707,7 @@ static tdse_status adams_steps(tdse_ctx* c, int n0, int k, cudaStream_t s) {
 static tdse_status residual_check(tdse_ctx* c, cudaStream_t s) {
     ResArgs r{};
     r.a = base_args(c);
+    set_time(c, r.a, SUB * c->step);
     r.n = c->step;
     r.slot = slot_of(c, c->step);
     r.z[0] = c->zdither[2 * c->step];

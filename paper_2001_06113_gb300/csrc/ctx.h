@@ -64,6 +64,9 @@ struct tdse_ctx {
             res_rho, res_flags, res_ncorr, scratch, end;
     } off{};
     std::vector<char> have_V, have_u0;
+    bool vtable = false;        // TDSE_V_TABLE(_SHARED): V(x, t_r) rows in V0 / V0f
+    bool vshared = false;       // one table for every instance
+    int vrows = 1;              // rows per instance (1 when separable)
     int res_every = 0;          // FP64 residual check after every res_every-th Adams step (mixed; 0 = off)
     double res_tol = 0.0;
     int res_checks = 0;
@@ -101,6 +104,14 @@ inline int startup_interval(const tdse_ctx* c, int s, int chain, int i) {
 }
 inline int main_interval(const tdse_ctx* c, int n) {
     return n <= c->S_eff ? startup_interval(c, n, 0, 0) : c->n_int_startup + (n - c->S_eff - 1);
+}
+
+// Row of the potential table holding V(t_tf), t_tf = tf dt / 8: every fine
+// time of the start-up steps, then one row per Adams step (tf a multiple of 8).
+inline size_t vrow(const tdse_ctx* c, int tf) {
+    if (!c->vtable) return 0;
+    const int fine = tdse::SUB * c->S_eff;
+    return tf <= fine ? (size_t)tf : (size_t)fine + (size_t)(tf / tdse::SUB - c->S_eff);
 }
 
 // Free-space orchestration (fs_api.cpp), called by the entry points in api.cpp

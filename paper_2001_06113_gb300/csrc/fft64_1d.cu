@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(F4_T) k_f4_cols(const KArgs a, const double2* 
             if (a.ip) x = cmul(e_exact(a, b, a.e_step, kmode(n, F4_N), 0.0, 1), x);
         } else {
             x = u0[n];
-            if (src == F4_SRC_VU0) x = cscale(x, vfac * a.V0[off + n]);
+            if (src == F4_SRC_VU0) x = cscale(x, vfac * a.V0[(size_t)b * a.vstride + n]);
         }
         buf[n1 * F4_L + c] = x;
     }

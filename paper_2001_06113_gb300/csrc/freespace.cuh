@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_1d(FsArgs a, i
     const FsAxis& ax = a.ax[0];
     const int b = blockIdx.x, N = ax.N;
     const double vf = a.tfac[(size_t)b * a.ntf + a.tf];
-    const double* V0 = a.V0 + (size_t)b * M;
+    const double* V0 = a.V0 + (size_t)b * a.vstride;
     if (mode == FS_1D_FWD_ONLY) {
         for (int j = threadIdx.x; j < M; j += FS_T) {
             const double2 u = a.usrc[(size_t)b * M + j];
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_phys(FsArgs a,
     C* zcol = reinterpret_cast<C*>(a.Z) + (size_t)b * N0 * M1 + j1;
     const size_t NX = (size_t)M * M1;
     const double vf = a.tfac[(size_t)b * a.ntf + a.tf];
-    const double* V0 = a.V0 + (size_t)b * NX;
+    const double* V0 = a.V0 + (size_t)b * a.vstride;
     if (!from_usrc) {
         for (int m = threadIdx.x; m < N0; m += FS_T) Ln::stage_inv(m, zcol[(size_t)m * M1], E, dv, ax);
         Ln::zero_pad(E, ax.NE);

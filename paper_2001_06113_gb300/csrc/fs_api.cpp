@@ -199,9 +199,16 @@ FsArgs fs_base(const tdse_ctx* c) {
     a.Z = F.off.Z ? c->P<double2>(F.off.Z) : nullptr;
     a.u = c->P<double2>(F.off.u);
     a.V0 = c->P<double>(F.off.V0);
+    a.vstride = c->vshared ? 0 : (size_t)c->vrows * F.NX;
     a.tfac = c->P<double>(F.off.tfac);
     a.ntf = c->ntf;
     return a;
+}
+
+// The launch evaluates V at t = tf dt / 8 (with a potential table: that row).
+void set_time(const tdse_ctx* c, FsArgs& a, int tf) {
+    a.tf = tf;
+    a.V0 = c->P<double>(c->F.off.V0) + vrow(c, tf) * c->F.NX;
 }
 
 // Ring slot `slot` of a ring with rsz-byte elements (as the kernels' double2* field).
@@ -217,7 +224,7 @@ tdse_status forward_to(tdse_ctx* c, const double2* usrc, int mulV, int tf, doubl
     FsArgs a = fs_base(c);
     a.usrc = usrc;
     a.mulV = mulV;
-    a.tf = tf;
+    set_time(c, a, tf);
     a.fdst = fdst;
     a.fdst_bstride = bstride;
     a.fdst_ring = to_ring;
@@ -280,7 +287,7 @@ tdse_status fs_startup_step(tdse_ctx* c, int n, cudaStream_t s) {
             a.hist_slot[0] = 0;
             a.out_slot = 0;
             a.interval[0] = startup_interval(c, n, ch, i);
-            a.tf = SUB * (n - 1) + (i + 1) * len;
+            set_time(c, a, SUB * (n - 1) + (i + 1) * len);
             tdse_status st = one_step(c, a, s);
             if (st != TDSE_OK) return st;
         }
@@ -299,7 +306,7 @@ FsArgs adams_args(const tdse_ctx* c, int n) {
     for (int j = 1; j <= a.nhist; ++j) a.hist_slot[j - 1] = slot_of(c, n - j);
     a.out_slot = slot_of(c, n);
     for (int i = 0; i < a.nhist; ++i) a.interval[i] = main_interval(c, n - i);
-    a.tf = SUB * n;
+    set_time(c, a, SUB * n);
     return a;
 }
 
@@ -357,8 +364,9 @@ tdse_status fs_create(tdse_ctx* c) {
     F.off.chain_u = take((size_t)c->L * B * F.NX * 16);
     F.off.u = take(B * F.NX * 16);
     F.off.Z = c->d == 2 ? take(B * (size_t)F.ax[0].N * F.ax[1].M * c->rsz) : 0;
-    F.off.V0 = take(B * F.NX * 8);
-    const size_t V0f = take(B * F.NX * 8);
+    const size_t vcopies = c->vshared ? 1 : B;
+    F.off.V0 = take(vcopies * c->vrows * F.NX * 8);
+    const size_t V0f = take(vcopies * c->vrows * F.NX * 8);
     F.off.tfac = take(B * (size_t)c->ntf * 8);
     F.off.phi = take(B * (size_t)c->d * c->ntf * 8);
     F.off.iv = take((size_t)c->n_int * sizeof(int2));

@@ -77,7 +77,8 @@ struct FsArgs {
     size_t fdst_bstride;
     int fdst_ring;         // destination is a ring slot (transform type) rather than the FP64 state
     int mulV;              // forward-only: transform V(t) usrc instead of usrc
-    const double* V0;      // [B][M0 M1]
+    const double* V0;      // instance b at V0 + b vstride (separable: [B][M0 M1]; table: this time's row)
+    size_t vstride;
     const double* tfac;    // [B][ntf]
     int ntf;
 };

@@ -57,8 +57,9 @@ struct KArgs {
     double2* aux;             // 2D intermediate T1 (16 B per element)
     double2* aux2;            // 2D intermediate T2 / read-out output (16 B per element)
     // ---- problem tables
-    const double* V0;         // [B][NP]
-    const float2* V0f;        // [B][NP] (float(V0), float(V0 - float(V0)))
+    const double* V0;         // instance b at V0 + b vstride: V(x, t_tf) on the grid (separable: V0(x))
+    const float2* V0f;        // same layout (float(V), float(V - float(V)))
+    size_t vstride;           // NP (separable) or rows x NP (potential table, V0 then points at this time's row)
     const double* tfac;       // [B][ntf]
     int ntf;
     int n_int;                // phase intervals per instance

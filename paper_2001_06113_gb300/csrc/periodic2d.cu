@@ -189,8 +189,8 @@ __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_row_mid(const KArgs a) {
     const C* twl;
     if constexpr (F64) { tw = a.tw64_1; twl = tw; } else { tw = a.tw32_1; twl = a.tw32lo_1; }
     const double vfac = a.tfac[(size_t)b * a.ntf + a.tf];
-    const double* V0 = a.V0 + (size_t)b * NP;
-    const float2* V0f = a.V0f + (size_t)b * NP;
+    const double* V0 = a.V0 + (size_t)b * a.vstride;
+    const float2* V0f = a.V0f + (size_t)b * a.vstride;
     const float fh = (float)vfac, fl = (float)(vfac - (double)fh);
     const R scale = (R)1 / (R)N1;
 

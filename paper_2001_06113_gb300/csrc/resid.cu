@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(RT) k_res_1d(const ResArgs r) {
     __syncthreads();
     CtaFft<double2, N, 1, 1, RT, true>::run(buf, a.tw64_0, nullptr);
     const double vf = a.tfac[(size_t)b * a.ntf + 8 * r.n];
-    for (int j = threadIdx.x; j < N; j += RT) buf[j] = solve_times_V(buf[j], vf * a.V0[(size_t)b * N + j], r.hmu0);
+    for (int j = threadIdx.x; j < N; j += RT) buf[j] = solve_times_V(buf[j], vf * a.V0[(size_t)b * a.vstride + j], r.hmu0);
     __syncthreads();
     CtaFft<double2, N, 1, 1, RT, false>::run(buf, a.tw64_0, nullptr);
     for (int k = threadIdx.x; k < N; k += RT) X[k] = buf[k];
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(RT) k_res_rows(const ResArgs r) {
     const double vf = a.tfac[(size_t)b * a.ntf + 8 * r.n];
     for (int it = threadIdx.x; it < N * RL; it += RT) {
         const int c = it / N, j = it % N;
-        buf[j * LS + c] = solve_times_V(buf[j * LS + c], vf * a.V0[(size_t)b * a.n0 * N + (size_t)(r0 + c) * N + j],
+        buf[j * LS + c] = solve_times_V(buf[j * LS + c], vf * a.V0[(size_t)b * a.vstride + (size_t)(r0 + c) * N + j],
                                         r.hmu0);
     }
     __syncthreads();

@@ -28,8 +28,8 @@ __device__ __forceinline__ void step1d(const KArgs& a, const int b, const int ti
     const C* twl;
     if constexpr (F64) { tw = a.tw64_0; twl = tw; } else { tw = a.tw32_0; twl = a.tw32lo_0; }
     const double vfac = a.tfac[(size_t)b * a.ntf + a.tf];
-    const double* V0 = a.V0 + (size_t)b * NP;
-    const float2* V0f = a.V0f + (size_t)b * NP;
+    const double* V0 = a.V0 + (size_t)b * a.vstride;
+    const float2* V0f = a.V0f + (size_t)b * a.vstride;
     const R scale = (R)1 / (R)N;
     const float fh = (float)vfac, fl = (float)(vfac - (double)fh);
 

@@ -2,7 +2,8 @@
 
 This module only *samples the problem data* -- the initial wavefunction u0,
 the static potential profile V0 and its time factor f(t) (so that
-V(x, t) = f(t) V0(x)), and the parameters of the vector-potential pulse A(t)
+V(x, t) = f(t) V0(x)) or a general V(x, t), and the parameters of the
+vector-potential pulse A(t)
 -- on the spatial grid that the problem statement fixes.  It contains none of
 the solver's arithmetic (no transforms, no phases, no quadrature, no phi = int
 A); both the CPU oracle and the CUDA path receive exactly these arrays.
@@ -19,6 +20,10 @@ Workloads (shapes/values follow the paper's 1D/2D examples, Sec. 7):
     T=2, dt=1e-3;
   * ``periodic_1d_batch_member`` -- one member of the uneven 1D batch
     (N in {256..16384}), T=1, dt=1e-3;
+  * ``moving_well_1d`` -- Example 1: moving periodic Gaussian well
+    (V0 = 300, beta = 0.2, speed c, T = 2 pi / 15), u0 its ground state
+    (Fourier-Galerkin eigensolve of the static well); ``moving_wells_2d``,
+    ``free_moving_wells`` -- drifting wells (non-separable V(x, t));
   * ``free_bump_gaussians`` -- free space on [-1,1]^d (default 256^2):
     Gaussians (sigma ~ U[0.08,0.15], centres ~ U[-0.4,0.4]^d) times the
     C-infinity window exp(1 - 1/(1 - r^2)), r = |x| / 0.95, for u0 and for
@@ -73,12 +78,13 @@ class Instance:
     bc: int
     shape: tuple
     u0: np.ndarray            # complex128, shape `shape`
-    V0: np.ndarray            # float64, shape `shape`
+    V0: np.ndarray            # float64, shape `shape` (V(x, 0) when Vt is set)
     vfac: Callable            # f(t), vectorised; V(x,t) = f(t) V0(x)
     pulse: Optional[Pulse]    # None means A = 0
     dt: float
     nsteps: int
     name: str = ""
+    Vt: Optional[Callable] = None   # general V: t -> V(x, t) on the grid (vfac unused)
 
     @property
     def dim(self) -> int:
@@ -92,6 +98,16 @@ class Instance:
         """f(t) sampled at t = m dt / sub, m = 0 .. sub*nsteps."""
         m = np.arange(sub * self.nsteps + 1, dtype=np.float64)
         return np.asarray(self.vfac(m * self.dt / sub), dtype=np.float64).reshape(-1)
+
+    def V_at(self, t: float) -> np.ndarray:
+        """V(x, t) on the grid."""
+        if self.Vt is not None:
+            return np.asarray(self.Vt(t), dtype=np.float64)
+        return float(np.asarray(self.vfac(t)).reshape(-1)[0]) * self.V0
+
+    def potential_table(self, times) -> np.ndarray:
+        """V(x, t) on the grid at each of `times`: array [len(times)] + shape."""
+        return np.stack([self.V_at(float(t)) for t in times]).astype(np.float64)
 
 
 def _const_one(t):
@@ -251,6 +267,95 @@ def free_bump_gaussians(shape=(256, 256), seed: int = 3, dt: float = 5e-4, nstep
     pulse = Pulse(A0, omega, Tp, dirn) if A0 else None
     return Instance(FREE, tuple(shape), u0, V0, vfac or _const_one, pulse, dt, nsteps,
                     name=f"free_bump_gaussians_{'x'.join(map(str, shape))}")
+
+
+def _moving_gaussians(X: Sequence[np.ndarray], wells, t: float, period: Optional[float], images: int) -> np.ndarray:
+    """-sum_w depth_w exp(-|x - c_w - v_w t|^2 / (2 sigma_w^2)), summed over the
+    lattice images |m| <= images when `period` is set."""
+    out = np.zeros_like(X[0])
+    shifts = range(-images, images + 1) if period else (0,)
+    for depth, c, v, sigma in wells:
+        ctr = [ci + vi * t for ci, vi in zip(c, v)]
+        for m in np.ndindex(*([len(shifts)] * len(X))):
+            r2 = sum((x - cc - (period or 0.0) * shifts[mi]) ** 2 for x, cc, mi in zip(X, ctr, m))
+            out -= depth * np.exp(-r2 / (2.0 * sigma * sigma))
+    return out
+
+
+def well_ground_state_coeffs(V0: float, beta: float, K: int = 96):
+    """Ground state of -w'' + V w = E w on [-pi, pi] with V the periodic
+    extension of -V0 exp(-x^2 / (2 beta^2)): Fourier-Galerkin on |k| <= K with
+    the exact coefficients of the periodised Gaussian,
+    V^_m = -V0 beta / sqrt(2 pi) exp(-beta^2 m^2 / 2); dense symmetric
+    eigensolve.  Returns (E, k, c) with w(x) = sum_k c_k e^{i k x}, normalised
+    to unit L2 norm on [-pi, pi]."""
+    k = np.arange(-K, K + 1)
+    m = k[:, None] - k[None, :]
+    H = -V0 * beta / math.sqrt(2.0 * math.pi) * np.exp(-0.5 * beta * beta * m * m)
+    H = H + np.diag(k.astype(np.float64) ** 2)
+    E, vec = np.linalg.eigh(H)
+    c = vec[:, 0] / math.sqrt(2.0 * math.pi)
+    return float(E[0]), k, c.astype(np.complex128)
+
+
+def moving_well_1d(c: float = 30.0, M: int = 256, nsteps: int = 3200, T: float = 2.0 * math.pi / 15.0,
+                   V0: float = 300.0, beta: float = 0.2, x0: float = 0.0, u_shift: float = 0.0,
+                   K: int = 96) -> Instance:
+    """Moving periodic Gaussian well (Example 1): V(x, t) = -V0 sum_m
+    exp(-(x - 2 pi m - x0 - c t)^2 / (2 beta^2)), A = 0, u0 = the normalised
+    ground state of V(., 0) times e^{i u_shift x} (u_shift = c / 2 gives the
+    Galilean-boosted state that the well carries exactly when c / 2 is an
+    integer).  Defaults: V0 = 300, beta = 0.2, T = 2 pi / 15."""
+    x = periodic_grid(M)
+    E, k, coef = well_ground_state_coeffs(V0, beta, K)
+    u0 = (np.exp(1j * np.outer(x - x0, k)) @ coef) * np.exp(1j * u_shift * x)
+    wells = [(V0, (x0,), (c,), beta)]
+
+    def Vt(t, _x=(x,), _w=wells):
+        return _moving_gaussians(_x, _w, float(t), 2.0 * math.pi, 3)
+
+    dt = T / nsteps
+    return Instance(PERIODIC, (M,), u0.astype(np.complex128), Vt(0.0), _const_one, None, dt, nsteps,
+                    name=f"moving_well_1d_c{c:g}_M{M}", Vt=Vt)
+
+
+def moving_wells_2d(seed: int = 6, M: int = 64, dt: float = 1e-3, nsteps: int = 40, speed: float = 8.0,
+                    A0: float = 2.0, omega: float = 10.0) -> Instance:
+    """2D periodic wells drifting at constant velocity (a non-separable V):
+    the 2D wells workload's u0 and pulse, its four wells with velocities
+    ~ speed * U[-1,1]^2."""
+    base = periodic_2d_wells(seed=seed, M=M, dt=dt, nsteps=nsteps, A0=A0, omega=omega)
+    rng = np.random.default_rng([seed, 77])
+    x = periodic_grid(M)
+    X = tuple(np.meshgrid(x, x, indexing="ij"))
+    wells = [(rng.uniform(5.0, 20.0), tuple(rng.uniform(-1.5, 1.5, size=2)), tuple(speed * rng.uniform(-1, 1, size=2)),
+              rng.uniform(0.3, 0.6)) for _ in range(4)]
+
+    def Vt(t, _X=X, _w=wells):
+        return _moving_gaussians(_X, _w, float(t), 2.0 * math.pi, 3)
+
+    return Instance(PERIODIC, (M, M), base.u0, Vt(0.0), _const_one, base.pulse, dt, nsteps,
+                    name=f"moving_wells_2d_M{M}", Vt=Vt)
+
+
+def free_moving_wells(shape=(64,), seed: int = 7, dt: float = 1e-3, nsteps: int = 40, speed: float = 2.0,
+                      A0: float = 20.0, omega: float = 30.0) -> Instance:
+    """Free space on [-1,1]^d: the bump-windowed u0 and pulse of the
+    free-space workload with four wells drifting at velocities
+    ~ speed * U[-1,1]^d, the wells times the bump window at every t."""
+    base = free_bump_gaussians(shape, seed=seed, dt=dt, nsteps=nsteps, A0=A0, omega=omega)
+    d = len(shape)
+    rng = np.random.default_rng([seed, 78])
+    X = tuple(np.meshgrid(*[free_grid(M) for M in shape], indexing="ij"))
+    win = bump_window(X)
+    wells = [(rng.uniform(5.0, 20.0), tuple(rng.uniform(-0.4, 0.4, size=d)), tuple(speed * rng.uniform(-1, 1, size=d)),
+              rng.uniform(0.08, 0.15)) for _ in range(4)]
+
+    def Vt(t, _X=X, _w=wells, _win=win):
+        return _moving_gaussians(_X, _w, float(t), None, 0) * _win
+
+    return Instance(FREE, tuple(shape), base.u0, Vt(0.0), _const_one, base.pulse, dt, nsteps,
+                    name=f"free_moving_wells_{'x'.join(map(str, shape))}", Vt=Vt)
 
 
 def serve_requests(seed: int = 5, rate: float = 200.0, duration: float = 10.0, T_range=(0.5, 2.0),

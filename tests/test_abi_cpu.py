@@ -86,6 +86,10 @@ def _cfg(native, **kw):
     (dict(bc=1, nu=(512, 0), H=1.5, gauss_q=0, n_r=1), -1),
     (dict(bc=1, nu=(512, 0), H=1.5, gauss_q=32, n_r=4), -1),                # dense block > 128 modes
     (dict(precision=5), -1),
+    (dict(potential=1), 0),                                                  # general V(x, t) table
+    (dict(potential=2), 0),                                                  # one table for all instances
+    (dict(potential=3), -1),
+    (dict(bc=1, nu=(512, 0), H=1.5, gauss_q=10, n_r=1, potential=1), 0),
 ])
 def test_create_validates(native, kw, status):
     lib = native.lib()
@@ -194,3 +198,27 @@ def test_checkpoint_size_query_without_gpu(native):
     assert lib.tdse_save(ctx, buf, ctypes.byref(n), None) == -6          # workspace not bound
     assert lib.tdse_load(ctx, buf, n.value, None) == -6
     lib.tdse_destroy(ctx)
+
+
+@pytest.mark.parametrize("nsteps,startup,bc", [(20, -1, 0), (5, -1, 0), (30, 10, 1)])
+def test_potential_times(native, nsteps, startup, bc):
+    """Rows of a potential table: every dt/8 of the S start-up steps, then
+    every Adams step (host-only query; -1 for a separable context)."""
+    lib = native.lib()
+    kw = dict(nsteps=nsteps, startup_steps=startup, potential=1, dt=0.01)
+    if bc:
+        kw.update(bc=1, nu=(512, 0), H=1.5, gauss_q=10, n_r=1)
+    ctx = ctypes.c_void_p()
+    assert lib.tdse_create(ctypes.byref(_cfg(native, **kw)), ctypes.byref(ctx)) == 0
+    S = min(7 if startup < 0 else startup, nsteps)
+    R = lib.tdse_potential_times(ctx, None)
+    assert R == 8 * S + 1 + nsteps - S
+    t = np.empty(R)
+    assert lib.tdse_potential_times(ctx, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == R
+    want = np.concatenate([np.arange(8 * S + 1) * 0.01 / 8, np.arange(S + 1, nsteps + 1) * 0.01])
+    assert np.allclose(t, want, rtol=0, atol=1e-15)
+    lib.tdse_destroy(ctx)
+    sep = ctypes.c_void_p()
+    assert lib.tdse_create(ctypes.byref(_cfg(native)), ctypes.byref(sep)) == 0
+    assert lib.tdse_potential_times(sep, None) == -1
+    lib.tdse_destroy(sep)
