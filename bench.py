@@ -71,11 +71,13 @@ def parse():
     ap.add_argument("--precision", default=None, choices=["mixed", "fp64"],
                     help="default: mixed (periodic2d, batch1d, serve), fp64 (free2d)")
     ap.add_argument("--batch", type=int, default=0,
-                    help="instances per GPU (default: 64 periodic mixed, 4 periodic fp64, 1 free space)")
+                    help="instances per GPU (default: 64 periodic mixed, 4 periodic fp64, 1 free space; "
+                         "example1: initial states per speed, 2048)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="periodic2d", choices=["periodic2d", "free2d", "batch1d", "serve"])
+    ap.add_argument("--workload", default="periodic2d",
+                    choices=["periodic2d", "free2d", "batch1d", "serve", "example1"])
     ap.add_argument("--profile-adams", type=int, default=0,
                     help="profiling run: start-up + this many Adams steps of the batch, then exit")
     return ap.parse_args()
@@ -980,6 +982,220 @@ def main_batch1d(args, ws, rank, local):
     return 0
 
 
+# ------------------------------------------------------------ Example 1 arm (moving periodic well)
+EX_M, EX_NSTEPS, EX_T, EX_SPEEDS, EX_B = 512, 3200, 2.0 * math.pi / 15.0, (15.0, 30.0, 45.0), 2048
+EX_METRIC = ("point-steps/s (Example 1 moving periodic Gaussian well, V0=300, beta=0.2: 3 speeds x 2048 initial "
+             "states, M=512, 3200 steps to T=2pi/15, 8th-order, mixed)")
+# per point-step: state in/out 32, 7 ring reads 56, 1 ring write 8; the V row
+# (one shared table per speed) is read once per step for all instances
+EX_ALGO_BYTES = 16 + 7 * 8 + 16 + 8
+
+
+def example1_oracle_sample(nadams: int = 400):
+    """The periodic oracle (as it stands) on `nadams` Adams steps of one
+    Example 1 instance (c = 30, M = 512), history seeded with (Vu)^ of u0."""
+    from oracle import fields
+    from oracle.periodic import PeriodicOracle
+    it = synth.moving_well_1d(c=30.0, M=EX_M, nsteps=EX_NSTEPS, T=EX_T)
+    orc = PeriodicOracle(it.shape, it.dt, it.Vt, None, fields.phi_callable(None, 1))
+    u = it.u0
+    h0 = orc.fwd(orc.V(0.0) * u)
+    n0 = 100
+    hist = {n0 - j: h0 for j in range(1, ORDER)}
+    t0 = time.perf_counter()
+    for k in range(nadams):
+        n = n0 + k
+        t = n * it.dt
+        u = orc.adams_step(u, t, hist, n)
+        hist[n] = orc.fwd(orc.V(t) * u)
+        hist.pop(n - ORDER, None)
+    el = time.perf_counter() - t0
+    return EX_M * nadams / el, el
+
+
+def run_example1(args, ws, rank, local):
+    import torch
+    from paper_2001_06113_gb300 import Batch, Problem
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    B = args.batch if args.batch > 0 else EX_B
+    sweeps = [synth.example1_sweep(B, c, seed=11 + 1000 * rank, M=EX_M, nsteps=EX_NSTEPS, T=EX_T)
+              for c in EX_SPEEDS]
+    dt = sweeps[0][0].dt
+    probs = [Problem((EX_M,), dt, EX_NSTEPS, batch=B, precision="mixed", stream=stream, potential="shared_table")
+             for _ in EX_SPEEDS]
+    times_v = probs[0].potential_times()
+    tables = [torch.from_numpy(base.potential_table(times_v)).pin_memory() for base, _ in sweeps]
+    u0s = [torch.from_numpy(u0).pin_memory() for _, u0 in sweeps]
+
+    def reset():
+        for pr, u0 in zip(probs, u0s):
+            for b in range(B):
+                pr.set_initial(u0[b], instance=b)
+
+    def load_inputs():
+        for pr, tab in zip(probs, tables):
+            pr.set_potential_table(tab)
+        reset()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    load_inputs()
+    batch = Batch(probs, stream=stream)
+    batch.tune(5)
+    shape = batch.describe()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=torch.device("cuda", local))
+    for _ in range(args.warmup):
+        reset()
+        batch.step(EX_NSTEPS)
+    stream.synchronize()
+    points = len(probs) * B * EX_M
+    times = []
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                reset()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                batch.step(EX_NSTEPS)
+                e1.record(stream)
+            stream.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        torch.cuda.synchronize()
+        barrier()
+    t_solve = max_over_ranks(float(np.mean(times)), ws, "cuda")
+    value = ws * points * EX_NSTEPS / t_solve
+    # per-step latency of the fused launch
+    reset()
+    stream.synchronize()
+    dstream = torch.cuda.default_stream()
+    batch.step(STARTUP + 8, stream=dstream)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(101)]
+    with torch.cuda.stream(dstream):
+        evs[0].record(dstream)
+        for i in range(100):
+            batch.step(1, stream=dstream)
+            evs[i + 1].record(dstream)
+    dstream.synchronize()
+    dts = np.array([evs[i].elapsed_time(evs[i + 1]) / 1e3 for i in range(100)])
+    t_step = float(np.mean(dts))
+    peak, peak_src = hbm_peak()
+    achieved = EX_ALGO_BYTES * points / t_step / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": peak_src,
+                "kernel": "k_periodic1d_multi (one persistent launch per Adams step for all instances of the three "
+                          "speeds), timed per step over 100 steps",
+                "algorithmic_bytes_per_point_step": EX_ALGO_BYTES,
+                "step_ms_p50": round(float(np.percentile(dts, 50)) * 1e3, 4),
+                "step_ms_p99": round(float(np.percentile(dts, 99)) * 1e3, 4)}
+    # accuracy: the first initial state of each speed solved alone in FP64 (its own table), and
+    # the FP64 time-discretisation error at c = 30 (3200 against 6400 steps)
+    reset()
+    batch.step(EX_NSTEPS)
+    stream.synchronize()
+
+    def fp64_solve(c, u0, nsteps):
+        it = synth.moving_well_1d(c=c, M=EX_M, nsteps=nsteps, T=EX_T)
+        ref = Problem((EX_M,), it.dt, nsteps, precision="fp64", potential="table")
+        ref.set_potential_fn(it.V_at)
+        ref.set_initial(u0)
+        ref.step(nsteps)
+        u = ref.read_u(0)
+        ref.close()
+        return u
+
+    errs = {}
+    for (base, u0), pr, c in zip(sweeps, probs, EX_SPEEDS):
+        ref = fp64_solve(c, u0[0], EX_NSTEPS)
+        errs[f"c={c:g}"] = float(np.linalg.norm(pr.read_u(0) - ref) / np.linalg.norm(ref))
+        if c == 30.0:
+            fine = fp64_solve(c, u0[0], 2 * EX_NSTEPS)
+            err_dt = float(np.linalg.norm(ref - fine) / np.linalg.norm(fine))
+    e2e = None
+    if not args.no_e2e:
+        out = [torch.empty((B, EX_M), dtype=torch.complex128).pin_memory() for _ in probs]
+        e2e_times = []
+        for _ in range(max(1, min(args.steps, 3))):
+            stream.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            load_inputs()
+            batch.step(EX_NSTEPS)
+            for pr, o in zip(probs, out):
+                pr.read_u(-1, out=o)
+            e2e_times.append(time.perf_counter() - t0)
+        te = max_over_ranks(float(np.mean(e2e_times)), ws, "cuda")
+        e2e = {"value": ws * points * EX_NSTEPS / te, "unit": "point-steps/s",
+               "h2d_bytes_per_step": points * 16 + sum(int(t.numel()) * 8 for t in tables),
+               "d2h_bytes_per_step": points * 16}
+    batch.close()
+    for pr in probs:
+        pr.close()
+    return dict(value=value, t_solve=t_solve, roofline=roofline, e2e=e2e, clocks=clk.summary(), points=points,
+                B=B, shape=shape, errs=errs, err_dt=err_dt, rows=int(times_v.size))
+
+
+def main_example1(args, ws, rank, local):
+    import torch
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        for _ in range(args.warmup):
+            example1_oracle_sample(20)
+        vals = [example1_oracle_sample(400)[0] for _ in range(args.steps)]
+        value = float(np.mean(vals))
+        print(json.dumps({"impl": "reference", "metric": EX_METRIC, "value": value, "unit": "point-steps/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1e3 * EX_M / value, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "Example 1 moving well (CPU oracle sample: 400 Adams steps of one "
+                                                 "M=512 instance, c=30)"},
+                          "cpu_baseline": {"value": value, "unit": "point-steps/s", "cores": cpu_cores(),
+                                           "kind": "oracle", "sample": "400 Adams steps of one M=512 instance"},
+                          "e2e": {"value": value, "unit": "point-steps/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return 0
+    if ws > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    res = run_example1(args, ws, rank, local)
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and ws == 1:
+            v, el = example1_oracle_sample(2000)
+            cpu = {"value": v, "unit": "point-steps/s", "cores": cpu_cores(), "kind": "oracle",
+                   "sample": f"2000 8th-order Adams steps of one M=512 instance ({el:.1f} s; direct DFT sums)"}
+        line = {
+            "metric": EX_METRIC, "value": res["value"], "unit": "point-steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["t_solve"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
+            "data": "synthetic",
+            "config": {"workload": f"Example 1: periodic Gaussian well V0=300, beta=0.2 moving at c=15, 30, 45; per "
+                                   f"speed {res['B']} initial states (ground state shifted and momentum-kicked) "
+                                   f"sharing one V(x,t) table ({res['rows']} rows); M=512, T=2pi/15, 3200 steps, "
+                                   "8th-order Adams, mixed; the three speeds in one fused launch per step",
+                       "grid": [EX_M], "nsteps": EX_NSTEPS, "dt": EX_T / EX_NSTEPS, "order": ORDER,
+                       "instances_per_gpu": 3 * res["B"], "launch_shape": res["shape"],
+                       "l2": f"flushed (256 MB write) before each timed solve; per-step working set "
+                             f"{res['points'] * 80 / 1e6:.0f} MB",
+                       "step": "one whole solve (init, 7 Richardson start-up steps, 3193 Adams steps)",
+                       "parallelism": f"replicas x{ws}"},
+            "rel_l2_vs_fp64": res["errs"], "fp64_dt_error_c30": res["err_dt"],
+            "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
+            "gpu_launches": (3 * (1 + STARTUP * (4 + 15 + 1 + 1) + 1) + (EX_NSTEPS - STARTUP)) * args.steps,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 # ------------------------------------------------------------ request loop arm
 SV_RATE, SV_DURATION, SV_T, SV_BUDGET = 200.0, 1.0, (0.05, 0.2), 64 << 30
 SV_METRICS = {"fp64": "aggregate point-steps/s of a served request stream (1D/2D periodic mixed, 2D free space FP64)",
@@ -1089,7 +1305,7 @@ def main():
     ws, rank, local = dist_env()
     if args.precision is None:
         args.precision = "fp64" if args.workload == "free2d" else "mixed"
-    if args.batch <= 0:
+    if args.batch <= 0 and args.workload != "example1":
         args.batch = 1 if args.workload == "free2d" else (64 if args.precision == "mixed" else 4)
     if args.workload == "free2d":
         return main_free(args, ws, rank, local)
@@ -1097,6 +1313,8 @@ def main():
         return main_batch1d(args, ws, rank, local)
     if args.workload == "serve":
         return main_serve(args, ws, rank, local)
+    if args.workload == "example1":
+        return main_example1(args, ws, rank, local)
     if args.impl == "reference":
         if rank != 0:
             return 0

@@ -319,6 +319,21 @@ def moving_well_1d(c: float = 30.0, M: int = 256, nsteps: int = 3200, T: float =
                     name=f"moving_well_1d_c{c:g}_M{M}", Vt=Vt)
 
 
+def example1_sweep(count: int, c: float, seed: int = 11, M: int = 512, nsteps: int = 3200,
+                   T: float = 2.0 * math.pi / 15.0, V0: float = 300.0, beta: float = 0.2):
+    """A sweep over initial states for one well speed of Example 1: the well
+    instance (its V(x, t) is shared) and `count` initial states, the ground
+    state displaced by s grid points (s ~ U{-12..12}) and kicked by e^{i k0 x}
+    (k0 ~ U{-6..6}).  Returns (instance, u0 array [count, M])."""
+    base = moving_well_1d(c=c, M=M, nsteps=nsteps, T=T, V0=V0, beta=beta)
+    rng = np.random.default_rng([seed, int(round(c * 1000))])
+    x = periodic_grid(M)
+    shifts = rng.integers(-12, 13, size=count)
+    kicks = rng.integers(-6, 7, size=count)
+    u0 = np.stack([np.roll(base.u0, int(s)) * np.exp(1j * int(k) * x) for s, k in zip(shifts, kicks)])
+    return base, u0.astype(np.complex128)
+
+
 def moving_wells_2d(seed: int = 6, M: int = 64, dt: float = 1e-3, nsteps: int = 40, speed: float = 8.0,
                     A0: float = 2.0, omega: float = 10.0) -> Instance:
     """2D periodic wells drifting at constant velocity (a non-separable V):
