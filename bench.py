@@ -809,12 +809,14 @@ def run_batch1d(args, ws, rank, local):
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = B1_ALGO_BYTES * points / t_step / 1e9
+    fused = shape.get("mode", "fused") == "fused"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": B1_MULTI_TRAFFIC,
+                "frac": round(achieved / peak, 4), "traffic": B1_MULTI_TRAFFIC if fused else None,
                 "traffic_unit": "DRAM bytes per k_periodic1d_multi launch (ncu, default launch shape)",
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "kernel": "k_periodic1d_multi (one persistent launch per Adams step for all 512 instances), "
-                          "timed per step over 100 steps",
+                "kernel": ("k_periodic1d_multi (one persistent launch per Adams step for all 512 instances)" if fused
+                           else "k_periodic1d<float2,float2,N> per member size, on parallel streams (tuner's "
+                                "choice over the fused launch)") + ", timed per step over 100 steps",
                 "algorithmic_bytes_per_point_step": B1_ALGO_BYTES,
                 "step_ms_p50": round(float(np.percentile(dts, 50)) * 1e3, 4),
                 "step_ms_p99": round(float(np.percentile(dts, 99)) * 1e3, 4)}
@@ -961,8 +963,9 @@ def main_batch1d(args, ws, rank, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
             "data": "synthetic",
             "config": {"workload": f"512 uneven 1D periodic instances per GPU (N histogram {res['sizes']}), "
-                                   "T=1, dt=1e-3 (1000 steps), 8th-order Adams, mixed precision, one persistent "
-                                   "launch per Adams step, whole solve replayed from a CUDA graph",
+                                   "T=1, dt=1e-3 (1000 steps), 8th-order Adams, mixed precision, one batch (tuned: "
+                                   "one persistent launch per Adams step or the members' kernels on parallel streams), "
+                                   "whole solve replayed from a CUDA graph",
                        "points_per_gpu": res["points"], "nsteps": B1_NSTEPS, "dt": B1_DT, "order": ORDER,
                        "launch_shape_tuned": res["shape"], "launch_shape_default": res["default_shape"],
                        "l2": "flushed (256 MB write) before each timed solve; per-step working set "
@@ -1090,8 +1093,10 @@ def run_example1(args, ws, rank, local):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "peak_source": peak_src,
-                "kernel": "k_periodic1d_multi (one persistent launch per Adams step for all instances of the three "
-                          "speeds), timed per step over 100 steps",
+                "kernel": ("k_periodic1d_multi (one persistent launch per Adams step for all instances of the three "
+                           "speeds)" if shape.get("mode", "fused") == "fused" else
+                           "k_periodic1d<float2,float2,512> per speed on parallel streams (tuner's choice over the "
+                           "fused launch)") + ", timed per step over 100 steps",
                 "algorithmic_bytes_per_point_step": EX_ALGO_BYTES,
                 "step_ms_p50": round(float(np.percentile(dts, 50)) * 1e3, 4),
                 "step_ms_p99": round(float(np.percentile(dts, 99)) * 1e3, 4)}
@@ -1179,7 +1184,8 @@ def main_example1(args, ws, rank, local):
             "config": {"workload": f"Example 1: periodic Gaussian well V0=300, beta=0.2 moving at c=15, 30, 45; per "
                                    f"speed {res['B']} initial states (ground state shifted and momentum-kicked) "
                                    f"sharing one V(x,t) table ({res['rows']} rows); M=512, T=2pi/15, 3200 steps, "
-                                   "8th-order Adams, mixed; the three speeds in one fused launch per step",
+                                   "8th-order Adams, mixed; the three speeds in one batch (tuned: fused launch or "
+                                   "parallel streams)",
                        "grid": [EX_M], "nsteps": EX_NSTEPS, "dt": EX_T / EX_NSTEPS, "order": ORDER,
                        "instances_per_gpu": 3 * res["B"], "launch_shape": res["shape"],
                        "l2": f"flushed (256 MB write) before each timed solve; per-step working set "

@@ -65,6 +65,7 @@ enum { TDSE_PERIODIC = 0, TDSE_FREE = 1 };
 enum { TDSE_FP64 = 0, TDSE_MIXED = 1 };
 enum { TDSE_HOST = 0, TDSE_DEVICE = 1 };
 enum { TDSE_V_SEPARABLE = 0, TDSE_V_TABLE = 1, TDSE_V_TABLE_SHARED = 2 };
+enum { TDSE_BATCH_FUSED = 0, TDSE_BATCH_STREAMS = 1 };
 
 /*
  * Problem configuration.
@@ -336,9 +337,17 @@ typedef struct tdse_batch tdse_batch;
  * periodic mixed). */
 tdse_status tdse_batch_create(tdse_ctx* const* members, int count, tdse_batch** out);
 
+/* Execution of the Adams phase: TDSE_BATCH_FUSED (0, the default) = one
+ * persistent launch per step for all members; TDSE_BATCH_STREAMS (1) = each
+ * member's own single-size kernel on its own stream, forked from and joined
+ * to the caller's stream (parallel branches of the captured graph).  Same
+ * results either way.  Cached graphs are dropped.  TDSE_EINVAL otherwise. */
+tdse_status tdse_batch_set_mode(tdse_batch* b, int mode);
+
 /* Autotuner: choose the instances per work item of each member (all that fit
  * the CTA, a half or a quarter) and the CTA count by timing `trial_steps`
- * launches of each candidate on `stream`.  The members must have V and u0 set; tuning runs their start
+ * launches of each candidate on `stream`, then the faster of that fused launch
+ * and the per-member streams (tdse_batch_set_mode).  The members must have V and u0 set; tuning runs their start
  * if needed and leaves their state undefined: call tdse_set_initial on every
  * member before the next tdse_batch_step.  Cached graphs are dropped. */
 tdse_status tdse_batch_tune(tdse_batch* b, int trial_steps, void* stream);

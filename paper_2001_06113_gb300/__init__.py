@@ -346,8 +346,13 @@ class Batch:
             raw = self._lib.tdse_batch_last_error(self._b)
             raise TdseError(st, raw.decode() if raw else "")
 
+    def set_mode(self, mode: str):
+        """Adams phase as one fused launch per step ("fused") or each member's
+        own kernel on its own stream ("streams"); same results."""
+        self._check(self._lib.tdse_batch_set_mode(self._b, {"fused": 0, "streams": 1}[mode]))
+
     def tune(self, trial_steps: int = 5):
-        """Autotune the launch shape; afterwards every member needs set_initial."""
+        """Autotune the launch shape and the mode; afterwards every member needs set_initial."""
         self._check(self._lib.tdse_batch_tune(self._b, int(trial_steps), _stream_handle(self._stream)))
 
     def step(self, n: int, stream=None):

@@ -26,7 +26,7 @@ EXPORTS = [
     "tdse_set_vector_potential", "tdse_set_pulse", "tdse_set_initial", "tdse_step", "tdse_solve_to",
     "tdse_read_u", "tdse_check_finite", "tdse_step_index", "tdse_time", "tdse_adams_weights",
     "tdse_last_error", "tdse_destroy", "tdse_modes_to_grid_2d_noalloc", "tdse_read_modes", "tdse_free_rule",
-    "tdse_free_choose_H", "tdse_free_choose_H_prec", "tdse_potential_times", "tdse_set_potential_table", "tdse_batch_create", "tdse_batch_tune", "tdse_batch_step", "tdse_batch_describe",
+    "tdse_free_choose_H", "tdse_free_choose_H_prec", "tdse_potential_times", "tdse_set_potential_table", "tdse_batch_create", "tdse_batch_tune", "tdse_batch_set_mode", "tdse_batch_step", "tdse_batch_describe",
     "tdse_batch_last_error", "tdse_batch_destroy", "tdse_set_residual_check", "tdse_residual_report",
     "tdse_save", "tdse_load",
 ]
@@ -91,6 +91,7 @@ def load(path: str = _LIB_PATH) -> ctypes.CDLL:
         "tdse_free_choose_H_prec": ([cd, cd, cd, ip, ip, dp], ip),
         "tdse_batch_create": ([ctypes.POINTER(vp), ip, ctypes.POINTER(vp)], ip),
         "tdse_batch_tune": ([vp, ip, vp], ip),
+        "tdse_batch_set_mode": ([vp, ip], ip),
         "tdse_batch_step": ([vp, ip, vp], ip),
         "tdse_batch_describe": ([vp, ctypes.c_char_p, ctypes.c_size_t], ip),
         "tdse_batch_last_error": ([vp], ctypes.c_char_p),

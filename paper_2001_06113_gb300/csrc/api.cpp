@@ -986,6 +986,14 @@ struct tdse_batch {
     size_t smem = 0;
     std::vector<MultiItem> items;
     MultiArgs1D args{};             // reused launch argument block (22 KB)
+    // Adams phase: 0 = one fused persistent launch per step for all members;
+    // 1 = each member's own single-size kernel on its own stream (forked from
+    // and joined to the caller's stream; parallel branches of the graph)
+    int mode = 0;
+    float fused_ms = 0, stream_ms = 0;   // tuner's per-step times of the two modes
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
     struct Graph {
         int from, n;
         bool inited;
@@ -1069,6 +1077,23 @@ static tdse_status batch_adams(tdse_batch* b, int n, int grid, cudaStream_t s) {
     return TDSE_OK;
 }
 
+// Adams steps n0+1 .. n0+k of every member, each member on its own stream.
+static tdse_status batch_adams_streams(tdse_batch* b, int n0, int k, cudaStream_t s) {
+    cudaError_t e = cudaEventRecord(b->fork, s);
+    for (size_t g = 0; g < b->m.size() && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(b->streams[g], b->fork, 0);
+    for (int n = n0 + 1; n <= n0 + k && e == cudaSuccess; ++n)
+        for (size_t g = 0; g < b->m.size() && e == cudaSuccess; ++g)
+            e = run(b->m[g], adams_args(b->m[g], n), step_combo(b->m[g]), b->streams[g]);
+    for (size_t g = 0; g < b->m.size(); ++g) {   // always join, so that a capture can end
+        cudaError_t j = cudaEventRecord(b->join[g], b->streams[g]);
+        if (j == cudaSuccess) j = cudaStreamWaitEvent(s, b->join[g], 0);
+        if (e == cudaSuccess) e = j;
+    }
+    if (e != cudaSuccess) return b->fail(TDSE_ECUDA, std::string("member streams: ") + cudaGetErrorString(e));
+    for (tdse_ctx* c : b->m) c->step = n0 + k;
+    return TDSE_OK;
+}
+
 // The launch sequence of nsteps steps (no capture logic).
 static tdse_status batch_run(tdse_batch* b, int nsteps, cudaStream_t s) {
     for (tdse_ctx* c : b->m)
@@ -1093,6 +1118,12 @@ static tdse_status batch_run(tdse_batch* b, int nsteps, cudaStream_t s) {
                 tdse_status st = member_status(b, c, enter_interaction(c, c->step, s));
                 if (st != TDSE_OK) return st;
             }
+        if (b->mode == 1) {
+            tdse_status st = batch_adams_streams(b, n - 1, nsteps - k, s);
+            if (st != TDSE_OK) return st;
+            k = nsteps;
+            continue;
+        }
         tdse_status st = batch_adams(b, n, b->grid, s);
         if (st != TDSE_OK) return st;
         ++k;
@@ -1152,6 +1183,16 @@ tdse_status tdse_batch_create(tdse_ctx* const* members, int count, tdse_batch** 
         return TDSE_ECUDA;
     }
     b->grid = default_grid(b);
+    b->streams.assign(b->m.size(), nullptr);
+    b->join.assign(b->m.size(), nullptr);
+    bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (size_t g = 0; g < b->m.size() && ok; ++g)
+        ok = cudaStreamCreateWithFlags(&b->streams[g], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->join[g], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        tdse_batch_destroy(b);
+        return TDSE_ECUDA;
+    }
     *out = b;
     return TDSE_OK;
 }
@@ -1309,6 +1350,30 @@ tdse_status tdse_batch_tune(tdse_batch* b, int trial_steps, void* stream) {
         }
         b->grid = best_grid;
     }
+    // the members' own kernels on parallel streams against the best fused launch
+    b->mode = 0;
+    if (st == TDSE_OK && b->m.size() >= 1) {
+        auto timed_streams = [&](float& ms) -> tdse_status {
+            tdse_status r = batch_adams_streams(b, n - 1, 1, s);
+            for (tdse_ctx* c : b->m) c->step = n - 1;
+            if (r != TDSE_OK) return r;
+            cudaEventRecord(e0, s);
+            for (int i = 0; i < trial_steps && r == TDSE_OK; ++i) {
+                r = batch_adams_streams(b, n - 1, 1, s);
+                for (tdse_ctx* c : b->m) c->step = n - 1;
+            }
+            if (r != TDSE_OK) return r;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return b->fail(TDSE_ECUDA, "event sync");
+            cudaEventElapsedTime(&ms, e0, e1);
+            return TDSE_OK;
+        };
+        float ms = 0;
+        st = timed_streams(ms);
+        b->stream_ms = ms / trial_steps;
+        b->fused_ms = best / trial_steps;
+        if (st == TDSE_OK && ms < best) b->mode = 1;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != TDSE_OK) return st;
@@ -1327,7 +1392,9 @@ tdse_status tdse_batch_describe(const tdse_batch* b, char* buf, size_t len) {
     std::string js = "{\"grid\": " + std::to_string(b->grid) + ", \"sms\": " + std::to_string(b->sms) +
                      ", \"items\": " + std::to_string(b->items.size()) + ", \"smem\": " + std::to_string(b->smem) +
                      ", \"graphs\": " + std::to_string(b->graphs.size()) + ", \"tuned\": " +
-                     (b->tuned ? "true" : "false") + ", \"members\": [";
+                     (b->tuned ? "true" : "false") + ", \"mode\": \"" + (b->mode ? "streams" : "fused") +
+                     "\", \"fused_ms\": " + std::to_string(b->fused_ms) + ", \"streams_ms\": " +
+                     std::to_string(b->stream_ms) + ", \"members\": [";
     for (size_t g = 0; g < b->m.size(); ++g) {
         const int t = multi_variant_t(b->var[g]);
         js += std::string(g ? ", " : "") + "{\"n\": " + std::to_string(b->m[g]->n0) + ", \"batch\": " +
@@ -1340,11 +1407,23 @@ tdse_status tdse_batch_describe(const tdse_batch* b, char* buf, size_t len) {
     return TDSE_OK;
 }
 
+tdse_status tdse_batch_set_mode(tdse_batch* b, int mode) {
+    if (!b || (mode != TDSE_BATCH_FUSED && mode != TDSE_BATCH_STREAMS)) return TDSE_EINVAL;
+    if (mode != b->mode) drop_graphs(b);
+    b->mode = mode;
+    return TDSE_OK;
+}
+
 const char* tdse_batch_last_error(const tdse_batch* b) { return b ? b->err.c_str() : "null batch"; }
 
 void tdse_batch_destroy(tdse_batch* b) {
     if (!b) return;
     drop_graphs(b);
+    for (cudaStream_t st : b->streams)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->join)
+        if (ev) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
 }
 

@@ -98,7 +98,7 @@ def test_batch_graph_replay_and_tuning_keep_results():
         assert np.array_equal(pr.read_u(), u)
     batch.tune(3)
     shape = batch.describe()
-    assert shape["tuned"] and shape["grid"] >= 1
+    assert shape["tuned"] and shape["grid"] >= 1 and shape["mode"] in ("fused", "streams")
     for pr, insts in zip(probs, data.values()):
         reset(pr, insts)
     batch.step(15)
@@ -181,3 +181,27 @@ def test_mixed_16384_against_fp64_8192():
     load(ref, [it8])
     ref.step(NSTEPS)
     assert rel_l2(u16.read_u(0)[::2], ref.read_u(0)) < 2e-6
+
+
+@pytest.mark.parametrize("mode", ["fused", "streams"])
+def test_batch_modes_give_the_same_bits(mode):
+    """Both execution modes of the Adams phase (one fused launch per step;
+    each member's own kernel on its own stream, parallel graph branches)
+    give the bits of the members run alone."""
+    import torch
+    from paper_2001_06113_gb300 import Batch
+    data = members_data([(512, 6), (4096, 2), (16384, 1)], seed=9)
+    stream = torch.cuda.Stream()
+    probs = [make_problem(insts, stream) for insts in data.values()]
+    batch = Batch(probs, stream=stream)
+    batch.set_mode(mode)
+    assert batch.describe()["mode"] == mode
+    batch.step(NSTEPS - 5)
+    stream.synchronize()
+    for pr, insts in zip(probs, data.values()):
+        ub = pr.read_u()
+        for b, it in enumerate(insts):
+            solo = make_problem([it])
+            solo.step(NSTEPS - 5)
+            assert np.array_equal(solo.read_u(0), ub[b]), (mode, it.shape, b)
+            solo.close()
