@@ -1147,6 +1147,27 @@ def run_example1(args, ws, rank, local):
                 B=B, shape=shape, errs=errs, err_dt=err_dt, rows=int(times_v.size))
 
 
+def example1_profile_run(args):
+    """Small fixed launch sequence for ncu: the three speeds' Problems one
+    after the other, each init + start-up + K Adams steps (single-size kernels)."""
+    import torch
+    from paper_2001_06113_gb300 import Problem
+    B = args.batch if args.batch > 0 else EX_B
+    for c in EX_SPEEDS:
+        base, u0 = synth.example1_sweep(B, c, M=EX_M, nsteps=EX_NSTEPS, T=EX_T)
+        pr = Problem((EX_M,), base.dt, EX_NSTEPS, batch=B, precision="mixed", potential="shared_table")
+        pr.set_potential_fn(base.V_at)
+        for b in range(B):
+            pr.set_initial(u0[b], instance=b)
+        pr.step(STARTUP + args.profile_adams)
+        torch.cuda.synchronize()
+        pr.check_finite()
+        pr.close()
+    print(json.dumps({"profile_adams": args.profile_adams, "batch_per_speed": B, "workload": "example1",
+                      "k_periodic1d_launches_before_adams": 1 + STARTUP * 16}))
+    return 0
+
+
 def main_example1(args, ws, rank, local):
     import torch
     if args.impl == "reference":
@@ -1167,6 +1188,8 @@ def main_example1(args, ws, rank, local):
                           "e2e": {"value": value, "unit": "point-steps/s", "h2d_bytes_per_step": 0,
                                   "d2h_bytes_per_step": 0}}))
         return 0
+    if args.profile_adams:
+        return example1_profile_run(args)
     if ws > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     res = run_example1(args, ws, rank, local)

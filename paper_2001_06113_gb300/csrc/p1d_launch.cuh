@@ -1,12 +1,29 @@
 // One-CTA-per-instance 1D step kernel and its launch (templates shared by
 // the FP64 and FP32 translation units).
 #pragma once
+#include <type_traits>
+
 #include "step1d.cuh"
 
 namespace tdse {
 
+// Resident warps per SM the FP32 kernels of n <= 2048 are sized for (64
+// registers; the FP64 kernels and larger n keep the compiler's choice).  Step
+// times at 3M points, 16 -> 32 warps: n = 256 0.113 -> 0.101 ms, 512 0.117 ->
+// 0.105, 1024 0.131 -> 0.116, 2048 0.142 -> 0.124 (a few hundred bytes of
+// spills cost less than the latency the extra warps hide).
+#ifndef P1D_MINW32
+#define P1D_MINW32 32
+#endif
+template <class C, int T>
+constexpr int p1d_min_blocks() {
+    if (!std::is_same<C, float2>::value || T > 256) return 1;
+    const int b = P1D_MINW32 * 32 / T;
+    return b < 1 ? 1 : (b > 32 ? 32 : b);
+}
+
 template <class C, class RT, int N>
-__global__ void __launch_bounds__(threads_1d(N)) k_periodic1d(const KArgs a) {
+__global__ void __launch_bounds__(threads_1d(N), p1d_min_blocks<C, threads_1d(N)>()) k_periodic1d(const KArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     step1d<C, RT, N, threads_1d(N)>(a, blockIdx.x, threadIdx.x, CtaSync{}, reinterpret_cast<C*>(smem_raw));
 }
