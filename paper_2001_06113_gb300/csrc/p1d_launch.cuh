@@ -15,15 +15,23 @@ namespace tdse {
 #ifndef P1D_MINW32
 #define P1D_MINW32 32
 #endif
-template <class C, int T>
+// 512-thread FP32 kernels (n = 4096, 8192): two resident CTAs per SM (64
+// registers, ~200-280 bytes spilled): 0.163 -> 0.138 ms (4096) and 0.180 ->
+// 0.157 ms (8192) per step at 3M points.  n = 16384 holds 128 KB of shared
+// memory, one CTA per SM either way.
+#ifndef P1D_MINB512
+#define P1D_MINB512 2
+#endif
+template <class C, int N, int T>
 constexpr int p1d_min_blocks() {
-    if (!std::is_same<C, float2>::value || T > 256) return 1;
+    if (!std::is_same<C, float2>::value || N > 8192) return 1;
+    if (T > 256) return P1D_MINB512;
     const int b = P1D_MINW32 * 32 / T;
     return b < 1 ? 1 : (b > 32 ? 32 : b);
 }
 
 template <class C, class RT, int N>
-__global__ void __launch_bounds__(threads_1d(N), p1d_min_blocks<C, threads_1d(N)>()) k_periodic1d(const KArgs a) {
+__global__ void __launch_bounds__(threads_1d(N), p1d_min_blocks<C, N, threads_1d(N)>()) k_periodic1d(const KArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     step1d<C, RT, N, threads_1d(N)>(a, blockIdx.x, threadIdx.x, CtaSync{}, reinterpret_cast<C*>(smem_raw));
 }

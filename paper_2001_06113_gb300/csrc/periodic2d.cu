@@ -38,6 +38,14 @@ constexpr int T2D = 256;
 #ifndef TDSE_MINB2D
 #define TDSE_MINB2D 4          // resident CTAs per SM the register budget is sized for
 #endif
+// FP32 row pass (less shared memory per CTA): 5 or 6 CTAs per SM (48 / 40
+// registers, 330 / 940 bytes spilled) measured slower than 4 (0.526 / 0.592
+// against 0.519 ms per 64 x 512^2 step).
+#ifndef TDSE_MINB2D_ROW
+#define TDSE_MINB2D_ROW TDSE_MINB2D
+#endif
+template <class C>
+constexpr int row_min_blocks() { return std::is_same<C, float2>::value ? TDSE_MINB2D_ROW : TDSE_MINB2D; }
 
 // 16-byte asynchronous global -> shared copies (no registers held while in flight)
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
@@ -172,7 +180,7 @@ __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_begin(const KArgs a) {
 
 // ------------------------------------------------------------------ row_mid
 template <class C, int N1>
-__global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_row_mid(const KArgs a) {
+__global__ void __launch_bounds__(T2D, row_min_blocks<C>()) k_row_mid(const KArgs a) {
     constexpr int L = LANES2D;
     constexpr int LS = L + 1;
     using FI = CtaFft<C, N1, L, LS, T2D, true>;
