@@ -186,7 +186,10 @@ tdse_status tdse_set_vector_potential(tdse_ctx* ctx, int instance, tdse_field_fn
                                       void* user, void* stream);
 
 /* Built-in pulse A(t) = A0 sin^2(pi t / T_pulse) sin(omega t) * direction
- * (direction: dim values).  Same integration as tdse_set_vector_potential. */
+ * (direction: dim values).  phi(t) = int_0^t A (eq. phi) is evaluated in
+ * closed form on the device, A0 / 2 [F(omega) - (F(omega + W) + F(omega - W)) / 2]
+ * with W = 2 pi / T_pulse and F(a) = 2 sin^2(a t / 2) / a (0 for a = 0), then
+ * the phase tables as for tdse_set_vector_potential; asynchronous on `stream`. */
 tdse_status tdse_set_pulse(tdse_ctx* ctx, int instance, double A0, double omega,
                            double T_pulse, const double* direction, void* stream);
 

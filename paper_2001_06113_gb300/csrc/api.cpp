@@ -69,18 +69,6 @@ bool adams_weights(int n, double* mu) {
     return true;
 }
 
-struct Pulse {
-    double A0, omega, Tp, dir[2];
-};
-
-void pulse_fn(double t, double* A, void* user) {
-    const Pulse* p = static_cast<const Pulse*>(user);
-    const double s = std::sin(M_PI * t / p->Tp);
-    const double amp = p->A0 * s * s * std::sin(p->omega * t);
-    A[0] = amp * p->dir[0];
-    A[1] = amp * p->dir[1];
-}
-
 }  // namespace
 
 // q-point Gauss-Legendre nodes/weights on [-1,1] by Newton on P_q (long double).
@@ -549,8 +537,19 @@ tdse_status tdse_set_vector_potential(tdse_ctx* c, int instance, tdse_field_fn A
 tdse_status tdse_set_pulse(tdse_ctx* c, int instance, double A0, double omega, double Tp, const double* dir,
                            void* stream) {
     if (!c || !dir || !(Tp > 0.0) || !std::isfinite(A0) || !std::isfinite(omega)) return TDSE_EINVAL;
-    Pulse p{A0, omega, Tp, {dir[0], c->d == 2 ? dir[1] : 0.0}};
-    return set_field(c, instance, pulse_fn, &p, stream);
+    if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
+    int lo, hi;
+    if (!instance_range(c, instance, lo, hi)) return c->fail(TDSE_EINVAL, "instance out of range");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // phi in closed form on the device (no host pass over the fine time grid)
+    const double d2[2] = {dir[0], c->d == 2 ? dir[1] : 0.0};
+    for (int b = lo; b < hi; ++b) {
+        TDSE_CK(c, launch_pulse_phi(c->P<double>(c->off.phi) + (size_t)b * c->d * c->ntf, c->ntf, c->d,
+                                    c->cfg.dt / SUB, A0, omega, Tp, d2, s));
+        tdse_status st = build_phase_tables(c, b, s);
+        if (st != TDSE_OK) return st;
+    }
+    return TDSE_OK;
 }
 
 tdse_status tdse_set_initial(tdse_ctx* c, int instance, const double* u0, int where, void* stream) {

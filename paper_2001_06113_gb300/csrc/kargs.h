@@ -154,6 +154,9 @@ cudaError_t launch_k1d(float2* klo, float2* khi, int nhi, int n, double dt, cuda
 cudaError_t launch_a1d(float2* a1d, const double* phi, int ntf, int nsteps, int n, int nh, int nl,
                        cudaStream_t s);
 cudaError_t launch_split_float(float2* hilo, const double* src, size_t n, cudaStream_t s);
+// phi(m dt/8), m = 0..ntf-1, of the built-in pulse in closed form into phi[d][ntf]
+cudaError_t launch_pulse_phi(double* phi, int ntf, int d, double hs, double A0, double omega, double Tp,
+                             const double* dir, cudaStream_t s);
 // state <- sum_c coef[c] * chain[c] (chains laid out [L][n]); ff = state is double-float
 cudaError_t launch_combine(void* state, const void* chains, size_t chain_stride, int L, const double* coef,
                            size_t n, bool ff, cudaStream_t s);

@@ -256,6 +256,35 @@ cudaError_t launch_a1d(float2* a1d, const double* phi, int ntf, int nsteps, int 
     return cudaGetLastError();
 }
 
+// phi(t) = int_0^t A for the built-in pulse A(t) = A0 sin^2(pi t / Tp)
+// sin(omega t) dir (eq. phi), in closed form: with sin^2(x) = (1 - cos 2x) / 2
+// and Omega = 2 pi / Tp the integrand is (A0 / 2)(sin(omega s) - (sin((omega +
+// Omega) s) + sin((omega - Omega) s)) / 2), and int_0^t sin(a s) ds =
+// 2 sin^2(a t / 2) / a (0 for a = 0; no cancellation for small a).
+__device__ __forceinline__ double int_sin(double a, double t) {
+    if (a == 0.0) return 0.0;
+    const double s = sin(0.5 * a * t);
+    return 2.0 * s * s / a;
+}
+
+__global__ void k_pulse_phi(double* phi, int ntf, int d, double hs, double A0, double omega, double Om,
+                            double dir0, double dir1) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < ntf; m += gridDim.x * blockDim.x) {
+        const double t = (double)m * hs;
+        const double v = 0.5 * A0 * (int_sin(omega, t) - 0.5 * (int_sin(omega + Om, t) + int_sin(omega - Om, t)));
+        phi[m] = v * dir0;
+        if (d == 2) phi[(size_t)ntf + m] = v * dir1;
+    }
+}
+
+cudaError_t launch_pulse_phi(double* phi, int ntf, int d, double hs, double A0, double omega, double Tp,
+                             const double* dir, cudaStream_t s) {
+    const double Om = 2.0 * 3.14159265358979323846 / Tp;
+    k_pulse_phi<<<grid_for((size_t)ntf, 256), 256, 0, s>>>(phi, ntf, d, hs, A0, omega, Om, dir[0],
+                                                            d == 2 ? dir[1] : 0.0);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_split_float(float2* hilo, const double* src, size_t n, cudaStream_t s) {
     k_split_float<<<grid_for(n, 256), 256, 0, s>>>(hilo, src, n);
     return cudaGetLastError();

@@ -244,6 +244,30 @@ def test_device_pointers_and_callback_field():
     assert err <= FP64_TOL, err
 
 
+@pytest.mark.parametrize("shape", [(128,), (32, 32)])
+def test_builtin_pulse_equals_callback(shape):
+    """The built-in pulse (phi in closed form on the device) and the same A(t)
+    as a callback (8-point Gauss-Legendre per dt/8 on the host) agree to
+    rounding: both are phi to ~1e-16."""
+    from paper_2001_06113_gb300 import Problem
+    d = len(shape)
+    pulse = synth.Pulse(30.0, 150.0, 0.05, (1.0, -0.7)[:d])
+    inst = synth.random_periodic(shape, 12, 1e-3, 40, pulse=pulse)
+    out = []
+    for builtin in (True, False):
+        p = Problem(inst.shape, inst.dt, inst.nsteps)
+        p.set_potential(inst.V0)
+        if builtin:
+            p.set_pulse(pulse.A0, pulse.omega, pulse.T_pulse, pulse.direction)
+        else:
+            p.set_vector_potential(lambda t: pulse.A(t))
+        p.set_initial(inst.u0)
+        p.step(40)
+        out.append(p.read_u(0))
+        p.close()
+    assert rel_l2(out[0], out[1]) < 1e-13
+
+
 def test_mixed_2d_single_steps_equal_fused_sequence():
     """Mixed 2D: k calls of step(1) (separate end and begin column passes)
     and one step(k) (fused column passes with staged history reads) give the
