@@ -40,13 +40,15 @@ namespace tdse {
 namespace fs {
 
 // Resident CTAs per SM the register allocation is sized for: the FP64
-// kernels are bound by the FP64 pipe at one or two CTAs; the FP32 ones wait on
-// memory latency and need more warps in flight (4 CTAs: 64 registers, a few
-// words spilled; 0.41 ms against 0.45 ms per 256^2 step at 2 or 3 CTAs).
+// kernels keep the FP64 pipe busy at two CTAs (left to itself the compiler
+// takes 152 registers for the row pass: one CTA per SM, 2.46 against 2.26 ms
+// per 256^2 step); the FP32 ones wait on memory latency and need more warps in
+// flight (4 CTAs: 64 registers, a few words spilled; 0.41 ms against 0.45 ms
+// per 256^2 step at 2 or 3 CTAs).
 #ifndef FS_MINB32
 #define FS_MINB32 4
 #endif
-template <class C> struct MinBlocks { static constexpr int value = 1; };
+template <class C> struct MinBlocks { static constexpr int value = 2; };   // FP64: 128 registers, 2 CTAs/SM
 template <> struct MinBlocks<float2> { static constexpr int value = FS_MINB32; };
 
 __device__ __forceinline__ double2 zero2() { return make_double2(0.0, 0.0); }
