@@ -319,6 +319,24 @@ def moving_well_1d(c: float = 30.0, M: int = 256, nsteps: int = 3200, T: float =
                     name=f"moving_well_1d_c{c:g}_M{M}", Vt=Vt)
 
 
+def free_moving_well(M: int = 256, V0: float = 3000.0, beta: float = 0.06, x0: float = -0.1, c: float = 1.0,
+                     T: float = 0.02, nsteps: int = 800, K: int = 320) -> Instance:
+    """Free space on [-1,1]: a deep Gaussian well V(x, t) = -V0 exp(-(x - x0 -
+    c t)^2 / (2 beta^2)) moving at speed c, A = 0; u0 = its ground state (the
+    Fourier-Galerkin eigensolve of `well_ground_state_coeffs`, whose [-pi, pi]
+    box holds the state's exponentially small tails) boosted by e^{i c x / 2},
+    the state the well carries along (below 1e-15 at x = +-1 for the defaults)."""
+    x = free_grid(M)
+    E, k, coef = well_ground_state_coeffs(V0, beta, K)
+    u0 = (np.exp(1j * np.outer(x - x0, k)) @ coef) * np.exp(0.5j * c * x)
+
+    def Vt(t, _x=x):
+        return -V0 * np.exp(-(_x - x0 - c * float(t)) ** 2 / (2.0 * beta * beta))
+
+    return Instance(FREE, (M,), u0.astype(np.complex128), Vt(0.0), _const_one, None, T / nsteps, nsteps,
+                    name=f"free_moving_well_M{M}", Vt=Vt)
+
+
 def example1_sweep(count: int, c: float, seed: int = 11, M: int = 512, nsteps: int = 3200,
                    T: float = 2.0 * math.pi / 15.0, V0: float = 300.0, beta: float = 0.2):
     """A sweep over initial states for one well speed of Example 1: the well

@@ -188,6 +188,28 @@ def test_table_validation():
 
 
 # ------------------------------------------------------------ free space
+def test_free_galilean_closed_form_on_gpu():
+    """The deep well moving in free space carries its boosted ground state
+    (closed form, any c): the GPU contour scheme converges at 8th order to it
+    as the oracle does (oracle: 5.6e-7, 2.4e-9 at 400, 800 steps)."""
+    from paper_2001_06113_gb300 import Problem
+    M, V0, beta, x0, c, T = 256, 3000.0, 0.06, -0.1, 1.0, 0.02
+    E, k, coef = synth.well_ground_state_coeffs(V0, beta, 320)
+    x = synth.free_grid(M)
+    ref = (np.exp(1j * np.outer(x - x0 - c * T, k)) @ coef) * np.exp(-1j * E * T) * np.exp(1j * (c * x / 2 - c * c * T / 4))
+    H = gamma.choose_H(1e-12, V0 * math.sqrt(beta * math.sqrt(math.pi)), 0.0, 1)
+    errs = []
+    for n in (400, 800):
+        inst = synth.free_moving_well(M=M, V0=V0, beta=beta, x0=x0, c=c, T=T, nsteps=n)
+        pr = Problem((M,), inst.dt, n, bc="free", nu=(2048,), H=H, gauss_q=16, n_r=2, potential="table")
+        pr.set_potential_fn(inst.V_at)
+        pr.set_initial(inst.u0)
+        pr.step(n)
+        errs.append(rel_l2(pr.read_u(0), ref))
+    assert errs[1] < 1e-8 and errs[0] / errs[1] > 100.0, errs
+
+
+
 @pytest.mark.parametrize("shape,nu,precision,tol", [((64,), (512,), "fp64", FP64_TOL),
                                                      ((32, 32), (256, 256), "fp64", FP64_TOL),
                                                      ((64,), (512,), "mixed", MIXED_TOL)])

@@ -183,3 +183,40 @@ def test_planted_mistakes_fail(monkeypatch, mistake):
         except AssertionError:
             failed = True
     assert failed
+
+
+# ------------------------------------------------ general V(x, t): moving well
+def _free_galilean_errors(steps, M=256, nu=2048, V0=3000.0, beta=0.06, x0=-0.1, c=1.0, T=0.02):
+    """Galilean invariance in free space: the ground state w0 of a static well
+    carried by the well moving at speed c is u(x, t) = w0(x - x0 - c t)
+    e^{-i E t} e^{i (c x / 2 - c^2 t / 4)} (any c).  A closed form for a
+    non-separable V(x, t) on the contour scheme."""
+    from oracle.periodic import rel_l2
+    E, k, coef = synth.well_ground_state_coeffs(V0, beta, 320)
+    x = synth.free_grid(M)
+    ref = (np.exp(1j * np.outer(x - x0 - c * T, k)) @ coef) * np.exp(-1j * E * T) * np.exp(1j * (c * x / 2 - c * c * T / 4))
+    vnorm = V0 * math.sqrt(beta * math.sqrt(math.pi))
+    rule = gamma.GammaRule.for_nu(M, nu, gamma.choose_H(1e-12, vnorm, 0.0, 1), q=16, n_r=2)
+    out = []
+    for n in steps:
+        inst = synth.free_moving_well(M=M, V0=V0, beta=beta, x0=x0, c=c, T=T, nsteps=n)
+        orc = freespace.FreeSpaceOracle([rule], inst.dt, inst.Vt, None, fields.phi_callable(None, 1))
+        out.append(rel_l2(orc.solve(inst.u0, n), ref))
+    return out
+
+
+def test_free_moving_well_galilean_closed_form():
+    """8th order in dt (measured 5.6e-7, 2.4e-9 at 400, 800 steps)."""
+    e400, e800 = _free_galilean_errors((400, 800))
+    assert e800 < 1e-8 and e400 / e800 > 100.0
+
+
+def test_free_moving_well_pin_catches_lagged_potential(monkeypatch):
+    """Planted mistake: the implicit solve takes V one step late."""
+    orig = freespace.FreeSpaceOracle.V
+
+    def lagged(self, t):
+        return orig(self, t - self.dt) if t > 8 * self.dt else orig(self, t)
+    monkeypatch.setattr(freespace.FreeSpaceOracle, "V", lagged)
+    e400, e800 = _free_galilean_errors((400, 800))
+    assert not (e800 < 1e-8 and e400 / e800 > 100.0)
