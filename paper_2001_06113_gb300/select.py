@@ -30,7 +30,7 @@ from typing import Dict, List, Optional, Sequence
 
 import numpy as np
 
-from . import Problem, free_choose_H
+from . import Problem, TdseError, free_choose_H
 
 EPS_M32 = 2.0 ** -23
 
@@ -68,7 +68,7 @@ def candidates(inst, eps: float, R_values: Sequence[int] = (4, 8, 16), allow_mix
     for prec in (("mixed", "fp64") if allow_mixed else ("fp64",)):
         try:
             H = free_choose_H(eps, vnorm, phimax, inst.dim, precision=prec)
-        except Exception:          # eps below this precision's floor: H would not be positive
+        except TdseError:          # eps below this precision's floor: H would not be positive
             continue
         for R in R_values:
             nu = [R * n for n in inst.shape]
