@@ -199,7 +199,7 @@ def run_gpu(args, ws, rank, local):
     B = len(insts)
     prob = Problem((M, M), DT, NSTEPS, order=ORDER, batch=B, precision=args.precision, stream=stream)
     pinned_V = [torch.from_numpy(it.V0).pin_memory() for it in insts]
-    pinned_u = [torch.from_numpy(it.u0).pin_memory() for it in insts]
+    pinned_u = torch.from_numpy(np.stack([it.u0 for it in insts])).pin_memory()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def load_inputs():
@@ -207,7 +207,7 @@ def run_gpu(args, ws, rank, local):
             prob.set_potential(pinned_V[b], None, instance=b)
             p = it.pulse
             prob.set_pulse(p.A0, p.omega, p.T_pulse, p.direction, instance=b)
-            prob.set_initial(pinned_u[b], instance=b)
+        prob.set_initial_batch(pinned_u)
 
     def barrier():
         if ws > 1:
@@ -216,9 +216,7 @@ def run_gpu(args, ws, rank, local):
     load_inputs()
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            prob.set_initial(pinned_u[0], instance=0)
-            for b in range(1, B):
-                prob.set_initial(pinned_u[b], instance=b)
+            prob.set_initial_batch(pinned_u)
             prob.step(NSTEPS)
         stream.synchronize()
 
@@ -230,8 +228,7 @@ def run_gpu(args, ws, rank, local):
         for _ in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.zero_()
-                for b in range(B):
-                    prob.set_initial(pinned_u[b], instance=b)   # resets the run (H2D outside the events)
+                prob.set_initial_batch(pinned_u)   # resets the run (H2D outside the events)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -250,8 +247,7 @@ def run_gpu(args, ws, rank, local):
     #      (2D: per step one row pass + one fused column pass)
     GROUP, NGROUPS = 10, 20
     with torch.cuda.stream(stream):
-        for b in range(B):
-            prob.set_initial(pinned_u[b], instance=b)
+        prob.set_initial_batch(pinned_u)
         prob.step(STARTUP + 8)
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(NGROUPS + 1)]
         evs[0].record(stream)
@@ -287,9 +283,7 @@ def run_gpu(args, ws, rank, local):
         ref.set_initial(it.u0)
         with torch.cuda.stream(stream):
             ref.step(NSTEPS)
-            prob.set_initial(pinned_u[0], instance=0)
-            for b in range(1, B):
-                prob.set_initial(pinned_u[b], instance=b)
+            prob.set_initial_batch(pinned_u)
             prob.step(NSTEPS)
         u_ref = ref.read_u(0)
         u_mix = prob.read_u(0)
@@ -417,7 +411,7 @@ def run_free(args, ws, rank, local):
     prob = Problem((FS_M, FS_M), FS_DT, FS_NSTEPS, order=ORDER, batch=B, precision=prec, stream=stream, bc="free",
                    nu=(FS_NU, FS_NU), H=H, gauss_q=FS_Q, n_r=FS_NR)
     pinned_V = [torch.from_numpy(it.V0).pin_memory() for it in insts]
-    pinned_u = [torch.from_numpy(it.u0).pin_memory() for it in insts]
+    pinned_u = torch.from_numpy(np.stack([it.u0 for it in insts])).pin_memory()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def load_inputs():
@@ -425,15 +419,14 @@ def run_free(args, ws, rank, local):
             prob.set_potential(pinned_V[b], None, instance=b)
             p = it.pulse
             prob.set_pulse(p.A0, p.omega, p.T_pulse, p.direction, instance=b)
-            prob.set_initial(pinned_u[b], instance=b)
+        prob.set_initial_batch(pinned_u)
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
 
     def reset():
-        for b in range(B):
-            prob.set_initial(pinned_u[b], instance=b)
+        prob.set_initial_batch(pinned_u)
 
     load_inputs()
     with torch.cuda.stream(stream):
@@ -736,8 +729,8 @@ def run_batch1d(args, ws, rank, local):
         groups.setdefault(it.shape[0], []).append(it)
     sizes = sorted(groups)
     probs = [Problem((N,), B1_DT, B1_NSTEPS, batch=len(groups[N]), precision="mixed", stream=stream) for N in sizes]
-    pinned = {N: [(torch.from_numpy(it.V0).pin_memory(), torch.from_numpy(it.u0).pin_memory()) for it in groups[N]]
-              for N in sizes}
+    pinned = {N: [(torch.from_numpy(it.V0).pin_memory(), None) for it in groups[N]] for N in sizes}
+    pinned_u = {N: torch.from_numpy(np.stack([it.u0 for it in groups[N]])).pin_memory() for N in sizes}
 
     def load_inputs():
         for N, pr in zip(sizes, probs):
@@ -745,12 +738,11 @@ def run_batch1d(args, ws, rank, local):
                 pr.set_potential(pinned[N][b][0], None, instance=b)
                 p = it.pulse
                 pr.set_pulse(p.A0, p.omega, p.T_pulse, p.direction, instance=b)
-                pr.set_initial(pinned[N][b][1], instance=b)
+            pr.set_initial_batch(pinned_u[N])
 
     def reset():
         for N, pr in zip(sizes, probs):
-            for b in range(len(groups[N])):
-                pr.set_initial(pinned[N][b][1], instance=b)
+            pr.set_initial_batch(pinned_u[N])
 
     def barrier():
         if ws > 1:
@@ -1033,8 +1025,7 @@ def run_example1(args, ws, rank, local):
 
     def reset():
         for pr, u0 in zip(probs, u0s):
-            for b in range(B):
-                pr.set_initial(u0[b], instance=b)
+            pr.set_initial_batch(u0)
 
     def load_inputs():
         for pr, tab in zip(probs, tables):

@@ -199,6 +199,12 @@ tdse_status tdse_set_pulse(tdse_ctx* ctx, int instance, double A0, double omega,
 tdse_status tdse_set_initial(tdse_ctx* ctx, int instance, const double* u0, int where,
                              void* stream);
 
+/* Initial wavefunctions of every instance in one copy: u0 holds batch
+ * consecutive arrays of n0*n1 interleaved complex values (instance b at
+ * u0 + 2 b n0 n1), host or device per `where`; copied during the call.
+ * Resets the step counter as tdse_set_initial. */
+tdse_status tdse_set_initial_batch(tdse_ctx* ctx, const double* u0, int where, void* stream);
+
 /* Advance every instance by `nsteps` steps of dt (asynchronous on `stream`).
  * The first call after tdse_set_initial transforms u0 and V(0)u0; the first
  * startup_steps steps use Richardson start-up, later ones the Adams scheme.

@@ -218,6 +218,13 @@ class Problem:
         _check(self._lib.tdse_set_initial(self._ctx, instance, pu, where, _stream_handle(self._stream)), self._ctx)
         del keep
 
+    def set_initial_batch(self, u0):
+        """u0 of every instance at once: array [batch] + shape (numpy or torch,
+        host or cuda, complex128), one copy."""
+        pu, where, keep = _as_buffer(u0, np.complex128)
+        _check(self._lib.tdse_set_initial_batch(self._ctx, pu, where, _stream_handle(self._stream)), self._ctx)
+        del keep
+
     def step(self, n: int = 1):
         _check(self._lib.tdse_step(self._ctx, int(n), _stream_handle(self._stream)), self._ctx)
 

@@ -23,7 +23,7 @@ TDSE_ESTATE = -6
 # Every symbol include/tdse.h declares (checked by the CPU test suite).
 EXPORTS = [
     "tdse_create", "tdse_workspace_bytes", "tdse_bind_workspace", "tdse_set_potential",
-    "tdse_set_vector_potential", "tdse_set_pulse", "tdse_set_initial", "tdse_step", "tdse_solve_to",
+    "tdse_set_vector_potential", "tdse_set_pulse", "tdse_set_initial", "tdse_set_initial_batch", "tdse_step", "tdse_solve_to",
     "tdse_read_u", "tdse_check_finite", "tdse_step_index", "tdse_time", "tdse_adams_weights",
     "tdse_last_error", "tdse_destroy", "tdse_modes_to_grid_2d_noalloc", "tdse_read_modes", "tdse_free_rule",
     "tdse_free_choose_H", "tdse_free_choose_H_prec", "tdse_potential_times", "tdse_set_potential_table", "tdse_batch_create", "tdse_batch_tune", "tdse_batch_set_mode", "tdse_batch_step", "tdse_batch_describe",
@@ -75,6 +75,7 @@ def load(path: str = _LIB_PATH) -> ctypes.CDLL:
         "tdse_set_vector_potential": ([vp, ip, FIELD_FN, vp, vp], ip),
         "tdse_set_pulse": ([vp, ip, cd, cd, cd, dp, vp], ip),
         "tdse_set_initial": ([vp, ip, vp, ip, vp], ip),
+        "tdse_set_initial_batch": ([vp, vp, ip, vp], ip),
         "tdse_step": ([vp, ip, vp], ip),
         "tdse_solve_to": ([vp, cd, vp], ip),
         "tdse_read_u": ([vp, ip, vp, ip, vp], ip),

@@ -581,6 +581,28 @@ tdse_status tdse_set_initial(tdse_ctx* c, int instance, const double* u0, int wh
     return TDSE_OK;
 }
 
+tdse_status tdse_set_initial_batch(tdse_ctx* c, const double* u0, int where, void* stream) {
+    if (!c || !u0) return TDSE_EINVAL;
+    if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
+    if (where != TDSE_HOST && where != TDSE_DEVICE) return TDSE_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const cudaMemcpyKind kind = where == TDSE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    // the grid values of all instances are contiguous in the workspace (stride n0 n1)
+    double2* dst = c->fs ? c->P<double2>(c->F.off.u) : c->P<double2>(c->off.uhat);
+    TDSE_CK(c, cudaMemcpyAsync(dst, u0, (size_t)c->B * c->NP * 16, kind, s));
+    std::fill(c->have_u0.begin(), c->have_u0.end(), 1);
+    if (c->mixed && c->off.res_ncorr) {
+        TDSE_CK(c, cudaMemsetAsync(c->P<int>(c->off.res_ncorr), 0, (size_t)c->B * 4, s));
+        TDSE_CK(c, cudaMemsetAsync(c->P<double>(c->off.res_rho), 0, (size_t)c->B * 8, s));
+    }
+    if (where == TDSE_HOST) TDSE_CK(c, cudaStreamSynchronize(s));
+    c->step = 0;
+    c->inited = false;
+    c->ip = false;
+    c->res_checks = 0;
+    return TDSE_OK;
+}
+
 static tdse_status do_init(tdse_ctx* c, cudaStream_t s) {
     KArgs a = base_args(c);
     a.mode = MODE_INIT;

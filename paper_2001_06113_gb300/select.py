@@ -32,7 +32,6 @@ import numpy as np
 
 from . import Problem, TdseError, free_choose_H
 
-EPS_M32 = 2.0 ** -23
 
 
 @dataclasses.dataclass

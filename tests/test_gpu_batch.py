@@ -205,3 +205,28 @@ def test_batch_modes_give_the_same_bits(mode):
             solo.step(NSTEPS - 5)
             assert np.array_equal(solo.read_u(0), ub[b]), (mode, it.shape, b)
             solo.close()
+
+
+def test_set_initial_batch_equals_per_instance():
+    """One copy of all instances' u0 gives the bits of per-instance uploads
+    (periodic and free space)."""
+    from paper_2001_06113_gb300 import Problem
+    data = members_data([(512, 3)], seed=5)[512]
+    a, b = make_problem(data), make_problem(data)
+    b.set_initial_batch(np.stack([it.u0 for it in data]))
+    a.step(12)
+    b.step(12)
+    assert np.array_equal(a.read_u(), b.read_u())
+    insts = [synth.free_bump_gaussians((64,), seed=30 + i, dt=1e-3, nsteps=14) for i in range(2)]
+    out = []
+    for batched in (False, True):
+        pr = Problem((64,), 1e-3, 14, batch=2, bc="free", nu=(512,), H=2.0)
+        for i, it in enumerate(insts):
+            pr.set_potential(it.V0, instance=i)
+            if not batched:
+                pr.set_initial(it.u0, instance=i)
+        if batched:
+            pr.set_initial_batch(np.stack([it.u0 for it in insts]))
+        pr.step(10)
+        out.append(pr.read_u())
+    assert np.array_equal(out[0], out[1])
