@@ -50,6 +50,14 @@ namespace fs {
 #endif
 template <class C> struct MinBlocks { static constexpr int value = 2; };   // FP64: 128 registers, 2 CTAs/SM
 template <> struct MinBlocks<float2> { static constexpr int value = FS_MINB32; };
+// Threads per CTA: FS_T for the FP64 kernels, FS_T32 for the FP32 ones (512
+// threads at two CTAs per SM measured slower than 256 at four: 0.467 against
+// 0.409 ms per 256^2 step).
+#ifndef FS_T32
+#define FS_T32 FS_T
+#endif
+template <class C> struct FsThreads { static constexpr int value = FS_T; };
+template <> struct FsThreads<float2> { static constexpr int value = FS_T32; };
 
 __device__ __forceinline__ double2 zero2() { return make_double2(0.0, 0.0); }
 template <class C> __device__ __forceinline__ C zeroc() { return czero<C>(); }
@@ -86,8 +94,8 @@ struct FsLine {
     static constexpr int LS = 2 * R + 1;
     static constexpr int NU = M * R;
     static constexpr int EBUF = M * LS;
-    using FftF = CtaFft<C, M, L, LS, FS_T, false>;
-    using FftI = CtaFft<C, M, L, LS, FS_T, true>;
+    using FftF = CtaFft<C, M, L, LS, FsThreads<C>::value, false>;
+    using FftI = CtaFft<C, M, L, LS, FsThreads<C>::value, true>;
 
     __device__ static __forceinline__ int epos(int b, int i) { return (i / R) * LS + b * R + (i % R); }
 
@@ -96,13 +104,13 @@ struct FsLine {
     // dense results.  Ends with a barrier.
     __device__ static void forward(const C* f, C* E, C* dv, const FsAxis& ax) {
         const C* preF = T::preF(ax);
-        for (int it = threadIdx.x; it < 2 * NU; it += FS_T) {
+        for (int it = threadIdx.x; it < 2 * NU; it += FsThreads<C>::value) {
             const int b = it / NU, r = it - b * NU;
             const int j = r / R, s = r % R;
             E[j * LS + b * R + s] = cmul(f[j], __ldg(&preF[it]));
         }
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int dd = warp; dd < ax.ND; dd += FS_T / 32) {
+        for (int dd = warp; dd < ax.ND; dd += FsThreads<C>::value / 32) {
             C acc = zeroc<C>();
             const C* row = T::Fd(ax) + (size_t)dd * M;
             for (int j = lane; j < M; j += 32) acc = acc + cmul(__ldg(&row[j]), f[j]);
@@ -142,7 +150,7 @@ struct FsLine {
     // Zero the inputs NE..nu-1 of both blocks (the zero padding of eq. ssfftgen).
     __device__ static void zero_pad(C* E, int NE) {
         const int per = NU - NE;
-        for (int it = threadIdx.x; it < 2 * per; it += FS_T) {
+        for (int it = threadIdx.x; it < 2 * per; it += FsThreads<C>::value) {
             const int b = it / per, i = NE + (it - b * per);
             E[epos(b, i)] = zeroc<C>();
         }
@@ -153,7 +161,7 @@ struct FsLine {
     __device__ static void inverse(C* E, const C* dv, C* y, const FsAxis& ax) {
         __syncthreads();
         FftI::run(E, T::tw(ax), nullptr);
-        for (int j = threadIdx.x; j < M; j += FS_T) {
+        for (int j = threadIdx.x; j < M; j += FsThreads<C>::value) {
             C acc = zeroc<C>();
             const C* pj = T::postI(ax) + (size_t)j * R;
 #pragma unroll
@@ -219,7 +227,7 @@ __device__ __forceinline__ void store_fwd(const FsArgs& a, size_t idx, C F) {
 }
 
 template <class C, int M, int R>
-__global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_1d(FsArgs a, int mode) {
+__global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs_1d(FsArgs a, int mode) {
     using Ln = FsLine<C, M, R>;
     using Rl = typename cx_traits<C>::real;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -231,13 +239,13 @@ __global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_1d(FsArgs a, i
     const double vf = a.tfac[(size_t)b * a.ntf + a.tf];
     const double* V0 = a.V0 + (size_t)b * a.vstride;
     if (mode == FS_1D_FWD_ONLY) {
-        for (int j = threadIdx.x; j < M; j += FS_T) {
+        for (int j = threadIdx.x; j < M; j += FsThreads<C>::value) {
             const double2 u = a.usrc[(size_t)b * M + j];
             y[j] = cvt<C>(a.mulV ? cscale(u, vf * V0[j]) : u);
         }
         __syncthreads();
         Ln::forward(y, E, dv, ax);
-        for (int m = threadIdx.x; m < N; m += FS_T)
+        for (int m = threadIdx.x; m < N; m += FsThreads<C>::value)
             store_fwd(a, (size_t)b * a.fdst_bstride + m, Ln::fwd_value(m, E, dv, ax));
         return;
     }
@@ -248,7 +256,7 @@ __global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_1d(FsArgs a, i
     C cj[FS_MAX_HIST + 1];
 #pragma unroll
     for (int j = 0; j <= FS_MAX_HIST; ++j) cj[j] = cvt<C>(make_double2(a.mu[j], 0.0));
-    for (int m = threadIdx.x; m < N; m += FS_T) {
+    for (int m = threadIdx.x; m < N; m += FsThreads<C>::value) {
         const C S = history_sep<C>(
             a, cj, [&](int j) { return ring[(size_t)a.hist_slot[j - 1] * N + m]; },
             [&](int i) { return __ldg(&Pc[(size_t)a.interval[i] * N + m]); });
@@ -259,7 +267,7 @@ __global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_1d(FsArgs a, i
     Ln::zero_pad(E, ax.NE);
     Ln::inverse(E, dv, y, ax);
     const double hm0 = a.h * a.mu[0];
-    for (int j = threadIdx.x; j < M; j += FS_T) {
+    for (int j = threadIdx.x; j < M; j += FsThreads<C>::value) {
         const double V = vf * V0[j];
         const C u = implicit_solve(y[j], (Rl)(hm0 * V));
         a.u[(size_t)b * M + j] = cvt<double2>(u);
@@ -267,7 +275,7 @@ __global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_1d(FsArgs a, i
     }
     __syncthreads();
     Ln::forward(y, E, dv, ax);
-    for (int m = threadIdx.x; m < N; m += FS_T) {
+    for (int m = threadIdx.x; m < N; m += FsThreads<C>::value) {
         const C F = Ln::fwd_value(m, E, dv, ax);
         uh[m] = uh[m] + times_minus_i(cvt<double2>(F), hm0);
         ring[(size_t)a.out_slot * N + m] = F;
@@ -275,7 +283,7 @@ __global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_1d(FsArgs a, i
 }
 
 template <class C, int M, int R>
-__global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_row(FsArgs a, int flags) {
+__global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs_row(FsArgs a, int flags) {
     using Ln = FsLine<C, M, R>;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     C* E = reinterpret_cast<C*>(sm_raw);
@@ -289,12 +297,12 @@ __global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_row(FsArgs a, 
     C* zrow = reinterpret_cast<C*>(a.Z) + ((size_t)b * N0 + k0) * M;
     const bool end = flags & FS_ROW_END, begin = flags & FS_ROW_BEGIN;
     if (end || (flags & FS_ROW_FWD_ONLY)) {
-        for (int j = threadIdx.x; j < M; j += FS_T) f[j] = zrow[j];
+        for (int j = threadIdx.x; j < M; j += FsThreads<C>::value) f[j] = zrow[j];
         __syncthreads();
         Ln::forward(f, E, dv, ax);
         if (flags & FS_ROW_FWD_ONLY) {
             const size_t base = (size_t)b * a.fdst_bstride + (size_t)k0 * N1;
-            for (int m = threadIdx.x; m < N1; m += FS_T) store_fwd(a, base + m, Ln::fwd_value(m, E, dv, ax));
+            for (int m = threadIdx.x; m < N1; m += FsThreads<C>::value) store_fwd(a, base + m, Ln::fwd_value(m, E, dv, ax));
             return;
         }
     }
@@ -314,7 +322,7 @@ __global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_row(FsArgs a, 
     }
     const double hm0 = a.h * a.mu[0];
     C* ring = reinterpret_cast<C*>(a.ring) + (size_t)b * a.ring_slots * NPm + (size_t)k0 * N1;
-    for (int m = threadIdx.x; m < N1; m += FS_T) {
+    for (int m = threadIdx.x; m < N1; m += FsThreads<C>::value) {
         double2 uh;
         C F = zeroc<C>();
         if (end) {
@@ -342,11 +350,11 @@ __global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_row(FsArgs a, 
     if (!begin) return;
     Ln::zero_pad(E, ax.NE);
     Ln::inverse(E, dv, f, ax);
-    for (int j = threadIdx.x; j < M; j += FS_T) zrow[j] = f[j];
+    for (int j = threadIdx.x; j < M; j += FsThreads<C>::value) zrow[j] = f[j];
 }
 
 template <class C, int M, int R>
-__global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_phys(FsArgs a, int from_usrc) {
+__global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs_phys(FsArgs a, int from_usrc) {
     using Ln = FsLine<C, M, R>;
     using Rl = typename cx_traits<C>::real;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -361,11 +369,11 @@ __global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_phys(FsArgs a,
     const double vf = a.tfac[(size_t)b * a.ntf + a.tf];
     const double* V0 = a.V0 + (size_t)b * a.vstride;
     if (!from_usrc) {
-        for (int m = threadIdx.x; m < N0; m += FS_T) Ln::stage_inv(m, zcol[(size_t)m * M1], E, dv, ax);
+        for (int m = threadIdx.x; m < N0; m += FsThreads<C>::value) Ln::stage_inv(m, zcol[(size_t)m * M1], E, dv, ax);
         Ln::zero_pad(E, ax.NE);
         Ln::inverse(E, dv, y, ax);
         const double hm0 = a.h * a.mu[0];
-        for (int j0 = threadIdx.x; j0 < M; j0 += FS_T) {
+        for (int j0 = threadIdx.x; j0 < M; j0 += FsThreads<C>::value) {
             const size_t g = (size_t)j0 * M1 + j1;
             const double V = vf * V0[g];
             const C u = implicit_solve(y[j0], (Rl)(hm0 * V));
@@ -373,7 +381,7 @@ __global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_phys(FsArgs a,
             y[j0] = cscale(u, (Rl)V);
         }
     } else {
-        for (int j0 = threadIdx.x; j0 < M; j0 += FS_T) {
+        for (int j0 = threadIdx.x; j0 < M; j0 += FsThreads<C>::value) {
             const size_t g = (size_t)j0 * M1 + j1;
             const double2 u = a.usrc[(size_t)b * NX + g];
             y[j0] = cvt<C>(a.mulV ? cscale(u, vf * V0[g]) : u);
@@ -381,7 +389,7 @@ __global__ void __launch_bounds__(FS_T, MinBlocks<C>::value) k_fs_phys(FsArgs a,
     }
     __syncthreads();
     Ln::forward(y, E, dv, ax);
-    for (int m = threadIdx.x; m < N0; m += FS_T) zcol[(size_t)m * M1] = Ln::fwd_value(m, E, dv, ax);
+    for (int m = threadIdx.x; m < N0; m += FsThreads<C>::value) zcol[(size_t)m * M1] = Ln::fwd_value(m, E, dv, ax);
 }
 
 template <class C, int M, int R>
@@ -405,13 +413,13 @@ cudaError_t launch_mr(const FsArgs& a, int which, int flag, cudaStream_t s) {
     cudaError_t e;
     if (which == 0) {
         if ((e = prepare<C>(k_fs_1d<C, M, R>, sm)) != cudaSuccess) return e;
-        k_fs_1d<C, M, R><<<a.B, FS_T, sm, s>>>(a, flag);
+        k_fs_1d<C, M, R><<<a.B, FsThreads<C>::value, sm, s>>>(a, flag);
     } else if (which == 1) {
         if ((e = prepare<C>(k_fs_row<C, M, R>, sm)) != cudaSuccess) return e;
-        k_fs_row<C, M, R><<<dim3(a.ax[0].N, a.B), FS_T, sm, s>>>(a, flag);
+        k_fs_row<C, M, R><<<dim3(a.ax[0].N, a.B), FsThreads<C>::value, sm, s>>>(a, flag);
     } else {
         if ((e = prepare<C>(k_fs_phys<C, M, R>, sm)) != cudaSuccess) return e;
-        k_fs_phys<C, M, R><<<dim3(a.ax[1].M, a.B), FS_T, sm, s>>>(a, flag);
+        k_fs_phys<C, M, R><<<dim3(a.ax[1].M, a.B), FsThreads<C>::value, sm, s>>>(a, flag);
     }
     return cudaGetLastError();
 }
