@@ -152,6 +152,32 @@ def test_2d_free_particle_full_length():
     assert rel_l2(u, field(inst.t_max)) <= 1e-12
 
 
+@pytest.mark.parametrize("shape,precision,tol", [((1024, 1024), "fp64", 1e-12), ((1024, 1024), "mixed", 2e-6),
+                                                   ((8, 1024), "fp64", 1e-12), ((1024, 8), "mixed", 2e-6)])
+def test_2d_free_particle_extreme_shapes(shape, precision, tol):
+    """The largest and the most elongated 2D grids (8..1024 per dimension),
+    V = 0 with a pulse along (0.6, -0.8): the closed form
+    sum_k c_k e^{i k.x - i |k|^2 t + i k.phi(t)}."""
+    n0, n1 = shape
+    pulse = synth.Pulse(2.0, 10.0, 0.03, (0.6, -0.8))
+    rng = np.random.default_rng(4)
+    K0, K1 = min(n0 // 2 - 1, 30), min(n1 // 2 - 1, 30)
+    modes = [((int(a), int(b)), complex(rng.normal(), rng.normal()))
+             for a, b in zip(rng.integers(-K0, K0 + 1, size=10), rng.integers(-K1, K1 + 1, size=10))]
+    X, Y = np.meshgrid(synth.periodic_grid(n0), synth.periodic_grid(n1), indexing="ij")
+
+    def field(t):
+        ph = fields.phi_callable(pulse, 2)(t)
+        u = np.zeros(shape, dtype=np.complex128)
+        for (a, b), c in modes:
+            u += c * np.exp(1j * (a * X + b * Y - (a * a + b * b) * t + a * ph[0] + b * ph[1]))
+        return u
+    free = synth.Instance(synth.PERIODIC, shape, field(0.0), np.zeros(shape), lambda t: np.ones_like(np.asarray(t)),
+                          pulse, 1e-3, 30)
+    u = gpu_solve(free, precision=precision)[0]
+    assert rel_l2(u, field(free.t_max)) <= tol
+
+
 # ------------------------------------------------------------------ batching
 def test_batch_members_equal_single_runs():
     """Each batch member is bit-identical to the same instance solved alone."""
