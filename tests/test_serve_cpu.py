@@ -147,3 +147,33 @@ def test_cancellation_waiting_and_active():
     assert reqs[0].result is None and reqs[0].admitted is not None
     assert reqs[3].admitted is None
     assert ("start", 3) not in be.log and be.live == 0
+
+
+def test_trace_routes_free_space_by_precision():
+    """requests_from_trace: periodic classes in mixed precision; free space in
+    FP64 on the eps = 1e-10 contour or with FP32 transforms on the contour for
+    eps = 1e-4 with FP32 sums (smaller H, same nu = 8 n)."""
+    pytest.importorskip("torch")
+    import __graft_entry__
+    __graft_entry__.build()
+    import math
+    import synth
+    from paper_2001_06113_gb300.serve import requests_from_trace
+    trace = synth.serve_requests(seed=3, rate=80.0, duration=0.2, T_range=(0.01, 0.02), sizes_1d=(1024,),
+                                 sizes_2d=(128,), sizes_free=(64,))
+    f64 = requests_from_trace(trace)
+    f32 = requests_from_trace(trace, free_precision="mixed")
+    assert any(r.bc == "free" for r in f64)
+    for a, b in zip(f64, f32):
+        assert a.bc == b.bc
+        if a.bc != "free":
+            assert a.precision == b.precision == "mixed"
+            continue
+        assert (a.precision, b.precision) == ("fp64", "mixed")
+        assert a.free["nu"] == b.free["nu"] == [8 * n for n in a.inst.shape]
+        # same ||V|| and phi_max, machine epsilon 2^-52 at 1e-10 against 2^-23 at 1e-4
+        d = a.inst.dim
+        lhs = a.free["H"] * 2 * d                        # = log(eps / ((1 + |V|) eps_m)) / (1 + phimax)
+        rhs = b.free["H"] * 2 * d
+        ratio = (lhs - rhs) / (math.log(1e-10 / 1e-4) + 29 * math.log(2.0))
+        assert 0.0 < ratio <= 1.0 + 1e-12                 # = 1 / (1 + phimax)
