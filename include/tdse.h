@@ -252,8 +252,10 @@ tdse_status tdse_free_choose_H(double eps, double vnorm, double phimax, int dim,
  * precision or a result that is not positive and finite. */
 tdse_status tdse_free_choose_H_prec(double eps, double vnorm, double phimax, int dim, int precision, double* H_out);
 
-/* FP64 residual check of the mixed-precision implicit step (TDSE_MIXED,
- * periodic; 1D n <= 8192, 2D n <= 1024 per dimension).  After every
+/* FP64 residual check of the mixed-precision implicit step (TDSE_MIXED;
+ * periodic 1D n <= 8192, 2D n <= 1024 per dimension; free space with the
+ * contour forward / inverse transforms in place of DFT / IDFT, and u on the
+ * grid replaced by the FP64 solve as well).  After every
  * `every`-th Adams step (0 = off) the library evaluates, in FP64 on the GPU,
  * with u^_n and R_n = (Vu)^_n as stored (taken back to the lab frame):
  *     W = u^_n + i mu_0 dt R_n,  R64 = DFT(V IDFT(W) / (1 + i mu_0 dt V)),
@@ -262,7 +264,7 @@ tdse_status tdse_free_choose_H_prec(double eps, double vnorm, double phimax, int
  * and where rho > tol (or is not finite) redoes the step in FP64:
  * u^_n <- W - i mu_0 dt R64, R_n <- R64.  The check and the redo stay on the
  * device (no host synchronisation).  Errors: TDSE_EUNSUPPORTED outside the
- * sizes above or for FP64 / free-space contexts (every > 0). */
+ * sizes above or for FP64 contexts (every > 0). */
 tdse_status tdse_set_residual_check(tdse_ctx* ctx, int every, double tol);
 
 /* Last checked residual rho per instance and the number of FP64 redos per

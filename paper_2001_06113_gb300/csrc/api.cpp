@@ -342,6 +342,10 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     if (main_tables)
         for (int n = c->S_eff + 1; n <= cfg->nsteps; ++n)
             c->intervals[main_interval(c, n)] = make_int2(SUB * (n - 1), SUB * n);
+    if (fs && c->mixed) {   // zero-length interval: the FP64 residual check re-evaluates a step with p_0 = 1
+        c->intervals.push_back(make_int2(0, 0));
+        c->F.zero_iv = c->n_int++;
+    }
     c->nhi = cfg->nsteps / E1D_NLO + 1;
     // Ring dither: r~_n = z_n r^_n with z_n = e^{i psi_n}, psi_n = 2 pi frac(n (sqrt2 - 1)),
     // rounded to FP32 once; the history weights divide it out exactly (FP64).
@@ -876,8 +880,8 @@ tdse_status tdse_read_modes(tdse_ctx* c, int instance, double* u_out, int where,
 tdse_status tdse_set_residual_check(tdse_ctx* c, int every, double tol) {
     if (!c) return TDSE_EINVAL;
     if (every < 0 || !(tol >= 0.0)) return c->fail(TDSE_EINVAL, "every >= 0 and tol >= 0 required");
-    if (every > 0 && (!c->mixed || c->fs)) return c->fail(TDSE_EUNSUPPORTED, "residual check: periodic TDSE_MIXED only");
-    if (every > 0 && !residual_supported(c->d, c->n0, c->n1))
+    if (every > 0 && !c->mixed) return c->fail(TDSE_EUNSUPPORTED, "residual check: TDSE_MIXED only");
+    if (every > 0 && !c->fs && !residual_supported(c->d, c->n0, c->n1))
         return c->fail(TDSE_EUNSUPPORTED, "residual check: n up to 8192 (1D) or 1024 per dimension (2D)");
     c->res_every = every;
     c->res_tol = tol;
@@ -888,7 +892,7 @@ tdse_status tdse_residual_report(tdse_ctx* c, double* rho, int* corrections, int
     if (!c) return TDSE_EINVAL;
     if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
     if (checks) *checks = c->res_checks;
-    if (!c->mixed || c->fs) return TDSE_OK;
+    if (!c->mixed || !c->off.res_rho) return TDSE_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (rho) TDSE_CK(c, cudaMemcpyAsync(rho, c->P<double>(c->off.res_rho), (size_t)c->B * 8, cudaMemcpyDeviceToHost, s));
     if (corrections)

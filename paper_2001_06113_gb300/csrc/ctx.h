@@ -35,7 +35,10 @@ struct FsState {
         size_t zeta[2], preI[2], postI[2], preF[2], postF[2], Gd[2], Fd[2], tw[2], P[2];
         // FP32 copies (f32 only; 0 otherwise)
         size_t preI_f[2], postI_f[2], preF_f[2], postF_f[2], Gd_f[2], Fd_f[2], tw_f[2], P_f[2];
+        // FP64 residual check of the FP32 step (f32 only): W / corrected state, R64, u64, 2D intermediate
+        size_t res_W, res_R, res_u, Z64;
     } off{};
+    int zero_iv = -1;   // f32: interval of zero length (one-step phase 1) for the FP64 re-evaluation
 };
 
 }  // namespace tdse

@@ -330,6 +330,53 @@ tdse_status fs_adams(tdse_ctx* c, int n0, int k, cudaStream_t s) {
     return TDSE_OK;
 }
 
+// FP64 residual of the implicit step just completed (step c->step, FP32
+// transforms): W = u^ + i mu_0 h R_n, then the step's implicit part
+// re-evaluated in FP64 (the FP64 kernels with no history term and a one-step
+// phase of 1): u64 = inverse(W) / (1 + i mu_0 h V), R64 = forward(V u64),
+// Wc = W - i mu_0 h R64; rho = mu_0 h ||R64 - R_n|| / ||u^||; where rho > tol
+// (or is not finite) the step's results are replaced by the FP64 ones.
+tdse_status fs_residual_check(tdse_ctx* c, cudaStream_t s) {
+    const FsState& F = c->F;
+    const int n = c->step;
+    const double hm0 = c->cfg.dt * c->mu[0];
+    const size_t rstride = (size_t)c->RS * F.NM;
+    float2* ring_n = reinterpret_cast<float2*>(ring_at(c, F.off.ring, (size_t)slot_of(c, n) * F.NM));
+    double2* uhat = c->P<double2>(F.off.uhat);
+    double2* W = c->P<double2>(F.off.res_W);
+    double2* R64 = c->P<double2>(F.off.res_R);
+    double2* u64 = c->P<double2>(F.off.res_u);
+    TDSE_CK(c, launch_fs_res_prep(W, uhat, ring_n, rstride, F.NM, c->B, hm0, s));
+    FsArgs a = fs_base(c);
+    a.uhat = W;                 // W in, W - i mu_0 h R64 out
+    a.ring = R64;               // one FP64 slot: R64
+    a.ring_slots = 1;
+    a.u = u64;
+    a.Z = F.off.Z64 ? c->P<double2>(F.off.Z64) : nullptr;
+    a.nhist = 0;
+    a.h = c->cfg.dt;
+    a.mu[0] = c->mu[0];
+    a.out_slot = 0;
+    a.interval[0] = F.zero_iv;
+    set_time(c, a, SUB * n);
+    if (c->d == 1) {
+        TDSE_CK(c, launch_fs_1d(a, FS_1D_STEP, 0, s));
+    } else {
+        TDSE_CK(c, launch_fs_row(a, FS_ROW_BEGIN, 0, s));
+        TDSE_CK(c, launch_fs_phys(a, 0, 0, s));
+        TDSE_CK(c, launch_fs_row(a, FS_ROW_END, 0, s));
+    }
+    double* sums = c->P<double>(c->off.res_sums);
+    int* flags = c->P<int>(c->off.res_flags);
+    TDSE_CK(c, launch_fs_res_norms(R64, ring_n, rstride, uhat, F.NM, c->B, sums, s));
+    TDSE_CK(c, launch_fs_res_decide(sums, c->B, hm0, c->res_tol, c->P<double>(c->off.res_rho), flags,
+                                    c->P<int>(c->off.res_ncorr), s));
+    TDSE_CK(c, launch_fs_res_apply(flags, c->B, F.NM, F.NX, uhat, W, ring_n, rstride, R64, c->P<double2>(F.off.u),
+                                   u64, s));
+    ++c->res_checks;
+    return TDSE_OK;
+}
+
 }  // namespace
 
 tdse_status fs_create(tdse_ctx* c) {
@@ -392,6 +439,17 @@ tdse_status fs_create(tdse_ctx* c) {
             F.off.P_f[x] = take(B * (size_t)c->n_int * A.N * 8);
         }
     }
+    size_t res_sums = 0, res_rho = 0, res_flags = 0, res_ncorr = 0;
+    if (F.f32) {   // FP64 residual check of the FP32 step
+        F.off.res_W = take(B * F.NM * 16);
+        F.off.res_R = take(B * F.NM * 16);
+        F.off.res_u = take(B * F.NX * 16);
+        F.off.Z64 = c->d == 2 ? take(B * (size_t)F.ax[0].N * F.ax[1].M * 16) : 0;
+        res_sums = take(B * 16);
+        res_rho = take(B * 8);
+        res_flags = take(B * 4);
+        res_ncorr = take(B * 4);
+    }
     F.off.scratch = take(256);
     F.off.end = o;
     c->ws_need = o;
@@ -404,6 +462,10 @@ tdse_status fs_create(tdse_ctx* c) {
     c->off.phi = F.off.phi;
     c->off.iv = F.off.iv;
     c->off.scratch = F.off.scratch;
+    c->off.res_sums = res_sums;
+    c->off.res_rho = res_rho;
+    c->off.res_flags = res_flags;
+    c->off.res_ncorr = res_ncorr;
     return TDSE_OK;
 }
 
@@ -479,11 +541,20 @@ tdse_status fs_steps(tdse_ctx* c, int nsteps, cudaStream_t s) {
             ++k;
             continue;
         }
-        const int run_len = nsteps - k;
+        int run_len = nsteps - k;
+        const bool check = c->F.f32 && c->res_every > 0;
+        if (check) {   // stop at the next step to check
+            const int to_check = c->res_every - c->step % c->res_every;
+            if (to_check < run_len) run_len = to_check;
+        }
         tdse_status st = fs_adams(c, c->step, run_len, s);
         if (st != TDSE_OK) return st;
         c->step += run_len;
         k += run_len;
+        if (check && c->step % c->res_every == 0) {
+            st = fs_residual_check(c, s);
+            if (st != TDSE_OK) return st;
+        }
     }
     return TDSE_OK;
 }

@@ -96,6 +96,22 @@ cudaError_t launch_fs_1d(const FsArgs& a, int mode, int f32, cudaStream_t s);
 cudaError_t launch_fs_f32(const FsArgs& a, int which, int flag, cudaStream_t s);   // freespace_f32.cu
 // FP32 copy of n complex values
 cudaError_t launch_fs_to_f32(float2* dst, const double2* src, size_t n, cudaStream_t s);
+
+// FP64 residual check of the FP32-transform step (free space).  Per instance b
+// (NM modes, ring slot R_n in FP32 at ring + b rstride):
+//   prep:   W = u^ + i hm0 R_n  (FP64)
+//   norms:  sums[b] = (sum |R64 - R_n|^2, sum |u^|^2)
+//   decide: rho[b] = hm0 sqrt(s0 / s1); flag[b] = !(rho <= tol); ncorr[b] += flag
+//   apply:  where flagged, u^ <- Wc, R_n <- R64 (FP32), u <- u64
+cudaError_t launch_fs_res_prep(double2* W, const double2* uhat, const float2* ring, size_t rstride, size_t NM, int B,
+                               double hm0, cudaStream_t s);
+cudaError_t launch_fs_res_norms(const double2* R64, const float2* ring, size_t rstride, const double2* uhat, size_t NM,
+                                int B, double* sums, cudaStream_t s);
+cudaError_t launch_fs_res_decide(const double* sums, int B, double hm0, double tol, double* rho, int* flags, int* ncorr,
+                                 cudaStream_t s);
+cudaError_t launch_fs_res_apply(const int* flags, int B, size_t NM, size_t NX, double2* uhat, const double2* Wc,
+                                float2* ring, size_t rstride, const double2* R64, double2* u, const double2* u64,
+                                cudaStream_t s);
 // P[iv][m] of one instance and axis: zeta [N] complex, phi_axis [ntf] = that
 // component of phi at t = m dt / 8.
 cudaError_t launch_fs_phase(double2* P, const double2* zeta, int N, const int2* intervals, int n_int,

@@ -320,3 +320,36 @@ def test_free_mixed_batch_and_checkpoint():
     assert pc.step_index == 5
     pc.step(n - 5)
     assert np.array_equal(pc.read_u(), ub)
+
+
+@pytest.mark.parametrize("shape,nu", [((64,), (512,)), ((32, 32), (256, 256))])
+def test_free_mixed_residual_check(shape, nu):
+    """FP64 residual of the FP32-transform step: small and reported; with no
+    redo the results keep their bits; a redo of every checked step (tol = 0)
+    stays within the mixed bar of the FP64 oracle."""
+    n = 14
+    inst = _instance(shape, n + 2)
+    H = _H(inst, 1e-4, EPS_M32)
+
+    def run(every, tol):
+        from paper_2001_06113_gb300 import Problem
+        pr = Problem(inst.shape, inst.dt, inst.nsteps, bc="free", nu=nu, H=H, gauss_q=10, n_r=1, precision="mixed")
+        if every:
+            pr.set_residual_check(every, tol)
+        pr.set_potential(inst.V0, inst.vfac_table())
+        pr.set_pulse(inst.pulse.A0, inst.pulse.omega, inst.pulse.T_pulse, inst.pulse.direction)
+        pr.set_initial(inst.u0)
+        pr.step(n)
+        out = (pr.read_u(0), pr.read_modes(0), pr.residual_report())
+        pr.close()
+        return out
+
+    u0, m0, _ = run(0, 0.0)
+    u1, m1, (rho, corr, checks) = run(3, 1e-3)
+    assert checks == 2 and int(np.sum(corr)) == 0           # steps 9 and 12 (Adams steps 8..14)
+    assert 0.0 < float(np.max(rho)) < 1e-6
+    assert np.array_equal(u0, u1) and np.array_equal(m0, m1)
+    u2, m2, (rho2, corr2, checks2) = run(3, 0.0)
+    assert checks2 == 2 and int(np.min(corr2)) == 2
+    uo, uho = _oracle(inst, nu, H, n)
+    assert rel(u2, uo) < MIXED_TOL and rel(m2, uho) < MIXED_TOL, (rel(u2, uo), rel(m2, uho))

@@ -83,3 +83,6 @@ def test_residual_check_refused_off_path():
         Problem((64,), 1e-3, 10, precision="fp64").set_residual_check(5, 1e-6)
     with pytest.raises(TdseError):
         Problem((64,), 1e-3, 10, precision="mixed").set_residual_check(-1, 1e-6)
+    with pytest.raises(TdseError):   # free space in FP64: nothing to check
+        Problem((64,), 1e-3, 10, bc="free", nu=(512,), H=2.0).set_residual_check(5, 1e-6)
+    Problem((64,), 1e-3, 10, bc="free", nu=(512,), H=1.0, precision="mixed").set_residual_check(5, 1e-6)
