@@ -326,7 +326,8 @@ FS_METRICS = {"fp64": "point-steps/s (2D free space 256^2, nu=2048, 8th-order, T
               "mixed": "point-steps/s (2D free space 256^2, nu=2048, 8th-order, T=1, FP32 transforms, eps=1e-4)"}
 # DRAM bytes of one fused k_fs_row launch (end + begin) of one 256^2 instance,
 # from the ncu capture summarised in profiles/step2d_free_256x256_fp64.md.
-FS_ROW_TRAFFIC = {"fp64": 484.806912e6 + 123.36256e6, "mixed": None}
+# FP32-transform variant: profiles/step2d_free_256x256_mixed.md (4 CTAs per SM).
+FS_ROW_TRAFFIC = {"fp64": 484.806912e6 + 123.36256e6, "mixed": 277.45024e6 + 114.500352e6}
 # FP32 FMA rate: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -984,6 +985,9 @@ EX_METRIC = ("point-steps/s (Example 1 moving periodic Gaussian well, V0=300, be
 # per point-step: state in/out 32, 7 ring reads 56, 1 ring write 8; the V row
 # (one shared table per speed) is read once per step for all instances
 EX_ALGO_BYTES = 16 + 7 * 8 + 16 + 8
+# DRAM bytes of one k_periodic1d<float2,float2,512> Adams-step launch over 2048
+# instances (ncu, profiles/example1_moving_well_512_mixed.md); per step x 3 speeds
+EX_LAUNCH_TRAFFIC = 77.75232e6 + 5.611776e6
 
 
 def example1_oracle_sample(nadams: int = 400):
@@ -1082,7 +1086,9 @@ def run_example1(args, ws, rank, local):
     peak, peak_src = hbm_peak()
     achieved = EX_ALGO_BYTES * points / t_step / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4),
+                "traffic": EX_LAUNCH_TRAFFIC * len(probs) * B / 2048 if shape.get("mode") == "streams" else None,
+                "traffic_unit": "DRAM bytes per Adams step (ncu launch of 2048 instances, scaled by instances)",
                 "peak_source": peak_src,
                 "kernel": ("k_periodic1d_multi (one persistent launch per Adams step for all instances of the three "
                            "speeds)" if shape.get("mode", "fused") == "fused" else
