@@ -184,6 +184,28 @@ def test_batch_create_validates_without_gpu(native):
     assert lib.tdse_batch_create(arr, 0, ctypes.byref(out)) == -1
     assert lib.tdse_batch_create(arr, 1, ctypes.byref(out)) == -1      # workspace not bound
     assert lib.tdse_batch_step(None, 1, None) == -1
+    assert lib.tdse_batch_set_mode(None, 0) == -1
+    lib.tdse_destroy(ctx)
+
+
+def test_entry_points_refuse_before_binding(native):
+    """Calls that need device memory fail with TDSE_ESTATE before the
+    workspace is bound, and bad arguments with TDSE_EINVAL; no CUDA call."""
+    lib = native.lib()
+    ctx = ctypes.c_void_p()
+    assert lib.tdse_create(ctypes.byref(_cfg(native, potential=1)), ctypes.byref(ctx)) == 0
+    u = np.zeros(2 * 64)
+    V = np.zeros(lib.tdse_potential_times(ctx, None) * 64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    assert lib.tdse_set_initial_batch(ctx, u.ctypes.data_as(dp), 0, None) == -6
+    assert lib.tdse_set_potential_table(ctx, -1, V.ctypes.data_as(dp), 0, None) == -6
+    assert lib.tdse_set_initial_batch(None, u.ctypes.data_as(dp), 0, None) == -1
+    assert lib.tdse_set_initial_batch(ctx, None, 0, None) == -1
+    assert lib.tdse_set_potential_table(ctx, -1, None, 0, None) == -1
+    d = (ctypes.c_double * 2)(1.0, 0.0)
+    assert lib.tdse_set_pulse(ctx, -1, 1.0, 10.0, 0.0, d, None) == -1       # T_pulse must be > 0
+    assert lib.tdse_set_pulse(ctx, -1, 1.0, 10.0, 1.0, d, None) == -6
+    assert lib.tdse_set_residual_check(ctx, 5, 1e-6) == -7                 # FP64: nothing to check
     lib.tdse_destroy(ctx)
 
 
