@@ -334,9 +334,11 @@ class Problem:
 
 class Batch:
     """Uneven batch of 1D periodic mixed-precision Problems stepped together
-    (``tdse_batch_*``): one persistent launch per Adams step for all members,
-    the whole step sequence of a call captured into a CUDA graph and replayed.
-    The members stay owned by the caller and must outlive the batch."""
+    (``tdse_batch_*``): the Adams phase as one persistent launch per step for
+    all members ("fused") or each member's own kernel on its own stream
+    ("streams"; chosen by ``tune``), the whole step sequence of a call
+    captured into a CUDA graph and replayed.  The members stay owned by the
+    caller and must outlive the batch."""
 
     def __init__(self, members: Sequence[Problem], stream=None):
         self._lib = _native.lib()
