@@ -615,6 +615,21 @@ def oracle_sample(nadams: int = 6, seed: int = 2):
     return M * M * nadams / el, el
 
 
+def oracle_sample_one_core(nadams: int):
+    """oracle_sample on one core: a child interpreter with one BLAS / OpenMP
+    thread (the thread pools are fixed at import).  None if it fails."""
+    import subprocess
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys; sys.argv = ['bench.py']; import bench; "
+            f"v, el = bench.oracle_sample(nadams={int(nadams)}); print(v)")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=600)
+        return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except (subprocess.SubprocessError, ValueError, IndexError, OSError):
+        return None
+
+
 def cpu_cores() -> int:
     try:
         from threadpoolctl import threadpool_info
@@ -1376,7 +1391,9 @@ def main():
             v, el = oracle_sample(nadams=60)
             cpu = {"value": v, "unit": "point-steps/s", "cores": cpu_cores(), "kind": "oracle",
                    "sample": f"60 8th-order Adams steps of one 512^2 instance ({el:.1f} s; direct O(M^2) DFT sums, "
-                             "numpy/OpenBLAS)"}
+                             "numpy/OpenBLAS)",
+                   "value_1core": oracle_sample_one_core(10),
+                   "sample_1core": "10 Adams steps of the same instance with one BLAS/OpenMP thread"}
         line = {
             "metric": METRIC, "value": res["value"], "unit": "point-steps/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["t_solve"] * 1e3,
