@@ -624,7 +624,7 @@ def oracle_sample_one_core(nadams: int):
             f"v, el = bench.oracle_sample(nadams={int(nadams)}); print(v)")
     try:
         r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
-                           timeout=600)
+                           timeout=120)
         return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
     except (subprocess.SubprocessError, ValueError, IndexError, OSError):
         return None
