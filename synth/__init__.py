@@ -337,6 +337,28 @@ def free_moving_well(M: int = 256, V0: float = 3000.0, beta: float = 0.06, x0: f
                     name=f"free_moving_well_M{M}", Vt=Vt)
 
 
+def moving_separable_wells_2d(M: int = 64, nsteps: int = 200, T: float = 0.2, wells=((40.0, 0.45), (60.0, 0.5)),
+                              c=(4.0, -2.0), K: int = 96) -> Instance:
+    """2D periodic V(x, y, t) = W_1(x - c_x t) + W_2(y - c_y t), W_a the
+    periodised Gaussian well -V0_a exp(-s^2 / (2 beta_a^2)); A = 0; u0 = the
+    product of the two wells' ground states boosted by e^{i c.x / 2} (the state
+    the wells carry along when c_x / 2, c_y / 2 are integers)."""
+    x = periodic_grid(M)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    g = [well_ground_state_coeffs(V0, b, K) for V0, b in wells]
+    w = [np.exp(1j * np.outer(x, k)) @ coef for _, k, coef in g]
+    u0 = np.outer(w[0], w[1]) * np.exp(0.5j * (c[0] * X + c[1] * Y))
+    mw = [[(V0, (0.0,), (cc,), b)] for (V0, b), cc in zip(wells, c)]
+
+    def Vt(t, _x=(x,), _m=mw):
+        a = _moving_gaussians(_x, _m[0], float(t), 2.0 * math.pi, 3)
+        b = _moving_gaussians(_x, _m[1], float(t), 2.0 * math.pi, 3)
+        return a[:, None] + b[None, :]
+
+    return Instance(PERIODIC, (M, M), u0.astype(np.complex128), Vt(0.0), _const_one, None, T / nsteps, nsteps,
+                    name=f"moving_separable_wells_2d_M{M}", Vt=Vt)
+
+
 def example1_sweep(count: int, c: float, seed: int = 11, M: int = 512, nsteps: int = 3200,
                    T: float = 2.0 * math.pi / 15.0, V0: float = 300.0, beta: float = 0.2):
     """A sweep over initial states for one well speed of Example 1: the well

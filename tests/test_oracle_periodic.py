@@ -234,6 +234,26 @@ def test_moving_well_pin_catches_lagged_potential(monkeypatch):
     assert not (e200 < 1e-9 and e400 < 1e-10 and e100 / e200 > 100.0)
 
 
+def test_moving_separable_wells_2d_galilean_closed_form():
+    """2D: two 1D wells moving along x and y (V = W_1(x - c_x t) + W_2(y - c_y t),
+    c = (4, -2)) carry the product of their boosted ground states:
+    u = w_1(x - c_x t) w_2(y - c_y t) e^{-i (E_1 + E_2) t} e^{i (c.x / 2 - |c|^2 t / 4)}.
+    8th order (measured 3.8e-7, 1.6e-9 at 100, 200 steps, M = 64)."""
+    (V1, b1), (V2, b2), c, T, M = (40.0, 0.45), (60.0, 0.5), (4.0, -2.0), 0.2, 64
+    E1, k1, c1 = synth.well_ground_state_coeffs(V1, b1)
+    E2, k2, c2 = synth.well_ground_state_coeffs(V2, b2)
+    x = synth.periodic_grid(M)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    ref = (np.outer(np.exp(1j * np.outer(x - c[0] * T, k1)) @ c1, np.exp(1j * np.outer(x - c[1] * T, k2)) @ c2)
+           * np.exp(-1j * (E1 + E2) * T) * np.exp(1j * (0.5 * (c[0] * X + c[1] * Y) - 0.25 * (c[0] ** 2 + c[1] ** 2) * T)))
+    errs = []
+    for n in (100, 200):
+        inst = synth.moving_separable_wells_2d(M=M, nsteps=n, T=T)
+        orc = PeriodicOracle(inst.shape, inst.dt, inst.Vt, None, _phi(None, 2))
+        errs.append(rel_l2(orc.solve(inst.u0, n), ref))
+    assert errs[1] < 1e-8 and errs[0] / errs[1] > 100.0, errs
+
+
 # ----------------------------------------------- the pins catch planted mistakes
 def _run_pins(monkeypatch_ctx):
     """Return which of three cheap pins still pass under a planted mistake."""
