@@ -93,6 +93,23 @@ def test_galilean_closed_form_on_gpu():
     assert errs[1] < 1e-9 and errs[2] < 1e-10 and errs[0] / errs[1] > 100.0, errs
 
 
+def test_galilean_closed_form_2d_on_gpu():
+    """Two wells moving along x and y carry their boosted ground-state product
+    (2D closed form): 8th order as on the oracle (3.8e-7, 1.6e-9)."""
+    (V1, b1), (V2, b2), c, T, M = (40.0, 0.45), (60.0, 0.5), (4.0, -2.0), 0.2, 64
+    E1, k1, c1 = synth.well_ground_state_coeffs(V1, b1)
+    E2, k2, c2 = synth.well_ground_state_coeffs(V2, b2)
+    x = synth.periodic_grid(M)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    ref = (np.outer(np.exp(1j * np.outer(x - c[0] * T, k1)) @ c1, np.exp(1j * np.outer(x - c[1] * T, k2)) @ c2)
+           * np.exp(-1j * (E1 + E2) * T) * np.exp(1j * (0.5 * (c[0] * X + c[1] * Y) - 0.25 * (c[0] ** 2 + c[1] ** 2) * T)))
+    errs = []
+    for n in (100, 200):
+        inst = synth.moving_separable_wells_2d(M=M, nsteps=n, T=T)
+        errs.append(rel_l2(gpu(inst, n).read_u(0), ref))
+    assert errs[1] < 1e-8 and errs[0] / errs[1] > 100.0, errs
+
+
 @pytest.mark.parametrize("shape,precision", [((256,), "fp64"), ((64, 64), "fp64"), ((256,), "mixed"),
                                              ((64, 64), "mixed"), ((16384,), "mixed")])
 def test_table_of_separable_potential_equals_separable_path(shape, precision):
