@@ -226,9 +226,10 @@ tdse_status tdse_read_u(tdse_ctx* ctx, int instance, double* u_out, int where, v
 
 /* The mode state u^(t_current) of one instance (or -1 = all) into u_out
  * (interleaved complex FP64, host or device): periodic [n0][n1] in FFT order,
- * free space [N0][N1] in the node order of tdse_free_rule.  TDSE_FP64 only
- * (TDSE_EUNSUPPORTED for TDSE_MIXED, whose state is held in another
- * representation); TDSE_ESTATE before the first step. */
+ * free space [N0][N1] in the node order of tdse_free_rule.  TDSE_FP64, and
+ * free space in TDSE_MIXED (its mode state is FP64); TDSE_EUNSUPPORTED for the
+ * periodic TDSE_MIXED state (double-float, interaction picture); TDSE_ESTATE
+ * before the first step. */
 tdse_status tdse_read_modes(tdse_ctx* ctx, int instance, double* u_out, int where, void* stream);
 
 /* Free space: the contour rule of dimension `axis` (Sec. 3.4): *N receives
