@@ -140,20 +140,28 @@ typedef struct {
 typedef void (*tdse_field_fn)(double t, double* A_out, void* user);
 
 /* Validate `cfg` and create a context (host only; no CUDA call).
+ * Paper: the problem is the initial value problem eq. schrodfree (Sec. 1) on
+ * [-pi,pi]^dim with periodic data (Sec. 2) or in free space with data
+ * supported in [-1,1]^dim (Sec. 3); the grid, dt and the Adams order n are
+ * the discretisation parameters of Sec. 2.1-2.2 (and Sec. 3.4 for the contour).
  * Errors: TDSE_EINVAL for an invalid configuration, TDSE_EUNSUPPORTED for a
  * size this build does not instantiate, TDSE_ENOMEM if host allocation fails. */
 tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out);
 
-/* Bytes of device workspace the context needs (0 if ctx is NULL). */
+/* Bytes of device workspace the context needs (0 if ctx is NULL).  The
+ * paper has no counterpart (memory management of this library). */
 size_t tdse_workspace_bytes(const tdse_ctx* ctx);
 
 /* Bind caller-owned device memory of at least tdse_workspace_bytes() bytes,
- * 256-byte aligned, and build the device tables (twiddles, Adams weights,
+ * 256-byte aligned (no paper counterpart), and build the device tables (twiddles, Adams weights,
  * kinetic phase tables) on `stream`.  Errors: TDSE_ENOMEM if too small,
  * TDSE_EINVAL if misaligned, TDSE_ECUDA on a CUDA failure. */
 tdse_status tdse_bind_workspace(tdse_ctx* ctx, void* device_ptr, size_t bytes, void* stream);
 
 /* V(x,t) = f(t) V0(x) for instance `instance` (0-based; -1 = every instance).
+ * Paper: the potential V(x,t) of eq. schrodfree (Sec. 1); the scheme samples
+ * it on the grid at the step times (eq. uadamsk) and at the trapezoid
+ * sub-step times of the Richardson start-up (Sec. 2.2).
  *   V0           n0*n1 real values on the grid (host or device per `where`).
  *   time_factor  NULL for f = 1, else HOST array of 8*nsteps+1 values
  *                f(m dt/8), m = 0..8*nsteps (the step and Richardson sub-step
@@ -194,7 +202,9 @@ tdse_status tdse_set_pulse(tdse_ctx* ctx, int instance, double A0, double omega,
                            double T_pulse, const double* direction, void* stream);
 
 /* Initial wavefunction u0 (n0*n1 interleaved complex, host or device) for an
- * instance (-1 = all instances get the same u0).  Resets the step counter of
+ * instance (-1 = all instances get the same u0): the initial data u(x,0) of
+ * eq. schrodfree (Sec. 1), sampled on the grid of Sec. 2.1 (periodic) or
+ * Sec. 3.4 (free space).  Resets the step counter of
  * the whole context to 0. */
 tdse_status tdse_set_initial(tdse_ctx* ctx, int instance, const double* u0, int where,
                              void* stream);
@@ -205,18 +215,26 @@ tdse_status tdse_set_initial(tdse_ctx* ctx, int instance, const double* u0, int 
  * Resets the step counter as tdse_set_initial. */
 tdse_status tdse_set_initial_batch(tdse_ctx* ctx, const double* u0, int where, void* stream);
 
-/* Advance every instance by `nsteps` steps of dt (asynchronous on `stream`).
+/* Advance every instance by `nsteps` steps of dt (asynchronous on `stream`):
+ * the marching loop of Sec. 2.1-2.2 (periodic: eq. utrapkdisc for the
+ * start-up chains, eq. uadamsk with Table 1's weights afterwards) and of
+ * Sec. 3.4 with Remark highorderfs (free space: the same recurrence on the
+ * contour modes, eqs. uhatzfd and fzdft/uciftdisc for the transforms).
  * The first call after tdse_set_initial transforms u0 and V(0)u0; the first
  * startup_steps steps use Richardson start-up, later ones the Adams scheme.
  * Errors: TDSE_ESTATE if an instance lacks V, A or u0 (A may be left unset:
  * then A == 0), TDSE_EINVAL if the tables' nsteps would be exceeded. */
 tdse_status tdse_step(tdse_ctx* ctx, int nsteps, void* stream);
 
-/* Step until t >= T (T rounded to the nearest multiple of dt). */
+/* Step until t >= T (T rounded to the nearest multiple of dt): the marching
+ * loop of Sec. 2.1-2.2 / Sec. 3.4 run to the final time, as tdse_step. */
 tdse_status tdse_solve_to(tdse_ctx* ctx, double T, void* stream);
 
 /* u(x, t_current) on the grid for one instance (or -1 = all, laid out
  * [batch][n0*n1]), into u_out (interleaved complex FP64, host or device).
+ * Paper: the read-out is the inverse transform of the mode state (periodic:
+ * the inverse DFT of Sec. 2.1 that eq. utrapkdisc applies; free space: the
+ * grid values of eq. uciftdisc that the implicit solve produces, Sec. 3.4).
  * Periodic: the inverse DFT of u^ in FP64.  Free space: the grid values of the
  * last implicit solve (or the Richardson combination of the start-up, or u0
  * before the first step), which the scheme carries alongside u^ (u is not

@@ -17,6 +17,11 @@
 //    threads) race on it and give wrong results; serialise them;
 //  * the first call on a device looks up the array's device address (with
 //    that device current); make that first call before any stream capture.
+//    The address is cached per device together with the id of the CUDA
+//    context it belongs to; after a device reset (a new context) the next
+//    call looks it up again, and that call too should precede any capture.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "kargs.h"
@@ -34,19 +39,59 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// Per device: the address of the array and the id of the CUDA context it was
+// looked up in.  A device reset (cudaDeviceReset, or a primary-context reset)
+// gives the device a new context in which the module, and so the array, may
+// sit at another address; the id then differs and the address is looked up
+// again instead of reusing a stale pointer.
 void* g_addr[kMaxDevices] = {nullptr};
+unsigned long long g_ctx_id[kMaxDevices] = {0};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Id of the current context (driver entry points found through the runtime,
+// so the library needs no link against the driver library).
+cudaError_t current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess || q1 != cudaDriverEntryPointSuccess) return cudaErrorNotSupported;
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess || q2 != cudaDriverEntryPointSuccess) return cudaErrorNotSupported;
+        get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    if (!ctx) {         // no context yet: a runtime call creates the primary one
+        *id = 0;
+        return cudaSuccess;
+    }
+    if (get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
 
 cudaError_t scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    unsigned long long id = 0;
+    e = current_context_id(&id);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    if (!g_addr[dev] || id == 0 || g_ctx_id[dev] != id) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // creates the context if there was none
         if (e != cudaSuccess) return e;
+        if (id == 0 && (e = current_context_id(&id)) != cudaSuccess) return e;
         g_addr[dev] = p;
+        g_ctx_id[dev] = id;
     }
     *out = g_addr[dev];
     return cudaSuccess;

@@ -84,6 +84,27 @@ def test_noalloc_matches_read_u_on_two_calls(env):
         assert st == 0
         for b in range(batch):
             assert _rel(got[b], ref[b]) <= TOL, (shape, b)
+            # and an independent inverse DFT (numpy's, without its 1/(n0 n1))
+            assert _rel(got[b], np.fft.ifft2(modes[b]) * (shape[0] * shape[1])) <= TOL, (shape, b)
+        prob.close()
+
+
+def test_noalloc_at_the_size_limit(env):
+    """Calls that fill the fixed scratch exactly: 512 x 1024 (one array, the
+    intermediate reaching the end of its region) and 64 arrays of 1024 x 8 (a
+    full 1024-entry twiddle axis), each against tdse_read_u and numpy."""
+    torch, native = env
+    stream = torch.cuda.current_stream()
+    cases = [((512, 1024), 1, 3, 1e-3, 5), ((1024, 8), 64, 3, 1e-3, 6)]
+    for shape, batch, nsteps, dt, seed in cases:
+        assert batch * shape[0] * shape[1] == native.NOALLOC_MAX_POINTS
+        prob, modes = _free_problem(shape, batch, nsteps, dt, seed)
+        ref = prob.read_u(-1)
+        st, got = _noalloc(torch, native, modes, stream)
+        assert st == 0
+        for b in range(batch):
+            assert _rel(got[b], ref[b]) <= TOL, (shape, b)
+            assert _rel(got[b], np.fft.ifft2(modes[b]) * (shape[0] * shape[1])) <= TOL, (shape, b)
         prob.close()
 
 
