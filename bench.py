@@ -168,8 +168,9 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------- GPU arm
-def launches_per_solve(dim: int, mixed: bool) -> int:
-    """Kernel launches of one tdse_step(NSTEPS) call (init, start-up, Adams)."""
+def launches_per_solve(dim: int, mixed: bool, path: str = "passes") -> int:
+    """Kernel launches of one tdse_step(NSTEPS) call (init, start-up, Adams);
+    the cluster path runs all Adams steps of the call in one launch."""
     L = ORDER // 2
     sub = sum(2 ** c for c in range(L))      # trapezoid sub-steps per start-up step
     per_op = 1 if dim == 1 else 3            # kernels per unfused application of the step operator
@@ -177,6 +178,8 @@ def launches_per_solve(dim: int, mixed: bool) -> int:
     init = 1 if dim == 1 else 2
     k = NSTEPS - STARTUP
     adams = k if dim == 1 else 2 * k + 1     # 2D: col_begin, (row_mid, col_fused) x (k-1), row_mid, col_end
+    if dim == 2 and path == "cluster":
+        adams = 1
     return init + startup + (1 if mixed else 0) + adams
 
 
@@ -184,8 +187,8 @@ def launches_per_solve(dim: int, mixed: bool) -> int:
 # from the ncu capture of the 512^2 mixed workload at batch 8 (summarised under
 # profiles/); traffic scales with the number of instances.  None = not captured
 # for the current kernels.
-TRAFFIC_BYTES_PER_POINT_STEP = {"mixed": (151.20896e6 + 29.985792e6 + 33.609216e6 + 37.632e6) / (8 * 512 * 512),
-                                "fp64": None}
+TRAFFIC_BYTES_PER_POINT_STEP = {("mixed", "passes"): (151.20896e6 + 29.985792e6 + 33.609216e6 + 37.632e6)
+                                / (8 * 512 * 512)}
 
 
 def run_gpu(args, ws, rank, local):
@@ -245,7 +248,7 @@ def run_gpu(args, ws, rank, local):
 
     # ---- step-operator roofline: events around groups of consecutive Adams steps
     #      (2D: per step one row pass + one fused column pass)
-    GROUP, NGROUPS = 10, 20
+    GROUP, NGROUPS = 50, 8
     with torch.cuda.stream(stream):
         prob.set_initial_batch(pinned_u)
         prob.step(STARTUP + 8)
@@ -260,12 +263,16 @@ def run_gpu(args, ws, rank, local):
     algo = ALGO_BYTES[args.precision] * B * points
     peak, peak_src = hbm_peak()
     achieved = algo / t_step / 1e9
-    tb = TRAFFIC_BYTES_PER_POINT_STEP.get(args.precision)
+    shape = prob.describe_steps()
+    tb = TRAFFIC_BYTES_PER_POINT_STEP.get((args.precision, shape["path"]))
     traffic = None if tb is None else round(tb * B * points)
+    kname = {"cluster": "k_step2d_cluster (one 16-CTA cluster per instance, a run of steps per launch)",
+             "passes": "k_row_mid + k_col_fused_ip" if args.precision == "mixed" else "k_row_mid + k_col_end (FP64)"}
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "traffic_unit": "bytes per step (all instances)",
                 "peak_source": peak_src,
-                "kernel": "2D Adams step operator (k_row_mid + k_col_fused_ip), timed over groups of 10 steps",
+                "kernel": f"2D Adams step operator: {kname[shape['path']]}, timed over groups of {GROUP} steps",
+                "launch_shape": shape,
                 "algorithmic_bytes_per_point_step": ALGO_BYTES[args.precision],
                 "step_ms_p50": round(float(np.percentile(dts, 50)) * 1e3, 4),
                 "step_ms_p99": round(float(np.percentile(dts, 99)) * 1e3, 4)}
@@ -1409,7 +1416,8 @@ def main():
                        "parallelism": f"replicas x{ws}"},
             "rel_l2_vs_fp64": res["stated_err"], "norm_drift_T": res["norm_drift"],
             "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
-            "gpu_launches": launches_per_solve(2, args.precision == "mixed") * args.steps,
+            "gpu_launches": launches_per_solve(2, args.precision == "mixed",
+                                               res["roofline"]["launch_shape"]["path"]) * args.steps,
         }
         print(json.dumps(line))
     if ws > 1:

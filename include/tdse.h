@@ -66,6 +66,7 @@ enum { TDSE_FP64 = 0, TDSE_MIXED = 1 };
 enum { TDSE_HOST = 0, TDSE_DEVICE = 1 };
 enum { TDSE_V_SEPARABLE = 0, TDSE_V_TABLE = 1, TDSE_V_TABLE_SHARED = 2 };
 enum { TDSE_BATCH_FUSED = 0, TDSE_BATCH_STREAMS = 1 };
+enum { TDSE_PATH_AUTO = 0, TDSE_PATH_PASSES = 1, TDSE_PATH_CLUSTER = 2 };
 
 /*
  * Problem configuration.
@@ -293,7 +294,9 @@ tdse_status tdse_set_residual_check(tdse_ctx* ctx, int every, double tol);
 tdse_status tdse_residual_report(tdse_ctx* ctx, double* rho, int* corrections, int* checks, void* stream);
 
 /* Scan the mode state of every instance for NaN/Inf (synchronises `stream`).
- * Returns TDSE_ENONFINITE if any is found. */
+ * Returns TDSE_ENONFINITE if any is found, TDSE_ETIMEOUT if a bounded wait
+ * inside a step kernel gave up since the workspace was bound (the results
+ * are then invalid). */
 tdse_status tdse_check_finite(tdse_ctx* ctx, void* stream);
 
 /* Checkpoint of the whole solve state: the context's workspace (mode state,
@@ -308,6 +311,38 @@ tdse_status tdse_save(tdse_ctx* ctx, void* blob, size_t* size, void* stream);
  * configuration (TDSE_EINVAL for another configuration or a short blob).
  * Synchronises `stream`. */
 tdse_status tdse_load(tdse_ctx* ctx, const void* blob, size_t size, void* stream);
+
+/* Kernels of the 2D periodic TDSE_MIXED Adams steps (the step operator of
+ * eq. uadamsk, Sec. 2.2, in the interaction picture; no change to what is
+ * computed):
+ *   TDSE_PATH_PASSES   two launches per step: a row pass and a fused column
+ *                      pass that exchange the transform intermediates
+ *                      through global memory;
+ *   TDSE_PATH_CLUSTER  512 x 512 grids: one launch per run of steps, each
+ *                      instance on a cluster of 16 CTAs that keeps the
+ *                      intermediates in (distributed) shared memory and
+ *                      streams the state, history and V by TMA (measured
+ *                      about 2x slower than the passes on a GB300: one CTA
+ *                      per SM, 7 clusters resident, and only a 3-stage load
+ *                      pipeline beside the 128 KB intermediate);
+ *   TDSE_PATH_AUTO     (default) the pass kernels.
+ * Both paths give the same bits.  TDSE_EUNSUPPORTED for TDSE_PATH_CLUSTER
+ * where it is not available (another size or precision, 1D, free space, or a
+ * device or driver that cannot run the cluster); TDSE_EINVAL for another
+ * value.  May be called at any time between steps. */
+tdse_status tdse_set_step_path(tdse_ctx* ctx, int path);
+
+/* The path the next 2D mixed Adams steps take (TDSE_PATH_PASSES or
+ * TDSE_PATH_CLUSTER; TDSE_PATH_PASSES for every other context), or -1 for
+ * NULL.  The cluster path needs the bound workspace (its plan is made at
+ * tdse_bind_workspace). */
+int tdse_step_path(const tdse_ctx* ctx);
+
+/* The launch shape of the 2D mixed Adams steps as a JSON object ("path",
+ * and for the cluster path "clusters" resident at once, "ctas_per_cluster",
+ * "threads", "smem_bytes") into buf (len bytes, NUL-terminated).
+ * TDSE_EINVAL for NULL arguments or a buffer too small. */
+tdse_status tdse_describe_steps(const tdse_ctx* ctx, char* buf, size_t len);
 
 /* Number of completed steps and the current time t = steps * dt. */
 int tdse_step_index(const tdse_ctx* ctx);

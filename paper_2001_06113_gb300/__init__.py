@@ -306,6 +306,26 @@ class Problem:
     def check_finite(self):
         _check(self._lib.tdse_check_finite(self._ctx, _stream_handle(self._stream)), self._ctx)
 
+    def set_step_path(self, path: str):
+        """Kernels of the 2D mixed Adams steps: "auto" (default), "passes" (row
+        and column pass kernels) or "cluster" (512^2: one cluster of 16 CTAs per
+        instance, intermediates in shared memory).  Same results either way."""
+        code = {"auto": _native.PATH_AUTO, "passes": _native.PATH_PASSES, "cluster": _native.PATH_CLUSTER}[path]
+        _check(self._lib.tdse_set_step_path(self._ctx, code), self._ctx)
+
+    @property
+    def step_path(self) -> str:
+        """The kernels the next 2D mixed Adams steps use: "passes" or "cluster"."""
+        return {_native.PATH_PASSES: "passes", _native.PATH_CLUSTER: "cluster"}.get(
+            int(self._lib.tdse_step_path(self._ctx)), "passes")
+
+    def describe_steps(self) -> dict:
+        """Launch shape of the 2D mixed Adams steps (path, clusters, ...)."""
+        import json
+        buf = ctypes.create_string_buffer(512)
+        _check(self._lib.tdse_describe_steps(self._ctx, buf, 512), self._ctx)
+        return json.loads(buf.value.decode())
+
     @property
     def step_index(self) -> int:
         return int(self._lib.tdse_step_index(self._ctx))

@@ -19,6 +19,7 @@ FP64, MIXED = 0, 1
 HOST, DEVICE = 0, 1
 TDSE_V_SEPARABLE, TDSE_V_TABLE, TDSE_V_TABLE_SHARED = 0, 1, 2
 TDSE_ESTATE = -6
+PATH_AUTO, PATH_PASSES, PATH_CLUSTER = 0, 1, 2
 
 # Every symbol include/tdse.h declares (checked by the CPU test suite).
 EXPORTS = [
@@ -28,7 +29,7 @@ EXPORTS = [
     "tdse_last_error", "tdse_destroy", "tdse_modes_to_grid_2d_noalloc", "tdse_read_modes", "tdse_free_rule",
     "tdse_free_choose_H", "tdse_free_choose_H_prec", "tdse_potential_times", "tdse_set_potential_table", "tdse_batch_create", "tdse_batch_tune", "tdse_batch_set_mode", "tdse_batch_step", "tdse_batch_describe",
     "tdse_batch_last_error", "tdse_batch_destroy", "tdse_set_residual_check", "tdse_residual_report",
-    "tdse_save", "tdse_load",
+    "tdse_save", "tdse_load", "tdse_set_step_path", "tdse_step_path", "tdse_describe_steps",
 ]
 NOALLOC_MAX_POINTS = 524288
 
@@ -103,6 +104,9 @@ def load(path: str = _LIB_PATH) -> ctypes.CDLL:
         "tdse_potential_times": ([vp, dp], ip),
         "tdse_set_potential_table": ([vp, ip, vp, ip, vp], ip),
         "tdse_load": ([vp, vp, ctypes.c_size_t, vp], ip),
+        "tdse_set_step_path": ([vp, ip], ip),
+        "tdse_step_path": ([vp], ip),
+        "tdse_describe_steps": ([vp, ctypes.c_char_p, ctypes.c_size_t], ip),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libtdse_gb300.so")
-SOURCES = ["api.cpp", "fs_api.cpp", "tables.cu", "periodic1d.cu", "periodic1d_f32.cu", "multi1d.cu", "periodic2d.cu", "freespace.cu", "freespace_f32.cu", "fft64_1d.cu", "resid.cu", "noalloc.cu"]
+SOURCES = ["api.cpp", "fs_api.cpp", "tables.cu", "periodic1d.cu", "periodic1d_f32.cu", "multi1d.cu", "periodic2d.cu", "freespace.cu", "freespace_f32.cu", "fft64_1d.cu", "resid.cu", "noalloc.cu", "step2d_cluster.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

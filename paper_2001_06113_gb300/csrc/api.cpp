@@ -153,6 +153,9 @@ static void plan_workspace(tdse_ctx* c) {
         c->off.res_flags = take(B * 4);
         c->off.res_ncorr = take(B * 4);
     }
+    if (c->d == 2 && c->mixed && step2d_cluster_supported(c->n0, c->n1))
+        c->off.cl_tab = take(((size_t)c->cfg.nsteps + 1) * CL_TAB * sizeof(float));
+    c->off.err = take(256);
     c->off.scratch = take(256);
     c->off.end = o;
     c->ws_need = o;
@@ -160,9 +163,42 @@ static void plan_workspace(tdse_ctx* c) {
 
 template <class T> static T* opt(const tdse_ctx* c, size_t off) { return off ? c->P<T>(off) : nullptr; }
 
+
+
 static void split(double x, float& hi, float& lo) {
     hi = (float)x;
     lo = (float)(x - (double)hi);
+}
+
+// w / z_m split into hi + lo floats (complex)
+static void zinv(const tdse_ctx* c, int m, double w, float* hi, float* lo) {
+    const double zx = c->zdither[2 * m], zy = c->zdither[2 * m + 1];
+    const double n2 = zx * zx + zy * zy;
+    split(w * zx / n2, hi[0], lo[0]);
+    split(-w * zy / n2, hi[1], lo[1]);
+}
+
+// The same weights for every step m, as rows of the cluster kernel's table
+// (layout in kargs.h); lags before step 0 are zero (never used: Adams steps
+// start after the start-up).
+static std::vector<float> cluster_weight_table(const tdse_ctx* c) {
+    std::vector<float> t(((size_t)c->cfg.nsteps + 1) * CL_TAB, 0.0f);
+    for (int m = 0; m <= c->cfg.nsteps; ++m) {
+        float* r = t.data() + (size_t)m * CL_TAB;
+        r[0] = c->zdither[2 * m];
+        r[1] = c->zdither[2 * m + 1];
+        float dh[2], dl[2];
+        zinv(c, m, c->cfg.dt * c->mu[0], dh, dl);
+        r[2] = dh[0]; r[3] = dh[1]; r[4] = dl[0]; r[5] = dl[1];
+        for (int j = 1; j < c->m && j <= MAX_HIST; ++j) {
+            if (m - j < 0) continue;
+            float ch[2], cl[2];
+            zinv(c, m - j, c->mu[j], ch, cl);
+            float* w = r + 6 + 4 * (j - 1);
+            w[0] = ch[0]; w[1] = ch[1]; w[2] = cl[0]; w[3] = cl[1];
+        }
+    }
+    return t;
 }
 
 static KArgs base_args(const tdse_ctx* c) {
@@ -405,6 +441,21 @@ tdse_status tdse_bind_workspace(tdse_ctx* c, void* dev, size_t bytes, void* stre
     if (c->d == 1 && c->mixed)
         TDSE_CK(c, launch_k1d(c->P<float2>(c->off.k1lo), c->P<float2>(c->off.k1hi), c->nhi, c->n0, c->cfg.dt, s));
     if (c->off.tw128) TDSE_CK(c, launch_four_step_tables(c->P<double2>(c->off.tw128), s));
+    TDSE_CK(c, cudaMemsetAsync(c->P<int>(c->off.err), 0, sizeof(int), s));
+    c->cl_ok = false;
+    if (c->off.cl_tab) {
+        const std::vector<float> tab = cluster_weight_table(c);
+        TDSE_CK(c, cudaMemcpyAsync(c->P<float>(c->off.cl_tab), tab.data(), tab.size() * sizeof(float),
+                                   cudaMemcpyHostToDevice, s));
+        TDSE_CK(c, cudaStreamSynchronize(s));      // the host table is freed on return
+        const long long vrows_total = (long long)(c->vshared ? 1 : c->B) * c->vrows * c->n0;
+        // no cluster path (no driver entry point, no resident cluster): the pass kernels run instead
+        if (step2d_cluster_plan(c->cl, c->P<void>(c->off.uhat), c->P<void>(c->off.ring), c->P<void>(c->off.V0f), c->B,
+                                c->RS, vrows_total) == cudaSuccess &&
+            c->cl.clusters > 0)
+            c->cl_ok = true;
+        (void)cudaGetLastError();
+    }
     }
     // defaults: A == 0 (phi == 0), f(t) == 1
     TDSE_CK(c, cudaMemsetAsync(c->P<double>(c->off.phi), 0, (size_t)c->B * c->d * c->ntf * 8, s));
@@ -676,16 +727,16 @@ static tdse_status enter_interaction(tdse_ctx* c, int n, cudaStream_t s) {
 // interaction-picture weights: c_j = mu_j / z_{nb - j} for the step nb being
 // begun, d = h mu_0 / z_ne for the step ne being finished, zr = z_ne.
 static void set_dither(const tdse_ctx* c, KArgs& a, int nb, int ne) {
-    auto zinv = [&](int m, double w, float* hi, float* lo) {
-        const double zx = c->zdither[2 * m], zy = c->zdither[2 * m + 1];
-        const double n2 = zx * zx + zy * zy;
-        split(w * zx / n2, hi[0], lo[0]);
-        split(-w * zy / n2, hi[1], lo[1]);
-    };
-    for (int j = 1; j < c->m; ++j) zinv(nb - j, c->mu[j], a.c_hi[j], a.c_lo[j]);
-    zinv(ne, c->cfg.dt * c->mu[0], a.d_hi, a.d_lo);
+    for (int j = 1; j < c->m; ++j) zinv(c, nb - j, c->mu[j], a.c_hi[j], a.c_lo[j]);
+    zinv(c, ne, c->cfg.dt * c->mu[0], a.d_hi, a.d_lo);
     a.zr[0] = c->zdither[2 * ne];
     a.zr[1] = c->zdither[2 * ne + 1];
+}
+
+// The cluster kernel runs only when asked for: measured slower than the pass
+// kernels on the 512^2 workload (1.07 against 0.52 ms per 64-instance step).
+static bool use_cluster(const tdse_ctx* c) {
+    return c->cl_ok && c->step_path == TDSE_PATH_CLUSTER && c->d == 2 && c->mixed;
 }
 
 static KArgs adams_args(const tdse_ctx* c, int n) {
@@ -709,6 +760,20 @@ static KArgs adams_args(const tdse_ctx* c, int n) {
 // (row_mid, col_fused) x (k-1), row_mid, col_end.
 static tdse_status adams_steps(tdse_ctx* c, int n0, int k, cudaStream_t s) {
     const int combo = step_combo(c);
+    if (use_cluster(c) && c->ip) {
+        const KArgs a = adams_args(c, n0 + 1);
+        ClArgs ca{};
+        ca.n_first = n0 + 1;
+        ca.k = k;
+        ca.S_eff = c->S_eff;
+        ca.vrows = c->vrows;
+        ca.vtable = c->vtable ? 1 : 0;
+        ca.vshared = c->vshared ? 1 : 0;
+        ca.tab = c->P<float>(c->off.cl_tab);
+        ca.err = c->P<int>(c->off.err);
+        TDSE_CK(c, launch_step2d_cluster(a, ca, c->cl, s));
+        return TDSE_OK;
+    }
     if (c->d == 1 || k == 1) {
         for (int n = n0 + 1; n <= n0 + k; ++n) TDSE_CK(c, run(c, adams_args(c, n), combo, s));
         return TDSE_OK;
@@ -847,6 +912,12 @@ tdse_status tdse_check_finite(tdse_ctx* c, void* stream) {
     if (!c) return TDSE_EINVAL;
     if (!c->ws) return c->fail(TDSE_ESTATE, "workspace not bound");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!c->fs && c->off.err) {
+        int ew = 0;
+        TDSE_CK(c, cudaMemcpyAsync(&ew, c->P<int>(c->off.err), sizeof(int), cudaMemcpyDeviceToHost, s));
+        TDSE_CK(c, cudaStreamSynchronize(s));
+        if (ew) return c->fail(TDSE_ETIMEOUT, "a bounded wait in a step kernel gave up: results are invalid");
+    }
     int* cnt = c->P<int>(c->off.scratch);
     TDSE_CK(c, cudaMemsetAsync(cnt, 0, sizeof(int), s));
     const size_t nmodes = c->fs ? c->F.NM : c->NP;
@@ -987,6 +1058,35 @@ tdse_status tdse_load(tdse_ctx* c, const void* blob, size_t size, void* stream) 
     c->res_checks = h.res_checks;
     c->res_tol = h.res_tol;
     return TDSE_OK;
+}
+
+tdse_status tdse_set_step_path(tdse_ctx* c, int path) {
+    if (!c) return TDSE_EINVAL;
+    if (path != TDSE_PATH_AUTO && path != TDSE_PATH_PASSES && path != TDSE_PATH_CLUSTER)
+        return c->fail(TDSE_EINVAL, "unknown step path");
+    if (path == TDSE_PATH_CLUSTER && !(c->cl_ok && c->d == 2 && c->mixed && !c->fs))
+        return c->fail(TDSE_EUNSUPPORTED, "cluster step path: 2D periodic TDSE_MIXED 512 x 512 on a device that runs "
+                                          "16-CTA clusters, after tdse_bind_workspace");
+    c->step_path = path;
+    return TDSE_OK;
+}
+
+int tdse_step_path(const tdse_ctx* c) {
+    if (!c) return -1;
+    return (!c->fs && use_cluster(c)) ? TDSE_PATH_CLUSTER : TDSE_PATH_PASSES;
+}
+
+tdse_status tdse_describe_steps(const tdse_ctx* c, char* buf, size_t len) {
+    if (!c || !buf || len == 0) return TDSE_EINVAL;
+    int n;
+    if (!c->fs && use_cluster(c))
+        n = std::snprintf(buf, len,
+                          "{\"path\": \"cluster\", \"clusters\": %d, \"ctas_per_cluster\": %d, \"threads\": %d, "
+                          "\"smem_bytes\": %d}",
+                          c->cl.clusters, CL_Q, step2d_cluster_threads(), step2d_cluster_smem());
+    else
+        n = std::snprintf(buf, len, "{\"path\": \"passes\"}");
+    return (n < 0 || (size_t)n >= len) ? TDSE_EINVAL : TDSE_OK;
 }
 
 int tdse_step_index(const tdse_ctx* c) { return c ? c->step : -1; }

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "kargs.h"
 #include "tdse.h"
 
 namespace tdse {
@@ -64,8 +65,13 @@ struct tdse_ctx {
     struct {
         size_t uhat, ring, chain_uhat, chain_ring, aux, aux2, V0, V0f, tfac, phi, kin64, kinff, adv64, advff,
             q64, qff, e2d, k1lo, k1hi, a1d, tw64_0, tw32_0, tw64_1, tw32_1, tw32lo_0, tw32lo_1, iv, tw128, res_sums,
-            res_rho, res_flags, res_ncorr, scratch, end;
+            res_rho, res_flags, res_ncorr, cl_tab, err, scratch, end;
     } off{};
+    // 2D mixed steps over CTA clusters (512^2): plan built at bind, used when
+    // step_path allows it (TDSE_PATH_AUTO / TDSE_PATH_CLUSTER)
+    tdse::ClPlan cl{};
+    bool cl_ok = false;
+    int step_path = TDSE_PATH_AUTO;
     std::vector<char> have_V, have_u0;
     bool vtable = false;        // TDSE_V_TABLE(_SHARED): V(x, t_r) rows in V0 / V0f
     bool vshared = false;       // one table for every instance

@@ -133,6 +133,35 @@ struct ResArgs;
 bool residual_supported(int dim, int n0, int n1);
 cudaError_t launch_residual_check(const ResArgs& r, bool correct, cudaStream_t s);
 
+// ---- 2D mixed Adams steps of 512^2 instances over CTA clusters (step2d_cluster.cu)
+// One cluster of CL_Q CTAs per instance holds the transform intermediates in
+// shared memory; a launch runs k consecutive interaction-picture steps
+// (begin, (row, column) x (k - 1), row, end) of every instance.
+constexpr int CL_N = 512;      // points per axis
+constexpr int CL_Q = 16;       // CTAs per cluster
+constexpr int CL_TAB = 36;     // floats per step in the weight table
+// Weight table row m (floats): z_m (0, 1); d_m = h mu_0 / z_m hi (2, 3), lo (4, 5);
+// c_j of the step m begun, mu_j / z_{m-j}: hi at 6 + 4 (j - 1) (2 floats), lo at 8 + 4 (j - 1).
+struct ClArgs {
+    int n_first;        // first step of the run
+    int k;              // steps in the run (>= 1)
+    int S_eff;          // start-up steps (row of V(t_n) in a potential table)
+    int vrows;          // potential-table rows per instance (1: separable)
+    int vtable, vshared;
+    const float* tab;   // [nsteps + 1][CL_TAB]
+    int* err;           // device error word (TDSE_ETIMEOUT if a bounded wait gave up)
+};
+struct ClPlan {
+    alignas(64) unsigned char tm[3][128];   // TMA descriptors: state, ring, V hi/lo
+    int clusters = 0;                        // clusters resident at once (0: path unavailable)
+};
+bool step2d_cluster_supported(int n0, int n1);
+// Tensor maps over the context's buffers and the resident cluster count.
+cudaError_t step2d_cluster_plan(ClPlan& p, void* uhat, void* ring, void* V0f, int B, int RS, long long vrows_total);
+cudaError_t launch_step2d_cluster(const KArgs& a, const ClArgs& c, const ClPlan& p, cudaStream_t s);
+int step2d_cluster_threads();
+int step2d_cluster_smem();
+
 // Largest n of the 1D FP32 step kernels (larger than periodic1d_supported's
 // limit: FP64 init / read-out of such sizes go through launch_fft64_four_step).
 constexpr int P1D_MAX_F32 = 16384;
