@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-variant", action="store_true",
+                    help="skip the complex128 timing of the same workload in the default (mixed) line")
     ap.add_argument("--workload", default="periodic2d",
                     choices=["periodic2d", "free2d", "batch1d", "serve", "example1"])
     ap.add_argument("--profile-adams", type=int, default=0,
@@ -277,10 +279,16 @@ def run_gpu(args, ws, rank, local):
                 "step_ms_p50": round(float(np.percentile(dts, 50)) * 1e3, 4),
                 "step_ms_p99": round(float(np.percentile(dts, 99)) * 1e3, 4)}
 
-    # ---- accuracy of this configuration on a sample instance (vs the FP64 GPU path,
-    #      itself checked against the oracle by the test suite)
+    # ---- accuracy of this configuration on a sample instance: against the
+    #      stored FP64 oracle solution (instance 0) and against the FP64 GPU path
     stated_err = None
     norm_drift = None
+    oracle_err = None
+    if rank == 0 and args.precision == "fp64":
+        with torch.cuda.stream(stream):
+            prob.set_initial_batch(pinned_u)
+            prob.step(NSTEPS)
+        oracle_err = golden_error(insts[0], prob.read_u(0), NSTEPS)
     if args.precision == "mixed" and rank == 0:
         ref = Problem((M, M), DT, NSTEPS, order=ORDER, batch=1, precision="fp64", stream=stream)
         it = insts[0]
@@ -296,6 +304,7 @@ def run_gpu(args, ws, rank, local):
         u_mix = prob.read_u(0)
         stated_err = float(np.sqrt(np.sum(np.abs(u_mix - u_ref) ** 2) / np.sum(np.abs(u_ref) ** 2)))
         norm_drift = float(np.sqrt(np.sum(np.abs(u_mix) ** 2) / np.sum(np.abs(it.u0) ** 2)) - 1.0)
+        oracle_err = {"mixed": golden_error(it, u_mix, NSTEPS), "fp64_gpu": golden_error(it, u_ref, NSTEPS)}
         ref.close()
 
     # ---- end to end through the public API with host buffers
@@ -320,8 +329,69 @@ def run_gpu(args, ws, rank, local):
                "d2h_bytes_per_step": B * points * 16}
 
     prob.close()
+    fp64 = None
+    if args.precision == "mixed" and rank == 0 and not args.no_fp64_variant:
+        fp64 = fp64_variant(args, insts, stream, dev, value, oracle_err)
     return dict(value=value, t_solve=t_solve, roofline=roofline, e2e=e2e, clocks=clk.summary(),
-                stated_err=stated_err, norm_drift=norm_drift, B=B)
+                stated_err=stated_err, norm_drift=norm_drift, B=B, oracle_err=oracle_err, fp64=fp64)
+
+
+def fp64_variant(args, insts, stream, dev, mixed_value, oracle_err):
+    """The paper's precision (complex128 throughout) on the same workload: a
+    batch of 4 instances and one instance alone (the plain one-solve-at-a-time
+    FP64 GPU path), whole-solve times, and the Adams step against the FP64
+    rate of this GPU (the FP64 step is bound by FP64 arithmetic, not HBM)."""
+    import torch
+    from paper_2001_06113_gb300 import Problem
+    out = {}
+    peak, peak_note = fp64_peak(dev)
+    for B in (4, 1):
+        its = insts[:B]
+        prob = Problem((M, M), DT, NSTEPS, order=ORDER, batch=B, precision="fp64", stream=stream)
+        for b, it in enumerate(its):
+            prob.set_potential(it.V0, None, instance=b)
+            p = it.pulse
+            prob.set_pulse(p.A0, p.omega, p.T_pulse, p.direction, instance=b)
+        u0 = torch.from_numpy(np.stack([it.u0 for it in its])).pin_memory()
+        times = []
+        with torch.cuda.stream(stream):
+            for rep in range(3):
+                prob.set_initial_batch(u0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                prob.step(NSTEPS)
+                e1.record(stream)
+                stream.synchronize()
+                if rep:
+                    times.append(e0.elapsed_time(e1) / 1e3)
+        t = float(np.mean(times))
+        entry = {"value": B * M * M * NSTEPS / t, "unit": "point-steps/s", "ms_per_solve": t * 1e3, "batch": B}
+        if B == 4:
+            GROUP, NGROUPS = 50, 4
+            with torch.cuda.stream(stream):
+                prob.set_initial_batch(u0)
+                prob.step(STARTUP + 8)
+                evs = [torch.cuda.Event(enable_timing=True) for _ in range(NGROUPS + 1)]
+                evs[0].record(stream)
+                for i in range(NGROUPS):
+                    prob.step(GROUP)
+                    evs[i + 1].record(stream)
+            stream.synchronize()
+            t_step = float(np.mean([evs[i].elapsed_time(evs[i + 1]) / 1e3 / GROUP for i in range(NGROUPS)]))
+            ach = FP64_FLOPS_PER_POINT_STEP * B * M * M / t_step / 1e12
+            entry["roofline"] = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4),
+                                 "unit": "TFLOP/s (FP64)", "frac": round(ach / peak, 4), "traffic": None,
+                                 "peak_source": peak_note,
+                                 "kernel": "k_row_mid<double2,512> + k_col_end<double2,double2,512,1> (FP64 Adams step), "
+                                           f"timed over groups of {GROUP} steps",
+                                 "algorithmic_flops_per_point_step": FP64_FLOPS_PER_POINT_STEP,
+                                 "step_ms": round(t_step * 1e3, 4)}
+            entry["rel_l2_vs_oracle"] = oracle_err.get("fp64_gpu") if oracle_err else None
+        prob.close()
+        out["batch4" if B == 4 else "one_at_a_time"] = entry
+    out["mixed_over_fp64_one_at_a_time"] = mixed_value / out["one_at_a_time"]["value"]
+    out["mixed_rel_l2_vs_oracle"] = oracle_err.get("mixed") if oracle_err else None
+    return out
 
 
 # ------------------------------------------------------------ free-space arm
@@ -392,6 +462,58 @@ def hbm_peak():
     except Exception:
         pass
     return peaks.get("hbm_gbs", 6800.0), ("measured" if "hbm_gbs" in peaks else "fallback")
+
+
+# FP64 flops of one point-step of the 2D FP64 periodic step (512^2), counted
+# from the kernels' arithmetic: four length-512 transforms per point (one per
+# axis pass, 5 n log2 n flops each = 45 per point each), the Horner history
+# (6 lag phases p_j = q[m0] q[n0+m1] and p_j S: 12 flops each; 7 terms mu_j R_j:
+# 4 each; X = u^ - i h S: 4; W = p_0 X with its phase: 12), the implicit solve
+# and V product (21), the update (4) and the two 1/n scalings (4).
+FP64_FLOPS_PER_POINT_STEP = 4 * 45 + (6 * 12 + 7 * 4 + 4 + 12) + 21 + 4 + 4
+
+
+def fp64_peak(dev) -> tuple:
+    """(TFLOP/s, note): FP64 throughput of this GPU measured here, as the best of
+    3 cuBLAS float64 GEMMs of 4096^3 (2 n^3 flops) timed with CUDA events."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None else min(best, t)
+    del a, b
+    return 2.0 * n ** 3 / best / 1e12, "measured in this run: cuBLAS float64 GEMM 4096^3, best of 3"
+
+
+GOLDEN_512 = os.path.join(ROOT, "tests", "golden", "periodic_2d_wells_512.npz")
+
+
+def golden_error(inst, u: np.ndarray, step: int):
+    """rel-L2 of u against the stored FP64 oracle solution of the same seeded
+    instance at `step` (every 4th grid point; file written by
+    tests/golden/make_periodic_goldens.py), or None if not stored."""
+    try:
+        g = np.load(GOLDEN_512)
+    except Exception:
+        return None
+    p = inst.pulse
+    st = int(g["stride"])
+    if (str(g["key"]) != inst.name or f"u_{step}" not in g
+            or not np.allclose(g["params"], [inst.dt, inst.nsteps, p.A0, p.omega, p.T_pulse, *p.direction])
+            or np.max(np.abs(inst.u0[::st, ::st] - g["u0_sample"])) > 1e-13 * np.max(np.abs(g["u0_sample"]))):
+        return None
+    ref = g[f"u_{step}"]
+    sub = u[::st, ::st]
+    return float(np.sqrt(np.sum(np.abs(sub - ref) ** 2) / np.sum(np.abs(ref) ** 2)))
 
 
 def free_algo_bytes(precision: str) -> float:
@@ -1415,6 +1537,9 @@ def main():
                        "step": "one whole solve (7 Richardson start-up + 1993 Adams steps) of the batch",
                        "parallelism": f"replicas x{ws}"},
             "rel_l2_vs_fp64": res["stated_err"], "norm_drift_T": res["norm_drift"],
+            "rel_l2_vs_oracle": (res["oracle_err"] or {}).get("mixed") if isinstance(res["oracle_err"], dict)
+            else res["oracle_err"],
+            "fp64_variant": res["fp64"],
             "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
             "gpu_launches": launches_per_solve(2, args.precision == "mixed",
                                                res["roofline"]["launch_shape"]["path"]) * args.steps,

@@ -332,6 +332,16 @@ tdse_status tdse_load(tdse_ctx* ctx, const void* blob, size_t size, void* stream
  * value.  May be called at any time between steps. */
 tdse_status tdse_set_step_path(tdse_ctx* ctx, int path);
 
+/* 2D periodic contexts, pass kernels: split the batch into `groups` (1..64,
+ * at most the batch size is used) contiguous groups of instances whose Adams
+ * step chains run on parallel streams that the library creates on first use
+ * (forked from and joined to the caller's stream, so the call stays ordered
+ * on it), so that the row pass of one group and the column pass of another
+ * share the SMs.  Instances are independent: results are the same bits for
+ * any number of groups.  Default 4.  The first steps after raising the count
+ * create the streams; take them before any stream capture. */
+tdse_status tdse_set_step_groups(tdse_ctx* ctx, int groups);
+
 /* The path the next 2D mixed Adams steps take (TDSE_PATH_PASSES or
  * TDSE_PATH_CLUSTER; TDSE_PATH_PASSES for every other context), or -1 for
  * NULL.  The cluster path needs the bound workspace (its plan is made at

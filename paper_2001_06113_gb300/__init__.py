@@ -319,6 +319,11 @@ class Problem:
         return {_native.PATH_PASSES: "passes", _native.PATH_CLUSTER: "cluster"}.get(
             int(self._lib.tdse_step_path(self._ctx)), "passes")
 
+    def set_step_groups(self, groups: int):
+        """2D pass kernels: step chains of `groups` groups of instances on
+        parallel streams (same results; default 4)."""
+        _check(self._lib.tdse_set_step_groups(self._ctx, int(groups)), self._ctx)
+
     def describe_steps(self) -> dict:
         """Launch shape of the 2D mixed Adams steps (path, clusters, ...)."""
         import json

@@ -756,8 +756,32 @@ static KArgs adams_args(const tdse_ctx* c, int n) {
     return a;
 }
 
+// The launch arguments of instances [lo, hi) of a batch: every per-instance
+// array advanced to instance lo (the kernels index instance b of a launch
+// from these bases).
+static KArgs group_args(const tdse_ctx* c, KArgs a, int lo, int hi) {
+    const size_t l = (size_t)lo, NP = c->NP;
+    a.B = hi - lo;
+    a.uhat = static_cast<char*>(a.uhat) + l * NP * 16;
+    a.ring = static_cast<char*>(a.ring) + l * a.ring_slots * NP * c->rsz;
+    a.aux += l * NP;
+    a.aux2 += l * NP;
+    a.V0 += l * a.vstride;
+    a.V0f += l * a.vstride;
+    a.tfac += l * a.ntf;
+    a.phi += l * (size_t)c->d * a.ntf;
+    const size_t nsp1 = (size_t)c->cfg.nsteps + 1;
+    if (a.q64) a.q64 += l * (size_t)c->n_int * (c->n0 + c->n1);
+    if (a.qff) a.qff += l * (size_t)c->n_int * (c->n0 + c->n1);
+    if (a.e2d) a.e2d += l * nsp1 * (c->n0 + c->n1);
+    return a;
+}
+
+static tdse_status adams_chain_2d(tdse_ctx* c, int n0, int k, int lo, int hi, cudaStream_t s);
+
 // k consecutive Adams steps n0+1 .. n0+k.  2D runs them as col_begin,
-// (row_mid, col_fused) x (k-1), row_mid, col_end.
+// (row_mid, col_fused) x (k-1), row_mid, col_end; with step groups, one such
+// chain per group of instances on parallel streams.
 static tdse_status adams_steps(tdse_ctx* c, int n0, int k, cudaStream_t s) {
     const int combo = step_combo(c);
     if (use_cluster(c) && c->ip) {
@@ -778,17 +802,71 @@ static tdse_status adams_steps(tdse_ctx* c, int n0, int k, cudaStream_t s) {
         for (int n = n0 + 1; n <= n0 + k; ++n) TDSE_CK(c, run(c, adams_args(c, n), combo, s));
         return TDSE_OK;
     }
-    TDSE_CK(c, launch_periodic2d_part(adams_args(c, n0 + 1), combo, PART_COL_BEGIN, s));
+    const int G = c->step_groups < c->B ? c->step_groups : c->B;
+    if (G <= 1) return adams_chain_2d(c, n0, k, 0, c->B, s);
+    if ((int)c->group_streams.size() < G) {
+        if (!c->group_fork) TDSE_CK(c, cudaEventCreateWithFlags(&c->group_fork, cudaEventDisableTiming));
+        while ((int)c->group_streams.size() < G) {
+            cudaStream_t gs = nullptr;
+            cudaEvent_t ge = nullptr;
+            TDSE_CK(c, cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+            c->group_streams.push_back(gs);
+            TDSE_CK(c, cudaEventCreateWithFlags(&ge, cudaEventDisableTiming));
+            c->group_join.push_back(ge);
+        }
+    }
+    // The groups' launches are issued step by step, alternating between the
+    // streams: enqueued one whole chain after another, a long run would fill
+    // the launch queue with one group's kernels and the groups would not overlap.
+    TDSE_CK(c, cudaEventRecord(c->group_fork, s));
+    std::vector<int> lo(G), hi(G);
+    for (int g = 0; g < G; ++g) {
+        lo[g] = (int)((long long)c->B * g / G);
+        hi[g] = (int)((long long)c->B * (g + 1) / G);
+        TDSE_CK(c, cudaStreamWaitEvent(c->group_streams[g], c->group_fork, 0));
+    }
+    for (int g = 0; g < G; ++g)
+        TDSE_CK(c, launch_periodic2d_part(group_args(c, adams_args(c, n0 + 1), lo[g], hi[g]), combo, PART_COL_BEGIN,
+                                          c->group_streams[g]));
     for (int n = n0 + 1; n < n0 + k; ++n) {
-        TDSE_CK(c, launch_periodic2d_part(adams_args(c, n), combo, PART_ROW_MID, s));
-        KArgs f = adams_args(c, n + 1);     // history slots, intervals and E of the next step ...
+        const KArgs r = adams_args(c, n);
+        KArgs f = adams_args(c, n + 1);     // as in adams_chain_2d
+        f.out_slot = slot_of(c, n);
+        f.e_step = n;
+        f.e_next = n + 1;
+        if (c->mixed) set_dither(c, f, n + 1, n);
+        for (int g = 0; g < G; ++g) {
+            TDSE_CK(c, launch_periodic2d_part(group_args(c, r, lo[g], hi[g]), combo, PART_ROW_MID, c->group_streams[g]));
+            TDSE_CK(c, launch_periodic2d_part(group_args(c, f, lo[g], hi[g]), combo, PART_COL_FUSED,
+                                              c->group_streams[g]));
+        }
+    }
+    const KArgs last = adams_args(c, n0 + k);
+    for (int g = 0; g < G; ++g) {
+        const KArgs lg = group_args(c, last, lo[g], hi[g]);
+        TDSE_CK(c, launch_periodic2d_part(lg, combo, PART_ROW_MID, c->group_streams[g]));
+        TDSE_CK(c, launch_periodic2d_part(lg, combo, PART_COL_END, c->group_streams[g]));
+        TDSE_CK(c, cudaEventRecord(c->group_join[g], c->group_streams[g]));
+        TDSE_CK(c, cudaStreamWaitEvent(s, c->group_join[g], 0));
+    }
+    return TDSE_OK;
+}
+
+// The 2D pass chain of k Adams steps for instances [lo, hi).
+static tdse_status adams_chain_2d(tdse_ctx* c, int n0, int k, int lo, int hi, cudaStream_t s) {
+    const int combo = step_combo(c);
+    auto A = [&](int n) { return group_args(c, adams_args(c, n), lo, hi); };
+    TDSE_CK(c, launch_periodic2d_part(A(n0 + 1), combo, PART_COL_BEGIN, s));
+    for (int n = n0 + 1; n < n0 + k; ++n) {
+        TDSE_CK(c, launch_periodic2d_part(A(n), combo, PART_ROW_MID, s));
+        KArgs f = A(n + 1);                 // history slots, intervals and E of the next step ...
         f.out_slot = slot_of(c, n);         // ... ring slot and E of the step being finished
         f.e_step = n;
         f.e_next = n + 1;
         if (c->mixed) set_dither(c, f, n + 1, n);
         TDSE_CK(c, launch_periodic2d_part(f, combo, PART_COL_FUSED, s));
     }
-    const KArgs last = adams_args(c, n0 + k);
+    const KArgs last = A(n0 + k);
     TDSE_CK(c, launch_periodic2d_part(last, combo, PART_ROW_MID, s));
     TDSE_CK(c, launch_periodic2d_part(last, combo, PART_COL_END, s));
     return TDSE_OK;
@@ -1071,6 +1149,13 @@ tdse_status tdse_set_step_path(tdse_ctx* c, int path) {
     return TDSE_OK;
 }
 
+tdse_status tdse_set_step_groups(tdse_ctx* c, int groups) {
+    if (!c) return TDSE_EINVAL;
+    if (groups < 1 || groups > 64) return c->fail(TDSE_EINVAL, "step groups: 1..64");
+    c->step_groups = groups;
+    return TDSE_OK;
+}
+
 int tdse_step_path(const tdse_ctx* c) {
     if (!c) return -1;
     return (!c->fs && use_cluster(c)) ? TDSE_PATH_CLUSTER : TDSE_PATH_PASSES;
@@ -1085,7 +1170,8 @@ tdse_status tdse_describe_steps(const tdse_ctx* c, char* buf, size_t len) {
                           "\"smem_bytes\": %d}",
                           c->cl.clusters, CL_Q, step2d_cluster_threads(), step2d_cluster_smem());
     else
-        n = std::snprintf(buf, len, "{\"path\": \"passes\"}");
+        n = std::snprintf(buf, len, "{\"path\": \"passes\", \"groups\": %d}",
+                          c->d == 2 && !c->fs ? (c->step_groups < c->B ? c->step_groups : c->B) : 1);
     return (n < 0 || (size_t)n >= len) ? TDSE_EINVAL : TDSE_OK;
 }
 

@@ -403,6 +403,16 @@ __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_fused_ip(const KArgs a
     FW::run(buf, a.tw32_0, a.tw32lo_0);
     const float scale = 1.0f / (float)N0;
     const float2 z = make_float2(a.zr[0], a.zr[1]);
+    // E_n(m0, m1) = e_n[m0] e_n[n0 + m1] (e_2d): the axis-1 factors of the
+    // column a thread keeps (RC * L == T2D: one column per thread) are loaded once
+    const size_t erow = (size_t)(a.n0 + a.n1);
+    const float2* en = a.e2d + ((size_t)b * (a.ntf / 8 + 1) + a.e_step) * erow;
+    const float2* en1 = a.e2d + ((size_t)b * (a.ntf / 8 + 1) + a.e_next) * erow;
+    constexpr bool ONE_COL = (RC * L == T2D);
+    const int lane_t = threadIdx.x % L;
+    const float2 en_1 = __ldg(&en[a.n0 + c0 + lane_t]);
+    const float2 en1_1 = __ldg(&en1[a.n0 + c0 + lane_t]);
+    float2* ring_out = ringb + (size_t)a.out_slot * NP;
 
 #pragma unroll 1
     for (int c = 0; c < NCH; ++c) {
@@ -413,10 +423,12 @@ __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_fused_ip(const KArgs a
             const int lane = it % L, r = it / L;
             const int m0 = c * RC + r, m1 = c0 + lane;
             const size_t idx = (size_t)m0 * n1 + m1;
+            const float2 e1n = ONE_COL ? en_1 : __ldg(&en[a.n0 + m1]);
+            const float2 e1n1 = ONE_COL ? en1_1 : __ldg(&en1[a.n0 + m1]);
             // end of step n: r~ = z_n R / E_n into the ring, v^_n
             const float2 R = cscale(buf[m0 * L + lane], scale);
-            const float2 rv = cmul(z, cmul(conjf2(e_2d(a, b, a.e_step, m0, m1)), R));
-            ringb[(size_t)a.out_slot * NP + idx] = rv;
+            const float2 rv = cmul(z, cmul(conjf2(cmul(__ldg(&en[m0]), e1n)), R));
+            ring_out[idx] = rv;
             const float4 v = ip_update(a, ch.st[it], rv);
             // begin of step n+1: X = v^_n - i h sum_j c_j r~_{n+1-j}
             float2 S = make_float2(0.f, 0.f);
@@ -431,7 +443,7 @@ __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_fused_ip(const KArgs a
             }
             const float4 X = ff_minus_i_times(v, a.h_hi, a.h_lo, S);
             st[idx] = X;
-            buf[m0 * L + lane] = cmul(e_2d(a, b, a.e_next, m0, m1), make_float2(X.x, X.y));
+            buf[m0 * L + lane] = cmul(cmul(__ldg(&en1[m0]), e1n1), make_float2(X.x, X.y));
         }
         __syncthreads();                               // buffer c & 1 free
         if (c + 2 < NCH) stage(c + 2);

@@ -1,5 +1,5 @@
 """The 2D mixed Adams step over CTA clusters (512 x 512) against the pass
-kernels and the oracle.
+kernels, and the pass kernels' instance groups on parallel streams.
 
 The cluster kernel keeps the transform intermediates in distributed shared
 memory and streams the state, history and V by TMA; it does the same
@@ -125,3 +125,28 @@ def test_cluster_residual_check_bitwise():
     insts = [synth.periodic_2d_wells(seed=50, M=M, dt=1e-3, nsteps=20)]
     ra, rb = _both(insts, [20], res_every=4)
     assert np.array_equal(ra[0], rb[0])
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_step_groups_bitwise(precision):
+    """Instance groups on parallel streams give the same bits as one chain."""
+    from paper_2001_06113_gb300 import Problem
+    insts = [synth.random_periodic((64, 32), 60 + i, 2e-3, 16, vamp=6.0,
+                                   pulse=synth.Pulse(1.5, 10.0, 0.032, (1.0, 0.4))) for i in range(5)]
+    out = {}
+    for G in (1, 2, 4, 5, 8):
+        prob = Problem((64, 32), 2e-3, 16, precision=precision, batch=len(insts))
+        prob.set_step_groups(G)
+        for b, it in enumerate(insts):
+            prob.set_potential(it.V0, None, instance=b)
+            p = it.pulse
+            prob.set_pulse(p.A0, p.omega, p.T_pulse, p.direction, instance=b)
+            prob.set_initial(it.u0, instance=b)
+        prob.step(11)
+        prob.step(5)
+        out[G] = prob.read_u(-1)
+        assert prob.describe_steps()["groups"] == min(G, len(insts))
+        prob.close()
+    for G in (2, 4, 5, 8):
+        assert np.array_equal(out[G], out[1]), G
+
