@@ -189,8 +189,11 @@ def launches_per_solve(dim: int, mixed: bool, path: str = "passes") -> int:
 # from the ncu capture of the 512^2 mixed workload at batch 8 (summarised under
 # profiles/); traffic scales with the number of instances.  None = not captured
 # for the current kernels.
-TRAFFIC_BYTES_PER_POINT_STEP = {("mixed", "passes"): (151.20896e6 + 29.985792e6 + 33.609216e6 + 37.632e6)
-                                / (8 * 512 * 512)}
+TRAFFIC_BYTES_PER_POINT_STEP = {("mixed", "passes"): 72.143 + 16.105}
+TRAFFIC_NOTE = {("mixed", "passes"): "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_col_fused_ip<512> + "
+                "k_row_mid<float2,512>, batch 8 in 4 groups (2 instances per launch), scaled by points: reads "
+                "72.1 + 16.1 B per point-step; the state, history and intermediate writes (40 B) stayed in L2 "
+                "within that capture (profiles/step2d_512x512_mixed_fused.md)"}
 
 
 def run_gpu(args, ws, rank, local):
@@ -272,6 +275,7 @@ def run_gpu(args, ws, rank, local):
              "passes": "k_row_mid + k_col_fused_ip" if args.precision == "mixed" else "k_row_mid + k_col_end (FP64)"}
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "traffic_unit": "bytes per step (all instances)",
+                "traffic_note": TRAFFIC_NOTE.get((args.precision, shape["path"])),
                 "peak_source": peak_src,
                 "kernel": f"2D Adams step operator: {kname[shape['path']]}, timed over groups of {GROUP} steps",
                 "launch_shape": shape,
