@@ -70,7 +70,10 @@ enum { TDSE_PATH_AUTO = 0, TDSE_PATH_PASSES = 1, TDSE_PATH_CLUSTER = 2 };
 
 /*
  * Problem configuration.
- *   dim        1 or 2.
+ *   dim        1, 2 or 3 (3: periodic only; grid n[0] x n[1] x n_z, arrays
+ *              row-major [n0][n1][n_z], axis 2 contiguous; powers of two,
+ *              axes 0 and 2 in 8..1024, axis 1 in 8..256, at most 2^24
+ *              points; no FP64 residual check).
  *   bc         TDSE_PERIODIC: domain [-pi,pi]^dim, Fourier modes (Sec. 2).
  *              TDSE_FREE: free space, data supported in [-1,1]^dim, modes on
  *              the deformed contour Gamma (Sec. 3-4).
@@ -135,6 +138,9 @@ typedef struct {
     double H;
     /* potential form (both boundary conditions), appended last */
     int potential;
+    /* dim = 3 (periodic only): grid points along axis 2; n[0], n[1] are
+     * axes 0 and 1.  Ignored for dim < 3.  Appended last. */
+    int n_z;
 } tdse_config;
 
 /* Vector potential callback: writes A(t) (dim components) to A_out. */

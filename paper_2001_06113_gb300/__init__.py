@@ -63,6 +63,7 @@ def _config(shape, dt, nsteps, order, batch, precision, startup_steps, bc, nu, H
         cfg.H = float(H)
     cfg.n[0] = shape[0]
     cfg.n[1] = shape[1] if len(shape) > 1 else 1
+    cfg.n_z = shape[2] if len(shape) > 2 else 1
     cfg.batch = int(batch)
     cfg.dt = float(dt)
     cfg.nsteps = int(nsteps)
@@ -194,7 +195,7 @@ class Problem:
         self.set_potential_table(np.stack([np.asarray(Vt(float(tt)), dtype=np.float64) for tt in t]), instance)
 
     def set_pulse(self, A0: float, omega: float, T_pulse: float, direction, instance: int = -1):
-        d = (ctypes.c_double * 2)(*(list(direction) + [0.0, 0.0])[:2])
+        d = (ctypes.c_double * 3)(*(list(direction) + [0.0, 0.0, 0.0])[:3])
         _check(self._lib.tdse_set_pulse(self._ctx, instance, A0, omega, T_pulse, d, _stream_handle(self._stream)),
                self._ctx)
 

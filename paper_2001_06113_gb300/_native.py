@@ -51,6 +51,7 @@ class TdseConfig(ctypes.Structure):
         ("n_r", ctypes.c_int),
         ("H", ctypes.c_double),
         ("potential", ctypes.c_int),
+        ("n_z", ctypes.c_int),
     ]
 
 

@@ -133,18 +133,21 @@ static void plan_workspace(tdse_ctx* c) {
         }
     } else {
         if (c->mixed) {
-            c->off.qff = take(B * (size_t)c->n_int * (c->n0 + c->n1) * 16);
-            c->off.e2d = take(B * nsp1 * (c->n0 + c->n1) * 8);
+            c->off.qff = take(B * (size_t)c->n_int * c->ntab * 16);
+            c->off.e2d = take(B * nsp1 * c->ntab * 8);
         } else {
-            c->off.q64 = take(B * (size_t)c->n_int * (c->n0 + c->n1) * 16);
+            c->off.q64 = take(B * (size_t)c->n_int * c->ntab * 16);
         }
     }
     c->off.tw64_0 = take((size_t)c->n0 * 16);
     c->off.tw32_0 = take((size_t)c->n0 * 8);
-    c->off.tw64_1 = take((size_t)(c->d == 2 ? c->n1 : 1) * 16);
-    c->off.tw32_1 = take((size_t)(c->d == 2 ? c->n1 : 1) * 8);
+    c->off.tw64_1 = take((size_t)(c->d >= 2 ? c->n1 : 1) * 16);
+    c->off.tw32_1 = take((size_t)(c->d >= 2 ? c->n1 : 1) * 8);
+    c->off.tw64_2 = take((size_t)(c->d == 3 ? c->n2 : 1) * 16);
+    c->off.tw32_2 = take((size_t)(c->d == 3 ? c->n2 : 1) * 8);
+    c->off.tw32lo_2 = take((size_t)(c->d == 3 ? c->n2 : 1) * 8);
     c->off.tw32lo_0 = take((size_t)c->n0 * 8);
-    c->off.tw32lo_1 = take((size_t)(c->d == 2 ? c->n1 : 1) * 8);
+    c->off.tw32lo_1 = take((size_t)(c->d >= 2 ? c->n1 : 1) * 8);
     c->off.iv = take((size_t)c->n_int * sizeof(int2));
     c->off.tw128 = c->d == 1 && c->n0 > 8192 ? take(128 * 16) : 0;
     if (c->mixed) {
@@ -206,6 +209,9 @@ static KArgs base_args(const tdse_ctx* c) {
     a.B = c->B;
     a.n0 = c->n0;
     a.n1 = c->n1;
+    a.tn0 = c->n0;
+    a.tn1 = c->d >= 2 ? c->n1 : 1;
+    a.tn2 = c->d == 3 ? c->n2 : 0;
     a.uhat = c->P<void>(c->off.uhat);
     a.ring = c->P<void>(c->off.ring);
     a.ring_slots = c->RS;
@@ -238,6 +244,9 @@ static KArgs base_args(const tdse_ctx* c) {
     a.tw32_1 = c->P<float2>(c->off.tw32_1);
     a.tw32lo_0 = c->P<float2>(c->off.tw32lo_0);
     a.tw32lo_1 = c->P<float2>(c->off.tw32lo_1);
+    a.tw64_2 = c->P<double2>(c->off.tw64_2);
+    a.tw32_2 = c->P<float2>(c->off.tw32_2);
+    a.tw32lo_2 = c->P<float2>(c->off.tw32lo_2);
     return a;
 }
 
@@ -265,6 +274,7 @@ static int step_combo(const tdse_ctx* c) { return c->cfg.precision == TDSE_MIXED
 static int f64_combo(const tdse_ctx* c) { return c->cfg.precision == TDSE_MIXED ? COMBO_F64_R32 : COMBO_F64; }
 
 static cudaError_t run(const tdse_ctx* c, const KArgs& a, int combo, cudaStream_t s) {
+    if (c->d == 3) return launch_periodic3d(a, combo, s);
     return c->d == 1 ? launch_periodic1d(a, combo, s) : launch_periodic2d(a, combo, s);
 }
 
@@ -282,13 +292,14 @@ static tdse_status build_phase_tables(tdse_ctx* c, int b, cudaStream_t s) {
             TDSE_CK(c, launch_a1d(c->P<float2>(c->off.a1d) + b * nsp1 * (c->nh + c->nl), phi, c->ntf, c->cfg.nsteps,
                                   c->n0, c->nh, c->nl, s));
     } else {
-        const size_t per = (size_t)c->n_int * (c->n0 + c->n1);
+        const size_t per = (size_t)c->n_int * c->ntab;
+        const int n2t = c->d == 3 ? c->n2 : 0;
         TDSE_CK(c, launch_q2d(c->mixed ? nullptr : c->P<double2>(c->off.q64) + b * per,
                               c->mixed ? c->P<float4>(c->off.qff) + b * per : nullptr, iv, c->n_int, phi, c->ntf,
-                              c->n0, c->n1, c->cfg.dt, s));
+                              c->n0, c->n1, n2t, c->cfg.dt, s));
         if (c->mixed)
-            TDSE_CK(c, launch_e2d(c->P<float2>(c->off.e2d) + b * nsp1 * (c->n0 + c->n1), phi, c->ntf, c->cfg.nsteps,
-                                  c->n0, c->n1, c->cfg.dt, s));
+            TDSE_CK(c, launch_e2d(c->P<float2>(c->off.e2d) + b * nsp1 * c->ntab, phi, c->ntf, c->cfg.nsteps, c->n0,
+                                  c->n1, n2t, c->cfg.dt, s));
     }
     return TDSE_OK;
 }
@@ -312,7 +323,7 @@ tdse_status tdse_adams_weights(int order, double* mu_out) {
 tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     if (!cfg || !out) return TDSE_EINVAL;
     *out = nullptr;
-    if (cfg->dim != 1 && cfg->dim != 2) return TDSE_EINVAL;
+    if (cfg->dim != 1 && cfg->dim != 2 && cfg->dim != 3) return TDSE_EINVAL;
     if (cfg->bc != TDSE_PERIODIC && cfg->bc != TDSE_FREE) return TDSE_EINVAL;
     const bool fs = cfg->bc == TDSE_FREE;
     if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt) || cfg->nsteps < 1 || cfg->batch < 1) return TDSE_EINVAL;
@@ -320,8 +331,10 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     if (cfg->precision != TDSE_FP64 && cfg->precision != TDSE_MIXED) return TDSE_EINVAL;
     const int S = cfg->startup_steps < 0 ? cfg->order - 1 : cfg->startup_steps;
     if (S < cfg->order - 2) return TDSE_EINVAL;
-    const int n0 = cfg->n[0], n1 = cfg->dim == 2 ? cfg->n[1] : 1;
-    if (!is_pow2(n0) || (cfg->dim == 2 && !is_pow2(n1))) return TDSE_EINVAL;
+    const int n0 = cfg->n[0], n1 = cfg->dim >= 2 ? cfg->n[1] : 1, n2 = cfg->dim == 3 ? cfg->n_z : 1;
+    if (!is_pow2(n0) || (cfg->dim >= 2 && !is_pow2(n1)) || (cfg->dim == 3 && !is_pow2(n2))) return TDSE_EINVAL;
+    if (cfg->dim == 3 && fs) return TDSE_EUNSUPPORTED;
+    if (cfg->dim == 3 && !periodic3d_supported(n0, n1, n2)) return TDSE_EUNSUPPORTED;
     const bool big1d = !fs && cfg->dim == 1 && cfg->precision == TDSE_MIXED && n0 == four_step_n();
     if (!fs && cfg->dim == 1 && !periodic1d_supported(n0) && !big1d) return TDSE_EUNSUPPORTED;
     if (!fs && cfg->dim == 2 && !periodic2d_supported(n0, n1)) return TDSE_EUNSUPPORTED;
@@ -337,7 +350,9 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     c->d = cfg->dim;
     c->n0 = n0;
     c->n1 = n1;
-    c->NP = (size_t)n0 * n1;
+    c->n2 = n2;
+    c->NP = (size_t)n0 * n1 * n2;
+    c->ntab = (size_t)n0 + (cfg->dim >= 2 ? n1 : 0) + (cfg->dim == 3 ? n2 : 0);
     c->B = cfg->batch;
     c->m = cfg->order;
     c->L = cfg->order / 2;
@@ -433,7 +448,10 @@ tdse_status tdse_bind_workspace(tdse_ctx* c, void* dev, size_t bytes, void* stre
     } else {
     TDSE_CK(c, launch_twiddles(c->P<double2>(c->off.tw64_0), c->P<float2>(c->off.tw32_0),
                                c->P<float2>(c->off.tw32lo_0), c->n0, s));
-    if (c->d == 2)
+    if (c->d == 3)
+        TDSE_CK(c, launch_twiddles(c->P<double2>(c->off.tw64_2), c->P<float2>(c->off.tw32_2),
+                                   c->P<float2>(c->off.tw32lo_2), c->n2, s));
+    if (c->d >= 2)
         TDSE_CK(c, launch_twiddles(c->P<double2>(c->off.tw64_1), c->P<float2>(c->off.tw32_1),
                                    c->P<float2>(c->off.tw32lo_1), c->n1, s));
     else
@@ -597,7 +615,7 @@ tdse_status tdse_set_pulse(tdse_ctx* c, int instance, double A0, double omega, d
     if (!instance_range(c, instance, lo, hi)) return c->fail(TDSE_EINVAL, "instance out of range");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // phi in closed form on the device (no host pass over the fine time grid)
-    const double d2[2] = {dir[0], c->d == 2 ? dir[1] : 0.0};
+    const double d2[3] = {dir[0], c->d >= 2 ? dir[1] : 0.0, c->d == 3 ? dir[2] : 0.0};
     for (int b = lo; b < hi; ++b) {
         TDSE_CK(c, launch_pulse_phi(c->P<double>(c->off.phi) + (size_t)b * c->d * c->ntf, c->ntf, c->d,
                                     c->cfg.dt / SUB, A0, omega, Tp, d2, s));
@@ -756,6 +774,11 @@ static KArgs adams_args(const tdse_ctx* c, int n) {
     return a;
 }
 
+// One pass kernel of the 2D or 3D step chain.
+static cudaError_t step_part(const tdse_ctx* c, const KArgs& a, int combo, int part, cudaStream_t s) {
+    return c->d == 3 ? launch_periodic3d_part(a, combo, part, s) : launch_periodic2d_part(a, combo, part, s);
+}
+
 // The launch arguments of instances [lo, hi) of a batch: every per-instance
 // array advanced to instance lo (the kernels index instance b of a launch
 // from these bases).
@@ -771,9 +794,9 @@ static KArgs group_args(const tdse_ctx* c, KArgs a, int lo, int hi) {
     a.tfac += l * a.ntf;
     a.phi += l * (size_t)c->d * a.ntf;
     const size_t nsp1 = (size_t)c->cfg.nsteps + 1;
-    if (a.q64) a.q64 += l * (size_t)c->n_int * (c->n0 + c->n1);
-    if (a.qff) a.qff += l * (size_t)c->n_int * (c->n0 + c->n1);
-    if (a.e2d) a.e2d += l * nsp1 * (c->n0 + c->n1);
+    if (a.q64) a.q64 += l * (size_t)c->n_int * c->ntab;
+    if (a.qff) a.qff += l * (size_t)c->n_int * c->ntab;
+    if (a.e2d) a.e2d += l * nsp1 * c->ntab;
     return a;
 }
 
@@ -826,7 +849,7 @@ static tdse_status adams_steps(tdse_ctx* c, int n0, int k, cudaStream_t s) {
         TDSE_CK(c, cudaStreamWaitEvent(c->group_streams[g], c->group_fork, 0));
     }
     for (int g = 0; g < G; ++g)
-        TDSE_CK(c, launch_periodic2d_part(group_args(c, adams_args(c, n0 + 1), lo[g], hi[g]), combo, PART_COL_BEGIN,
+        TDSE_CK(c, step_part(c, group_args(c, adams_args(c, n0 + 1), lo[g], hi[g]), combo, PART_COL_BEGIN,
                                           c->group_streams[g]));
     for (int n = n0 + 1; n < n0 + k; ++n) {
         const KArgs r = adams_args(c, n);
@@ -836,16 +859,16 @@ static tdse_status adams_steps(tdse_ctx* c, int n0, int k, cudaStream_t s) {
         f.e_next = n + 1;
         if (c->mixed) set_dither(c, f, n + 1, n);
         for (int g = 0; g < G; ++g) {
-            TDSE_CK(c, launch_periodic2d_part(group_args(c, r, lo[g], hi[g]), combo, PART_ROW_MID, c->group_streams[g]));
-            TDSE_CK(c, launch_periodic2d_part(group_args(c, f, lo[g], hi[g]), combo, PART_COL_FUSED,
+            TDSE_CK(c, step_part(c, group_args(c, r, lo[g], hi[g]), combo, PART_ROW_MID, c->group_streams[g]));
+            TDSE_CK(c, step_part(c, group_args(c, f, lo[g], hi[g]), combo, PART_COL_FUSED,
                                               c->group_streams[g]));
         }
     }
     const KArgs last = adams_args(c, n0 + k);
     for (int g = 0; g < G; ++g) {
         const KArgs lg = group_args(c, last, lo[g], hi[g]);
-        TDSE_CK(c, launch_periodic2d_part(lg, combo, PART_ROW_MID, c->group_streams[g]));
-        TDSE_CK(c, launch_periodic2d_part(lg, combo, PART_COL_END, c->group_streams[g]));
+        TDSE_CK(c, step_part(c, lg, combo, PART_ROW_MID, c->group_streams[g]));
+        TDSE_CK(c, step_part(c, lg, combo, PART_COL_END, c->group_streams[g]));
         TDSE_CK(c, cudaEventRecord(c->group_join[g], c->group_streams[g]));
         TDSE_CK(c, cudaStreamWaitEvent(s, c->group_join[g], 0));
     }
@@ -856,19 +879,19 @@ static tdse_status adams_steps(tdse_ctx* c, int n0, int k, cudaStream_t s) {
 static tdse_status adams_chain_2d(tdse_ctx* c, int n0, int k, int lo, int hi, cudaStream_t s) {
     const int combo = step_combo(c);
     auto A = [&](int n) { return group_args(c, adams_args(c, n), lo, hi); };
-    TDSE_CK(c, launch_periodic2d_part(A(n0 + 1), combo, PART_COL_BEGIN, s));
+    TDSE_CK(c, step_part(c, A(n0 + 1), combo, PART_COL_BEGIN, s));
     for (int n = n0 + 1; n < n0 + k; ++n) {
-        TDSE_CK(c, launch_periodic2d_part(A(n), combo, PART_ROW_MID, s));
+        TDSE_CK(c, step_part(c, A(n), combo, PART_ROW_MID, s));
         KArgs f = A(n + 1);                 // history slots, intervals and E of the next step ...
         f.out_slot = slot_of(c, n);         // ... ring slot and E of the step being finished
         f.e_step = n;
         f.e_next = n + 1;
         if (c->mixed) set_dither(c, f, n + 1, n);
-        TDSE_CK(c, launch_periodic2d_part(f, combo, PART_COL_FUSED, s));
+        TDSE_CK(c, step_part(c, f, combo, PART_COL_FUSED, s));
     }
     const KArgs last = A(n0 + k);
-    TDSE_CK(c, launch_periodic2d_part(last, combo, PART_ROW_MID, s));
-    TDSE_CK(c, launch_periodic2d_part(last, combo, PART_COL_END, s));
+    TDSE_CK(c, step_part(c, last, combo, PART_ROW_MID, s));
+    TDSE_CK(c, step_part(c, last, combo, PART_COL_END, s));
     return TDSE_OK;
 }
 
@@ -1056,10 +1079,10 @@ tdse_status tdse_residual_report(tdse_ctx* c, double* rho, int* corrections, int
 
 // ---- checkpoint: header, then the whole workspace
 namespace {
-constexpr char kCkptMagic[8] = {'T', 'D', 'S', 'E', 'C', 'K', 'P', '1'};
+constexpr char kCkptMagic[8] = {'T', 'D', 'S', 'E', 'C', 'K', 'P', '2'};
 struct CkptHeader {
     char magic[8];
-    int dim, bc, n0, n1, batch, nsteps, order, startup, precision, nu0, nu1, alpert_p, gauss_q, n_r;
+    int dim, bc, n0, n1, n2, batch, nsteps, order, startup, precision, nu0, nu1, alpert_p, gauss_q, n_r;
     double dt, H;
     unsigned long long ws_bytes;
     int step, inited, ip, res_every, res_checks, pad;
@@ -1069,7 +1092,8 @@ void fill_header(const tdse_ctx* c, CkptHeader& h) {
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, kCkptMagic, 8);
     const tdse_config& g = c->cfg;
-    h.dim = g.dim; h.bc = g.bc; h.n0 = g.n[0]; h.n1 = g.dim == 2 ? g.n[1] : 1; h.batch = g.batch;
+    h.dim = g.dim; h.bc = g.bc; h.n0 = g.n[0]; h.n1 = g.dim >= 2 ? g.n[1] : 1; h.n2 = g.dim == 3 ? g.n_z : 1;
+    h.batch = g.batch;
     h.nsteps = g.nsteps; h.order = g.order; h.startup = c->S; h.precision = g.precision;
     if (g.bc == TDSE_FREE) {
         h.nu0 = g.nu[0]; h.nu1 = g.dim == 2 ? g.nu[1] : 0; h.alpert_p = g.alpert_p; h.gauss_q = g.gauss_q;
@@ -1115,7 +1139,7 @@ tdse_status tdse_load(tdse_ctx* c, const void* blob, size_t size, void* stream) 
     std::memcpy(&h, blob, sizeof(h));
     fill_header(c, mine);
     if (std::memcmp(h.magic, kCkptMagic, 8) != 0) return c->fail(TDSE_EINVAL, "not a checkpoint of this library");
-    const bool same = h.dim == mine.dim && h.bc == mine.bc && h.n0 == mine.n0 && h.n1 == mine.n1 &&
+    const bool same = h.dim == mine.dim && h.bc == mine.bc && h.n0 == mine.n0 && h.n1 == mine.n1 && h.n2 == mine.n2 &&
                       h.batch == mine.batch && h.nsteps == mine.nsteps && h.order == mine.order &&
                       h.startup == mine.startup && h.precision == mine.precision && h.nu0 == mine.nu0 &&
                       h.nu1 == mine.nu1 && h.alpert_p == mine.alpert_p && h.gauss_q == mine.gauss_q &&
@@ -1171,7 +1195,7 @@ tdse_status tdse_describe_steps(const tdse_ctx* c, char* buf, size_t len) {
                           c->cl.clusters, CL_Q, step2d_cluster_threads(), step2d_cluster_smem());
     else
         n = std::snprintf(buf, len, "{\"path\": \"passes\", \"groups\": %d}",
-                          c->d == 2 && !c->fs ? (c->step_groups < c->B ? c->step_groups : c->B) : 1);
+                          c->d >= 2 && !c->fs ? (c->step_groups < c->B ? c->step_groups : c->B) : 1);
     return (n < 0 || (size_t)n >= len) ? TDSE_EINVAL : TDSE_OK;
 }
 

@@ -28,7 +28,9 @@ constexpr int E1D_NLO = 32;    // 1D absolute kinetic phase: e^{-i k^2 n dt} = K
 struct KArgs {
     int mode;
     int B;                    // instances in this launch
-    int n0, n1;               // grid (n1 = 1 for 1D)
+    int n0, n1;               // launch geometry: lines x line length (n1 = 1 for 1D); for 3D the
+                              // column pass sees [n0][n1 n2] and the row pass [n0 n1][n2]
+    int tn0, tn1, tn2;        // the grid per axis for the phase and E tables (tn2 = 0 below 3D)
     // ---- step description
     int nhist;                // history terms j = 1..nhist
     double h;                 // step size
@@ -86,6 +88,9 @@ struct KArgs {
     const float2* tw32_1;
     const float2* tw32lo_0;   // e^{-2 pi i m / n} - tw32 (rounding residual)
     const float2* tw32lo_1;
+    const double2* tw64_2;    // axis 2 (3D)
+    const float2* tw32_2;
+    const float2* tw32lo_2;
 };
 
 // Launchers (return cudaGetLastError() of the launch).
@@ -96,6 +101,12 @@ cudaError_t launch_periodic1d(const KArgs& a, int combo, cudaStream_t s);
 cudaError_t launch_periodic2d(const KArgs& a, int combo, cudaStream_t s);
 cudaError_t launch_periodic2d_part(const KArgs& a, int combo, int part, cudaStream_t s);
 enum Part2D : int { PART_COL_BEGIN = 0, PART_ROW_MID = 1, PART_COL_END = 2, PART_COL_FUSED = 3 };
+// 3D [n0][n1][n2] (a.tn0..tn2; a.n0/a.n1 ignored): the 2D column pass over the
+// n1 n2 columns of axis 0, a transform pass along axis 1, and the 2D row pass
+// over the n0 n1 rows of axis 2; the same parts as in 2D.
+cudaError_t launch_periodic3d(const KArgs& a, int combo, cudaStream_t s);
+cudaError_t launch_periodic3d_part(const KArgs& a, int combo, int part, cudaStream_t s);
+bool periodic3d_supported(int n0, int n1, int n2);
 bool periodic1d_supported(int n);
 bool periodic2d_supported(int n0, int n1);
 // One-time kernel attributes of the 1D step for n and combo (before stream capture).
@@ -175,9 +186,10 @@ cudaError_t launch_twiddles(double2* tw64, float2* tw32, float2* tw32lo, int n, 
 cudaError_t launch_kin1d(double2* kin64, float4* kinff, int n, int L, double dt, cudaStream_t s);
 cudaError_t launch_adv1d(double2* adv64, float4* advff, const int2* intervals, int n_int, const double* phi,
                          int ntf, int n, int nh, int nl, cudaStream_t s);
+// 2D / 3D separable phase tables over the axes n0, n1 (and n2 > 0 for 3D): n0 + n1 + n2 entries per row
 cudaError_t launch_q2d(double2* q64, float4* qff, const int2* intervals, int n_int, const double* phi, int ntf,
-                       int n0, int n1, double dt, cudaStream_t s);
-cudaError_t launch_e2d(float2* e, const double* phi, int ntf, int nsteps, int n0, int n1, double dt,
+                       int n0, int n1, int n2, double dt, cudaStream_t s);
+cudaError_t launch_e2d(float2* e, const double* phi, int ntf, int nsteps, int n0, int n1, int n2, double dt,
                        cudaStream_t s);
 cudaError_t launch_k1d(float2* klo, float2* khi, int nhi, int n, double dt, cudaStream_t s);
 cudaError_t launch_a1d(float2* a1d, const double* phi, int ntf, int nsteps, int n, int nh, int nl,

@@ -125,8 +125,9 @@ __device__ __forceinline__ C begin_elem(const KArgs& a, bool step, int b, state_
         }
     }
     if (a.mode == MODE_READ && a.ip) {
-        const double2 v = cmul(e_exact(a, b, a.e_step, kmode(m0, a.n0), kmode(m1, a.n1), 2), st_to_d(W));
-        return cvt<C>(v);
+        const double2 E = a.tn2 ? e_exact3(a, b, a.e_step, m0, m1)
+                                : e_exact(a, b, a.e_step, kmode(m0, a.n0), kmode(m1, a.n1), 2);
+        return cvt<C>(cmul(E, st_to_d(W)));
     }
     return st_to_c<C>(W);
 }
@@ -405,13 +406,13 @@ __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_fused_ip(const KArgs a
     const float2 z = make_float2(a.zr[0], a.zr[1]);
     // E_n(m0, m1) = e_n[m0] e_n[n0 + m1] (e_2d): the axis-1 factors of the
     // column a thread keeps (RC * L == T2D: one column per thread) are loaded once
-    const size_t erow = (size_t)(a.n0 + a.n1);
+    const size_t erow = (size_t)(a.tn0 + a.tn1 + a.tn2);
     const float2* en = a.e2d + ((size_t)b * (a.ntf / 8 + 1) + a.e_step) * erow;
     const float2* en1 = a.e2d + ((size_t)b * (a.ntf / 8 + 1) + a.e_next) * erow;
     constexpr bool ONE_COL = (RC * L == T2D);
     const int lane_t = threadIdx.x % L;
-    const float2 en_1 = __ldg(&en[a.n0 + c0 + lane_t]);
-    const float2 en1_1 = __ldg(&en1[a.n0 + c0 + lane_t]);
+    const float2 en_1 = __ldg(&en[a.tn0 + c0 + lane_t]);
+    const float2 en1_1 = __ldg(&en1[a.tn0 + c0 + lane_t]);
     float2* ring_out = ringb + (size_t)a.out_slot * NP;
 
 #pragma unroll 1
@@ -423,8 +424,8 @@ __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_fused_ip(const KArgs a
             const int lane = it % L, r = it / L;
             const int m0 = c * RC + r, m1 = c0 + lane;
             const size_t idx = (size_t)m0 * n1 + m1;
-            const float2 e1n = ONE_COL ? en_1 : __ldg(&en[a.n0 + m1]);
-            const float2 e1n1 = ONE_COL ? en1_1 : __ldg(&en1[a.n0 + m1]);
+            const float2 e1n = ONE_COL ? en_1 : __ldg(&en[a.tn0 + m1]);
+            const float2 e1n1 = ONE_COL ? en1_1 : __ldg(&en1[a.tn0 + m1]);
             // end of step n: r~ = z_n R / E_n into the ring, v^_n
             const float2 R = cscale(buf[m0 * L + lane], scale);
             const float2 rv = cmul(z, cmul(conjf2(cmul(__ldg(&en[m0]), e1n)), R));
@@ -559,13 +560,149 @@ static cudaError_t part2d(const KArgs& a, int part, cudaStream_t s) {
         case PART_COL_END: return col_end<C, RT>(a, s);
         case PART_COL_FUSED:
             if constexpr (std::is_same<C, float2>::value && std::is_same<RT, float2>::value) {
-                if (a.mode == MODE_STEP && a.ip) {
+                if (a.mode == MODE_STEP && a.ip && a.tn2 == 0) {
 #define TDSE_CFI(n) col_fused_ip_n<n>
                     TDSE_SWITCH_N(a.n0, TDSE_CFI)
 #undef TDSE_CFI
                 }
             }
             return col_fused<C, RT>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// ------------------------------------------------------------------ 3D
+// Transform along axis 1 of [B n0][N1][n2] (one CTA per 8 consecutive i2 of
+// one (instance, i0) plane), in place in X: forward with 1/N1, or inverse.
+template <class C, int N1, bool INV>
+__global__ void __launch_bounds__(T2D, min_blocks_2d<C>()) k_axis1(const KArgs a, C* X) {
+    constexpr int L = LANES2D;
+    using F = CtaFft<C, N1, L, L, T2D, INV>;
+    using R = typename cx_traits<C>::real;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int n2 = a.tn2;
+    const size_t plane = (size_t)blockIdx.z * a.tn0 + blockIdx.y;
+    C* base = X + plane * (size_t)N1 * n2 + (size_t)blockIdx.x * L;
+    batched_copy<C, N1 * L>([&](int item) { return base[(size_t)(item / L) * n2 + item % L]; },
+                            [&](int item, C v) { buf[item] = v; });
+    __syncthreads();
+    const C* tw;
+    const C* twl;
+    if constexpr (is_f64<C>::value) { tw = a.tw64_1; twl = tw; } else { tw = a.tw32_1; twl = a.tw32lo_1; }
+    F::run(buf, tw, twl);
+    const R scale = (R)1 / (R)N1;
+    for (int item = threadIdx.x; item < N1 * L; item += T2D)
+        base[(size_t)(item / L) * n2 + item % L] = INV ? buf[item] : cscale(buf[item], scale);
+}
+
+template <class C, int N1>
+static cudaError_t axis1_n(const KArgs& a, bool inv, void* X, cudaStream_t s) {
+    const size_t smem = (size_t)N1 * LANES2D * sizeof(C);
+    static bool done_f = false, done_i = false;
+    cudaError_t e = inv ? set_smem(k_axis1<C, N1, true>, smem, done_i) : set_smem(k_axis1<C, N1, false>, smem, done_f);
+    if (e != cudaSuccess) return e;
+    const dim3 grid(a.tn2 / LANES2D, a.tn0, a.B);
+    if (inv) k_axis1<C, N1, true><<<grid, T2D, smem, s>>>(a, static_cast<C*>(X));
+    else k_axis1<C, N1, false><<<grid, T2D, smem, s>>>(a, static_cast<C*>(X));
+    return cudaGetLastError();
+}
+
+template <class C>
+static cudaError_t axis1(const KArgs& a, bool inv, void* X, cudaStream_t s) {
+    switch (a.tn1) {
+        case 8: return axis1_n<C, 8>(a, inv, X, s);
+        case 16: return axis1_n<C, 16>(a, inv, X, s);
+        case 32: return axis1_n<C, 32>(a, inv, X, s);
+        case 64: return axis1_n<C, 64>(a, inv, X, s);
+        case 128: return axis1_n<C, 128>(a, inv, X, s);
+        case 256: return axis1_n<C, 256>(a, inv, X, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Launch geometry of the 3D passes: the column pass over the n1 n2 columns of
+// [n0][n1 n2], the row pass over the n0 n1 rows of [n0 n1][n2] with the axis-2
+// twiddles.
+static KArgs col3(const KArgs& a) {
+    KArgs c = a;
+    c.n0 = a.tn0;
+    c.n1 = a.tn1 * a.tn2;
+    return c;
+}
+static KArgs row3(const KArgs& a) {
+    KArgs r = a;
+    r.n0 = a.tn0 * a.tn1;
+    r.n1 = a.tn2;
+    r.tw64_1 = a.tw64_2;
+    r.tw32_1 = a.tw32_2;
+    r.tw32lo_1 = a.tw32lo_2;
+    return r;
+}
+
+template <class C, class RT>
+static cudaError_t part3d(const KArgs& a, int part, cudaStream_t s) {
+    const KArgs c = col3(a), r = row3(a);
+    cudaError_t e = cudaSuccess;
+    switch (part) {
+        case PART_COL_BEGIN:
+            if ((e = col_begin<C, RT>(c, s)) != cudaSuccess) return e;
+            return axis1<C>(a, true, a.aux, s);
+        case PART_ROW_MID: return row_mid<C>(r, s);
+        case PART_COL_END:
+            if ((e = axis1<C>(a, false, a.aux2, s)) != cudaSuccess) return e;
+            return col_end<C, RT>(c, s);
+        case PART_COL_FUSED:
+            if ((e = axis1<C>(a, false, a.aux2, s)) != cudaSuccess) return e;
+            if ((e = col_fused<C, RT>(c, s)) != cudaSuccess) return e;
+            return axis1<C>(a, true, a.aux, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class C, class RT>
+static cudaError_t run3d(const KArgs& a, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    switch (a.mode) {
+        case MODE_STEP:
+        case MODE_REFRESH:
+            if ((e = part3d<C, RT>(a, PART_COL_BEGIN, s)) != cudaSuccess) return e;
+            if ((e = part3d<C, RT>(a, PART_ROW_MID, s)) != cudaSuccess) return e;
+            return part3d<C, RT>(a, PART_COL_END, s);
+        case MODE_INIT:   // T1 = F2 u0, T2 = F2 V u0, then axis 1 of both, then axis 0 into state and ring
+            if ((e = row_mid<C>(row3(a), s)) != cudaSuccess) return e;
+            if ((e = axis1<C>(a, false, a.aux, s)) != cudaSuccess) return e;
+            if ((e = axis1<C>(a, false, a.aux2, s)) != cudaSuccess) return e;
+            return col_end<C, RT>(col3(a), s);
+        case MODE_READ:
+            if ((e = part3d<C, RT>(a, PART_COL_BEGIN, s)) != cudaSuccess) return e;
+            return row_mid<C>(row3(a), s);
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+bool periodic3d_supported(int n0, int n1, int n2) {
+    auto ok = [](int n, int hi) { return n >= 8 && n <= hi && (n & (n - 1)) == 0; };
+    return ok(n0, 1024) && ok(n1, 256) && ok(n2, 1024) && (long long)n0 * n1 * n2 <= (1LL << 24);
+}
+
+cudaError_t launch_periodic3d(const KArgs& a, int combo, cudaStream_t s) {
+    if (!periodic3d_supported(a.tn0, a.tn1, a.tn2)) return cudaErrorInvalidValue;
+    switch (combo) {
+        case COMBO_F64: return run3d<double2, double2>(a, s);
+        case COMBO_F32: return run3d<float2, float2>(a, s);
+        case COMBO_F64_R32: return run3d<double2, float2>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_periodic3d_part(const KArgs& a, int combo, int part, cudaStream_t s) {
+    if (!periodic3d_supported(a.tn0, a.tn1, a.tn2)) return cudaErrorInvalidValue;
+    switch (combo) {
+        case COMBO_F64: return part3d<double2, double2>(a, part, s);
+        case COMBO_F32: return part3d<float2, float2>(a, part, s);
+        case COMBO_F64_R32: return part3d<double2, float2>(a, part, s);
         default: return cudaErrorInvalidValue;
     }
 }

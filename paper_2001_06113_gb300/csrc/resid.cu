@@ -281,6 +281,7 @@ cudaError_t dispatch_rows(const ResArgs& r, cudaStream_t s) {
 }  // namespace
 
 bool residual_supported(int dim, int n0, int n1) {
+    if (dim == 3) return false;
     if (dim == 1) return n0 >= 8 && n0 <= 8192;
     return n0 >= 8 && n0 <= 1024 && n1 >= 8 && n1 <= 1024;
 }

@@ -75,26 +75,47 @@ struct Phase1D {
     }
 };
 
+// Column index m1 of a 3D column pass ([n0][n1 n2]) -> (i1, i2); 2D: (m1, -1).
+__device__ __forceinline__ void split12(const KArgs& a, int m1, int& i1, int& i2) {
+    if (a.tn2 == 0) {
+        i1 = m1;
+        i2 = -1;
+    } else {
+        i1 = m1 / a.tn2;
+        i2 = m1 - i1 * a.tn2;
+    }
+}
+
+// Separable phases of the 2D (and 3D) steps: the product of one factor per axis.
 struct Phase2D {
     const KArgs& a;
     int b, m0, m1;
     __device__ __forceinline__ size_t base(int i) const {
-        return ((size_t)b * a.n_int + a.interval[i]) * (size_t)(a.n0 + a.n1);
+        return ((size_t)b * a.n_int + a.interval[i]) * (size_t)(a.tn0 + a.tn1 + a.tn2);
     }
     __device__ __forceinline__ double2 p64(int i) const {
         const double2* q = a.q64 + base(i);
-        return cmul(__ldg(&q[m0]), __ldg(&q[a.n0 + m1]));
+        if (a.tn2 == 0) return cmul(__ldg(&q[m0]), __ldg(&q[a.tn0 + m1]));
+        int i1, i2;
+        split12(a, m1, i1, i2);
+        return cmul(cmul(__ldg(&q[m0]), __ldg(&q[a.tn0 + i1])), __ldg(&q[a.tn0 + a.tn1 + i2]));
     }
     __device__ __forceinline__ float4 pff(int i) const {
         const float4* q = a.qff + base(i);
-        return ffc_mul(__ldg(&q[m0]), __ldg(&q[a.n0 + m1]));
+        if (a.tn2 == 0) return ffc_mul(__ldg(&q[m0]), __ldg(&q[a.tn0 + m1]));
+        int i1, i2;
+        split12(a, m1, i1, i2);
+        return ffc_mul(ffc_mul(__ldg(&q[m0]), __ldg(&q[a.tn0 + i1])), __ldg(&q[a.tn0 + a.tn1 + i2]));
     }
 };
 
 // ---- absolute phases E_n (interaction picture), FP32
 __device__ __forceinline__ float2 e_2d(const KArgs& a, int b, int n, int m0, int m1) {
-    const float2* e = a.e2d + ((size_t)b * (a.ntf / 8 + 1) + n) * (size_t)(a.n0 + a.n1);
-    return cmul(__ldg(&e[m0]), __ldg(&e[a.n0 + m1]));
+    const float2* e = a.e2d + ((size_t)b * (a.ntf / 8 + 1) + n) * (size_t)(a.tn0 + a.tn1 + a.tn2);
+    if (a.tn2 == 0) return cmul(__ldg(&e[m0]), __ldg(&e[a.tn0 + m1]));
+    int i1, i2;
+    split12(a, m1, i1, i2);
+    return cmul(cmul(__ldg(&e[m0]), __ldg(&e[a.tn0 + i1])), __ldg(&e[a.tn0 + a.tn1 + i2]));
 }
 __device__ __forceinline__ float2 e_1d(const KArgs& a, int b, int n, int m) {
     const float2 kin = cmul(__ldg(&a.k1d_hi[(size_t)(n / E1D_NLO) * a.n0 + m]),
@@ -108,6 +129,19 @@ __device__ __forceinline__ double2 e_exact(const KArgs& a, int b, int n, double 
     const double* ph = a.phi + (size_t)b * d * a.ntf;
     double arg = -(k0 * k0 + k1 * k1) * t + k0 * ph[8 * n];
     if (d == 2) arg += k1 * ph[a.ntf + 8 * n];
+    double s, c;
+    sincos(arg, &s, &c);
+    return make_double2(c, s);
+}
+// The same in 3D for the flattened column index m1 of mode (m0, i1, i2).
+__device__ __forceinline__ double2 e_exact3(const KArgs& a, int b, int n, int m0, int m1) {
+    int i1, i2;
+    split12(a, m1, i1, i2);
+    const double k0 = kmode(m0, a.tn0), k1 = kmode(i1, a.tn1), k2 = kmode(i2, a.tn2);
+    const double t = (double)n * a.dt;
+    const double* ph = a.phi + (size_t)b * 3 * a.ntf;
+    const double arg = -(k0 * k0 + k1 * k1 + k2 * k2) * t + k0 * ph[8 * n] + k1 * ph[a.ntf + 8 * n] +
+                       k2 * ph[2 * (size_t)a.ntf + 8 * n];
     double s, c;
     sincos(arg, &s, &c);
     return make_double2(c, s);

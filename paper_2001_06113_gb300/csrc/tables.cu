@@ -75,37 +75,45 @@ __global__ void k_adv1d(double2* adv64, float4* advff, const int2* iv, int n_int
     }
 }
 
+// Separable one-step phases of the 2D / 3D steps, one row of n0 + n1 (+ n2)
+// factors per interval: exp(-i k^2 h + i k dphi_axis) for each axis's k.
 __global__ void k_q2d(double2* q64, float4* qff, const int2* iv, int n_int, const double* phi, int ntf, int n0,
-                      int n1, double dt) {
+                      int n1, int n2, double dt) {
     const int i = blockIdx.x;
     const int2 ab = iv[i];
     const double h = (double)(ab.y - ab.x) * (dt * 0.125);
     const double* ph1 = phi + ntf;
+    const double* ph2 = phi + 2 * (size_t)ntf;
     const double d0 = phi[ab.y] - phi[ab.x];
     const double d1 = ph1[ab.y] - ph1[ab.x];
-    const size_t base = (size_t)i * (size_t)(n0 + n1);
-    for (int t = threadIdx.x; t < n0 + n1; t += blockDim.x) {
-        const bool ax0 = t < n0;
-        const int m = ax0 ? t : t - n0;
-        const double k = kmode(m, ax0 ? n0 : n1);
+    const double d2 = n2 > 0 ? ph2[ab.y] - ph2[ab.x] : 0.0;
+    const size_t base = (size_t)i * (size_t)(n0 + n1 + n2);
+    for (int t = threadIdx.x; t < n0 + n1 + n2; t += blockDim.x) {
+        const int ax = t < n0 ? 0 : (t < n0 + n1 ? 1 : 2);
+        const int m = ax == 0 ? t : (ax == 1 ? t - n0 : t - n0 - n1);
+        const double k = kmode(m, ax == 0 ? n0 : (ax == 1 ? n1 : n2));
         double s, c;
-        sincos(-(k * k) * h + k * (ax0 ? d0 : d1), &s, &c);
+        sincos(-(k * k) * h + k * (ax == 0 ? d0 : (ax == 1 ? d1 : d2)), &s, &c);
         if (q64) q64[base + t] = make_double2(c, s);
         if (qff) qff[base + t] = ff_from_cs(c, s);
     }
 }
 
-__global__ void k_e2d(float2* e, const double* phi, int ntf, int n0, int n1, double dt) {
+// Absolute phases E_n per axis (interaction picture), FP32, with the dither
+// angle on the axis-0 factor.
+__global__ void k_e2d(float2* e, const double* phi, int ntf, int n0, int n1, int n2, double dt) {
     const int n = blockIdx.x;
     const double t = (double)n * dt;
     const double p0 = phi[8 * (size_t)n], p1 = phi[ntf + 8 * (size_t)n];
+    const double p2 = n2 > 0 ? phi[2 * (size_t)ntf + 8 * (size_t)n] : 0.0;
     const double th = dither_angle(n);
-    const size_t base = (size_t)n * (size_t)(n0 + n1);
-    for (int j = threadIdx.x; j < n0 + n1; j += blockDim.x) {
-        const bool ax0 = j < n0;
-        const double k = kmode(ax0 ? j : j - n0, ax0 ? n0 : n1);
+    const size_t base = (size_t)n * (size_t)(n0 + n1 + n2);
+    for (int j = threadIdx.x; j < n0 + n1 + n2; j += blockDim.x) {
+        const int ax = j < n0 ? 0 : (j < n0 + n1 ? 1 : 2);
+        const int m = ax == 0 ? j : (ax == 1 ? j - n0 : j - n0 - n1);
+        const double k = kmode(m, ax == 0 ? n0 : (ax == 1 ? n1 : n2));
         double s, c;
-        sincos(-(k * k) * t + k * (ax0 ? p0 : p1) + (ax0 ? th : 0.0), &s, &c);
+        sincos(-(k * k) * t + k * (ax == 0 ? p0 : (ax == 1 ? p1 : p2)) + (ax == 0 ? th : 0.0), &s, &c);
         e[base + j] = make_float2((float)c, (float)s);
     }
 }
@@ -184,16 +192,20 @@ struct Steps8 { int s[8]; float z[8][2]; };
 // state (double-float, lab frame at step n) -> v^ = conj(E_n) u^, and ring slot
 // q (FP32, lab frame at step steps.s[q]) -> r~ = z_q conj(E) R; E in FP64.
 __global__ void k_to_interaction(float4* state, float2* ring, int ring_slots, const double* phi, int ntf, int d,
-                                 int n0, int n1, double dt, int n, Steps8 steps, int nslots) {
+                                 int n0, int n1, int n2, double dt, int n, Steps8 steps, int nslots) {
     const int b = blockIdx.y;
-    const size_t NP = (size_t)n0 * n1;
+    const size_t NP = (size_t)n0 * n1 * n2;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < NP; idx += (size_t)gridDim.x * blockDim.x) {
-        const int m0 = (int)(idx / n1), m1 = (int)(idx % n1);
-        const double k0 = kmode(m0, n0), k1 = d == 2 ? kmode(m1, n1) : 0.0;
+        const int m0 = (int)(idx / ((size_t)n1 * n2));
+        const int rem = (int)(idx - (size_t)m0 * n1 * n2);
+        const int m1 = rem / n2, m2 = rem - (rem / n2) * n2;
+        const double k0 = kmode(m0, n0), k1 = d >= 2 ? kmode(m1, n1) : 0.0, k2 = d == 3 ? kmode(m2, n2) : 0.0;
         const double* ph = phi + (size_t)b * d * ntf;
         auto E = [&](int step) {
-            double arg = -(k0 * k0 + k1 * k1) * ((double)step * dt) + k0 * ph[8 * (size_t)step];
-            if (d == 2) arg += k1 * ph[ntf + 8 * (size_t)step];
+            double arg = d == 3 ? -(k0 * k0 + k1 * k1 + k2 * k2) * ((double)step * dt) + k0 * ph[8 * (size_t)step]
+                                : -(k0 * k0 + k1 * k1) * ((double)step * dt) + k0 * ph[8 * (size_t)step];
+            if (d >= 2) arg += k1 * ph[ntf + 8 * (size_t)step];
+            if (d == 3) arg += k2 * ph[2 * (size_t)ntf + 8 * (size_t)step];
             double s, c;
             sincos(arg, &s, &c);
             return make_double2(c, -s);     // conj(E)
@@ -234,14 +246,15 @@ cudaError_t launch_adv1d(double2* adv64, float4* advff, const int2* intervals, i
 }
 
 cudaError_t launch_q2d(double2* q64, float4* qff, const int2* intervals, int n_int, const double* phi, int ntf,
-                       int n0, int n1, double dt, cudaStream_t s) {
+                       int n0, int n1, int n2, double dt, cudaStream_t s) {
     if (n_int <= 0) return cudaSuccess;
-    k_q2d<<<n_int, 256, 0, s>>>(q64, qff, intervals, n_int, phi, ntf, n0, n1, dt);
+    k_q2d<<<n_int, 256, 0, s>>>(q64, qff, intervals, n_int, phi, ntf, n0, n1, n2, dt);
     return cudaGetLastError();
 }
 
-cudaError_t launch_e2d(float2* e, const double* phi, int ntf, int nsteps, int n0, int n1, double dt, cudaStream_t s) {
-    k_e2d<<<nsteps + 1, 256, 0, s>>>(e, phi, ntf, n0, n1, dt);
+cudaError_t launch_e2d(float2* e, const double* phi, int ntf, int nsteps, int n0, int n1, int n2, double dt,
+                       cudaStream_t s) {
+    k_e2d<<<nsteps + 1, 256, 0, s>>>(e, phi, ntf, n0, n1, n2, dt);
     return cudaGetLastError();
 }
 
@@ -268,12 +281,13 @@ __device__ __forceinline__ double int_sin(double a, double t) {
 }
 
 __global__ void k_pulse_phi(double* phi, int ntf, int d, double hs, double A0, double omega, double Om,
-                            double dir0, double dir1) {
+                            double dir0, double dir1, double dir2) {
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < ntf; m += gridDim.x * blockDim.x) {
         const double t = (double)m * hs;
         const double v = 0.5 * A0 * (int_sin(omega, t) - 0.5 * (int_sin(omega + Om, t) + int_sin(omega - Om, t)));
         phi[m] = v * dir0;
-        if (d == 2) phi[(size_t)ntf + m] = v * dir1;
+        if (d >= 2) phi[(size_t)ntf + m] = v * dir1;
+        if (d == 3) phi[2 * (size_t)ntf + m] = v * dir2;
     }
 }
 
@@ -281,7 +295,7 @@ cudaError_t launch_pulse_phi(double* phi, int ntf, int d, double hs, double A0, 
                              const double* dir, cudaStream_t s) {
     const double Om = 2.0 * 3.14159265358979323846 / Tp;
     k_pulse_phi<<<grid_for((size_t)ntf, 256), 256, 0, s>>>(phi, ntf, d, hs, A0, omega, Om, dir[0],
-                                                            d == 2 ? dir[1] : 0.0);
+                                                            d >= 2 ? dir[1] : 0.0, d == 3 ? dir[2] : 0.0);
     return cudaGetLastError();
 }
 
@@ -325,12 +339,13 @@ cudaError_t launch_to_interaction(const KArgs& a, int n, const int* slot_steps, 
         st.z[q][0] = q < nslots ? slot_z[2 * q] : 1.f;
         st.z[q][1] = q < nslots ? slot_z[2 * q + 1] : 0.f;
     }
-    const size_t NP = (size_t)a.n0 * a.n1;
+    const int d = a.tn2 > 0 ? 3 : (a.n1 > 1 ? 2 : 1);
+    const int n0 = d == 3 ? a.tn0 : a.n0, n1 = d == 3 ? a.tn1 : a.n1, n2 = d == 3 ? a.tn2 : 1;
+    const size_t NP = (size_t)n0 * n1 * n2;
     size_t gx = (NP + 255) / 256;
     if (gx > 1024) gx = 1024;
     k_to_interaction<<<dim3((unsigned)gx, a.B), 256, 0, s>>>((float4*)a.uhat, (float2*)a.ring, a.ring_slots, a.phi,
-                                                              a.ntf, a.n1 > 1 ? 2 : 1, a.n0, a.n1, a.dt, n, st,
-                                                              nslots);
+                                                              a.ntf, d, n0, n1, n2, a.dt, n, st, nslots);
     return cudaGetLastError();
 }
 

@@ -63,7 +63,14 @@ def _cfg(native, **kw):
 @pytest.mark.parametrize("kw,status", [
     (dict(), 0),
     (dict(dim=2, n=(32, 16)), 0),
-    (dict(dim=3), -1),
+    (dict(dim=3), -1),                 # 3D needs n_z
+    (dict(dim=3, n=(16, 8), n_z=32), 0),
+    (dict(dim=3, n=(16, 8), n_z=32, precision=1), 0),
+    (dict(dim=3, n=(16, 12), n_z=32), -1),            # not a power of two
+    (dict(dim=3, n=(16, 512), n_z=32), -7),           # axis 1 at most 256
+    (dict(dim=3, n=(1024, 256), n_z=1024), -7),       # more than 2^24 points
+    (dict(dim=3, n=(16, 8), n_z=32, bc=1, nu=(128, 64), H=1.5, gauss_q=10, n_r=1), -7),   # free space 3D
+    (dict(dim=4), -1),
     (dict(n=(48, 1)), -1),             # not a power of two
     (dict(n=(16384, 1)), -7),          # 1D FP64 limit of this build (FP64 transform in shared memory)
     (dict(n=(16384, 1), precision=1), 0),   # mixed: FP32 steps, FP64 four-step start and read-out
