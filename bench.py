@@ -26,6 +26,9 @@ launch per step replayed from a CUDA graph, mixed precision.
 solves overlapped on their own streams) and reports time-to-solution p50/p99
 and aggregate point-steps/s.
 
+`--workload periodic3d` measures the 3D periodic wells workload (128^3,
+dt = 1e-3, 500 steps, a batch of 16 mixed / 2 FP64 instances).
+
 `--workload free2d` measures the free-space scheme instead: bump-windowed
 Gaussians on [-1,1]^2, 256x256 grid, nu = 2048 per dimension (2058 contour
 modes per dimension), p = 8, q = 10, n_r = 1, H for eps = 1e-10, T = 1,
@@ -79,7 +82,7 @@ def parse():
     ap.add_argument("--no-fp64-variant", action="store_true",
                     help="skip the complex128 timing of the same workload in the default (mixed) line")
     ap.add_argument("--workload", default="periodic2d",
-                    choices=["periodic2d", "free2d", "batch1d", "serve", "example1"])
+                    choices=["periodic2d", "free2d", "batch1d", "serve", "example1", "periodic3d"])
     ap.add_argument("--profile-adams", type=int, default=0,
                     help="profiling run: start-up + this many Adams steps of the batch, then exit")
     return ap.parse_args()
@@ -1474,11 +1477,202 @@ def main_serve(args, ws, rank, local):
     return 0
 
 
+# ------------------------------------------------------------ 3D periodic
+M3, DT3, NSTEPS3 = 128, 1e-3, 500
+
+
+def oracle_sample_3d(nadams: int = 1):
+    """The CPU oracle on one 128^3 instance of the 3D workload: `nadams`
+    Adams steps with a seeded history (direct O(M^2) sums per axis)."""
+    from oracle.periodic import oracle_for
+    it = synth.periodic_3d_wells(seed=2, M=M3, dt=DT3, nsteps=NSTEPS3)
+    orc = oracle_for(it)
+    u = it.u0
+    h0 = orc.fwd(orc.V(0.0) * u)
+    n0 = 100
+    hist = {n0 - j: h0 for j in range(1, ORDER)}
+    t0 = time.perf_counter()
+    for k in range(nadams):
+        n = n0 + k
+        u = orc.adams_step(u, n * DT3, hist, n)
+        hist[n] = orc.fwd(orc.V(n * DT3) * u)
+        hist.pop(n - ORDER, None)
+    el = time.perf_counter() - t0
+    return M3 ** 3 * nadams / el, el
+
+
+def launches_per_solve_3d(mixed: bool, groups: int) -> int:
+    """Kernel launches of one tdse_step(NSTEPS3) call on a 3D context: one
+    unfused application of the step operator is 5 kernels (column pass,
+    axis-1 pass, row pass, axis-1 pass, column pass); each Adams step of a
+    group chain is 4 (row pass, axis-1, fused column pass, axis-1)."""
+    L = ORDER // 2
+    sub = sum(2 ** c for c in range(L))
+    startup = STARTUP * (L + sub * 5 + 1 + 5)
+    k = NSTEPS3 - STARTUP
+    adams = groups * (2 + (k - 1) * 4 + 3)
+    return 4 + startup + (1 if mixed else 0) + adams
+
+
+def main_periodic3d(args, ws, rank, local):
+    """3D periodic wells (128^3, dt = 1e-3, 500 steps, 8th order), a batch of
+    seeded instances: whole-solve throughput, the Adams step against HBM
+    (mixed) or the FP64 rate, and the error against the FP64 GPU path."""
+    import torch
+    from paper_2001_06113_gb300 import Problem
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        for _ in range(args.warmup):
+            oracle_sample_3d(1)
+        vals = [oracle_sample_3d(1)[0] for _ in range(args.steps)]
+        v = float(np.mean(vals))
+        print(json.dumps({"impl": "reference", "metric": "point-steps/s (3D periodic 128^3, 8th-order)", "value": v,
+                          "unit": "point-steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1e3 * M3 ** 3 / v, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "3D periodic wells 128^3, dt=1e-3, 8th-order Adams (CPU oracle sample)"},
+                          "cpu_baseline": {"value": v, "unit": "point-steps/s", "cores": cpu_cores(), "kind": "oracle",
+                                           "sample": "1 Adams step of one 128^3 instance per bench step"},
+                          "e2e": {"value": v, "unit": "point-steps/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return 0
+    if ws > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    B = args.batch if args.batch > 0 else (8 if args.precision == "mixed" else 2)
+    insts = [synth.periodic_3d_wells(seed=1000 * rank + 2 + i, M=M3, dt=DT3, nsteps=NSTEPS3) for i in range(B)]
+    P3 = M3 ** 3
+    prob = Problem((M3, M3, M3), DT3, NSTEPS3, order=ORDER, batch=B, precision=args.precision, stream=stream)
+    pinned_V = [torch.from_numpy(it.V0).pin_memory() for it in insts]
+    pinned_u = torch.from_numpy(np.stack([it.u0 for it in insts])).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def load_inputs():
+        for b, it in enumerate(insts):
+            prob.set_potential(pinned_V[b], None, instance=b)
+            p = it.pulse
+            prob.set_pulse(p.A0, p.omega, p.T_pulse, p.direction, instance=b)
+        prob.set_initial_batch(pinned_u)
+
+    load_inputs()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            prob.set_initial_batch(pinned_u)
+            prob.step(NSTEPS3)
+    stream.synchronize()
+    times = []
+    with ClockSampler(local) as clk:
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                prob.set_initial_batch(pinned_u)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                prob.step(NSTEPS3)
+                e1.record(stream)
+            stream.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+    t_solve = max_over_ranks(float(np.mean(times)), ws, dev)
+    value = ws * B * P3 * NSTEPS3 / t_solve
+    GROUP, NGROUPS = 25, 8
+    with torch.cuda.stream(stream):
+        prob.set_initial_batch(pinned_u)
+        prob.step(STARTUP + 8)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(NGROUPS + 1)]
+        evs[0].record(stream)
+        for i in range(NGROUPS):
+            prob.step(GROUP)
+            evs[i + 1].record(stream)
+    stream.synchronize()
+    dts = np.array([evs[i].elapsed_time(evs[i + 1]) / 1e3 / GROUP for i in range(NGROUPS)])
+    t_step = float(np.mean(dts))
+    if args.precision == "mixed":
+        peak, src = hbm_peak()
+        ach = ALGO_BYTES["mixed"] * B * P3 / t_step / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                "traffic": None, "peak_source": src, "algorithmic_bytes_per_point_step": ALGO_BYTES["mixed"],
+                "kernel": "3D Adams step operator: column pass (axis 0), axis-1 passes, row pass (axis 2), "
+                          f"timed over groups of {GROUP} steps"}
+    else:
+        peak, src = fp64_peak(dev)
+        fl = 6 * 35 + (6 * 18 + 7 * 4 + 4 + 18) + 21 + 4 + 6   # six 128-point transforms per point, 3-axis phases
+        ach = fl * B * P3 / t_step / 1e12
+        roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4), "unit": "TFLOP/s (FP64)",
+                "frac": round(ach / peak, 4), "traffic": None, "peak_source": src,
+                "algorithmic_flops_per_point_step": fl,
+                "kernel": f"3D FP64 Adams step operator, timed over groups of {GROUP} steps"}
+    roof["step_ms_p50"] = round(float(np.percentile(dts, 50)) * 1e3, 4)
+    roof["step_ms_p99"] = round(float(np.percentile(dts, 99)) * 1e3, 4)
+    err = None
+    if args.precision == "mixed" and rank == 0:
+        ref = Problem((M3, M3, M3), DT3, NSTEPS3, order=ORDER, batch=1, precision="fp64", stream=stream)
+        it = insts[0]
+        ref.set_potential(it.V0)
+        p = it.pulse
+        ref.set_pulse(p.A0, p.omega, p.T_pulse, p.direction)
+        ref.set_initial(it.u0)
+        with torch.cuda.stream(stream):
+            ref.step(NSTEPS3)
+            prob.set_initial_batch(pinned_u)
+            prob.step(NSTEPS3)
+        a, r = prob.read_u(0), ref.read_u(0)
+        err = float(np.sqrt(np.sum(np.abs(a - r) ** 2) / np.sum(np.abs(r) ** 2)))
+        ref.close()
+    out = torch.empty((B,) + (M3,) * 3, dtype=torch.complex128).pin_memory()
+    e2e_t = []
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, min(args.steps, 2))):
+            flush.zero_()
+            stream.synchronize()
+            t0 = time.perf_counter()
+            load_inputs()
+            prob.step(NSTEPS3)
+            prob.read_u(-1, out=out)
+            e2e_t.append(time.perf_counter() - t0)
+    te = max_over_ranks(float(np.mean(e2e_t)), ws, dev)
+    shape = prob.describe_steps()
+    prob.close()
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and ws == 1:
+            v, el = oracle_sample_3d(1)
+            cpu = {"value": v, "unit": "point-steps/s", "cores": cpu_cores(), "kind": "oracle",
+                   "sample": f"1 Adams step of one 128^3 instance ({el:.1f} s; direct O(M^2) sums per axis)"}
+        print(json.dumps({
+            "metric": "point-steps/s (3D periodic 128^3, 8th-order, T=0.5)", "value": value, "unit": "point-steps/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64+f64" if args.precision == "mixed" else "c128", "data": "synthetic",
+            "config": {"workload": f"3D periodic wells 128^3, T=0.5, dt=1e-3 (500 steps), 8th-order Adams, "
+                                   f"batch of {B} seeded instances per GPU, {args.precision}",
+                       "l2": "flushed (256 MB write) before each timed solve", "launch_shape": shape,
+                       "step": "one whole solve (7 Richardson start-up + 493 Adams steps) of the batch"},
+            "rel_l2_vs_fp64": err, "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": ws * B * P3 * NSTEPS3 / te, "unit": "point-steps/s",
+                    "h2d_bytes_per_step": B * (P3 * 8 + P3 * 16), "d2h_bytes_per_step": B * P3 * 16},
+            "clocks": clk.summary(),
+            "gpu_launches": launches_per_solve_3d(args.precision == "mixed", shape.get("groups", 1)) * args.steps}))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.precision is None:
         args.precision = "fp64" if args.workload == "free2d" else "mixed"
+    if args.batch <= 0 and args.workload == "periodic3d":
+        args.batch = 16 if args.precision == "mixed" else 2
     if args.batch <= 0 and args.workload != "example1":
         args.batch = 1 if args.workload == "free2d" else (64 if args.precision == "mixed" else 4)
     if args.workload == "free2d":
@@ -1489,6 +1683,8 @@ def main():
         return main_serve(args, ws, rank, local)
     if args.workload == "example1":
         return main_example1(args, ws, rank, local)
+    if args.workload == "periodic3d":
+        return main_periodic3d(args, ws, rank, local)
     if args.impl == "reference":
         if rank != 0:
             return 0

@@ -172,6 +172,44 @@ def periodic_2d_wells(seed: int = 2, M: int = 512, dt: float = 1e-3, nsteps: int
                     name=f"periodic_2d_wells_M{M}")
 
 
+def _periodised_gaussian_1d(x, c, sigma, images=3):
+    L = 2.0 * math.pi
+    return sum(np.exp(-(x - c - L * m) ** 2 / (2.0 * sigma * sigma)) for m in range(-images, images + 1))
+
+
+def periodic_3d_wells(seed: int = 2, M: int = 128, dt: float = 1e-3, nsteps: int = 500,
+                      A0: float = 2.0, omega: float = 10.0) -> Instance:
+    """3D periodic workload on [-pi,pi]^3 shaped like the 2D wells workload:
+    u0 = normalised sum of 3 Gaussians (sigma ~ U[0.3,0.5], centres ~
+    U[-1,1]^3, random phases); V0 = sum of 4 attractive wells -depth
+    exp(-|x-c|^2/(2 sigma^2)), depth ~ U[5,20], sigma ~ U[0.4,0.7], centres ~
+    U[-1,1]^3; each Gaussian is a product of 1D lattice-image sums (|m| <= 3),
+    so both are smooth and periodic.  A(t) = A0 sin^2(pi t/T) sin(omega t)
+    (1,0,0), T = nsteps dt."""
+    rng = np.random.default_rng([seed, 3])
+    x = periodic_grid(M)
+
+    def gauss(c, s):
+        g = [_periodised_gaussian_1d(x, c[a], s) for a in range(3)]
+        return g[0][:, None, None] * g[1][None, :, None] * g[2][None, None, :]
+
+    u0 = np.zeros((M, M, M), dtype=np.complex128)
+    for _ in range(3):
+        s = rng.uniform(0.3, 0.5)
+        c = rng.uniform(-1.0, 1.0, size=3)
+        u0 += np.exp(1j * rng.uniform(0.0, 2.0 * math.pi)) * gauss(c, s)
+    h = 2.0 * math.pi / M
+    u0 = u0 / math.sqrt(float(np.sum(np.abs(u0) ** 2)) * h ** 3)
+    V0 = np.zeros((M, M, M), dtype=np.float64)
+    for _ in range(4):
+        depth = rng.uniform(5.0, 20.0)
+        s = rng.uniform(0.4, 0.7)
+        c = rng.uniform(-1.0, 1.0, size=3)
+        V0 -= depth * gauss(c, s)
+    pulse = Pulse(A0, omega, nsteps * dt, (1.0, 0.0, 0.0))
+    return Instance(PERIODIC, (M, M, M), u0, V0, _const_one, pulse, dt, nsteps, name=f"periodic_3d_wells_M{M}")
+
+
 BATCH_SIZES = tuple(2 ** p for p in range(8, 15))   # 256 .. 16384
 
 
