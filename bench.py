@@ -82,7 +82,7 @@ def parse():
     ap.add_argument("--no-fp64-variant", action="store_true",
                     help="skip the complex128 timing of the same workload in the default (mixed) line")
     ap.add_argument("--workload", default="periodic2d",
-                    choices=["periodic2d", "free2d", "batch1d", "serve", "example1", "periodic3d"])
+                    choices=["periodic2d", "free2d", "batch1d", "serve", "example1", "periodic3d", "free_ctype"])
     ap.add_argument("--profile-adams", type=int, default=0,
                     help="profiling run: start-up + this many Adams steps of the batch, then exit")
     return ap.parse_args()
@@ -1666,6 +1666,44 @@ def main_periodic3d(args, ws, rank, local):
     return 0
 
 
+def main_free_ctype(args, ws, rank, local):
+    """Cost of the C-type transforms against the dyadic refinement n_r of the
+    Gauss panels (N^C = 2 q n_r modes; n_r = O(log T) for long runs, Sec. 6):
+    ms per Adams step of the 2D free-space workload (256^2, nu = 2048, FP64)
+    with the C block as direct sums and through the Chebyshev interpolant
+    (Sec. 4.1), n_r = 1..4, timed over 40 steps after the start-up."""
+    import torch
+    from paper_2001_06113_gb300 import Problem
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    inst = free_instances(0, 1)[0]
+    H = free_H([inst], "fp64")
+    rows = []
+    for n_r in (1, 2, 3, 4):
+        for ct in ("direct", "chebyshev"):
+            prob = Problem((FS_M, FS_M), FS_DT, FS_NSTEPS, order=ORDER, precision="fp64", stream=stream, bc="free",
+                           nu=(FS_NU, FS_NU), H=H, gauss_q=FS_Q, n_r=n_r, c_transform=ct)
+            prob.set_potential(inst.V0, None)
+            p = inst.pulse
+            prob.set_pulse(p.A0, p.omega, p.T_pulse, p.direction)
+            prob.set_initial(inst.u0)
+            with torch.cuda.stream(stream):
+                prob.step(STARTUP + 4)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                prob.step(40)
+                e1.record(stream)
+            stream.synchronize()
+            rows.append({"n_r": n_r, "NC": FS_Q * 2 * n_r, "c_transform": ct, "N_T": prob.cheb_terms(0),
+                         "ms_per_step": round(e0.elapsed_time(e1) / 40, 4)})
+            prob.close()
+    print(json.dumps({"workload": "free-space C-type transform cost vs n_r (2D 256^2, nu = 2048, FP64, H for "
+                                  "eps = 1e-10)", "unit": "ms per Adams step", "rows": rows}))
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -1685,6 +1723,8 @@ def main():
         return main_example1(args, ws, rank, local)
     if args.workload == "periodic3d":
         return main_periodic3d(args, ws, rank, local)
+    if args.workload == "free_ctype":
+        return main_free_ctype(args, ws, rank, local)
     if args.impl == "reference":
         if rank != 0:
             return 0

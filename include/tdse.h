@@ -67,6 +67,7 @@ enum { TDSE_HOST = 0, TDSE_DEVICE = 1 };
 enum { TDSE_V_SEPARABLE = 0, TDSE_V_TABLE = 1, TDSE_V_TABLE_SHARED = 2 };
 enum { TDSE_BATCH_FUSED = 0, TDSE_BATCH_STREAMS = 1 };
 enum { TDSE_PATH_AUTO = 0, TDSE_PATH_PASSES = 1, TDSE_PATH_CLUSTER = 2 };
+enum { TDSE_CT_AUTO = 0, TDSE_CT_DIRECT = 1, TDSE_CT_CHEBYSHEV = 2 };
 
 /*
  * Problem configuration.
@@ -141,6 +142,13 @@ typedef struct {
     /* dim = 3 (periodic only): grid points along axis 2; n[0], n[1] are
      * axes 0 and 1.  Ignored for dim < 3.  Appended last. */
     int n_z;
+    /* free space: how the C-type transforms (the Gauss modes on Gamma_2)
+     * are evaluated (Sec. 4.1): TDSE_CT_DIRECT = direct sums, O(M N^C) per
+     * line; TDSE_CT_CHEBYSHEV = the Chebyshev interpolant in tau of
+     * e^{-+(1+i) tau x} (eqs. expintrpm, expintrpp), O(N_T (M + N^C)) with
+     * N_T chosen so that the interpolant is exact to FP64 rounding at the
+     * C nodes; TDSE_CT_AUTO (0) = Chebyshev when N_T < N^C.  Appended last. */
+    int c_transform;
 } tdse_config;
 
 /* Vector potential callback: writes A(t) (dim components) to A_out. */
@@ -264,6 +272,12 @@ tdse_status tdse_read_modes(tdse_ctx* ctx, int instance, double* u_out, int wher
  * (Gamma_3, equispaced), each in ascending real part.  TDSE_EINVAL for a
  * periodic context or a bad axis. */
 tdse_status tdse_free_rule(const tdse_ctx* ctx, int axis, int* N, double* zeta, double* w);
+
+/* Free space: the number N_T of Chebyshev terms with which the C-type
+ * transforms of dimension `axis` are evaluated (Sec. 4.1; see
+ * tdse_config.c_transform), 0 if they are direct sums, -1 for a periodic
+ * context, a bad axis or NULL. */
+int tdse_free_cheb_terms(const tdse_ctx* ctx, int axis);
 
 /* The contour offset of Remark Hchoice:
  *   H = log(eps / ((1 + vnorm) eps_m)) / (2 dim (1 + phimax)),  eps_m = 2^-52,

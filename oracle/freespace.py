@@ -32,6 +32,44 @@ def free_grid(M: int) -> np.ndarray:
     return -1.0 + 2.0 * np.arange(M, dtype=np.float64) / M
 
 
+def ctype_chebyshev(rule: GammaRule, NT: int):
+    """C-type transforms through Chebyshev interpolants (Sec. 4.1, eqs.
+    expintrpm and expintrpp), for one dimension of `rule`.
+
+    On Gamma_2, zeta = (1 - i) tau with tau in [-H, H], so
+        e^{-i zeta x_j} = e^{-tau x_j} e^{-i tau x_j} ~ sum_l lambda_{l,j} T_l^H(tau),
+        e^{+i zeta x_j} = e^{+tau x_j} e^{+i tau x_j} ~ sum_l rho_{j,l} T_l^H(tau),
+    with T_l^H(tau) = T_l(tau / H) and each interpolant the polynomial of degree
+    NT - 1 through the values at the Chebyshev points tau_m = H cos(pi (m + 1/2) / NT).
+    Changing the order of summation gives
+        f^_k = (2/M) sum_l T_l^H(tau_k) sum_j lambda_{l,j} f_j         (forward, C nodes)
+        f_j  = (1/2pi) sum_l rho_{j,l} sum_k T_l^H(tau_k) w_k f^_k    (inverse, C nodes)
+    Returns (fwd, inv): fwd(f) -> the NC C-node values, inv(fhat_C) -> M grid
+    values, with the same scalings as eqs. fzdft / uciftdisc."""
+    M, H = rule.M, rule.H
+    x = free_grid(M)
+    theta = math.pi * (np.arange(NT) + 0.5) / NT
+    tau_m = H * np.cos(theta)
+    Cmat = np.cos(np.outer(np.arange(NT), theta))                       # [l, m] = T_l(cos theta_m)
+    g_minus = np.exp(-(1.0 + 1.0j) * np.outer(tau_m, x))                # [m, j]
+    g_plus = np.exp((1.0 + 1.0j) * np.outer(tau_m, x))
+    lam = (2.0 / NT) * (Cmat @ g_minus)                                 # [l, j]
+    rho = (2.0 / NT) * (Cmat @ g_plus)
+    lam[0] *= 0.5
+    rho[0] *= 0.5
+    tau_k = rule.tau_c
+    Tk = np.cos(np.outer(np.arccos(np.clip(tau_k / H, -1.0, 1.0)), np.arange(NT)))   # [k, l] = T_l^H(tau_k)
+    w_c = rule.blocks["C"][1]
+
+    def fwd(f):
+        return (2.0 / M) * (Tk @ (lam @ np.asarray(f, dtype=np.complex128)))
+
+    def inv(fh_c):
+        return (rho.T @ (Tk.T @ (w_c * np.asarray(fh_c, dtype=np.complex128)))) / (2.0 * math.pi)
+
+    return fwd, inv
+
+
 class FreeSpaceOracle:
     """Direct implementation of the free-space scheme for d = 1 or 2.
 

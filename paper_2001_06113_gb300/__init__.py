@@ -47,8 +47,9 @@ def free_choose_H(eps: float, vnorm: float, phimax: float, dim: int, precision: 
 
 
 def _config(shape, dt, nsteps, order, batch, precision, startup_steps, bc, nu, H, alpert_p, gauss_q, n_r,
-            potential="separable"):
+            potential="separable", c_transform="auto"):
     cfg = _native.TdseConfig()
+    cfg.c_transform = {"auto": 0, "direct": 1, "chebyshev": 2}[c_transform]
     cfg.potential = {"separable": _native.TDSE_V_SEPARABLE, "table": _native.TDSE_V_TABLE,
                      "shared_table": _native.TDSE_V_TABLE_SHARED}[potential]
     cfg.dim = len(shape)
@@ -115,7 +116,7 @@ class Problem:
     def __init__(self, shape: Sequence[int], dt: float, nsteps: int, order: int = 8, batch: int = 1,
                  precision: str = "fp64", startup_steps: int = -1, device=None, stream=None, bc: str = "periodic",
                  nu: Optional[Sequence[int]] = None, H: float = 0.0, alpert_p: int = 8, gauss_q: int = 10,
-                 n_r: int = 1, potential: str = "separable"):
+                 n_r: int = 1, potential: str = "separable", c_transform: str = "auto"):
         import torch
         self._lib = _native.lib()
         self.shape = tuple(int(s) for s in shape)
@@ -126,7 +127,7 @@ class Problem:
         self.precision = precision
         self.potential = potential
         cfg = _config(self.shape, dt, nsteps, order, batch, precision, startup_steps, bc, nu, H, alpert_p, gauss_q,
-                      n_r, potential)
+                      n_r, potential, c_transform)
         self._ctx = ctypes.c_void_p()
         _check(self._lib.tdse_create(ctypes.byref(cfg), ctypes.byref(self._ctx)))
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
@@ -143,11 +144,11 @@ class Problem:
     def workspace_bytes_for(shape: Sequence[int], dt: float, nsteps: int, order: int = 8, batch: int = 1,
                             precision: str = "fp64", startup_steps: int = -1, bc: str = "periodic",
                             nu: Optional[Sequence[int]] = None, H: float = 0.0, alpert_p: int = 8, gauss_q: int = 10,
-                            n_r: int = 1, potential: str = "separable") -> int:
+                            n_r: int = 1, potential: str = "separable", c_transform: str = "auto") -> int:
         """Device workspace a Problem of this configuration needs (host-only query)."""
         lib = _native.lib()
         cfg = _config(tuple(int(s) for s in shape), dt, nsteps, order, batch, precision, startup_steps, bc, nu, H,
-                      alpert_p, gauss_q, n_r, potential)
+                      alpert_p, gauss_q, n_r, potential, c_transform)
         ctx = ctypes.c_void_p()
         _check(lib.tdse_create(ctypes.byref(cfg), ctypes.byref(ctx)))
         n = int(lib.tdse_workspace_bytes(ctx))
@@ -265,6 +266,11 @@ class Problem:
         if self.bc != "free":
             return self.shape
         return tuple(self.free_rule(a)[0].size for a in range(len(self.shape)))
+
+    def cheb_terms(self, axis: int) -> int:
+        """Free space: Chebyshev terms N_T of the C-type transforms of `axis`
+        (0: direct sums)."""
+        return int(self._lib.tdse_free_cheb_terms(self._ctx, axis))
 
     def free_rule(self, axis: int):
         """(zeta, w): nodes and weights of the contour rule of `axis` (free space)."""

@@ -29,7 +29,7 @@ EXPORTS = [
     "tdse_last_error", "tdse_destroy", "tdse_modes_to_grid_2d_noalloc", "tdse_read_modes", "tdse_free_rule",
     "tdse_free_choose_H", "tdse_free_choose_H_prec", "tdse_potential_times", "tdse_set_potential_table", "tdse_batch_create", "tdse_batch_tune", "tdse_batch_set_mode", "tdse_batch_step", "tdse_batch_describe",
     "tdse_batch_last_error", "tdse_batch_destroy", "tdse_set_residual_check", "tdse_residual_report",
-    "tdse_save", "tdse_load", "tdse_set_step_path", "tdse_step_path", "tdse_describe_steps", "tdse_set_step_groups",
+    "tdse_save", "tdse_load", "tdse_set_step_path", "tdse_step_path", "tdse_describe_steps", "tdse_set_step_groups", "tdse_free_cheb_terms",
 ]
 NOALLOC_MAX_POINTS = 524288
 
@@ -52,6 +52,7 @@ class TdseConfig(ctypes.Structure):
         ("H", ctypes.c_double),
         ("potential", ctypes.c_int),
         ("n_z", ctypes.c_int),
+        ("c_transform", ctypes.c_int),
     ]
 
 
@@ -109,6 +110,7 @@ def load(path: str = _LIB_PATH) -> ctypes.CDLL:
         "tdse_step_path": ([vp], ip),
         "tdse_describe_steps": ([vp, ctypes.c_char_p, ctypes.c_size_t], ip),
         "tdse_set_step_groups": ([vp, ip], ip),
+        "tdse_free_cheb_terms": ([vp, ip], ip),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -21,6 +21,7 @@ void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w);
 // One axis of the free-space contour rule (Sec. 3.4, 4.1), host copy.
 struct FsAxisHost {
     int M = 0, nu = 0, R = 0, NE = 0, ND = 0, NC = 0, N = 0, p = 0, kappa = 0, q = 0, n_r = 0;
+    int NT = 0;                 // terms of the Chebyshev form of the C-type transforms (0: direct sums)
     double H = 0, K = 0, h = 0;
     std::vector<double> zeta;   // [N][2] nodes (complex)
     std::vector<double> w;      // [N][2] weights (complex)
@@ -38,6 +39,8 @@ struct FsState {
         size_t preI_f[2], postI_f[2], preF_f[2], postF_f[2], Gd_f[2], Fd_f[2], tw_f[2], P_f[2];
         // FP64 residual check of the FP32 step (f32 only): W / corrected state, R64, u64, 2D intermediate
         size_t res_W, res_R, res_u, Z64;
+        // Chebyshev form of the C-type transforms (NT > 0 only)
+        size_t Lf[2], Li[2], Tc[2], TcW[2], Lf_f[2], Li_f[2], Tc_f[2], TcW_f[2];
     } off{};
     int zero_iv = -1;   // f32: interval of zero length (one-step phase 1) for the FP64 re-evaluation
 };

@@ -75,6 +75,10 @@ template <> struct Tab<double2> {
     static __device__ __forceinline__ const double2* Fd(const FsAxis& a) { return a.Fd; }
     static __device__ __forceinline__ const double2* tw(const FsAxis& a) { return a.tw; }
     static __device__ __forceinline__ const double2* P(const FsAxis& a) { return a.P; }
+    static __device__ __forceinline__ const double2* Lf(const FsAxis& a) { return a.Lf; }
+    static __device__ __forceinline__ const double2* Li(const FsAxis& a) { return a.Li; }
+    static __device__ __forceinline__ const double* Tc(const FsAxis& a) { return a.Tc; }
+    static __device__ __forceinline__ const double2* TcW(const FsAxis& a) { return a.TcW; }
 };
 template <> struct Tab<float2> {
     static __device__ __forceinline__ const float2* preI(const FsAxis& a) { return a.preI_f; }
@@ -85,6 +89,10 @@ template <> struct Tab<float2> {
     static __device__ __forceinline__ const float2* Fd(const FsAxis& a) { return a.Fd_f; }
     static __device__ __forceinline__ const float2* tw(const FsAxis& a) { return a.tw_f; }
     static __device__ __forceinline__ const float2* P(const FsAxis& a) { return a.P_f; }
+    static __device__ __forceinline__ const float2* Lf(const FsAxis& a) { return a.Lf_f; }
+    static __device__ __forceinline__ const float2* Li(const FsAxis& a) { return a.Li_f; }
+    static __device__ __forceinline__ const float* Tc(const FsAxis& a) { return a.Tc_f; }
+    static __device__ __forceinline__ const float2* TcW(const FsAxis& a) { return a.TcW_f; }
 };
 
 template <class C, int M, int R>
@@ -110,19 +118,36 @@ struct FsLine {
             E[j * LS + b * R + s] = cmul(f[j], __ldg(&preF[it]));
         }
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int dd = warp; dd < ax.ND; dd += FsThreads<C>::value / 32) {
+        const bool cheb = ax.NT > 0;
+        // one warp per row: the dense rows by direct sums (the C rows too
+        // unless they go through the interpolant), then the NT interpolant rows
+        const int nrow = ax.ND + (cheb ? ax.NT : 0);
+        for (int rr = warp; rr < nrow; rr += FsThreads<C>::value / 32) {
+            if (cheb && rr >= ax.p && rr < ax.p + ax.NC) continue;
+            const bool crow = rr >= ax.ND;
+            const C* row = crow ? T::Lf(ax) + (size_t)(rr - ax.ND) * M : T::Fd(ax) + (size_t)rr * M;
             C acc = zeroc<C>();
-            const C* row = T::Fd(ax) + (size_t)dd * M;
             for (int j = lane; j < M; j += 32) acc = acc + cmul(__ldg(&row[j]), f[j]);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
                 acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
             }
-            if (lane == 0) dv[dd] = acc;
+            if (lane == 0) {
+                if (crow) dv[FS_MAX_ND + rr - ax.ND] = acc;      // g_l = sum_j (2/M) lambda_l(x_j) f_j
+                else dv[rr] = acc;
+            }
         }
         __syncthreads();
-        FftF::run(E, T::tw(ax), nullptr);
+        if (cheb) {   // C rows: f^_k = sum_l T_l(tau_k / H) g_l
+            for (int k = threadIdx.x; k < ax.NC; k += FsThreads<C>::value) {
+                const auto* tc = T::Tc(ax) + (size_t)k * ax.NT;
+                C acc = zeroc<C>();
+                for (int l = 0; l < ax.NT; ++l) acc = acc + cscale(dv[FS_MAX_ND + l], __ldg(&tc[l]));
+                dv[ax.p + k] = acc;
+            }
+        }
+        FftF::run(E, T::tw(ax), nullptr);   // begins with reads of E only; ends with a barrier
     }
 
     // Forward result for mode m after forward().
@@ -160,6 +185,16 @@ struct FsLine {
     // Begins and ends with a barrier.
     __device__ static void inverse(C* E, const C* dv, C* y, const FsAxis& ax) {
         __syncthreads();
+        const bool cheb = ax.NT > 0;
+        if (cheb) {   // h_l = sum_k T_l(tau_k / H) (w_k / 2pi) f^_k (read after FftI's barriers)
+            C* hb = const_cast<C*>(dv) + FS_MAX_ND;
+            for (int l = threadIdx.x; l < ax.NT; l += FsThreads<C>::value) {
+                const C* tw = T::TcW(ax) + (size_t)l * ax.NC;
+                C acc = zeroc<C>();
+                for (int k = 0; k < ax.NC; ++k) acc = acc + cmul(__ldg(&tw[k]), dv[ax.p + k]);
+                hb[l] = acc;
+            }
+        }
         FftI::run(E, T::tw(ax), nullptr);
         for (int j = threadIdx.x; j < M; j += FsThreads<C>::value) {
             C acc = zeroc<C>();
@@ -169,7 +204,15 @@ struct FsLine {
 #pragma unroll
             for (int s = 0; s < R; ++s) acc = acc + cmul(E[j * LS + R + s], __ldg(&pj[NU + s]));
             const C* gd = T::Gd(ax);
-            for (int dd = 0; dd < ax.ND; ++dd) acc = acc + cmul(__ldg(&gd[(size_t)dd * M + j]), dv[dd]);
+            if (!cheb) {
+                for (int dd = 0; dd < ax.ND; ++dd) acc = acc + cmul(__ldg(&gd[(size_t)dd * M + j]), dv[dd]);
+            } else {   // Alpert rows directly, the C rows as sum_l rho_l(x_j) h_l
+                for (int dd = 0; dd < ax.p; ++dd) acc = acc + cmul(__ldg(&gd[(size_t)dd * M + j]), dv[dd]);
+                for (int dd = ax.p + ax.NC; dd < ax.ND; ++dd)
+                    acc = acc + cmul(__ldg(&gd[(size_t)dd * M + j]), dv[dd]);
+                const C* li = T::Li(ax);
+                for (int l = 0; l < ax.NT; ++l) acc = acc + cmul(__ldg(&li[(size_t)l * M + j]), dv[FS_MAX_ND + l]);
+            }
             y[j] = acc;
         }
         __syncthreads();
@@ -394,7 +437,7 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
 
 template <class C, int M, int R>
 constexpr size_t smem_of() {
-    return (size_t)(FsLine<C, M, R>::EBUF + M + FS_MAX_ND) * sizeof(C);
+    return (size_t)(FsLine<C, M, R>::EBUF + M + FS_MAX_ND + FS_MAX_NT) * sizeof(C);
 }
 
 // Dynamic shared memory of the kernel and, for the FP32 kernels, the largest

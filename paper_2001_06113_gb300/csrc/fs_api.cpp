@@ -99,7 +99,126 @@ bool build_rule(FsAxisHost& A, int M, int nu, int p, int q, int n_r, double H) {
 
 struct AxisTables {
     std::vector<double> zeta, preI, postI, preF, postF, Gd, Fd, tw;
+    std::vector<double> Lf, Li, Tc, TcW;   // Chebyshev form of the C-type transforms (NT > 0)
 };
+
+// Chebyshev form of the C-type transforms (Sec. 4.1).  For a grid point x the
+// function tau -> e^{s (1+i) tau x} (s = -1 forward: e^{-i zeta x}; s = +1
+// inverse: e^{+i zeta x}, zeta = (1 - i) tau) on [-H, H] is replaced by its
+// NT-point Chebyshev interpolant sum_l c_l T_l(tau / H), the coefficients from
+// the values at the Chebyshev points tau_m = H cos(pi (m + 1/2) / NT):
+//   c_l = (2 / NT) sum_m g(tau_m) cos(l pi (m + 1/2) / NT),  c_0 halved.
+// Long double throughout, rounded once.
+struct ChebPoints {
+    int NT;
+    std::vector<long double> u, cosl_;   // cos(th_m), cos(l th_m) [m][l]
+    ChebPoints(int nt) : NT(nt), u(nt), cosl_((size_t)nt * nt) {
+        for (int m = 0; m < nt; ++m) {
+            const long double th = kPiL * (m + 0.5L) / nt;
+            u[m] = cosl(th);
+            for (int l = 0; l < nt; ++l) cosl_[(size_t)m * nt + l] = cosl(l * th);
+        }
+    }
+};
+void cheb_coeffs(long double x, int s, long double H, const ChebPoints& P, std::vector<long double>& cr,
+                 std::vector<long double>& ci) {
+    const int NT = P.NT;
+    cr.assign(NT, 0.0L);
+    ci.assign(NT, 0.0L);
+    for (int m = 0; m < NT; ++m) {
+        const long double tau = H * P.u[m];
+        const long double mag = expl(s * tau * x), ang = s * tau * x;   // e^{s tau x} e^{i s tau x}
+        const long double gr = mag * cosl(ang), gi = mag * sinl(ang);
+        const long double* cl = &P.cosl_[(size_t)m * NT];
+        for (int l = 0; l < NT; ++l) {
+            cr[l] += gr * cl[l];
+            ci[l] += gi * cl[l];
+        }
+    }
+    for (int l = 0; l < NT; ++l) {
+        cr[l] *= 2.0L / NT;
+        ci[l] *= 2.0L / NT;
+    }
+    cr[0] *= 0.5L;
+    ci[0] *= 0.5L;
+}
+
+// T_l(u), l = 0..NT-1, by the three-term recurrence
+void cheb_T(long double u, int NT, std::vector<long double>& T) {
+    T.assign(NT, 0.0L);
+    T[0] = 1.0L;
+    if (NT > 1) T[1] = u;
+    for (int l = 2; l < NT; ++l) T[l] = 2.0L * u * T[l - 1] - T[l - 2];
+}
+
+// Smallest NT (8..FS_MAX_NT, even) whose interpolants reproduce e^{-+i zeta x}
+// at every C node and grid point to 4 units of FP64 rounding of the largest
+// value; 0 if none does.
+int choose_nt(const FsAxisHost& A) {
+    const int p = A.p, NC = A.NC, M = A.M, NE = A.NE;
+    const long double H = A.H;
+    std::vector<long double> cr, ci, T;
+    for (int NT = 8; NT <= FS_MAX_NT; NT += 2) {
+        const ChebPoints P(NT);
+        long double err = 0.0L, big = 0.0L;
+        for (int j = 0; j < M; ++j) {
+            const long double x = -1.0L + 2.0L * j / M;
+            for (int sg = -1; sg <= 1; sg += 2) {
+                cheb_coeffs(x, sg, H, P, cr, ci);
+                for (int k = 0; k < NC; ++k) {
+                    const long double tau = A.zeta[2 * (NE + p + k)];
+                    cheb_T(tau / H, NT, T);
+                    long double vr = 0.0L, vi = 0.0L;
+                    for (int l = 0; l < NT; ++l) {
+                        vr += cr[l] * T[l];
+                        vi += ci[l] * T[l];
+                    }
+                    const long double mag = expl(sg * tau * x), ang = sg * tau * x;
+                    const long double gr = mag * cosl(ang), gi = mag * sinl(ang);
+                    err = fmaxl(err, hypotl(vr - gr, vi - gi));
+                    big = fmaxl(big, mag);
+                }
+            }
+        }
+        if (err <= 4.0L * 2.220446049250313e-16L * big) return NT;
+    }
+    return 0;
+}
+
+void make_cheb_tables(const FsAxisHost& A, AxisTables& T) {
+    const int M = A.M, NT = A.NT, NC = A.NC, NE = A.NE, p = A.p;
+    const long double H = A.H;
+    std::vector<long double> cr, ci, Tl;
+    const ChebPoints P(NT);
+    T.Lf.assign((size_t)2 * NT * M, 0.0);
+    T.Li.assign((size_t)2 * NT * M, 0.0);
+    for (int j = 0; j < M; ++j) {
+        const long double x = -1.0L + 2.0L * j / M;
+        cheb_coeffs(x, -1, H, P, cr, ci);
+        for (int l = 0; l < NT; ++l) {
+            T.Lf[2 * ((size_t)l * M + j)] = (double)(cr[l] * 2.0L / M);
+            T.Lf[2 * ((size_t)l * M + j) + 1] = (double)(ci[l] * 2.0L / M);
+        }
+        cheb_coeffs(x, +1, H, P, cr, ci);
+        for (int l = 0; l < NT; ++l) {
+            T.Li[2 * ((size_t)l * M + j)] = (double)cr[l];
+            T.Li[2 * ((size_t)l * M + j) + 1] = (double)ci[l];
+        }
+    }
+    T.Tc.assign((size_t)NC * NT, 0.0);
+    T.TcW.assign((size_t)2 * NT * NC, 0.0);
+    const long double inv2pi = 1.0L / (2.0L * kPiL);
+    for (int k = 0; k < NC; ++k) {
+        const int m = NE + p + k;
+        cheb_T((long double)A.zeta[2 * m] / H, NT, Tl);
+        const long double wr = A.w[2 * m] * inv2pi, wi = A.w[2 * m + 1] * inv2pi;
+        for (int l = 0; l < NT; ++l) {
+            T.Tc[(size_t)k * NT + l] = (double)Tl[l];
+            T.TcW[2 * ((size_t)l * NC + k)] = (double)(Tl[l] * wr);
+            T.TcW[2 * ((size_t)l * NC + k) + 1] = (double)(Tl[l] * wi);
+        }
+    }
+}
 
 // Host tables of one axis (fsargs.h FsAxis), in FP64 from long double phases.
 AxisTables make_tables(const FsAxisHost& A) {
@@ -151,6 +270,7 @@ AxisTables make_tables(const FsAxisHost& A) {
         }
     }
     for (int m = 0; m < M; ++m) put(T.tw, 1.0, -2.0L * kPiL * m / M);
+    if (A.NT > 0) make_cheb_tables(A, T);
     return T;
 }
 
@@ -181,6 +301,21 @@ FsArgs fs_base(const tdse_ctx* c) {
         X.Fd = c->P<double2>(F.off.Fd[x]);
         X.tw = c->P<double2>(F.off.tw[x]);
         X.P = c->P<double2>(F.off.P[x]);
+        X.p = A.p;
+        X.NC = A.NC;
+        X.NT = A.NT;
+        if (A.NT > 0) {
+            X.Lf = c->P<double2>(F.off.Lf[x]);
+            X.Li = c->P<double2>(F.off.Li[x]);
+            X.Tc = c->P<double>(F.off.Tc[x]);
+            X.TcW = c->P<double2>(F.off.TcW[x]);
+            if (F.f32) {
+                X.Lf_f = c->P<float2>(F.off.Lf_f[x]);
+                X.Li_f = c->P<float2>(F.off.Li_f[x]);
+                X.Tc_f = c->P<float>(F.off.Tc_f[x]);
+                X.TcW_f = c->P<float2>(F.off.TcW_f[x]);
+            }
+        }
         if (F.f32) {
             X.preI_f = c->P<float2>(F.off.preI_f[x]);
             X.postI_f = c->P<float2>(F.off.postI_f[x]);
@@ -387,6 +522,8 @@ tdse_status fs_create(tdse_ctx* c) {
     if (g.gauss_q < 1 || g.gauss_q > 32) return c->fail(TDSE_EINVAL, "gauss_q must be in 1..32");
     if (g.n_r < 0 || g.n_r > 4) return c->fail(TDSE_EINVAL, "n_r must be in 0..4");
     if (!(g.H > 0.0) || !std::isfinite(g.H)) return c->fail(TDSE_EINVAL, "H must be positive");
+    if (g.c_transform < TDSE_CT_AUTO || g.c_transform > TDSE_CT_CHEBYSHEV)
+        return c->fail(TDSE_EINVAL, "c_transform: TDSE_CT_AUTO, TDSE_CT_DIRECT or TDSE_CT_CHEBYSHEV");
     F.f32 = g.precision == TDSE_MIXED;
     F.NM = 1;
     F.NX = 1;
@@ -396,6 +533,14 @@ tdse_status fs_create(tdse_ctx* c) {
         if (!fs_supported(M, nu / M)) return c->fail(TDSE_EUNSUPPORTED, "free space: n in 32..512, nu/n in {4,8,16}, nu <= 4096");
         if (!build_rule(F.ax[x], M, nu, p, g.gauss_q, g.n_r, g.H))
             return c->fail(TDSE_EINVAL, "contour rule: NE must exceed n/2 and the dense block 128 modes");
+        F.ax[x].NT = 0;
+        if (g.c_transform != TDSE_CT_DIRECT) {
+            const int nt = choose_nt(F.ax[x]);
+            if (g.c_transform == TDSE_CT_CHEBYSHEV && nt == 0)
+                return c->fail(TDSE_EUNSUPPORTED, "C-type transforms: no Chebyshev interpolant of at most 64 terms "
+                                                  "reaches FP64 rounding for this H");
+            if (g.c_transform == TDSE_CT_CHEBYSHEV || (nt > 0 && nt < F.ax[x].NC)) F.ax[x].NT = nt;
+        }
         F.NM *= (size_t)F.ax[x].N;
         F.NX *= (size_t)M;
     }
@@ -428,6 +573,18 @@ tdse_status fs_create(tdse_ctx* c) {
         F.off.Fd[x] = take((size_t)A.ND * A.M * 16);
         F.off.tw[x] = take((size_t)A.M * 16);
         F.off.P[x] = take(B * (size_t)c->n_int * A.N * 16);
+        if (A.NT > 0) {
+            F.off.Lf[x] = take((size_t)A.NT * A.M * 16);
+            F.off.Li[x] = take((size_t)A.NT * A.M * 16);
+            F.off.Tc[x] = take((size_t)A.NC * A.NT * 8);
+            F.off.TcW[x] = take((size_t)A.NT * A.NC * 16);
+            if (F.f32) {
+                F.off.Lf_f[x] = take((size_t)A.NT * A.M * 8);
+                F.off.Li_f[x] = take((size_t)A.NT * A.M * 8);
+                F.off.Tc_f[x] = take((size_t)A.NC * A.NT * 4);
+                F.off.TcW_f[x] = take((size_t)A.NT * A.NC * 8);
+            }
+        }
         if (F.f32) {
             F.off.preI_f[x] = take((size_t)2 * A.NE * 8);
             F.off.postI_f[x] = take((size_t)2 * A.nu * 8);
@@ -484,6 +641,12 @@ tdse_status fs_bind(tdse_ctx* c, cudaStream_t s) {
         TDSE_CK(c, up(F.off.Gd[x], T.Gd));
         TDSE_CK(c, up(F.off.Fd[x], T.Fd));
         TDSE_CK(c, up(F.off.tw[x], T.tw));
+        if (F.ax[x].NT > 0) {
+            TDSE_CK(c, up(F.off.Lf[x], T.Lf));
+            TDSE_CK(c, up(F.off.Li[x], T.Li));
+            TDSE_CK(c, up(F.off.Tc[x], T.Tc));
+            TDSE_CK(c, up(F.off.TcW[x], T.TcW));
+        }
         // FP32 copies: each complex value rounded from the FP64 table
         std::vector<float> t32;
         auto up32 = [&](size_t off, const std::vector<double>& v) -> cudaError_t {
@@ -499,6 +662,12 @@ tdse_status fs_bind(tdse_ctx* c, cudaStream_t s) {
             TDSE_CK(c, up32(F.off.Gd_f[x], T.Gd));
             TDSE_CK(c, up32(F.off.Fd_f[x], T.Fd));
             TDSE_CK(c, up32(F.off.tw_f[x], T.tw));
+            if (F.ax[x].NT > 0) {
+                TDSE_CK(c, up32(F.off.Lf_f[x], T.Lf));
+                TDSE_CK(c, up32(F.off.Li_f[x], T.Li));
+                TDSE_CK(c, up32(F.off.Tc_f[x], T.Tc));
+                TDSE_CK(c, up32(F.off.TcW_f[x], T.TcW));
+            }
         }
         TDSE_CK(c, cudaStreamSynchronize(s));    // T goes out of scope
     }
@@ -589,4 +758,9 @@ extern "C" tdse_status tdse_free_choose_H_prec(double eps, double vnorm, double 
 
 extern "C" tdse_status tdse_free_choose_H(double eps, double vnorm, double phimax, int dim, double* H_out) {
     return tdse_free_choose_H_prec(eps, vnorm, phimax, dim, TDSE_FP64, H_out);
+}
+
+extern "C" int tdse_free_cheb_terms(const tdse_ctx* c, int axis) {
+    if (!c || !c->fs || axis < 0 || axis >= c->d) return -1;
+    return c->F.ax[axis].NT;
 }

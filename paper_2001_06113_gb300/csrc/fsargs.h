@@ -26,6 +26,7 @@ namespace tdse {
 constexpr int FS_T = 256;         // threads per CTA of every free-space kernel
 constexpr int FS_MAX_ND = 128;    // dense (Alpert + Gauss) modes per axis
 constexpr int FS_MAX_HIST = 7;
+constexpr int FS_MAX_NT = 64;     // terms of the Chebyshev interpolant of the C-type transforms
 
 struct FsAxis {
     int M;        // physical points
@@ -51,6 +52,25 @@ struct FsAxis {
     const float2* Fd_f;
     const float2* tw_f;
     const float2* P_f;
+    // C-type transforms by Chebyshev interpolation in tau on Gamma_2 (Sec. 4.1,
+    // eqs. expintrpm, expintrpp): with zeta = (1 - i) tau, tau in [-H, H],
+    //   e^{-i zeta x} = e^{-(1+i) tau x} ~ sum_l lambda_l(x) T_l(tau / H),
+    //   e^{+i zeta x} = e^{+(1+i) tau x} ~ sum_l rho_l(x) T_l(tau / H),
+    // the NC Gauss rows of the dense block become
+    //   forward  f^_k = sum_l T_l(tau_k / H) [sum_j (2/M) lambda_l(x_j) f_j]
+    //   inverse  f_j += sum_l rho_l(x_j) [sum_k T_l(tau_k / H) (w_k / 2pi) f^_k]
+    // at O(NT (M + NC)) instead of O(NC M).  NT = 0: direct sums (Gd, Fd rows).
+    int p;                 // Alpert modes per side: the C rows are dd = p .. p + NC - 1
+    int NC;                // Gauss (C) modes
+    int NT;                // interpolant terms, 0 = C rows by direct sums
+    const double2* Lf;     // [NT][M]  (2/M) lambda_l(x_j)
+    const double2* Li;     // [NT][M]  rho_l(x_j)
+    const double* Tc;      // [NC][NT] T_l(tau_k / H)
+    const double2* TcW;    // [NT][NC] T_l(tau_k / H) w_k / 2pi
+    const float2* Lf_f;
+    const float2* Li_f;
+    const float* Tc_f;
+    const float2* TcW_f;
 };
 
 struct FsArgs {

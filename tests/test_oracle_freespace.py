@@ -239,3 +239,43 @@ def test_free_moving_well_pin_catches_lagged_potential(monkeypatch):
     monkeypatch.setattr(freespace.FreeSpaceOracle, "V", lagged)
     e400, e800 = _free_galilean_errors((400, 800))
     assert not (e800 < 1e-8 and e400 / e800 > 100.0)
+
+
+# ---------------------------------------------- Chebyshev form of the C-type transforms
+@pytest.mark.parametrize("H,n_r", [(2.0, 3), (1.2, 4), (3.0, 2)])
+def test_ctype_chebyshev_equals_direct_sums(H, n_r):
+    """Sec. 4.1: the interpolants of e^{-+(1+i) tau x} reproduce the direct
+    C-type sums (eq. fhatCsum and its inverse) to rounding once N_T is large
+    enough, and are far off with too few terms (the degree matters)."""
+    from oracle.freespace import ctype_chebyshev, free_grid
+    rule = gamma.GammaRule.for_nu(64, 512, H, q=10, n_r=n_r)
+    x = free_grid(64)
+    zc, wc = rule.blocks["C"]
+    rng = np.random.default_rng(7)
+    f = rng.normal(size=64) + 1j * rng.normal(size=64)
+    fh = rng.normal(size=zc.size) + 1j * rng.normal(size=zc.size)
+    direct_f = (2.0 / 64) * np.exp(-1j * np.outer(zc, x)) @ f
+    direct_i = (np.exp(1j * np.outer(x, zc)) * (wc[None, :] / (2.0 * math.pi))) @ fh
+    fwd, inv = ctype_chebyshev(rule, 28)
+    assert np.max(np.abs(fwd(f) - direct_f)) <= 1e-13 * np.max(np.abs(direct_f))
+    assert np.max(np.abs(inv(fh) - direct_i)) <= 1e-13 * np.max(np.abs(direct_i))
+    fwd6, _ = ctype_chebyshev(rule, 6)
+    assert np.max(np.abs(fwd6(f) - direct_f)) > 1e-7 * np.max(np.abs(direct_f))
+
+
+def test_ctype_chebyshev_is_exact_for_low_degree_interpolation_nodes():
+    """With tau restricted to the interpolation points themselves the
+    interpolant is exact for any N_T (a plain property of interpolation)."""
+    from oracle.freespace import ctype_chebyshev
+    rule = gamma.GammaRule.for_nu(32, 256, 1.5, q=10, n_r=1)
+    NT = 10
+    theta = math.pi * (np.arange(NT) + 0.5) / NT
+    rule.tau_c = 1.5 * np.cos(theta)                       # evaluate at the Chebyshev points
+    rule.blocks["C"] = ((1 - 1j) * rule.tau_c, np.ones(NT, dtype=np.complex128))
+    fwd, _ = ctype_chebyshev(rule, NT)
+    from oracle.freespace import free_grid
+    x = free_grid(32)
+    f = np.cos(3.0 * x) + 1j * x
+    direct = (2.0 / 32) * np.exp(-1j * np.outer((1 - 1j) * rule.tau_c, x)) @ f
+    assert np.max(np.abs(fwd(f) - direct)) <= 1e-13 * np.max(np.abs(direct))
+
