@@ -70,10 +70,14 @@ class PeriodicOracle:
     phi   : callable t -> array(d), phi(t) = int_0^t A.
     order : Adams order n (even, >= 2).
     n_startup : number of Richardson start-up steps (default n - 1).
+    transform : "direct" (the dense O(M^2) sums of eqs. ftperdisc / utrapkdisc)
+                or "fft" (the same DFT pair through numpy's FFT, a library
+                primitive, for grids where the dense matrices do not fit in
+                memory; pinned against "direct").
     """
 
     def __init__(self, shape, dt: float, V0: np.ndarray, vfac: Callable, phi: Callable,
-                 order: int = 8, n_startup: Optional[int] = None):
+                 order: int = 8, n_startup: Optional[int] = None, transform: str = "direct"):
         self.shape = tuple(int(m) for m in shape)
         self.d = len(self.shape)
         if order < 2 or order % 2:
@@ -88,9 +92,13 @@ class PeriodicOracle:
         if self.n_startup < order - 2:
             raise ValueError("need at least order-2 start-up steps")
         self.mu = adams.weights(order)
-        mats = [dft_matrices(M) for M in self.shape]
-        self.F = [m[0] for m in mats]
-        self.G = [m[1] for m in mats]
+        if transform not in ("direct", "fft"):
+            raise ValueError("transform: direct or fft")
+        self.transform = transform
+        if transform == "direct":
+            mats = [dft_matrices(M) for M in self.shape]
+            self.F = [m[0] for m in mats]
+            self.G = [m[1] for m in mats]
         ks = [wavenumbers(M) for M in self.shape]
         self.k = np.meshgrid(*ks, indexing="ij")                 # list of d arrays
         self.ksq = sum(kk * kk for kk in self.k)
@@ -104,10 +112,18 @@ class PeriodicOracle:
 
     def fwd(self, f):
         """(1/M^d) sum_j e^{-2 pi i j.k/M} f_j  (eq. ftperdisc, per dimension)."""
+        if self.transform == "fft":          # modes ordered k = -M/2 .. M/2-1, as the dense rows
+            axes = tuple(range(self.d))
+            return np.fft.fftshift(np.fft.fftn(np.asarray(f, dtype=np.complex128), axes=axes), axes=axes) / float(
+                np.prod(self.shape))
         return self._apply(self.F, f)
 
     def inv(self, fh):
         """sum_k e^{+2 pi i j.k/M} f^_k  (eq. utrapkdisc, per dimension)."""
+        if self.transform == "fft":
+            axes = tuple(range(self.d))
+            return np.fft.ifftn(np.fft.ifftshift(np.asarray(fh, dtype=np.complex128), axes=axes), axes=axes) * float(
+                np.prod(self.shape))
         return self._apply(self.G, fh)
 
     # -- problem data ---------------------------------------------------------
@@ -181,8 +197,8 @@ class PeriodicOracle:
         return (u, kept) if keep is not None else u
 
 
-def oracle_for(inst, order: int = 8, n_startup: Optional[int] = None) -> PeriodicOracle:
+def oracle_for(inst, order: int = 8, n_startup: Optional[int] = None, transform: str = "direct") -> PeriodicOracle:
     """Build the oracle for a synth.Instance (phi in closed form for its pulse)."""
     from .fields import phi_callable
     return PeriodicOracle(inst.shape, inst.dt, inst.V0, inst.vfac,
-                          phi_callable(inst.pulse, inst.dim), order=order, n_startup=n_startup)
+                          phi_callable(inst.pulse, inst.dim), order=order, n_startup=n_startup, transform=transform)

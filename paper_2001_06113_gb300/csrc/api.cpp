@@ -141,15 +141,21 @@ static void plan_workspace(tdse_ctx* c) {
     }
     c->off.tw64_0 = take((size_t)c->n0 * 16);
     c->off.tw32_0 = take((size_t)c->n0 * 8);
-    c->off.tw64_1 = take((size_t)(c->d >= 2 ? c->n1 : 1) * 16);
-    c->off.tw32_1 = take((size_t)(c->d >= 2 ? c->n1 : 1) * 8);
+    const int ax1 = c->four1d ? c->fs1 : (c->d >= 2 ? c->n1 : 1);
+    c->off.tw64_1 = take((size_t)ax1 * 16);
+    c->off.tw32_1 = take((size_t)ax1 * 8);
+    if (c->four1d) {
+        c->off.tw1d64 = take((size_t)c->n0 * 16);
+        c->off.tw1d32 = take((size_t)c->n0 * 8);
+        c->off.tw1d32lo = take((size_t)c->n0 * 8);
+    }
     c->off.tw64_2 = take((size_t)(c->d == 3 ? c->n2 : 1) * 16);
     c->off.tw32_2 = take((size_t)(c->d == 3 ? c->n2 : 1) * 8);
     c->off.tw32lo_2 = take((size_t)(c->d == 3 ? c->n2 : 1) * 8);
     c->off.tw32lo_0 = take((size_t)c->n0 * 8);
-    c->off.tw32lo_1 = take((size_t)(c->d >= 2 ? c->n1 : 1) * 8);
+    c->off.tw32lo_1 = take((size_t)ax1 * 8);
     c->off.iv = take((size_t)c->n_int * sizeof(int2));
-    c->off.tw128 = c->d == 1 && c->n0 > 8192 ? take(128 * 16) : 0;
+    c->off.tw128 = c->d == 1 && c->n0 > 8192 && !c->four1d ? take(128 * 16) : 0;
     if (c->mixed) {
         c->off.res_sums = take(B * 16);
         c->off.res_rho = take(B * 8);
@@ -247,6 +253,15 @@ static KArgs base_args(const tdse_ctx* c) {
     a.tw64_2 = c->P<double2>(c->off.tw64_2);
     a.tw32_2 = c->P<float2>(c->off.tw32_2);
     a.tw32lo_2 = c->P<float2>(c->off.tw32lo_2);
+    if (c->four1d) {   // 1D through the 2D passes: geometry fs0 x fs1, tables of the N-point grid
+        a.n0 = c->fs0;
+        a.n1 = c->fs1;
+        a.tn0 = c->n0;
+        a.tn1 = 1;
+        a.flat1d = 1;
+        a.tw1d64 = c->P<double2>(c->off.tw1d64);
+        a.tw1d32 = c->P<float2>(c->off.tw1d32);
+    }
     return a;
 }
 
@@ -275,7 +290,7 @@ static int f64_combo(const tdse_ctx* c) { return c->cfg.precision == TDSE_MIXED 
 
 static cudaError_t run(const tdse_ctx* c, const KArgs& a, int combo, cudaStream_t s) {
     if (c->d == 3) return launch_periodic3d(a, combo, s);
-    return c->d == 1 ? launch_periodic1d(a, combo, s) : launch_periodic2d(a, combo, s);
+    return c->d == 1 && !c->four1d ? launch_periodic1d(a, combo, s) : launch_periodic2d(a, combo, s);
 }
 
 static tdse_status build_phase_tables(tdse_ctx* c, int b, cudaStream_t s) {
@@ -336,7 +351,9 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     if (cfg->dim == 3 && fs) return TDSE_EUNSUPPORTED;
     if (cfg->dim == 3 && !periodic3d_supported(n0, n1, n2)) return TDSE_EUNSUPPORTED;
     const bool big1d = !fs && cfg->dim == 1 && cfg->precision == TDSE_MIXED && n0 == four_step_n();
-    if (!fs && cfg->dim == 1 && !periodic1d_supported(n0) && !big1d) return TDSE_EUNSUPPORTED;
+    // larger 1D grids: the four-step transform through the 2D passes, up to 2^20 points
+    const bool four1d = !fs && cfg->dim == 1 && !periodic1d_supported(n0) && !big1d && n0 >= 64 && n0 <= (1 << 20);
+    if (!fs && cfg->dim == 1 && !periodic1d_supported(n0) && !big1d && !four1d) return TDSE_EUNSUPPORTED;
     if (!fs && cfg->dim == 2 && !periodic2d_supported(n0, n1)) return TDSE_EUNSUPPORTED;
     if ((long long)cfg->nsteps * SUB + 1 > (1LL << 30)) return TDSE_EINVAL;
     if (cfg->potential != TDSE_V_SEPARABLE && cfg->potential != TDSE_V_TABLE &&
@@ -352,6 +369,13 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     c->n1 = n1;
     c->n2 = n2;
     c->NP = (size_t)n0 * n1 * n2;
+    c->four1d = four1d;
+    if (four1d) {
+        int lg = 0;
+        while ((1 << lg) < n0) ++lg;
+        c->fs1 = 1 << ((lg + 1) / 2);
+        c->fs0 = n0 / c->fs1;
+    }
     c->ntab = (size_t)n0 + (cfg->dim >= 2 ? n1 : 0) + (cfg->dim == 3 ? n2 : 0);
     c->B = cfg->batch;
     c->m = cfg->order;
@@ -447,7 +471,13 @@ tdse_status tdse_bind_workspace(tdse_ctx* c, void* dev, size_t bytes, void* stre
         if (st != TDSE_OK) return st;
     } else {
     TDSE_CK(c, launch_twiddles(c->P<double2>(c->off.tw64_0), c->P<float2>(c->off.tw32_0),
-                               c->P<float2>(c->off.tw32lo_0), c->n0, s));
+                               c->P<float2>(c->off.tw32lo_0), c->four1d ? c->fs0 : c->n0, s));
+    if (c->four1d) {
+        TDSE_CK(c, launch_twiddles(c->P<double2>(c->off.tw64_1), c->P<float2>(c->off.tw32_1),
+                                   c->P<float2>(c->off.tw32lo_1), c->fs1, s));
+        TDSE_CK(c, launch_twiddles(c->P<double2>(c->off.tw1d64), c->P<float2>(c->off.tw1d32),
+                                   c->P<float2>(c->off.tw1d32lo), c->n0, s));
+    }
     if (c->d == 3)
         TDSE_CK(c, launch_twiddles(c->P<double2>(c->off.tw64_2), c->P<float2>(c->off.tw32_2),
                                    c->P<float2>(c->off.tw32lo_2), c->n2, s));
@@ -504,7 +534,13 @@ tdse_status tdse_set_potential(tdse_ctx* c, int instance, const double* V0, cons
     const cudaMemcpyKind kind = where == TDSE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     for (int b = lo; b < hi; ++b) {
         double* dV = c->P<double>(c->off.V0) + (size_t)b * c->NP;
-        TDSE_CK(c, cudaMemcpyAsync(dV, V0, c->NP * 8, kind, s));
+        if (c->four1d) {    // natural order -> the passes' transposed layout (through the intermediate buffer)
+            double* tmp = c->P<double>(c->off.aux);
+            TDSE_CK(c, cudaMemcpyAsync(tmp, V0, c->NP * 8, kind, s));
+            TDSE_CK(c, launch_transpose_1d(dV, tmp, c->fs0, c->fs1, 1, 8, 1, s));
+        } else {
+            TDSE_CK(c, cudaMemcpyAsync(dV, V0, c->NP * 8, kind, s));
+        }
         TDSE_CK(c, launch_split_float(c->P<float2>(c->off.V0f) + (size_t)b * c->NP, dV, c->NP, s));
         if (tf) {
             for (int i = 0; i < c->ntf; ++i)
@@ -549,7 +585,15 @@ tdse_status tdse_set_potential_table(tdse_ctx* c, int instance, const double* V,
     for (int b = lo; b < hi; ++b) {
         if (!c->vshared || b == lo) {
             double* dV = c->P<double>(c->off.V0) + (size_t)b * per;
-            TDSE_CK(c, cudaMemcpyAsync(dV, V, per * 8, kind, s));
+            if (c->four1d) {   // each row into the transposed layout
+                double* tmp = c->P<double>(c->off.aux);
+                for (int r = 0; r < c->vrows; ++r) {
+                    TDSE_CK(c, cudaMemcpyAsync(tmp, V + (size_t)r * c->NP, c->NP * 8, kind, s));
+                    TDSE_CK(c, launch_transpose_1d(dV + (size_t)r * c->NP, tmp, c->fs0, c->fs1, 1, 8, 1, s));
+                }
+            } else {
+                TDSE_CK(c, cudaMemcpyAsync(dV, V, per * 8, kind, s));
+            }
             TDSE_CK(c, launch_split_float(c->P<float2>(c->off.V0f) + (size_t)b * per, dV, per, s));
         }
         TDSE_CK(c, cudaMemcpyAsync(c->P<double>(c->off.tfac) + (size_t)b * c->ntf, ones.data(), c->ntf * 8,
@@ -637,6 +681,11 @@ tdse_status tdse_set_initial(tdse_ctx* c, int instance, const double* u0, int wh
         if (c->fs) {
             tdse_status st = fs_set_initial(c, b, u0, kind, s);
             if (st != TDSE_OK) return st;
+        } else if (c->four1d) {
+            double2* tmp = c->P<double2>(c->off.aux);
+            TDSE_CK(c, cudaMemcpyAsync(tmp, u0, c->NP * 16, kind, s));
+            TDSE_CK(c, launch_transpose_1d(c->P<double2>(c->off.uhat) + (size_t)b * c->NP, tmp, c->fs0, c->fs1, 1, 16,
+                                           1, s));
         } else {
             TDSE_CK(c, cudaMemcpyAsync(c->P<double2>(c->off.uhat) + (size_t)b * c->NP, u0, c->NP * 16, kind, s));
         }
@@ -662,7 +711,13 @@ tdse_status tdse_set_initial_batch(tdse_ctx* c, const double* u0, int where, voi
     const cudaMemcpyKind kind = where == TDSE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     // the grid values of all instances are contiguous in the workspace (stride n0 n1)
     double2* dst = c->fs ? c->P<double2>(c->F.off.u) : c->P<double2>(c->off.uhat);
-    TDSE_CK(c, cudaMemcpyAsync(dst, u0, (size_t)c->B * c->NP * 16, kind, s));
+    if (c->four1d) {
+        double2* tmp = c->P<double2>(c->off.aux);
+        TDSE_CK(c, cudaMemcpyAsync(tmp, u0, (size_t)c->B * c->NP * 16, kind, s));
+        TDSE_CK(c, launch_transpose_1d(dst, tmp, c->fs0, c->fs1, c->B, 16, 1, s));
+    } else {
+        TDSE_CK(c, cudaMemcpyAsync(dst, u0, (size_t)c->B * c->NP * 16, kind, s));
+    }
     std::fill(c->have_u0.begin(), c->have_u0.end(), 1);
     if (c->mixed && c->off.res_ncorr) {
         TDSE_CK(c, cudaMemsetAsync(c->P<int>(c->off.res_ncorr), 0, (size_t)c->B * 4, s));
@@ -797,6 +852,9 @@ static KArgs group_args(const tdse_ctx* c, KArgs a, int lo, int hi) {
     if (a.q64) a.q64 += l * (size_t)c->n_int * c->ntab;
     if (a.qff) a.qff += l * (size_t)c->n_int * c->ntab;
     if (a.e2d) a.e2d += l * nsp1 * c->ntab;
+    if (a.adv64) a.adv64 += l * (size_t)c->n_int * (c->nh + c->nl);
+    if (a.advff) a.advff += l * (size_t)c->n_int * (c->nh + c->nl);
+    if (a.a1d) a.a1d += l * nsp1 * (c->nh + c->nl);
     return a;
 }
 
@@ -821,7 +879,7 @@ static tdse_status adams_steps(tdse_ctx* c, int n0, int k, cudaStream_t s) {
         TDSE_CK(c, launch_step2d_cluster(a, ca, c->cl, s));
         return TDSE_OK;
     }
-    if (c->d == 1 || k == 1) {
+    if ((c->d == 1 && !c->four1d) || k == 1) {
         for (int n = n0 + 1; n <= n0 + k; ++n) TDSE_CK(c, run(c, adams_args(c, n), combo, s));
         return TDSE_OK;
     }
@@ -1002,6 +1060,11 @@ tdse_status tdse_read_u(tdse_ctx* c, int instance, double* u_out, int where, voi
         else
             TDSE_CK(c, run(c, a, f64_combo(c), s));
         src = a.aux2;
+    }
+    if (c->four1d) {   // the passes' transposed layout -> natural order
+        double2* nat = c->P<double2>(c->off.aux);
+        TDSE_CK(c, launch_transpose_1d(nat, src, c->fs0, c->fs1, (int)nb, 16, 0, s));
+        src = nat;
     }
     const cudaMemcpyKind kind = where == TDSE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     TDSE_CK(c, cudaMemcpyAsync(u_out, src, nb * c->NP * 16, kind, s));
@@ -1195,7 +1258,7 @@ tdse_status tdse_describe_steps(const tdse_ctx* c, char* buf, size_t len) {
                           c->cl.clusters, CL_Q, step2d_cluster_threads(), step2d_cluster_smem());
     else
         n = std::snprintf(buf, len, "{\"path\": \"passes\", \"groups\": %d}",
-                          c->d >= 2 && !c->fs ? (c->step_groups < c->B ? c->step_groups : c->B) : 1);
+                          (c->d >= 2 || c->four1d) && !c->fs ? (c->step_groups < c->B ? c->step_groups : c->B) : 1);
     return (n < 0 || (size_t)n >= len) ? TDSE_EINVAL : TDSE_OK;
 }
 
@@ -1394,7 +1457,7 @@ tdse_status tdse_batch_create(tdse_ctx* const* members, int count, tdse_batch** 
         if (!c || !c->ws) return TDSE_EINVAL;
         for (int h = 0; h < g; ++h)
             if (members[h] == c) return TDSE_EINVAL;
-        if (c->fs || c->d != 1 || !c->mixed) return TDSE_EUNSUPPORTED;
+        if (c->fs || c->d != 1 || !c->mixed || c->four1d) return TDSE_EUNSUPPORTED;
         if (c->cfg.dt != c0->cfg.dt || c->cfg.nsteps != c0->cfg.nsteps || c->cfg.order != c0->cfg.order ||
             c->S != c0->S)
             return TDSE_EINVAL;

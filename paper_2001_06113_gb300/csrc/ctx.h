@@ -53,6 +53,10 @@ struct tdse_ctx {
     tdse_config cfg{};
     int d = 1, n0 = 0, n1 = 1, n2 = 1;   // n2: axis 2 of 3D periodic grids
     size_t ntab = 0;            // entries per row of the separable phase tables (n0 + n1 (+ n2))
+    // 1D grids beyond one CTA: N = n0 points through the 2D passes as fs0 x fs1
+    // (four-step transform, grid stored transposed in the workspace)
+    bool four1d = false;
+    int fs0 = 0, fs1 = 0;
     size_t NP = 0;
     int B = 1, m = 8, L = 4, S = 7, S_eff = 7, RS = 7, ntf = 0, n_int = 0, n_int_startup = 0, nhi = 1;
     bool mixed = false;
@@ -69,7 +73,7 @@ struct tdse_ctx {
     struct {
         size_t uhat, ring, chain_uhat, chain_ring, aux, aux2, V0, V0f, tfac, phi, kin64, kinff, adv64, advff,
             q64, qff, e2d, k1lo, k1hi, a1d, tw64_0, tw32_0, tw64_1, tw32_1, tw32lo_0, tw32lo_1, tw64_2, tw32_2,
-            tw32lo_2, iv, tw128, res_sums,
+            tw32lo_2, tw1d64, tw1d32, tw1d32lo, iv, tw128, res_sums,
             res_rho, res_flags, res_ncorr, cl_tab, err, scratch, end;
     } off{};
     // 2D mixed steps over CTA clusters (512^2): plan built at bind, used when

@@ -31,6 +31,14 @@ struct KArgs {
     int n0, n1;               // launch geometry: lines x line length (n1 = 1 for 1D); for 3D the
                               // column pass sees [n0][n1 n2] and the row pass [n0 n1][n2]
     int tn0, tn1, tn2;        // the grid per axis for the phase and E tables (tn2 = 0 below 3D)
+    // 1D grid of N = n0 n1 points through the 2D passes (four-step transform):
+    // grid point j = n0 c + r at [r][c] (the grid stored transposed), mode k at
+    // [k / n1][k % n1] (natural FFT order); the row pass multiplies by the
+    // twiddle e^{-+2 pi i r c / N} between its transform and the column pass's.
+    // tn0 = N and the 1D phase tables apply to the flattened mode index.
+    int flat1d;
+    const double2* tw1d64;    // e^{-2 pi i m / N}, m < N
+    const float2* tw1d32;
     // ---- step description
     int nhist;                // history terms j = 1..nhist
     double h;                 // step size
@@ -195,6 +203,11 @@ cudaError_t launch_k1d(float2* klo, float2* khi, int nhi, int n, double dt, cuda
 cudaError_t launch_a1d(float2* a1d, const double* phi, int ntf, int nsteps, int n, int nh, int nl,
                        cudaStream_t s);
 cudaError_t launch_split_float(float2* hilo, const double* src, size_t n, cudaStream_t s);
+// 1D grids through the 2D passes: natural order (point j = n0 c + r) <-> the
+// transposed layout [r][c] (r < n0, c < n1), B arrays of n0 n1 elements of
+// elem_bytes (8 or 16); to_passes = 1: natural -> [r][c].
+cudaError_t launch_transpose_1d(void* dst, const void* src, int n0, int n1, int B, int elem_bytes, int to_passes,
+                                cudaStream_t s);
 // phi(m dt/8), m = 0..ntf-1, of the built-in pulse in closed form into phi[d][ntf]
 cudaError_t launch_pulse_phi(double* phi, int ntf, int d, double hs, double A0, double omega, double Tp,
                              const double* dir, cudaStream_t s);

@@ -125,8 +125,9 @@ __device__ __forceinline__ C begin_elem(const KArgs& a, bool step, int b, state_
         }
     }
     if (a.mode == MODE_READ && a.ip) {
-        const double2 E = a.tn2 ? e_exact3(a, b, a.e_step, m0, m1)
-                                : e_exact(a, b, a.e_step, kmode(m0, a.n0), kmode(m1, a.n1), 2);
+        const double2 E = a.flat1d ? e_exact(a, b, a.e_step, kmode(m0 * a.n1 + m1, a.tn0), 0.0, 1)
+                          : a.tn2 ? e_exact3(a, b, a.e_step, m0, m1)
+                                  : e_exact(a, b, a.e_step, kmode(m0, a.n0), kmode(m1, a.n1), 2);
         return cvt<C>(cmul(E, st_to_d(W)));
     }
     return st_to_c<C>(W);
@@ -187,6 +188,21 @@ __global__ void __launch_bounds__(T2D, min_blocks_2d<C>()) k_col_begin(const KAr
     }
 }
 
+// 1D grids through the passes: the four-step twiddle e^{-2 pi i r c / N} of
+// row r, position c (conjugated before the inverse row transform).
+template <bool CONJ>
+__device__ __forceinline__ double2 tw1d(const KArgs& a, int r, int c, double2 v) {
+    double2 w = __ldg(&a.tw1d64[(size_t)r * c]);
+    if (CONJ) w.y = -w.y;
+    return cmul(v, w);
+}
+template <bool CONJ>
+__device__ __forceinline__ float2 tw1d(const KArgs& a, int r, int c, float2 v) {
+    float2 w = __ldg(&a.tw1d32[(size_t)r * c]);
+    if (CONJ) w.y = -w.y;
+    return cmul(v, w);
+}
+
 // ------------------------------------------------------------------ row_mid
 template <class C, int N1>
 __global__ void __launch_bounds__(T2D, row_min_blocks<C>()) k_row_mid(const KArgs a) {
@@ -229,7 +245,9 @@ __global__ void __launch_bounds__(T2D, row_min_blocks<C>()) k_row_mid(const KArg
             C* dst = pass == 0 ? T2 : T1;
             for (int item = threadIdx.x; item < N1 * L; item += T2D) {
                 const int lane = item / N1, k1 = item % N1;
-                dst[(size_t)(r0 + lane) * N1 + k1] = cscale(buf[k1 * LS + lane], scale);
+                C v = buf[k1 * LS + lane];
+                if (a.flat1d) v = tw1d<false>(a, r0 + lane, k1, v);
+                dst[(size_t)(r0 + lane) * N1 + k1] = cscale(v, scale);
             }
             __syncthreads();
         }
@@ -238,8 +256,14 @@ __global__ void __launch_bounds__(T2D, row_min_blocks<C>()) k_row_mid(const KArg
 
     if (!F64 && a.mode == MODE_STEP) prefetch_l2(V0f + (size_t)r0 * N1, (size_t)L * N1 * sizeof(float2));
     const C* T1 = reinterpret_cast<const C*>(a.aux) + (size_t)b * NP;
-    batched_copy<C, N1 * L>([&](int item) { return T1[(size_t)(r0 + item / N1) * N1 + item % N1]; },
-                            [&](int item, C v) { buf[(item % N1) * LS + item / N1] = v; });
+    if (a.flat1d)
+        batched_copy<C, N1 * L>([&](int item) { return T1[(size_t)(r0 + item / N1) * N1 + item % N1]; },
+                                [&](int item, C v) {
+                                    buf[(item % N1) * LS + item / N1] = tw1d<true>(a, r0 + item / N1, item % N1, v);
+                                });
+    else
+        batched_copy<C, N1 * L>([&](int item) { return T1[(size_t)(r0 + item / N1) * N1 + item % N1]; },
+                                [&](int item, C v) { buf[(item % N1) * LS + item / N1] = v; });
     __syncthreads();
     FI::run(buf, tw, twl);
 
@@ -272,7 +296,9 @@ __global__ void __launch_bounds__(T2D, row_min_blocks<C>()) k_row_mid(const KArg
     C* T2 = reinterpret_cast<C*>(a.aux2) + (size_t)b * NP;
     for (int item = threadIdx.x; item < N1 * L; item += T2D) {
         const int lane = item / N1, k1 = item % N1;
-        T2[(size_t)(r0 + lane) * N1 + k1] = cscale(buf[k1 * LS + lane], scale);
+        C v = buf[k1 * LS + lane];
+        if (a.flat1d) v = tw1d<false>(a, r0 + lane, k1, v);
+        T2[(size_t)(r0 + lane) * N1 + k1] = cscale(v, scale);
     }
 }
 
@@ -560,7 +586,7 @@ static cudaError_t part2d(const KArgs& a, int part, cudaStream_t s) {
         case PART_COL_END: return col_end<C, RT>(a, s);
         case PART_COL_FUSED:
             if constexpr (std::is_same<C, float2>::value && std::is_same<RT, float2>::value) {
-                if (a.mode == MODE_STEP && a.ip && a.tn2 == 0) {
+                if (a.mode == MODE_STEP && a.ip && a.tn2 == 0 && !a.flat1d) {
 #define TDSE_CFI(n) col_fused_ip_n<n>
                     TDSE_SWITCH_N(a.n0, TDSE_CFI)
 #undef TDSE_CFI

@@ -65,12 +65,12 @@ struct Phase1D {
     }
     __device__ __forceinline__ double2 p64(int i) const {
         const double2* t = a.adv64 + base(i);
-        const double2 kin = __ldg(&a.kin64[(size_t)a.kin * a.n0 + m]);
+        const double2 kin = __ldg(&a.kin64[(size_t)a.kin * a.tn0 + m]);
         return cmul(kin, cmul(__ldg(&t[m >> a.lb]), __ldg(&t[a.nh + (m & (a.nl - 1))])));
     }
     __device__ __forceinline__ float4 pff(int i) const {
         const float4* t = a.advff + base(i);
-        const float4 kin = __ldg(&a.kinff[(size_t)a.kin * a.n0 + m]);
+        const float4 kin = __ldg(&a.kinff[(size_t)a.kin * a.tn0 + m]);
         return ffc_mul(kin, ffc_mul(__ldg(&t[m >> a.lb]), __ldg(&t[a.nh + (m & (a.nl - 1))])));
     }
 };
@@ -94,6 +94,7 @@ struct Phase2D {
         return ((size_t)b * a.n_int + a.interval[i]) * (size_t)(a.tn0 + a.tn1 + a.tn2);
     }
     __device__ __forceinline__ double2 p64(int i) const {
+        if (a.flat1d) return Phase1D{a, b, m0 * a.n1 + m1}.p64(i);
         const double2* q = a.q64 + base(i);
         if (a.tn2 == 0) return cmul(__ldg(&q[m0]), __ldg(&q[a.tn0 + m1]));
         int i1, i2;
@@ -101,6 +102,7 @@ struct Phase2D {
         return cmul(cmul(__ldg(&q[m0]), __ldg(&q[a.tn0 + i1])), __ldg(&q[a.tn0 + a.tn1 + i2]));
     }
     __device__ __forceinline__ float4 pff(int i) const {
+        if (a.flat1d) return Phase1D{a, b, m0 * a.n1 + m1}.pff(i);
         const float4* q = a.qff + base(i);
         if (a.tn2 == 0) return ffc_mul(__ldg(&q[m0]), __ldg(&q[a.tn0 + m1]));
         int i1, i2;
@@ -109,19 +111,21 @@ struct Phase2D {
     }
 };
 
+__device__ __forceinline__ float2 e_1d(const KArgs& a, int b, int n, int m) {
+    const float2 kin = cmul(__ldg(&a.k1d_hi[(size_t)(n / E1D_NLO) * a.tn0 + m]),
+                            __ldg(&a.k1d_lo[(size_t)(n % E1D_NLO) * a.tn0 + m]));
+    const float2* t = a.a1d + ((size_t)b * (a.ntf / 8 + 1) + n) * (size_t)(a.nh + a.nl);
+    return cmul(kin, cmul(__ldg(&t[m >> a.lb]), __ldg(&t[a.nh + (m & (a.nl - 1))])));
+}
+
 // ---- absolute phases E_n (interaction picture), FP32
 __device__ __forceinline__ float2 e_2d(const KArgs& a, int b, int n, int m0, int m1) {
+    if (a.flat1d) return e_1d(a, b, n, m0 * a.n1 + m1);
     const float2* e = a.e2d + ((size_t)b * (a.ntf / 8 + 1) + n) * (size_t)(a.tn0 + a.tn1 + a.tn2);
     if (a.tn2 == 0) return cmul(__ldg(&e[m0]), __ldg(&e[a.tn0 + m1]));
     int i1, i2;
     split12(a, m1, i1, i2);
     return cmul(cmul(__ldg(&e[m0]), __ldg(&e[a.tn0 + i1])), __ldg(&e[a.tn0 + a.tn1 + i2]));
-}
-__device__ __forceinline__ float2 e_1d(const KArgs& a, int b, int n, int m) {
-    const float2 kin = cmul(__ldg(&a.k1d_hi[(size_t)(n / E1D_NLO) * a.n0 + m]),
-                            __ldg(&a.k1d_lo[(size_t)(n % E1D_NLO) * a.n0 + m]));
-    const float2* t = a.a1d + ((size_t)b * (a.ntf / 8 + 1) + n) * (size_t)(a.nh + a.nl);
-    return cmul(kin, cmul(__ldg(&t[m >> a.lb]), __ldg(&t[a.nh + (m & (a.nl - 1))])));
 }
 // E_n in FP64 from the phi table (read-out only): angle -|k|^2 t_n + k.phi(t_n)
 __device__ __forceinline__ double2 e_exact(const KArgs& a, int b, int n, double k0, double k1, int d) {

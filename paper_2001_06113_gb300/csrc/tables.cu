@@ -222,10 +222,41 @@ __global__ void k_to_interaction(float4* state, float2* ring, int ring_slots, co
     }
 }
 
+// natural order (point j = n0 c + r) <-> [r][c]; one thread per element of the destination
+template <class T>
+__global__ void k_transpose_1d(T* dst, const T* src, int n0, int n1, int to_passes) {
+    const size_t N = (size_t)n0 * n1;
+    const size_t off = (size_t)blockIdx.y * N;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+        if (to_passes) {          // dst [r][c] <- src[n0 c + r]
+            const size_t r = p / n1, c = p % n1;
+            dst[off + p] = src[off + n0 * c + r];
+        } else {                  // dst[j] <- src[r][c], j = n0 c + r
+            const size_t c = p / n0, r = p % n0;
+            dst[off + p] = src[off + r * n1 + c];
+        }
+    }
+}
+
 static int grid_for(size_t n, int threads) {
     size_t g = (n + threads - 1) / threads;
     if (g > 152 * 16) g = 152 * 16;
     return (int)(g ? g : 1);
+}
+
+cudaError_t launch_transpose_1d(void* dst, const void* src, int n0, int n1, int B, int elem_bytes, int to_passes,
+                                cudaStream_t s) {
+    const size_t N = (size_t)n0 * n1;
+    const dim3 grid((unsigned)grid_for(N, 256), (unsigned)B);
+    if (elem_bytes == 8)
+        k_transpose_1d<double><<<grid, 256, 0, s>>>(static_cast<double*>(dst), static_cast<const double*>(src), n0, n1,
+                                                    to_passes);
+    else if (elem_bytes == 16)
+        k_transpose_1d<double2><<<grid, 256, 0, s>>>(static_cast<double2*>(dst), static_cast<const double2*>(src), n0,
+                                                     n1, to_passes);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_twiddles(double2* tw64, float2* tw32, float2* tw32lo, int n, cudaStream_t s) {
@@ -339,8 +370,9 @@ cudaError_t launch_to_interaction(const KArgs& a, int n, const int* slot_steps, 
         st.z[q][0] = q < nslots ? slot_z[2 * q] : 1.f;
         st.z[q][1] = q < nslots ? slot_z[2 * q + 1] : 0.f;
     }
-    const int d = a.tn2 > 0 ? 3 : (a.n1 > 1 ? 2 : 1);
-    const int n0 = d == 3 ? a.tn0 : a.n0, n1 = d == 3 ? a.tn1 : a.n1, n2 = d == 3 ? a.tn2 : 1;
+    const int d = a.flat1d ? 1 : (a.tn2 > 0 ? 3 : (a.n1 > 1 ? 2 : 1));
+    const int n0 = a.flat1d ? a.tn0 : (d == 3 ? a.tn0 : a.n0);
+    const int n1 = a.flat1d ? 1 : (d == 3 ? a.tn1 : a.n1), n2 = d == 3 ? a.tn2 : 1;
     const size_t NP = (size_t)n0 * n1 * n2;
     size_t gx = (NP + 255) / 256;
     if (gx > 1024) gx = 1024;

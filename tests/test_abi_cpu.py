@@ -72,9 +72,11 @@ def _cfg(native, **kw):
     (dict(dim=3, n=(16, 8), n_z=32, bc=1, nu=(128, 64), H=1.5, gauss_q=10, n_r=1), -7),   # free space 3D
     (dict(dim=4), -1),
     (dict(n=(48, 1)), -1),             # not a power of two
-    (dict(n=(16384, 1)), -7),          # 1D FP64 limit of this build (FP64 transform in shared memory)
+    (dict(n=(16384, 1)), 0),           # 1D FP64 beyond one CTA: the four-step transform through the 2D passes
     (dict(n=(16384, 1), precision=1), 0),   # mixed: FP32 steps, FP64 four-step start and read-out
-    (dict(n=(32768, 1), precision=1), -7),
+    (dict(n=(32768, 1), precision=1), 0),
+    (dict(n=(65536, 1), precision=1), 0),
+    (dict(n=(1 << 21, 1), precision=1), -7),
     (dict(order=7), -1),
     (dict(order=10), -1),
     (dict(dt=0.0), -1),

@@ -7,7 +7,7 @@ import pytest
 
 import synth
 from oracle import fields
-from oracle.periodic import PeriodicOracle, dft_matrices, rel_l2, wavenumbers
+from oracle.periodic import PeriodicOracle, dft_matrices, rel_l2, wavenumbers, oracle_for
 from tests import _refs
 
 
@@ -379,3 +379,21 @@ def test_planted_mistakes_fail_a_pin(monkeypatch, mistake):
         monkeypatch.setattr(P.PeriodicOracle, "__init__", bad_init)
     res = _run_pins(None)
     assert not all(res.values()), res
+
+
+# ------------------------------------------------ the DFT pair through numpy's FFT (large grids)
+@pytest.mark.parametrize("shape", [(64,), (32, 16), (8, 4, 16)])
+def test_fft_transform_equals_direct_sums(shape):
+    """The "fft" transform of the oracle (for grids whose dense matrices do not
+    fit in memory) is the same DFT pair as the direct sums, mode order
+    included, and a solve through it follows the same trajectory."""
+    inst = synth.random_periodic(shape, 3, 2e-3, 10, pulse=synth.Pulse(1.0, 10.0, 0.02, (1.0, 0.5, -0.3)[:len(shape)]))
+    a = oracle_for(inst)
+    b = oracle_for(inst, transform="fft")
+    rng = np.random.default_rng(1)
+    f = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+    assert np.max(np.abs(a.fwd(f) - b.fwd(f))) <= 1e-14 * np.max(np.abs(a.fwd(f)))
+    assert np.max(np.abs(a.inv(f) - b.inv(f))) <= 1e-13 * np.max(np.abs(a.inv(f)))
+    ua, ub = a.solve(inst.u0, 10), b.solve(inst.u0, 10)
+    assert rel_l2(ub, ua) <= 1e-13
+
