@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--full-config", action="store_true",
+                    help="serve: the request stream at its stated sizes (1D N 2^10..2^16, 2D periodic 2^7..2^10, "
+                         "free space 2^6..2^9 with nu = 4n, T ~ U[0.5, 2], 10 s of arrivals)")
     ap.add_argument("--no-fp64-variant", action="store_true",
                     help="skip the complex128 timing of the same workload in the default (mixed) line")
     ap.add_argument("--workload", default="periodic2d",
@@ -1410,8 +1413,15 @@ def main_serve(args, ws, rank, local):
     warm = synth.serve_requests(seed=99, rate=100.0, duration=0.1, T_range=(0.005, 0.01), sizes_1d=(1024,),
                                 sizes_2d=(128,), sizes_free=(64,))
     Server(TorchBackend(), SV_BUDGET).run(requests_from_trace(warm, free_precision=fprec))
-    trace = synth.serve_requests(seed=5, rate=SV_RATE, duration=SV_DURATION, T_range=SV_T)
-    reqs = requests_from_trace(trace, free_precision=fprec)
+    if args.full_config:
+        dur, T_range, R = 10.0, (0.5, 2.0), 4
+        trace = synth.serve_requests(seed=5, rate=SV_RATE, duration=dur, T_range=T_range,
+                                     sizes_1d=tuple(2 ** p for p in range(10, 17)),
+                                     sizes_free=tuple(2 ** p for p in range(6, 10)))
+    else:
+        dur, T_range, R = SV_DURATION, SV_T, 8
+        trace = synth.serve_requests(seed=5, rate=SV_RATE, duration=SV_DURATION, T_range=SV_T)
+    reqs = requests_from_trace(trace, free_precision=fprec, free_R=R)
     srv = Server(TorchBackend(), SV_BUDGET, max_active=64)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -1455,10 +1465,14 @@ def main_serve(args, ws, rank, local):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "c64+f64 (periodic), " + ("c64+c128 (free space)" if fprec == "mixed" else "c128 (free space)"),
         "data": "synthetic",
-        "config": {"workload": f"Poisson stream {SV_RATE:.0f} req/s for {SV_DURATION:.1f} s ({len(reqs)} requests): "
-                               "1D periodic N 2^10..2^14, 2D periodic 2^7..2^10, 2D free space 2^6..2^8 (nu = 8n, "
+        "config": {"workload": f"Poisson stream {SV_RATE:.0f} req/s for {dur:.1f} s ({len(reqs)} requests): "
+                               f"1D periodic N 2^10..2^{16 if args.full_config else 14}, 2D periodic 2^7..2^10, "
+                               f"2D free space 2^6..2^{9 if args.full_config else 8} (nu = {R}n, "
                                f"{'FP32 transforms, eps = 1e-4' if fprec == 'mixed' else 'FP64, eps = 1e-10'}), "
-                               "one third each; T ~ U[0.05, 0.2], dt log-uniform [2e-4, 2e-3]",
+                               f"one third each; T ~ U[{T_range[0]}, {T_range[1]}], dt log-uniform [2e-4, 2e-3]"
+                               + (" (the stated request-stream configuration)" if args.full_config else
+                                  " (a reduced stream: T scaled by 0.1, 1 s of arrivals, smaller 1D and "
+                                  "free-space sizes)"),
                    "hbm_budget_bytes": SV_BUDGET, "max_active": 64,
                    "step": "the whole stream from the first arrival to the last result on the host"},
         "time_to_solution_s": {"p50": st["p50_s"], "p99": st["p99_s"], "mean": st["mean_s"]},

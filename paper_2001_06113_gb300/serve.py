@@ -278,17 +278,17 @@ def free_contour_params(inst, eps: float = 1e-10, R: int = 8, gauss_q: int = 10,
 FREE_EPS = {"fp64": 1e-10, "mixed": 1e-4}
 
 
-def requests_from_trace(trace, free_eps: Optional[float] = None, free_precision: str = "fp64"):
+def requests_from_trace(trace, free_eps: Optional[float] = None, free_precision: str = "fp64", free_R: int = 8):
     """Requests of a synth.serve_requests trace: periodic classes in mixed
     precision, free space in `free_precision` ("fp64", or "mixed" = FP32
     transforms) on the contour chosen for free_eps (default 1e-10 in FP64,
-    1e-4 with FP32 sums)."""
+    1e-4 with FP32 sums) with nu = free_R n per axis."""
     eps = FREE_EPS[free_precision] if free_eps is None else free_eps
     out = []
     for i, (t, kind, inst) in enumerate(trace):
         if kind == "free":
             out.append(Request(i, t, inst, bc="free", precision=free_precision,
-                               free=free_contour_params(inst, eps, precision=free_precision)))
+                               free=free_contour_params(inst, eps, R=free_R, precision=free_precision)))
         else:
             out.append(Request(i, t, inst, precision="mixed"))
     return out

@@ -119,12 +119,14 @@ def _grid_norm(u: np.ndarray, h: float) -> float:
 
 
 def _periodised_gaussian_2d(X, Y, cx, cy, sigma, images=3):
-    out = np.zeros_like(X)
+    """sum over the lattice images |m| <= images of exp(-|x - c - 2 pi m|^2 / (2 sigma^2))
+    on the grid X, Y (meshgrid, indexing "ij"): the Gaussian and the image
+    sum factor into the product of two 1D image sums along the grid lines."""
     L = 2.0 * math.pi
-    for mx in range(-images, images + 1):
-        for my in range(-images, images + 1):
-            out += np.exp(-((X - cx - L * mx) ** 2 + (Y - cy - L * my) ** 2) / (2.0 * sigma * sigma))
-    return out
+    x, y = X[:, 0], Y[0, :]
+    gx = sum(np.exp(-(x - cx - L * m) ** 2 / (2.0 * sigma * sigma)) for m in range(-images, images + 1))
+    gy = sum(np.exp(-(y - cy - L * m) ** 2 / (2.0 * sigma * sigma)) for m in range(-images, images + 1))
+    return np.outer(gx, gy)
 
 
 def periodic_1d_cosine(seed: int = 1, M: int = 128, dt: float = 1e-2, nsteps: int = 100,

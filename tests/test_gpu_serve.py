@@ -115,3 +115,40 @@ def test_bad_requests_fail_alone():
         be.start(h)
         torch.cuda.synchronize()
         assert np.array_equal(be.finish(h), r.result)
+
+
+def test_stated_stream_sample_against_the_oracle():
+    """The request stream at its stated sizes and lengths (1D N 2^10..2^16,
+    2D periodic 2^7..2^10, free space 2^6..2^9 with nu = 4n and FP32
+    transforms on the eps = 1e-4 contour, T ~ U[0.5, 2]): the two cheapest
+    requests of each class (points x steps) of the first second of arrivals,
+    served together, against the FP64 oracle (periodic: <= 1e-6 as stated for
+    the stream; free space: <= 2e-6 against the oracle on the same contour)."""
+    from oracle import fields, gamma
+    from oracle.freespace import FreeSpaceOracle
+    from oracle.periodic import oracle_for
+    from paper_2001_06113_gb300.serve import Server, TorchBackend, requests_from_trace
+    trace = synth.serve_requests(seed=5, rate=200.0, duration=1.0, T_range=(0.5, 2.0),
+                                 sizes_1d=tuple(2 ** p for p in range(10, 17)),
+                                 sizes_free=tuple(2 ** p for p in range(6, 10)))
+    picked = []
+    for kind in ("1d", "2d", "free"):
+        cls = sorted((x for x in trace if x[1] == kind), key=lambda x: np.prod(x[2].shape) * x[2].nsteps)
+        picked += cls[:2]
+    reqs = requests_from_trace(picked, free_precision="mixed", free_R=4)
+    Server(TorchBackend(), hbm_budget=8 << 30, max_active=8).run(reqs)
+    for r, (t, kind, inst) in zip(reqs, picked):
+        assert r.error is None, r.error
+        if kind == "free":
+            fp = r.free
+            rules = [gamma.GammaRule.for_nu(M, nu, fp["H"], q=fp["gauss_q"], n_r=fp["n_r"])
+                     for M, nu in zip(inst.shape, fp["nu"])]
+            ref = FreeSpaceOracle(rules, inst.dt, inst.V0, inst.vfac,
+                                  fields.phi_callable(inst.pulse, inst.dim)).solve(inst.u0, inst.nsteps)
+            tol = 2e-6
+        else:
+            ref = oracle_for(inst).solve(inst.u0, inst.nsteps)
+            tol = 1e-6
+        err = rel_l2(r.result, ref)
+        print(kind, inst.shape, inst.nsteps, err)
+        assert err <= tol, (kind, inst.shape, err)
