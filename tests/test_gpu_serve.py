@@ -119,7 +119,7 @@ def test_bad_requests_fail_alone():
 
 def test_stated_stream_sample_against_the_oracle():
     """The request stream at its stated sizes and lengths (1D N 2^10..2^16,
-    2D periodic 2^7..2^10, free space 2^6..2^9 with nu = 4n and FP32
+    2D periodic 2^7..2^10, free space 2^6..2^9 with nu = 8n and FP32
     transforms on the eps = 1e-4 contour, T ~ U[0.5, 2]): the two cheapest
     requests of each class (points x steps) of the first second of arrivals,
     served together, against the FP64 oracle (periodic: <= 1e-6 as stated for
@@ -135,7 +135,7 @@ def test_stated_stream_sample_against_the_oracle():
     for kind in ("1d", "2d", "free"):
         cls = sorted((x for x in trace if x[1] == kind), key=lambda x: np.prod(x[2].shape) * x[2].nsteps)
         picked += cls[:2]
-    reqs = requests_from_trace(picked, free_precision="mixed", free_R=4)
+    reqs = requests_from_trace(picked, free_precision="mixed", free_R=8)
     Server(TorchBackend(), hbm_budget=8 << 30, max_active=8).run(reqs)
     for r, (t, kind, inst) in zip(reqs, picked):
         assert r.error is None, r.error
