@@ -204,6 +204,11 @@ __device__ __forceinline__ float2 tw1d(const KArgs& a, int r, int c, float2 v) {
 }
 
 // ------------------------------------------------------------------ row_mid
+// V loads per thread in flight in the FP32 element phase: one at a time
+// 0.4653, 4 or 8 0.4537 ms per 64 x 512^2 mixed step (4 instance groups).
+#ifndef TDSE_ROW_VG
+#define TDSE_ROW_VG 8
+#endif
 template <class C, int N1>
 __global__ void __launch_bounds__(T2D, row_min_blocks<C>()) k_row_mid(const KArgs a) {
     constexpr int L = LANES2D;
@@ -277,19 +282,36 @@ __global__ void __launch_bounds__(T2D, row_min_blocks<C>()) k_row_mid(const KArg
     }
 
     const R hmu0 = (a.mode == MODE_STEP) ? (R)(a.h * a.mu[0]) : (R)0;
-    for (int item = threadIdx.x; item < N1 * L; item += T2D) {
-        const int lane = item / N1, j1 = item % N1;
-        const size_t idx = (size_t)(r0 + lane) * N1 + j1;
-        R vh, vl;
-        if constexpr (F64) {
-            vh = vfac * V0[idx];
-            vl = 0.0;
-        } else {
-            const float2 v2 = V0f[idx];
-            vh = fh * v2.x;
-            vl = fmaf(fh, v2.x, -vh) + fmaf(fh, v2.y, fl * v2.x);
+    if constexpr (F64) {
+        for (int item = threadIdx.x; item < N1 * L; item += T2D) {
+            const int lane = item / N1, j1 = item % N1;
+            const size_t idx = (size_t)(r0 + lane) * N1 + j1;
+            buf[j1 * LS + lane] = implicit_solve_times_V(buf[j1 * LS + lane], (R)(vfac * V0[idx]), (R)0, hmu0);
         }
-        buf[j1 * LS + lane] = implicit_solve_times_V(buf[j1 * LS + lane], vh, vl, hmu0);
+    } else {
+        // V hi/lo of TDSE_ROW_VG points per thread in flight at a time (L2 hits after the prefetch)
+        constexpr int PER = (N1 * L + T2D - 1) / T2D;
+        constexpr int G = PER < TDSE_ROW_VG ? PER : TDSE_ROW_VG;
+#pragma unroll 1
+        for (int k0 = 0; k0 < PER; k0 += G) {
+            float2 v2[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const int item = threadIdx.x + (k0 + k) * T2D;
+                if ((N1 * L) % T2D == 0 || item < N1 * L)
+                    v2[k] = __ldg(&V0f[(size_t)(r0 + item / N1) * N1 + item % N1]);
+            }
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const int item = threadIdx.x + (k0 + k) * T2D;
+                if ((N1 * L) % T2D == 0 || item < N1 * L) {
+                    const int lane = item / N1, j1 = item % N1;
+                    const float vh = fh * v2[k].x;
+                    const float vl = fmaf(fh, v2[k].x, -vh) + fmaf(fh, v2[k].y, fl * v2[k].x);
+                    buf[j1 * LS + lane] = implicit_solve_times_V(buf[j1 * LS + lane], vh, vl, hmu0);
+                }
+            }
+        }
     }
     __syncthreads();
     FW::run(buf, tw, twl);
@@ -449,11 +471,12 @@ __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_fused_ip(const KArgs a
         for (int it = threadIdx.x; it < RC * L; it += T2D) {
             const int lane = it % L, r = it / L;
             const int m0 = c * RC + r, m1 = c0 + lane;
+            const int pos = m0 * L + lane;
             const size_t idx = (size_t)m0 * n1 + m1;
             const float2 e1n = ONE_COL ? en_1 : __ldg(&en[a.tn0 + m1]);
             const float2 e1n1 = ONE_COL ? en1_1 : __ldg(&en1[a.tn0 + m1]);
             // end of step n: r~ = z_n R / E_n into the ring, v^_n
-            const float2 R = cscale(buf[m0 * L + lane], scale);
+            const float2 R = cscale(buf[pos], scale);
             const float2 rv = cmul(z, cmul(conjf2(cmul(__ldg(&en[m0]), e1n)), R));
             ring_out[idx] = rv;
             const float4 v = ip_update(a, ch.st[it], rv);
@@ -470,7 +493,7 @@ __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_fused_ip(const KArgs a
             }
             const float4 X = ff_minus_i_times(v, a.h_hi, a.h_lo, S);
             st[idx] = X;
-            buf[m0 * L + lane] = cmul(cmul(__ldg(&en1[m0]), e1n1), make_float2(X.x, X.y));
+            buf[pos] = cmul(cmul(__ldg(&en1[m0]), e1n1), make_float2(X.x, X.y));
         }
         __syncthreads();                               // buffer c & 1 free
         if (c + 2 < NCH) stage(c + 2);
