@@ -71,10 +71,12 @@ enum { TDSE_CT_AUTO = 0, TDSE_CT_DIRECT = 1, TDSE_CT_CHEBYSHEV = 2 };
 
 /*
  * Problem configuration.
- *   dim        1, 2 or 3 (3: periodic only; grid n[0] x n[1] x n_z, arrays
- *              row-major [n0][n1][n_z], axis 2 contiguous; powers of two,
- *              axes 0 and 2 in 8..1024, axis 1 in 8..256, at most 2^24
- *              points; no FP64 residual check).
+ *   dim        1, 2 or 3 (grid n[0] x n[1] x n_z for 3, arrays row-major
+ *              [n0][n1][n_z], axis 2 contiguous).  Periodic 3D: powers of
+ *              two, axes 0 and 2 in 8..1024, axis 1 in 8..256, at most 2^24
+ *              points, no FP64 residual check.  Free-space 3D: every axis as
+ *              a free-space axis below (n_z, nu_z for axis 2); the modes are
+ *              the tensor product of the three contour rules (Sec. 4.3).
  *   bc         TDSE_PERIODIC: domain [-pi,pi]^dim, Fourier modes (Sec. 2).
  *              TDSE_FREE: free space, data supported in [-1,1]^dim, modes on
  *              the deformed contour Gamma (Sec. 3-4).
@@ -139,8 +141,8 @@ typedef struct {
     double H;
     /* potential form (both boundary conditions), appended last */
     int potential;
-    /* dim = 3 (periodic only): grid points along axis 2; n[0], n[1] are
-     * axes 0 and 1.  Ignored for dim < 3.  Appended last. */
+    /* dim = 3: grid points along axis 2; n[0], n[1] are axes 0 and 1.
+     * Ignored for dim < 3.  Appended last. */
     int n_z;
     /* free space: how the C-type transforms (the Gauss modes on Gamma_2)
      * are evaluated (Sec. 4.1): TDSE_CT_DIRECT = direct sums, O(M N^C) per
@@ -149,6 +151,8 @@ typedef struct {
      * N_T chosen so that the interpolant is exact to FP64 rounding at the
      * C nodes; TDSE_CT_AUTO (0) = Chebyshev when N_T < N^C.  Appended last. */
     int c_transform;
+    /* free space, dim = 3: nu of axis 2 (as nu[2] above).  Appended last. */
+    int nu_z;
 } tdse_config;
 
 /* Vector potential callback: writes A(t) (dim components) to A_out. */
@@ -281,7 +285,7 @@ int tdse_free_cheb_terms(const tdse_ctx* ctx, int axis);
 
 /* The contour offset of Remark Hchoice:
  *   H = log(eps / ((1 + vnorm) eps_m)) / (2 dim (1 + phimax)),  eps_m = 2^-52,
- * vnorm = max_t ||V(., t)||_2 on [-1,1]^dim, phimax = max_t |phi(t)|.
+ * vnorm = max_t ||V(., t)||_2 on [-1,1]^dim, phimax = max_t |phi(t)|; dim 1..3.
  * TDSE_EINVAL if the result is not positive and finite. */
 tdse_status tdse_free_choose_H(double eps, double vnorm, double phimax, int dim, double* H_out);
 

@@ -58,6 +58,7 @@ def _config(shape, dt, nsteps, order, batch, precision, startup_steps, bc, nu, H
         nus = list(nu) if nu is not None else [8 * s for s in shape]
         cfg.nu[0] = int(nus[0])
         cfg.nu[1] = int(nus[1]) if len(nus) > 1 else 0
+        cfg.nu_z = int(nus[2]) if len(nus) > 2 else 0
         cfg.alpert_p = int(alpert_p)
         cfg.gauss_q = int(gauss_q)
         cfg.n_r = int(n_r)
@@ -101,7 +102,7 @@ def _as_buffer(x, dtype):
 class Problem:
     """A batch of TDSE instances sharing grid, dt, step count and order.
 
-    Parameters mirror ``tdse_config``: ``shape`` (n,) or (n0, n1); ``dt``;
+    Parameters mirror ``tdse_config``: ``shape`` (n,), (n0, n1) or (n0, n1, n2); ``dt``;
     ``nsteps`` (steps the tables cover); ``order`` (Adams order, even <= 8);
     ``batch``; ``precision`` ("fp64" or "mixed"); ``startup_steps`` (-1 =
     order-1); ``bc`` ("periodic" or "free").  Free space also takes ``nu``

@@ -53,6 +53,7 @@ class TdseConfig(ctypes.Structure):
         ("potential", ctypes.c_int),
         ("n_z", ctypes.c_int),
         ("c_transform", ctypes.c_int),
+        ("nu_z", ctypes.c_int),
     ]
 
 

@@ -348,8 +348,7 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     if (S < cfg->order - 2) return TDSE_EINVAL;
     const int n0 = cfg->n[0], n1 = cfg->dim >= 2 ? cfg->n[1] : 1, n2 = cfg->dim == 3 ? cfg->n_z : 1;
     if (!is_pow2(n0) || (cfg->dim >= 2 && !is_pow2(n1)) || (cfg->dim == 3 && !is_pow2(n2))) return TDSE_EINVAL;
-    if (cfg->dim == 3 && fs) return TDSE_EUNSUPPORTED;
-    if (cfg->dim == 3 && !periodic3d_supported(n0, n1, n2)) return TDSE_EUNSUPPORTED;
+    if (cfg->dim == 3 && !fs && !periodic3d_supported(n0, n1, n2)) return TDSE_EUNSUPPORTED;
     const bool big1d = !fs && cfg->dim == 1 && cfg->precision == TDSE_MIXED && n0 == four_step_n();
     // larger 1D grids: the four-step transform through the 2D passes, up to 2^20 points
     const bool four1d = !fs && cfg->dim == 1 && !periodic1d_supported(n0) && !big1d && n0 >= 64 && n0 <= (1 << 20);
@@ -1148,7 +1147,7 @@ struct CkptHeader {
     int dim, bc, n0, n1, n2, batch, nsteps, order, startup, precision, nu0, nu1, alpert_p, gauss_q, n_r;
     double dt, H;
     unsigned long long ws_bytes;
-    int step, inited, ip, res_every, res_checks, pad;
+    int step, inited, ip, res_every, res_checks, nu2;
     double res_tol;
 };
 void fill_header(const tdse_ctx* c, CkptHeader& h) {
@@ -1159,7 +1158,7 @@ void fill_header(const tdse_ctx* c, CkptHeader& h) {
     h.batch = g.batch;
     h.nsteps = g.nsteps; h.order = g.order; h.startup = c->S; h.precision = g.precision;
     if (g.bc == TDSE_FREE) {
-        h.nu0 = g.nu[0]; h.nu1 = g.dim == 2 ? g.nu[1] : 0; h.alpert_p = g.alpert_p; h.gauss_q = g.gauss_q;
+        h.nu0 = g.nu[0]; h.nu1 = g.dim >= 2 ? g.nu[1] : 0; h.nu2 = g.dim == 3 ? g.nu_z : 0; h.alpert_p = g.alpert_p; h.gauss_q = g.gauss_q;
         h.n_r = g.n_r; h.H = g.H;
     }
     h.dt = g.dt;

@@ -28,19 +28,19 @@ struct FsAxisHost {
 };
 
 struct FsState {
-    FsAxisHost ax[2];
-    size_t NM = 0;   // modes per instance (N0 N1)
-    size_t NX = 0;   // grid points per instance (M0 M1)
+    FsAxisHost ax[3];
+    size_t NM = 0;   // modes per instance (N0 N1 N2)
+    size_t NX = 0;   // grid points per instance (M0 M1 M2)
     bool f32 = false;   // TDSE_MIXED: FP32 transforms, ring, intermediate and history sum
     struct {
-        size_t uhat, ring, chain_uhat, chain_ring, chain_u, u, Z, V0, tfac, phi, iv, scratch, end;
-        size_t zeta[2], preI[2], postI[2], preF[2], postF[2], Gd[2], Fd[2], tw[2], P[2];
+        size_t uhat, ring, chain_uhat, chain_ring, chain_u, u, Z, Y, V0, tfac, phi, iv, scratch, end;
+        size_t zeta[3], preI[3], postI[3], preF[3], postF[3], Gd[3], Fd[3], tw[3], P[3];
         // FP32 copies (f32 only; 0 otherwise)
-        size_t preI_f[2], postI_f[2], preF_f[2], postF_f[2], Gd_f[2], Fd_f[2], tw_f[2], P_f[2];
-        // FP64 residual check of the FP32 step (f32 only): W / corrected state, R64, u64, 2D intermediate
-        size_t res_W, res_R, res_u, Z64;
+        size_t preI_f[3], postI_f[3], preF_f[3], postF_f[3], Gd_f[3], Fd_f[3], tw_f[3], P_f[3];
+        // FP64 residual check of the FP32 step (f32 only): W / corrected state, R64, u64, intermediates
+        size_t res_W, res_R, res_u, Z64, Y64;
         // Chebyshev form of the C-type transforms (NT > 0 only)
-        size_t Lf[2], Li[2], Tc[2], TcW[2], Lf_f[2], Li_f[2], Tc_f[2], TcW_f[2];
+        size_t Lf[3], Li[3], Tc[3], TcW[3], Lf_f[3], Li_f[3], Tc_f[3], TcW_f[3];
     } off{};
     int zero_iv = -1;   // f32: interval of zero length (one-step phase 1) for the FP64 re-evaluation
 };

@@ -119,6 +119,7 @@ cudaError_t launch_fs_row(const FsArgs& a, int flags, int f32, cudaStream_t s) {
 cudaError_t launch_fs_phys(const FsArgs& a, int from_usrc, int f32, cudaStream_t s) {
     return run(a, 2, from_usrc, f32, s);
 }
+cudaError_t launch_fs_mid(const FsArgs& a, int dir, int f32, cudaStream_t s) { return run(a, 3, dir, f32, s); }
 
 cudaError_t launch_fs_phase(double2* P, const double2* zeta, int N, const int2* intervals, int n_int,
                             const double* phi, double dt, cudaStream_t s) {

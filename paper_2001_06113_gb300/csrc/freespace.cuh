@@ -21,13 +21,17 @@
 //
 // Kernels:
 //   k_fs_1d   one CTA per instance: the whole 1D step;
-//   k_fs_row  (2D) one CTA per mode row k0: forward along axis 1 of the row
-//             of the intermediate Z, mode update and ring write (end of a
-//             step), then W of the next step and its inverse along axis 1
-//             back into Z (begin of a step);
-//   k_fs_phys (2D) one CTA per grid column j1: inverse along axis 0 of the
-//             column of Z, implicit solve and V u on the grid, forward along
-//             axis 0 back into the same column of Z.
+//   k_fs_row  (2D, 3D) one CTA per mode row (k0 in 2D, (k0, k1) in 3D):
+//             forward along the last axis of the row of the intermediate Z,
+//             mode update and ring write (end of a step), then W of the next
+//             step and its inverse along the last axis back into Z (begin of
+//             a step);
+//   k_fs_mid  (3D) one CTA per line (k0, j2) along axis 1: inverse from the
+//             N1 modes in Z to the M1 grid values in Y, or forward back;
+//   k_fs_phys (2D, 3D) one CTA per grid column (j1 in 2D, (j1, j2) in 3D):
+//             inverse along axis 0 of the column of Z (3D: Y), implicit solve
+//             and V u on the grid, forward along axis 0 back into the same
+//             column.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -332,12 +336,14 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
     C* E = reinterpret_cast<C*>(sm_raw);
     C* f = E + Ln::EBUF;
     C* dv = f + M;
-    const FsAxis& ax = a.ax[1];
-    const int k0 = blockIdx.x, b = blockIdx.y;
+    const bool d3 = a.d == 3;
+    const FsAxis& ax = a.ax[d3 ? 2 : 1];                // the line axis (the last one)
+    const int k0 = blockIdx.x, b = blockIdx.y;           // k0: the row (k0 N1 + k1 in 3D)
     const int N0 = a.ax[0].N, N1 = ax.N;
-    const size_t NPm = (size_t)N0 * N1;
+    const int nrows = d3 ? N0 * a.ax[1].N : N0;
+    const size_t NPm = (size_t)nrows * N1;
     double2* urow = a.uhat + (size_t)b * NPm + (size_t)k0 * N1;
-    C* zrow = reinterpret_cast<C*>(a.Z) + ((size_t)b * N0 + k0) * M;
+    C* zrow = reinterpret_cast<C*>(a.Z) + ((size_t)b * nrows + k0) * M;
     const bool end = flags & FS_ROW_END, begin = flags & FS_ROW_BEGIN;
     if (end || (flags & FS_ROW_FWD_ONLY)) {
         for (int j = threadIdx.x; j < M; j += FsThreads<C>::value) f[j] = zrow[j];
@@ -352,15 +358,22 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
     const double2* P0 = a.ax[0].P + (size_t)b * a.n_int * N0;
     const double2* P1 = ax.P + (size_t)b * a.n_int * N1;
     const C* P1c = Tab<C>::P(ax) + (size_t)b * a.n_int * N1;
+    // phase of the row over interval iv: P0 (2D), P0 P1 of axes 0 and 1 (3D)
+    auto row_phase = [&](int iv) -> double2 {
+        if (!d3) return __ldg(&P0[(size_t)iv * N0 + k0]);
+        const int NA = a.ax[1].N, i0 = k0 / NA, i1 = k0 - i0 * NA;
+        const double2* PA = a.ax[1].P + (size_t)b * a.n_int * NA;
+        return cmul(__ldg(&P0[(size_t)iv * N0 + i0]), __ldg(&PA[(size_t)iv * NA + i1]));
+    };
     double2 a0 = zero2();
     C cj[FS_MAX_HIST + 1];
     if (begin) {
-        a0 = __ldg(&P0[(size_t)a.interval[0] * N0 + k0]);
+        a0 = row_phase(a.interval[0]);
         double2 A = make_double2(1.0, 0.0);
 #pragma unroll
         for (int j = 1; j <= FS_MAX_HIST; ++j) {
             cj[j] = cvt<C>(cscale(A, a.mu[j]));
-            if (j < FS_MAX_HIST && j < a.nhist) A = cmul(A, __ldg(&P0[(size_t)a.interval[j] * N0 + k0]));
+            if (j < FS_MAX_HIST && j < a.nhist) A = cmul(A, row_phase(a.interval[j]));
         }
     }
     const double hm0 = a.h * a.mu[0];
@@ -405,9 +418,10 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
     C* y = E + Ln::EBUF;
     C* dv = y + M;
     const FsAxis& ax = a.ax[0];
-    const int j1 = blockIdx.x, b = blockIdx.y;
-    const int M1 = a.ax[1].M, N0 = ax.N;
-    C* zcol = reinterpret_cast<C*>(a.Z) + (size_t)b * N0 * M1 + j1;
+    const int j1 = blockIdx.x, b = blockIdx.y;          // j1: the column (j1 M2 + j2 in 3D)
+    const bool d3 = a.d == 3;
+    const int M1 = d3 ? a.ax[1].M * a.ax[2].M : a.ax[1].M, N0 = ax.N;
+    C* zcol = reinterpret_cast<C*>(d3 ? a.Y : a.Z) + (size_t)b * N0 * M1 + j1;
     const size_t NX = (size_t)M * M1;
     const double vf = a.tfac[(size_t)b * a.ntf + a.tf];
     const double* V0 = a.V0 + (size_t)b * a.vstride;
@@ -435,6 +449,33 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
     for (int m = threadIdx.x; m < N0; m += FsThreads<C>::value) zcol[(size_t)m * M1] = Ln::fwd_value(m, E, dv, ax);
 }
 
+// 3D, axis 1: line (k0, j2) between the N1 modes Z[b][k0][.][j2] and the M1
+// grid values Y[b][k0][.][j2] (both with stride M2).
+template <class C, int M, int R>
+__global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs_mid(FsArgs a, int dir) {
+    using Ln = FsLine<C, M, R>;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* E = reinterpret_cast<C*>(sm_raw);
+    C* f = E + Ln::EBUF;
+    C* dv = f + M;
+    const FsAxis& ax = a.ax[1];
+    const int j2 = blockIdx.x, k0 = blockIdx.y, b = blockIdx.z;
+    const int M2 = a.ax[2].M, N0 = a.ax[0].N, N1 = ax.N;
+    C* zl = reinterpret_cast<C*>(a.Z) + ((size_t)b * N0 + k0) * N1 * M2 + j2;
+    C* yl = reinterpret_cast<C*>(a.Y) + ((size_t)b * N0 + k0) * M * M2 + j2;
+    if (dir == FS_MID_INV) {
+        for (int m = threadIdx.x; m < N1; m += FsThreads<C>::value) Ln::stage_inv(m, zl[(size_t)m * M2], E, dv, ax);
+        Ln::zero_pad(E, ax.NE);
+        Ln::inverse(E, dv, f, ax);
+        for (int j = threadIdx.x; j < M; j += FsThreads<C>::value) yl[(size_t)j * M2] = f[j];
+    } else {
+        for (int j = threadIdx.x; j < M; j += FsThreads<C>::value) f[j] = yl[(size_t)j * M2];
+        __syncthreads();
+        Ln::forward(f, E, dv, ax);
+        for (int m = threadIdx.x; m < N1; m += FsThreads<C>::value) zl[(size_t)m * M2] = Ln::fwd_value(m, E, dv, ax);
+    }
+}
+
 template <class C, int M, int R>
 constexpr size_t smem_of() {
     return (size_t)(FsLine<C, M, R>::EBUF + M + FS_MAX_ND + FS_MAX_NT) * sizeof(C);
@@ -459,10 +500,15 @@ cudaError_t launch_mr(const FsArgs& a, int which, int flag, cudaStream_t s) {
         k_fs_1d<C, M, R><<<a.B, FsThreads<C>::value, sm, s>>>(a, flag);
     } else if (which == 1) {
         if ((e = prepare<C>(k_fs_row<C, M, R>, sm)) != cudaSuccess) return e;
-        k_fs_row<C, M, R><<<dim3(a.ax[0].N, a.B), FsThreads<C>::value, sm, s>>>(a, flag);
-    } else {
+        const unsigned rows = a.d == 3 ? (unsigned)(a.ax[0].N * a.ax[1].N) : (unsigned)a.ax[0].N;
+        k_fs_row<C, M, R><<<dim3(rows, a.B), FsThreads<C>::value, sm, s>>>(a, flag);
+    } else if (which == 2) {
         if ((e = prepare<C>(k_fs_phys<C, M, R>, sm)) != cudaSuccess) return e;
-        k_fs_phys<C, M, R><<<dim3(a.ax[1].M, a.B), FsThreads<C>::value, sm, s>>>(a, flag);
+        const unsigned cols = a.d == 3 ? (unsigned)(a.ax[1].M * a.ax[2].M) : (unsigned)a.ax[1].M;
+        k_fs_phys<C, M, R><<<dim3(cols, a.B), FsThreads<C>::value, sm, s>>>(a, flag);
+    } else {
+        if ((e = prepare<C>(k_fs_mid<C, M, R>, sm)) != cudaSuccess) return e;
+        k_fs_mid<C, M, R><<<dim3(a.ax[2].M, a.ax[0].N, a.B), FsThreads<C>::value, sm, s>>>(a, flag);
     }
     return cudaGetLastError();
 }
@@ -487,7 +533,10 @@ cudaError_t dispatch(const FsArgs& a, const FsAxis& ax, int which, int flag, cud
     return cudaErrorInvalidValue;
 }
 
-inline const FsAxis& axis_of(const FsArgs& a, int which) { return which == 1 ? a.ax[1] : a.ax[0]; }
+// which: 0 = 1D step, 1 = row pass (last axis), 2 = phys pass (axis 0), 3 = axis-1 pass (3D)
+inline const FsAxis& axis_of(const FsArgs& a, int which) {
+    return which == 1 ? a.ax[a.d - 1] : (which == 3 ? a.ax[1] : a.ax[0]);
+}
 
 }  // namespace fs
 }  // namespace tdse

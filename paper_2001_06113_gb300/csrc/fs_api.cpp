@@ -281,7 +281,7 @@ FsArgs fs_base(const tdse_ctx* c) {
     FsArgs a{};
     a.B = c->B;
     a.d = c->d;
-    for (int x = 0; x < 2; ++x) {
+    for (int x = 0; x < 3; ++x) {
         FsAxis& X = a.ax[x];
         if (x >= c->d) {
             X.M = 1;
@@ -334,6 +334,7 @@ FsArgs fs_base(const tdse_ctx* c) {
     a.ring = c->P<double2>(F.off.ring);
     a.ring_slots = c->RS;
     a.Z = F.off.Z ? c->P<double2>(F.off.Z) : nullptr;
+    a.Y = F.off.Y ? c->P<double2>(F.off.Y) : nullptr;
     a.u = c->P<double2>(F.off.u);
     a.V0 = c->P<double>(F.off.V0);
     a.vstride = c->vshared ? 0 : (size_t)c->vrows * F.NX;
@@ -370,19 +371,31 @@ tdse_status forward_to(tdse_ctx* c, const double2* usrc, int mulV, int tf, doubl
         TDSE_CK(c, launch_fs_1d(a, FS_1D_FWD_ONLY, f32, s));
     } else {
         TDSE_CK(c, launch_fs_phys(a, 1, f32, s));
+        if (c->d == 3) TDSE_CK(c, launch_fs_mid(a, FS_MID_FWD, f32, s));
         TDSE_CK(c, launch_fs_row(a, FS_ROW_FWD_ONLY, f32, s));
     }
     return TDSE_OK;
 }
 
-// One step with the description in a: 1D fused kernel, 2D begin / phys / end.
+// The part of a 2D / 3D step between the row passes: the grid work along
+// axis 0 (3D: between the inverse and the forward transform along axis 1).
+tdse_status grid_part(tdse_ctx* c, const FsArgs& a, int f32, cudaStream_t s) {
+    if (c->d == 3) TDSE_CK(c, launch_fs_mid(a, FS_MID_INV, f32, s));
+    TDSE_CK(c, launch_fs_phys(a, 0, f32, s));
+    if (c->d == 3) TDSE_CK(c, launch_fs_mid(a, FS_MID_FWD, f32, s));
+    return TDSE_OK;
+}
+
+// One step with the description in a: 1D fused kernel; 2D / 3D row begin,
+// grid part, row end.
 tdse_status one_step(tdse_ctx* c, const FsArgs& a, cudaStream_t s) {
     const int f32 = c->F.f32 ? 1 : 0;
     if (c->d == 1) {
         TDSE_CK(c, launch_fs_1d(a, FS_1D_STEP, f32, s));
     } else {
         TDSE_CK(c, launch_fs_row(a, FS_ROW_BEGIN, f32, s));
-        TDSE_CK(c, launch_fs_phys(a, 0, f32, s));
+        tdse_status st = grid_part(c, a, f32, s);
+        if (st != TDSE_OK) return st;
         TDSE_CK(c, launch_fs_row(a, FS_ROW_END, f32, s));
     }
     return TDSE_OK;
@@ -447,7 +460,8 @@ FsArgs adams_args(const tdse_ctx* c, int n) {
     return a;
 }
 
-// Adams steps n0+1 .. n0+k.  2D: row begin, (phys, row end+begin) x (k-1), phys, row end.
+// Adams steps n0+1 .. n0+k.  2D / 3D: row begin, (grid part, row end+begin)
+// x (k-1), grid part, row end.
 tdse_status fs_adams(tdse_ctx* c, int n0, int k, cudaStream_t s) {
     const int f32 = c->F.f32 ? 1 : 0;
     if (c->d == 1) {
@@ -456,13 +470,15 @@ tdse_status fs_adams(tdse_ctx* c, int n0, int k, cudaStream_t s) {
     }
     TDSE_CK(c, launch_fs_row(adams_args(c, n0 + 1), FS_ROW_BEGIN, f32, s));
     for (int n = n0 + 1; n < n0 + k; ++n) {
-        TDSE_CK(c, launch_fs_phys(adams_args(c, n), 0, f32, s));
+        tdse_status st = grid_part(c, adams_args(c, n), f32, s);
+        if (st != TDSE_OK) return st;
         FsArgs f = adams_args(c, n + 1);
         f.out_slot = slot_of(c, n);
         TDSE_CK(c, launch_fs_row(f, FS_ROW_END | FS_ROW_BEGIN, f32, s));
     }
     const FsArgs last = adams_args(c, n0 + k);
-    TDSE_CK(c, launch_fs_phys(last, 0, f32, s));
+    tdse_status st = grid_part(c, last, f32, s);
+    if (st != TDSE_OK) return st;
     TDSE_CK(c, launch_fs_row(last, FS_ROW_END, f32, s));
     return TDSE_OK;
 }
@@ -490,6 +506,7 @@ tdse_status fs_residual_check(tdse_ctx* c, cudaStream_t s) {
     a.ring_slots = 1;
     a.u = u64;
     a.Z = F.off.Z64 ? c->P<double2>(F.off.Z64) : nullptr;
+    a.Y = F.off.Y64 ? c->P<double2>(F.off.Y64) : nullptr;
     a.nhist = 0;
     a.h = c->cfg.dt;
     a.mu[0] = c->mu[0];
@@ -500,7 +517,8 @@ tdse_status fs_residual_check(tdse_ctx* c, cudaStream_t s) {
         TDSE_CK(c, launch_fs_1d(a, FS_1D_STEP, 0, s));
     } else {
         TDSE_CK(c, launch_fs_row(a, FS_ROW_BEGIN, 0, s));
-        TDSE_CK(c, launch_fs_phys(a, 0, 0, s));
+        tdse_status st = grid_part(c, a, 0, s);
+        if (st != TDSE_OK) return st;
         TDSE_CK(c, launch_fs_row(a, FS_ROW_END, 0, s));
     }
     double* sums = c->P<double>(c->off.res_sums);
@@ -530,7 +548,7 @@ tdse_status fs_create(tdse_ctx* c) {
     F.NM = 1;
     F.NX = 1;
     for (int x = 0; x < c->d; ++x) {
-        const int M = g.n[x], nu = g.nu[x];
+        const int M = x < 2 ? g.n[x] : g.n_z, nu = x < 2 ? g.nu[x] : g.nu_z;
         if (M <= 0 || nu <= 0 || nu % M) return c->fail(TDSE_EINVAL, "nu must be a multiple of n");
         if (!fs_supported(M, nu / M)) return c->fail(TDSE_EUNSUPPORTED, "free space: n in 32..512, nu/n in {4,8,16}, nu <= 4096");
         if (!build_rule(F.ax[x], M, nu, p, g.gauss_q, g.n_r, g.H))
@@ -557,7 +575,12 @@ tdse_status fs_create(tdse_ctx* c) {
     F.off.chain_ring = take((size_t)c->L * B * F.NM * c->rsz);
     F.off.chain_u = take((size_t)c->L * B * F.NX * 16);
     F.off.u = take(B * F.NX * 16);
-    F.off.Z = c->d == 2 ? take(B * (size_t)F.ax[0].N * F.ax[1].M * c->rsz) : 0;
+    // 2D: Z [N0][M1]; 3D: Z [N0][N1][M2] and Y [N0][M1][M2]
+    const size_t zel = c->d == 2 ? (size_t)F.ax[0].N * F.ax[1].M
+                                 : (c->d == 3 ? (size_t)F.ax[0].N * F.ax[1].N * F.ax[2].M : 0);
+    const size_t yel = c->d == 3 ? (size_t)F.ax[0].N * F.ax[1].M * F.ax[2].M : 0;
+    F.off.Z = zel ? take(B * zel * c->rsz) : 0;
+    F.off.Y = yel ? take(B * yel * c->rsz) : 0;
     const size_t vcopies = c->vshared ? 1 : B;
     F.off.V0 = take(vcopies * c->vrows * F.NX * 8);
     const size_t V0f = take(vcopies * c->vrows * F.NX * 8);
@@ -603,7 +626,8 @@ tdse_status fs_create(tdse_ctx* c) {
         F.off.res_W = take(B * F.NM * 16);
         F.off.res_R = take(B * F.NM * 16);
         F.off.res_u = take(B * F.NX * 16);
-        F.off.Z64 = c->d == 2 ? take(B * (size_t)F.ax[0].N * F.ax[1].M * 16) : 0;
+        F.off.Z64 = zel ? take(B * zel * 16) : 0;
+        F.off.Y64 = yel ? take(B * yel * 16) : 0;
         res_sums = take(B * 16);
         res_rho = take(B * 8);
         res_flags = take(B * 4);
@@ -748,7 +772,7 @@ extern "C" tdse_status tdse_free_rule(const tdse_ctx* c, int axis, int* N, doubl
 
 extern "C" tdse_status tdse_free_choose_H_prec(double eps, double vnorm, double phimax, int dim, int precision,
                                                double* H_out) {
-    if (!H_out || (dim != 1 && dim != 2) || !(eps > 0.0) || !(vnorm >= 0.0) || !(phimax >= 0.0)) return TDSE_EINVAL;
+    if (!H_out || dim < 1 || dim > 3 || !(eps > 0.0) || !(vnorm >= 0.0) || !(phimax >= 0.0)) return TDSE_EINVAL;
     if (precision != TDSE_FP64 && precision != TDSE_MIXED) return TDSE_EINVAL;
     // machine epsilon of the arithmetic that evaluates the contour sums
     const double eps_m = std::ldexp(1.0, precision == TDSE_FP64 ? -52 : -23);

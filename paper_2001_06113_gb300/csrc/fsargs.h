@@ -9,7 +9,8 @@
 //            the middle ND = 2p + NC modes are the "dense" block;
 //   forward  f^_m = (2/M) sum_j e^{-i zeta_m x_j} f_j                  (eq. fzdft)
 //   inverse  f_j  = (1/2pi) sum_m w_m e^{i zeta_m x_j} f^_m            (eq. uciftdisc)
-// In 2D both are tensor products (axis 0 then axis 1, row-major arrays).
+// In 2D and 3D both are tensor products over the axes (row-major arrays, the
+// last axis contiguous).
 //
 // An equispaced block has zeta_i = zeta0 + i h, i = 0..NE-1, weight h, with
 // h = pi M / nu, so e^{i i h x_j} = e^{-i i h} e^{2 pi i i j / nu}: its sums are
@@ -75,8 +76,8 @@ struct FsAxis {
 
 struct FsArgs {
     int B;                 // instances in the launch
-    int d;                 // 1 or 2
-    FsAxis ax[2];
+    int d;                 // 1, 2 or 3
+    FsAxis ax[3];
     int n_int;             // phase intervals per instance
     // ---- step description (eq. uadamsk with zeta for k; eq. utrapzfd for nhist = 1)
     int nhist;             // history terms j = 1..nhist
@@ -90,7 +91,8 @@ struct FsArgs {
     double2* uhat;         // [B][N0 N1] mode state: u^ between steps, W inside a step (FP64 in both variants)
     double2* ring;         // [B][ring_slots][N0 N1] history of (Vu)^ (elements of the transform type)
     int ring_slots;
-    double2* Z;            // [B][N0][M1] 2D intermediate (axis-1 transformed rows; transform type)
+    double2* Z;            // 2D: [B][N0][M1]; 3D: [B][N0][N1][M2] (last axis on the grid; transform type)
+    double2* Y;            // 3D: [B][N0][M1][M2] (axes 1 and 2 on the grid; transform type)
     double2* u;            // [B][M0 M1] physical state written by the implicit solve
     const double2* usrc;   // forward-only source on the grid
     double2* fdst;         // forward-only destination in mode space, instance b at fdst + b fdst_bstride
@@ -103,15 +105,20 @@ struct FsArgs {
     int ntf;
 };
 
-// Row pass flags (2D) and 1D modes.
+// Row pass flags (2D, 3D), 1D modes, directions of the 3D axis-1 pass.
 enum FsRow : int { FS_ROW_END = 1, FS_ROW_BEGIN = 2, FS_ROW_FWD_ONLY = 4 };
 enum Fs1D : int { FS_1D_STEP = 0, FS_1D_FWD_ONLY = 1 };
+enum FsMid : int { FS_MID_INV = 0, FS_MID_FWD = 1 };
 
 bool fs_supported(int M, int R);
-// 2D: row pass over the N0 mode rows (axis 1), phys pass over the M1 grid columns (axis 0).
-// f32 = 1 selects the FP32-transform kernels (freespace_f32.cu).
+// 2D: row pass over the N0 mode rows (last axis, Z), phys pass over the M1
+// grid columns (axis 0, Z).  3D: row pass over the N0 N1 mode rows (axis 2,
+// Z), axis-1 pass between Z and Y over the N0 M2 lines, phys pass over the
+// M1 M2 grid columns (axis 0, Y).  f32 = 1 selects the FP32-transform
+// kernels (freespace_f32.cu).
 cudaError_t launch_fs_row(const FsArgs& a, int flags, int f32, cudaStream_t s);
 cudaError_t launch_fs_phys(const FsArgs& a, int from_usrc, int f32, cudaStream_t s);
+cudaError_t launch_fs_mid(const FsArgs& a, int dir, int f32, cudaStream_t s);
 cudaError_t launch_fs_1d(const FsArgs& a, int mode, int f32, cudaStream_t s);
 cudaError_t launch_fs_f32(const FsArgs& a, int which, int flag, cudaStream_t s);   // freespace_f32.cu
 // FP32 copy of n complex values

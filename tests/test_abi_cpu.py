@@ -69,7 +69,10 @@ def _cfg(native, **kw):
     (dict(dim=3, n=(16, 12), n_z=32), -1),            # not a power of two
     (dict(dim=3, n=(16, 512), n_z=32), -7),           # axis 1 at most 256
     (dict(dim=3, n=(1024, 256), n_z=1024), -7),       # more than 2^24 points
-    (dict(dim=3, n=(16, 8), n_z=32, bc=1, nu=(128, 64), H=1.5, gauss_q=10, n_r=1), -7),   # free space 3D
+    (dict(dim=3, n=(32, 64), n_z=32, bc=1, nu=(128, 256), nu_z=128, H=1.5, gauss_q=10, n_r=1), 0),  # free space 3D
+    (dict(dim=3, n=(32, 64), n_z=32, bc=1, nu=(128, 256), nu_z=128, H=1.5, gauss_q=10, n_r=1, precision=1), 0),
+    (dict(dim=3, n=(32, 64), n_z=32, bc=1, nu=(128, 256), H=1.5, gauss_q=10, n_r=1), -1),   # no nu_z
+    (dict(dim=3, n=(32, 64), n_z=16, bc=1, nu=(128, 256), nu_z=64, H=1.5, gauss_q=10, n_r=1), -7),  # n_z < 32
     (dict(dim=4), -1),
     (dict(n=(48, 1)), -1),             # not a power of two
     (dict(n=(16384, 1)), 0),           # 1D FP64 beyond one CTA: the four-step transform through the 2D passes
@@ -152,6 +155,33 @@ def test_free_rule_matches_oracle_rule(native, p, q, n_r):
     assert z.size == r.N
     assert np.max(np.abs(z - r.zeta) / np.maximum(1.0, np.abs(r.zeta))) < 4e-16
     assert np.max(np.abs(w - r.w)) < 2e-15      # Gauss-Legendre weights by two routes: a few ulps
+
+
+def test_free_rule_3d_per_axis(native):
+    """3D free space: each axis has its own contour rule (M, nu of that axis)
+    and the mode state is their tensor product."""
+    from oracle import gamma
+    lib = native.lib()
+    ctx = ctypes.c_void_p()
+    M, nus, H = (32, 64, 32), (128, 256, 256), 1.5
+    cfg = _cfg(native, dim=3, bc=1, n=M[:2], n_z=M[2], nu=nus[:2], nu_z=nus[2], H=H, gauss_q=10, n_r=1)
+    assert lib.tdse_create(ctypes.byref(cfg), ctypes.byref(ctx)) == 0
+    dp = ctypes.POINTER(ctypes.c_double)
+    Ns = []
+    for ax in range(3):
+        n = ctypes.c_int()
+        assert lib.tdse_free_rule(ctx, ax, ctypes.byref(n), None, None) == 0
+        z = np.empty(n.value, dtype=np.complex128)
+        w = np.empty(n.value, dtype=np.complex128)
+        assert lib.tdse_free_rule(ctx, ax, ctypes.byref(n), z.ctypes.data_as(dp), w.ctypes.data_as(dp)) == 0
+        r = gamma.GammaRule.for_nu(M[ax], nus[ax], H, q=10, n_r=1)
+        assert z.size == r.N
+        assert np.max(np.abs(z - r.zeta) / np.maximum(1.0, np.abs(r.zeta))) < 4e-16
+        Ns.append(r.N)
+    assert lib.tdse_free_rule(ctx, 3, ctypes.byref(ctypes.c_int()), None, None) == -1
+    # the workspace holds at least u^ and the ring (7 slots) over N0 N1 N2 modes
+    assert lib.tdse_workspace_bytes(ctx) >= 16 * 8 * Ns[0] * Ns[1] * Ns[2]
+    lib.tdse_destroy(ctx)
 
 
 @pytest.mark.parametrize("eps,vnorm,phimax,dim", [(1e-10, 20.0, 0.3, 2), (1e-12, 0.0, 0.0, 1), (1e-8, 5.0, 1.0, 2),
