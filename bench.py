@@ -85,7 +85,8 @@ def parse():
     ap.add_argument("--no-fp64-variant", action="store_true",
                     help="skip the complex128 timing of the same workload in the default (mixed) line")
     ap.add_argument("--workload", default="periodic2d",
-                    choices=["periodic2d", "free2d", "batch1d", "serve", "example1", "periodic3d", "free_ctype"])
+                    choices=["periodic2d", "free2d", "batch1d", "serve", "example1", "periodic3d", "free_ctype",
+                             "free3d"])
     ap.add_argument("--profile-adams", type=int, default=0,
                     help="profiling run: start-up + this many Adams steps of the batch, then exit")
     return ap.parse_args()
@@ -1724,6 +1725,241 @@ def main_free_ctype(args, ws, rank, local):
     return 0
 
 
+# ------------------------------------------------------------ 3D free space
+F3_M, F3_NU, F3_DT, F3_NSTEPS, F3_Q, F3_NR = 64, 256, 1e-3, 200, 10, 1
+F3_EPS = {"fp64": 1e-10, "mixed": 1e-4}
+F3_DIR = (1.0, -0.5, 0.3)
+
+
+def free3d_instance(seed: int = 3):
+    return synth.free_bump_gaussians((F3_M,) * 3, seed=seed, dt=F3_DT, nsteps=F3_NSTEPS, A0=2.0, omega=10.0,
+                                     direction=F3_DIR)
+
+
+def free3d_H(inst, precision: str) -> float:
+    from paper_2001_06113_gb300 import free_choose_H
+    vnorm = math.sqrt(float(np.sum(inst.V0 ** 2)) * (2.0 / F3_M) ** 3)
+    t = np.linspace(0.0, F3_NSTEPS * F3_DT, 4001)
+    A = inst.pulse.A(t)
+    phi = np.concatenate([np.zeros((1, A.shape[1])), np.cumsum(0.5 * (A[1:] + A[:-1]) * (t[1] - t[0]), axis=0)])
+    return free_choose_H(F3_EPS[precision], vnorm, float(np.max(np.abs(phi))), 3, precision=precision)
+
+
+def free3d_flops_per_step(N: int) -> float:
+    """Real FP64 flops of one 3D free-space Adams step (64^3, nu = 256), per
+    instance, counted as for 2D (complex mul 6, add 2, FFT 5 n log2 n): the
+    row pass over the N0 N1 mode rows (forward and inverse along axis 2 and
+    the per-mode update and Horner history), the axis-1 passes over the N0 M2
+    lines (one inverse, one forward), the grid pass over the M1 M2 columns
+    (inverse and forward along axis 0, implicit solve and V u)."""
+    M, nu = F3_M, F3_NU
+    R = nu // M
+    ne = nu // 2 - 13
+    nd = N - 2 * ne
+    fft = 2 * R * 5 * M * math.log2(M)
+    fwd = 2 * nu * 6 + fft + 2 * ne * 6 + nd * M * 8
+    inv = 2 * ne * 6 + fft + 2 * nu * 8 + nd * M * 8
+    horner = 7 * 2 + 6 * (6 + 6 + 2) + 6 + 6 + 4 + 6          # + the product of the two row phases
+    row = N * N * (fwd + inv + N * (4 + horner))
+    mid = N * M * (inv + fwd)
+    col = M * M * (inv + fwd + M * 14)
+    return row + mid + col
+
+
+def free3d_algo_bytes(N: int, e: int) -> float:
+    """Algorithmic DRAM bytes of one 3D free-space Adams step (e = ring and
+    intermediate element bytes): per mode the FP64 state read and W written
+    (32 B), 6 ring lags read and the new (Vu)^ written (7 e); Z [N0][N1][M2]
+    and Y [N0][M1][M2] each written and read twice (once per direction); per
+    grid point V read (8 B) and u written (16 B)."""
+    M = F3_M
+    return N ** 3 * (32 + 7 * e) + 4 * N * N * M * e + 4 * N * M * M * e + M ** 3 * 24
+
+
+# DRAM bytes of one fused k_fs_row<float2, 64, 4> launch of the 64^3 step (ncu
+# launch list, read 1169.4 MB + write 445.5 MB).
+F3_ROW_TRAFFIC_MIXED = 1169.4e6 + 445.5e6
+
+
+def free3d_oracle_sample(N_adams: int = 1):
+    """point-steps/s of the CPU oracle: Adams steps of one 64^3 instance from a
+    synthetic history (dense transform matrices per axis)."""
+    from oracle import fields, gamma
+    from oracle.freespace import FreeSpaceOracle
+    inst = free3d_instance()
+    H = free3d_H(inst, "fp64")
+    rules = [gamma.GammaRule.for_nu(F3_M, F3_NU, H, q=F3_Q, n_r=F3_NR) for _ in range(3)]
+    orc = FreeSpaceOracle(rules, F3_DT, inst.V0, inst.vfac, fields.phi_callable(inst.pulse, 3), order=ORDER)
+    uh = orc.fwd(inst.u0)
+    h0 = orc.fwd(orc.V(0.0) * inst.u0)
+    n0 = 20
+    hist = {n0 - j: h0 for j in range(1, ORDER)}
+    t0 = time.perf_counter()
+    for k in range(N_adams):
+        n = n0 + k
+        uh, _, hist[n] = orc.adams_step(uh, n * F3_DT, hist, n)
+        hist.pop(n - ORDER, None)
+    el = time.perf_counter() - t0
+    return F3_M ** 3 * N_adams / el, el
+
+
+def main_free3d(args, ws, rank, local):
+    """3D free space (Sec. 4.3): one 64^3 instance, nu = 256 per axis (N = 266
+    modes per axis, 1.9e7 modes), q = 10, n_r = 1, 8th-order Adams, T = 0.2
+    (200 steps), A along (1, -0.5, 0.3).  Whole-solve throughput in grid
+    point-steps/s; the Adams step against the FP64 rate measured here (FP64)
+    or against the FP32 rate (mixed), with the error of the mixed path against
+    the FP64 path on the same contour."""
+    import torch
+    from paper_2001_06113_gb300 import Problem
+    prec = args.precision
+    metric = f"point-steps/s (3D free space 64^3, nu=256, 8th-order, T=0.2, {prec})"
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        for _ in range(args.warmup):
+            free3d_oracle_sample(1)
+        vals = [free3d_oracle_sample(1)[0] for _ in range(args.steps)]
+        v = float(np.mean(vals))
+        print(json.dumps({"impl": "reference", "metric": metric, "value": v, "unit": "point-steps/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1e3 * F3_M ** 3 / v, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "3D free space 64^3, nu=256 (CPU oracle sample)"},
+                          "cpu_baseline": {"value": v, "unit": "point-steps/s", "cores": cpu_cores(), "kind": "oracle",
+                                           "sample": "1 Adams step of one 64^3 instance per bench step"},
+                          "e2e": {"value": v, "unit": "point-steps/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return 0
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    inst = free3d_instance()
+    H = free3d_H(inst, prec)
+
+    def make(precision, Hh):
+        pr = Problem((F3_M,) * 3, F3_DT, F3_NSTEPS, order=ORDER, precision=precision, stream=stream, bc="free",
+                     nu=(F3_NU,) * 3, H=Hh, gauss_q=F3_Q, n_r=F3_NR)
+        pr.set_potential(inst.V0, None)
+        p = inst.pulse
+        pr.set_pulse(p.A0, p.omega, p.T_pulse, p.direction)
+        pr.set_initial(inst.u0)
+        return pr
+
+    prob = make(prec, H)
+    N = prob.mode_shape[0]
+    if args.profile_adams:      # launch sequence for ncu: start-up + K Adams steps, untimed
+        with torch.cuda.stream(stream):
+            prob.step(STARTUP + args.profile_adams)
+        stream.synchronize()
+        prob.close()
+        print(json.dumps({"profile_adams": args.profile_adams, "workload": "free3d", "precision": prec}))
+        return 0
+    pinned_u = torch.from_numpy(inst.u0.copy()).pin_memory()
+    pinned_V = torch.from_numpy(inst.V0.copy()).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            prob.set_initial(pinned_u)
+            prob.step(F3_NSTEPS)
+    stream.synchronize()
+    times = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                prob.set_initial(pinned_u)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                prob.step(F3_NSTEPS)
+                e1.record(stream)
+            stream.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+    t_solve = float(np.mean(times))
+    points = F3_M ** 3
+    value = points * F3_NSTEPS / t_solve
+    GROUP, NGROUPS = 5, 10
+    with torch.cuda.stream(stream):
+        prob.set_initial(pinned_u)
+        prob.step(STARTUP + 4)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(NGROUPS + 1)]
+        evs[0].record(stream)
+        for i in range(NGROUPS):
+            prob.step(GROUP)
+            evs[i + 1].record(stream)
+    stream.synchronize()
+    dts = np.array([evs[i].elapsed_time(evs[i + 1]) / 1e3 / GROUP for i in range(NGROUPS)])
+    t_step = float(np.mean(dts))
+    flops = free3d_flops_per_step(N)
+    achieved = flops / t_step / 1e12
+    timing = {"kernel": "3D free-space Adams step (k_fs_row end+begin, k_fs_mid inverse, k_fs_phys, k_fs_mid "
+                        "forward), timed over groups of 5 steps",
+              "algorithmic_flops_per_step": flops, "modes_per_axis": N,
+              "step_ms_p50": round(float(np.percentile(dts, 50)) * 1e3, 4)}
+    if prec == "fp64":
+        peak, src = fp64_peak(dev)
+        roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                    "frac": round(achieved / peak, 4), "traffic": None, "peak_source": src, **timing}
+    else:
+        # FP32 transforms: both ceilings, the nearer one reported as the bound
+        algo = free3d_algo_bytes(N, 8)
+        hpk, hsrc = hbm_peak()
+        gbs = algo / t_step / 1e9
+        hbm = {"achieved": round(gbs, 1), "peak": hpk, "unit": "GB/s", "frac": round(gbs / hpk, 4),
+               "algorithmic_bytes_per_step": algo, "peak_source": hsrc}
+        alu = {"achieved": round(achieved, 4), "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
+               "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
+        top, other = ("hbm", "alu") if hbm["frac"] >= alu["frac"] else ("alu", "hbm")
+        pick = {"hbm": hbm, "alu": alu}
+        roofline = {"bound": top, **pick[top], "traffic": F3_ROW_TRAFFIC_MIXED,
+                    "traffic_unit": "DRAM bytes per fused k_fs_row launch (ncu), the step's dominant kernel",
+                    "other_ceiling": {"bound": other, **pick[other]}, **timing}
+    e2e = None
+    if not args.no_e2e:
+        out = torch.empty((F3_M,) * 3, dtype=torch.complex128).pin_memory()
+        with torch.cuda.stream(stream):
+            stream.synchronize()
+            t0 = time.perf_counter()
+            prob.set_potential(pinned_V, None)
+            prob.set_initial(pinned_u)
+            prob.step(F3_NSTEPS)
+            prob.read_u(0, out=out)
+            te = time.perf_counter() - t0
+        e2e = {"value": points * F3_NSTEPS / te, "unit": "point-steps/s", "h2d_bytes_per_step": points * 24,
+               "d2h_bytes_per_step": points * 16}
+    err = None
+    if prec == "mixed":
+        ref = make("fp64", H)
+        with torch.cuda.stream(stream):
+            prob.set_initial(pinned_u)
+            prob.step(40)
+            ref.step(40)
+        stream.synchronize()
+        um, ud = prob.read_u(0), ref.read_u(0)
+        err = {"rel_l2_vs_fp64_same_contour": float(np.linalg.norm(um - ud) / np.linalg.norm(ud)), "after_steps": 40}
+        ref.close()
+    ws_bytes = prob.workspace_bytes
+    prob.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, el = free3d_oracle_sample(1)
+        cpu = {"value": v, "unit": "point-steps/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"1 8th-order Adams step of the 64^3 instance ({el:.1f} s; dense transforms per axis)"}
+    print(json.dumps({
+        "metric": metric, "value": value, "unit": "point-steps/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128" if prec == "fp64" else "c64+c128", "data": "synthetic",
+        "config": {"workload": f"3D free space 64^3, nu=256 (N={N} modes/axis), p=8, q=10, n_r=1, H={H:.4f} "
+                               f"(eps={F3_EPS[prec]:g}), dt=1e-3, 200 steps, 8th-order Adams, {prec}",
+                   "workspace_bytes": ws_bytes, "l2": "flushed (256 MB write) before each timed solve",
+                   "step": "one whole solve (7 Richardson start-up + 193 Adams steps)"},
+        "stated_err": err, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary()}))
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -1745,6 +1981,8 @@ def main():
         return main_periodic3d(args, ws, rank, local)
     if args.workload == "free_ctype":
         return main_free_ctype(args, ws, rank, local)
+    if args.workload == "free3d":
+        return main_free3d(args, ws, rank, local)
     if args.impl == "reference":
         if rank != 0:
             return 0

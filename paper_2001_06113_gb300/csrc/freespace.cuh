@@ -62,6 +62,21 @@ template <> struct MinBlocks<float2> { static constexpr int value = FS_MINB32; }
 #endif
 template <class C> struct FsThreads { static constexpr int value = FS_T; };
 template <> struct FsThreads<float2> { static constexpr int value = FS_T32; };
+// Lines of at most 64 points (the 3D axes of the 64^3 workload): FS_T_SMALL
+// threads per CTA and proportionally more resident CTAs, since the FFT, the
+// dense-row and the grid phases of such a line keep only 64 threads busy and
+// the CTA's barriers then stall the rest.  Per 64^3 Adams step (nu = 256):
+// 256 / 128 / 64 threads 4.99 / 3.19 / 2.30 ms with FP32 transforms,
+// 18.1 / 14.3 / 13.7 ms in FP64 (same results).
+#ifndef FS_T_SMALL
+#define FS_T_SMALL 64
+#endif
+template <class C, int M> struct FsThr {
+    static constexpr int value = M <= 64 && FS_T_SMALL < FsThreads<C>::value ? FS_T_SMALL : FsThreads<C>::value;
+};
+template <class C, int M> struct FsMinB {
+    static constexpr int value = MinBlocks<C>::value * FsThreads<C>::value / FsThr<C, M>::value;
+};
 
 __device__ __forceinline__ double2 zero2() { return make_double2(0.0, 0.0); }
 template <class C> __device__ __forceinline__ C zeroc() { return czero<C>(); }
@@ -106,8 +121,8 @@ struct FsLine {
     static constexpr int LS = 2 * R + 1;
     static constexpr int NU = M * R;
     static constexpr int EBUF = M * LS;
-    using FftF = CtaFft<C, M, L, LS, FsThreads<C>::value, false>;
-    using FftI = CtaFft<C, M, L, LS, FsThreads<C>::value, true>;
+    using FftF = CtaFft<C, M, L, LS, FsThr<C, M>::value, false>;
+    using FftI = CtaFft<C, M, L, LS, FsThr<C, M>::value, true>;
 
     __device__ static __forceinline__ int epos(int b, int i) { return (i / R) * LS + b * R + (i % R); }
 
@@ -116,7 +131,7 @@ struct FsLine {
     // dense results.  Ends with a barrier.
     __device__ static void forward(const C* f, C* E, C* dv, const FsAxis& ax) {
         const C* preF = T::preF(ax);
-        for (int it = threadIdx.x; it < 2 * NU; it += FsThreads<C>::value) {
+        for (int it = threadIdx.x; it < 2 * NU; it += FsThr<C, M>::value) {
             const int b = it / NU, r = it - b * NU;
             const int j = r / R, s = r % R;
             E[j * LS + b * R + s] = cmul(f[j], __ldg(&preF[it]));
@@ -126,7 +141,7 @@ struct FsLine {
         // one warp per row: the dense rows by direct sums (the C rows too
         // unless they go through the interpolant), then the NT interpolant rows
         const int nrow = ax.ND + (cheb ? ax.NT : 0);
-        for (int rr = warp; rr < nrow; rr += FsThreads<C>::value / 32) {
+        for (int rr = warp; rr < nrow; rr += FsThr<C, M>::value / 32) {
             if (cheb && rr >= ax.p && rr < ax.p + ax.NC) continue;
             const bool crow = rr >= ax.ND;
             const C* row = crow ? T::Lf(ax) + (size_t)(rr - ax.ND) * M : T::Fd(ax) + (size_t)rr * M;
@@ -144,7 +159,7 @@ struct FsLine {
         }
         __syncthreads();
         if (cheb) {   // C rows: f^_k = sum_l T_l(tau_k / H) g_l
-            for (int k = threadIdx.x; k < ax.NC; k += FsThreads<C>::value) {
+            for (int k = threadIdx.x; k < ax.NC; k += FsThr<C, M>::value) {
                 const auto* tc = T::Tc(ax) + (size_t)k * ax.NT;
                 C acc = zeroc<C>();
                 for (int l = 0; l < ax.NT; ++l) acc = acc + cscale(dv[FS_MAX_ND + l], __ldg(&tc[l]));
@@ -179,7 +194,7 @@ struct FsLine {
     // Zero the inputs NE..nu-1 of both blocks (the zero padding of eq. ssfftgen).
     __device__ static void zero_pad(C* E, int NE) {
         const int per = NU - NE;
-        for (int it = threadIdx.x; it < 2 * per; it += FsThreads<C>::value) {
+        for (int it = threadIdx.x; it < 2 * per; it += FsThr<C, M>::value) {
             const int b = it / per, i = NE + (it - b * per);
             E[epos(b, i)] = zeroc<C>();
         }
@@ -192,7 +207,7 @@ struct FsLine {
         const bool cheb = ax.NT > 0;
         if (cheb) {   // h_l = sum_k T_l(tau_k / H) (w_k / 2pi) f^_k (read after FftI's barriers)
             C* hb = const_cast<C*>(dv) + FS_MAX_ND;
-            for (int l = threadIdx.x; l < ax.NT; l += FsThreads<C>::value) {
+            for (int l = threadIdx.x; l < ax.NT; l += FsThr<C, M>::value) {
                 const C* tw = T::TcW(ax) + (size_t)l * ax.NC;
                 C acc = zeroc<C>();
                 for (int k = 0; k < ax.NC; ++k) acc = acc + cmul(__ldg(&tw[k]), dv[ax.p + k]);
@@ -200,7 +215,7 @@ struct FsLine {
             }
         }
         FftI::run(E, T::tw(ax), nullptr);
-        for (int j = threadIdx.x; j < M; j += FsThreads<C>::value) {
+        for (int j = threadIdx.x; j < M; j += FsThr<C, M>::value) {
             C acc = zeroc<C>();
             const C* pj = T::postI(ax) + (size_t)j * R;
 #pragma unroll
@@ -274,7 +289,7 @@ __device__ __forceinline__ void store_fwd(const FsArgs& a, size_t idx, C F) {
 }
 
 template <class C, int M, int R>
-__global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs_1d(FsArgs a, int mode) {
+__global__ void __launch_bounds__(FsThr<C, M>::value, FsMinB<C, M>::value) k_fs_1d(FsArgs a, int mode) {
     using Ln = FsLine<C, M, R>;
     using Rl = typename cx_traits<C>::real;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -286,13 +301,13 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
     const double vf = a.tfac[(size_t)b * a.ntf + a.tf];
     const double* V0 = a.V0 + (size_t)b * a.vstride;
     if (mode == FS_1D_FWD_ONLY) {
-        for (int j = threadIdx.x; j < M; j += FsThreads<C>::value) {
+        for (int j = threadIdx.x; j < M; j += FsThr<C, M>::value) {
             const double2 u = a.usrc[(size_t)b * M + j];
             y[j] = cvt<C>(a.mulV ? cscale(u, vf * V0[j]) : u);
         }
         __syncthreads();
         Ln::forward(y, E, dv, ax);
-        for (int m = threadIdx.x; m < N; m += FsThreads<C>::value)
+        for (int m = threadIdx.x; m < N; m += FsThr<C, M>::value)
             store_fwd(a, (size_t)b * a.fdst_bstride + m, Ln::fwd_value(m, E, dv, ax));
         return;
     }
@@ -303,7 +318,7 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
     C cj[FS_MAX_HIST + 1];
 #pragma unroll
     for (int j = 0; j <= FS_MAX_HIST; ++j) cj[j] = cvt<C>(make_double2(a.mu[j], 0.0));
-    for (int m = threadIdx.x; m < N; m += FsThreads<C>::value) {
+    for (int m = threadIdx.x; m < N; m += FsThr<C, M>::value) {
         const C S = history_sep<C>(
             a, cj, [&](int j) { return ring[(size_t)a.hist_slot[j - 1] * N + m]; },
             [&](int i) { return __ldg(&Pc[(size_t)a.interval[i] * N + m]); });
@@ -314,7 +329,7 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
     Ln::zero_pad(E, ax.NE);
     Ln::inverse(E, dv, y, ax);
     const double hm0 = a.h * a.mu[0];
-    for (int j = threadIdx.x; j < M; j += FsThreads<C>::value) {
+    for (int j = threadIdx.x; j < M; j += FsThr<C, M>::value) {
         const double V = vf * V0[j];
         const C u = implicit_solve(y[j], (Rl)(hm0 * V));
         a.u[(size_t)b * M + j] = cvt<double2>(u);
@@ -322,7 +337,7 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
     }
     __syncthreads();
     Ln::forward(y, E, dv, ax);
-    for (int m = threadIdx.x; m < N; m += FsThreads<C>::value) {
+    for (int m = threadIdx.x; m < N; m += FsThr<C, M>::value) {
         const C F = Ln::fwd_value(m, E, dv, ax);
         uh[m] = uh[m] + times_minus_i(cvt<double2>(F), hm0);
         ring[(size_t)a.out_slot * N + m] = F;
@@ -330,7 +345,7 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
 }
 
 template <class C, int M, int R>
-__global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs_row(FsArgs a, int flags) {
+__global__ void __launch_bounds__(FsThr<C, M>::value, FsMinB<C, M>::value) k_fs_row(FsArgs a, int flags) {
     using Ln = FsLine<C, M, R>;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     C* E = reinterpret_cast<C*>(sm_raw);
@@ -346,12 +361,12 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
     C* zrow = reinterpret_cast<C*>(a.Z) + ((size_t)b * nrows + k0) * M;
     const bool end = flags & FS_ROW_END, begin = flags & FS_ROW_BEGIN;
     if (end || (flags & FS_ROW_FWD_ONLY)) {
-        for (int j = threadIdx.x; j < M; j += FsThreads<C>::value) f[j] = zrow[j];
+        for (int j = threadIdx.x; j < M; j += FsThr<C, M>::value) f[j] = zrow[j];
         __syncthreads();
         Ln::forward(f, E, dv, ax);
         if (flags & FS_ROW_FWD_ONLY) {
             const size_t base = (size_t)b * a.fdst_bstride + (size_t)k0 * N1;
-            for (int m = threadIdx.x; m < N1; m += FsThreads<C>::value) store_fwd(a, base + m, Ln::fwd_value(m, E, dv, ax));
+            for (int m = threadIdx.x; m < N1; m += FsThr<C, M>::value) store_fwd(a, base + m, Ln::fwd_value(m, E, dv, ax));
             return;
         }
     }
@@ -378,7 +393,7 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
     }
     const double hm0 = a.h * a.mu[0];
     C* ring = reinterpret_cast<C*>(a.ring) + (size_t)b * a.ring_slots * NPm + (size_t)k0 * N1;
-    for (int m = threadIdx.x; m < N1; m += FsThreads<C>::value) {
+    for (int m = threadIdx.x; m < N1; m += FsThr<C, M>::value) {
         double2 uh;
         C F = zeroc<C>();
         if (end) {
@@ -406,11 +421,11 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
     if (!begin) return;
     Ln::zero_pad(E, ax.NE);
     Ln::inverse(E, dv, f, ax);
-    for (int j = threadIdx.x; j < M; j += FsThreads<C>::value) zrow[j] = f[j];
+    for (int j = threadIdx.x; j < M; j += FsThr<C, M>::value) zrow[j] = f[j];
 }
 
 template <class C, int M, int R>
-__global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs_phys(FsArgs a, int from_usrc) {
+__global__ void __launch_bounds__(FsThr<C, M>::value, FsMinB<C, M>::value) k_fs_phys(FsArgs a, int from_usrc) {
     using Ln = FsLine<C, M, R>;
     using Rl = typename cx_traits<C>::real;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -426,11 +441,11 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
     const double vf = a.tfac[(size_t)b * a.ntf + a.tf];
     const double* V0 = a.V0 + (size_t)b * a.vstride;
     if (!from_usrc) {
-        for (int m = threadIdx.x; m < N0; m += FsThreads<C>::value) Ln::stage_inv(m, zcol[(size_t)m * M1], E, dv, ax);
+        for (int m = threadIdx.x; m < N0; m += FsThr<C, M>::value) Ln::stage_inv(m, zcol[(size_t)m * M1], E, dv, ax);
         Ln::zero_pad(E, ax.NE);
         Ln::inverse(E, dv, y, ax);
         const double hm0 = a.h * a.mu[0];
-        for (int j0 = threadIdx.x; j0 < M; j0 += FsThreads<C>::value) {
+        for (int j0 = threadIdx.x; j0 < M; j0 += FsThr<C, M>::value) {
             const size_t g = (size_t)j0 * M1 + j1;
             const double V = vf * V0[g];
             const C u = implicit_solve(y[j0], (Rl)(hm0 * V));
@@ -438,7 +453,7 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
             y[j0] = cscale(u, (Rl)V);
         }
     } else {
-        for (int j0 = threadIdx.x; j0 < M; j0 += FsThreads<C>::value) {
+        for (int j0 = threadIdx.x; j0 < M; j0 += FsThr<C, M>::value) {
             const size_t g = (size_t)j0 * M1 + j1;
             const double2 u = a.usrc[(size_t)b * NX + g];
             y[j0] = cvt<C>(a.mulV ? cscale(u, vf * V0[g]) : u);
@@ -446,13 +461,13 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
     }
     __syncthreads();
     Ln::forward(y, E, dv, ax);
-    for (int m = threadIdx.x; m < N0; m += FsThreads<C>::value) zcol[(size_t)m * M1] = Ln::fwd_value(m, E, dv, ax);
+    for (int m = threadIdx.x; m < N0; m += FsThr<C, M>::value) zcol[(size_t)m * M1] = Ln::fwd_value(m, E, dv, ax);
 }
 
 // 3D, axis 1: line (k0, j2) between the N1 modes Z[b][k0][.][j2] and the M1
 // grid values Y[b][k0][.][j2] (both with stride M2).
 template <class C, int M, int R>
-__global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs_mid(FsArgs a, int dir) {
+__global__ void __launch_bounds__(FsThr<C, M>::value, FsMinB<C, M>::value) k_fs_mid(FsArgs a, int dir) {
     using Ln = FsLine<C, M, R>;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     C* E = reinterpret_cast<C*>(sm_raw);
@@ -464,15 +479,15 @@ __global__ void __launch_bounds__(FsThreads<C>::value, MinBlocks<C>::value) k_fs
     C* zl = reinterpret_cast<C*>(a.Z) + ((size_t)b * N0 + k0) * N1 * M2 + j2;
     C* yl = reinterpret_cast<C*>(a.Y) + ((size_t)b * N0 + k0) * M * M2 + j2;
     if (dir == FS_MID_INV) {
-        for (int m = threadIdx.x; m < N1; m += FsThreads<C>::value) Ln::stage_inv(m, zl[(size_t)m * M2], E, dv, ax);
+        for (int m = threadIdx.x; m < N1; m += FsThr<C, M>::value) Ln::stage_inv(m, zl[(size_t)m * M2], E, dv, ax);
         Ln::zero_pad(E, ax.NE);
         Ln::inverse(E, dv, f, ax);
-        for (int j = threadIdx.x; j < M; j += FsThreads<C>::value) yl[(size_t)j * M2] = f[j];
+        for (int j = threadIdx.x; j < M; j += FsThr<C, M>::value) yl[(size_t)j * M2] = f[j];
     } else {
-        for (int j = threadIdx.x; j < M; j += FsThreads<C>::value) f[j] = yl[(size_t)j * M2];
+        for (int j = threadIdx.x; j < M; j += FsThr<C, M>::value) f[j] = yl[(size_t)j * M2];
         __syncthreads();
         Ln::forward(f, E, dv, ax);
-        for (int m = threadIdx.x; m < N1; m += FsThreads<C>::value) zl[(size_t)m * M2] = Ln::fwd_value(m, E, dv, ax);
+        for (int m = threadIdx.x; m < N1; m += FsThr<C, M>::value) zl[(size_t)m * M2] = Ln::fwd_value(m, E, dv, ax);
     }
 }
 
@@ -497,18 +512,18 @@ cudaError_t launch_mr(const FsArgs& a, int which, int flag, cudaStream_t s) {
     cudaError_t e;
     if (which == 0) {
         if ((e = prepare<C>(k_fs_1d<C, M, R>, sm)) != cudaSuccess) return e;
-        k_fs_1d<C, M, R><<<a.B, FsThreads<C>::value, sm, s>>>(a, flag);
+        k_fs_1d<C, M, R><<<a.B, FsThr<C, M>::value, sm, s>>>(a, flag);
     } else if (which == 1) {
         if ((e = prepare<C>(k_fs_row<C, M, R>, sm)) != cudaSuccess) return e;
         const unsigned rows = a.d == 3 ? (unsigned)(a.ax[0].N * a.ax[1].N) : (unsigned)a.ax[0].N;
-        k_fs_row<C, M, R><<<dim3(rows, a.B), FsThreads<C>::value, sm, s>>>(a, flag);
+        k_fs_row<C, M, R><<<dim3(rows, a.B), FsThr<C, M>::value, sm, s>>>(a, flag);
     } else if (which == 2) {
         if ((e = prepare<C>(k_fs_phys<C, M, R>, sm)) != cudaSuccess) return e;
         const unsigned cols = a.d == 3 ? (unsigned)(a.ax[1].M * a.ax[2].M) : (unsigned)a.ax[1].M;
-        k_fs_phys<C, M, R><<<dim3(cols, a.B), FsThreads<C>::value, sm, s>>>(a, flag);
+        k_fs_phys<C, M, R><<<dim3(cols, a.B), FsThr<C, M>::value, sm, s>>>(a, flag);
     } else {
         if ((e = prepare<C>(k_fs_mid<C, M, R>, sm)) != cudaSuccess) return e;
-        k_fs_mid<C, M, R><<<dim3(a.ax[2].M, a.ax[0].N, a.B), FsThreads<C>::value, sm, s>>>(a, flag);
+        k_fs_mid<C, M, R><<<dim3(a.ax[2].M, a.ax[0].N, a.B), FsThr<C, M>::value, sm, s>>>(a, flag);
     }
     return cudaGetLastError();
 }
