@@ -366,6 +366,18 @@ tdse_status tdse_set_step_path(tdse_ctx* ctx, int path);
  * create the streams; take them before any stream capture. */
 tdse_status tdse_set_step_groups(tdse_ctx* ctx, int groups);
 
+/* 1D periodic TDSE_MIXED contexts of n <= 16384 (one CTA per instance):
+ * launch shape of the step kernel.  Shape 0 (default): n/8 threads per
+ * instance (32..1024); shape 1: half of them, each thread taking twice the
+ * points of every transform pass (built for n >= 512).  The transform's
+ * butterflies and the step's arithmetic are the same in both (Sec. 2.1-2.2),
+ * so the results are the same bits; tdse_batch_tune sets the faster shape
+ * per member.  Errors: TDSE_EUNSUPPORTED for another context or where shape 1
+ * is not built (the shape stays), TDSE_EINVAL for another value.
+ * tdse_shape_1d returns the current shape (-1 for a null context). */
+tdse_status tdse_set_shape_1d(tdse_ctx* ctx, int shape);
+int tdse_shape_1d(const tdse_ctx* ctx);
+
 /* The path the next 2D mixed Adams steps take (TDSE_PATH_PASSES or
  * TDSE_PATH_CLUSTER; TDSE_PATH_PASSES for every other context), or -1 for
  * NULL.  The cluster path needs the bound workspace (its plan is made at
@@ -443,10 +455,13 @@ tdse_status tdse_batch_create(tdse_ctx* const* members, int count, tdse_batch** 
  * results either way.  Cached graphs are dropped.  TDSE_EINVAL otherwise. */
 tdse_status tdse_batch_set_mode(tdse_batch* b, int mode);
 
-/* Autotuner: choose the instances per work item of each member (all that fit
- * the CTA, a half or a quarter) and the CTA count by timing `trial_steps`
- * launches of each candidate on `stream`, then the faster of that fused launch
- * and the per-member streams (tdse_batch_set_mode).  The members must have V and u0 set; tuning runs their start
+/* Autotuner: choose, by timing `trial_steps` launches of each candidate on
+ * `stream`, for the fused launch the launch shape of each member (threads per
+ * instance among the variants built for its n: n/8, or half of that for
+ * n = 2048, 4096, 8192), its instances per work item (all that fit the CTA, a
+ * half or a quarter) and the CTA count; for the per-member streams each
+ * member's kernel shape (tdse_set_shape_1d); then the faster of the two
+ * modes (tdse_batch_set_mode).  The members must have V and u0 set; tuning runs their start
  * if needed and leaves their state undefined: call tdse_set_initial on every
  * member before the next tdse_batch_step.  Cached graphs are dropped. */
 tdse_status tdse_batch_tune(tdse_batch* b, int trial_steps, void* stream);

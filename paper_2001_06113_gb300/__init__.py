@@ -332,6 +332,15 @@ class Problem:
         parallel streams (same results; default 4)."""
         _check(self._lib.tdse_set_step_groups(self._ctx, int(groups)), self._ctx)
 
+    def set_shape_1d(self, shape: int):
+        """1D mixed contexts: launch shape of the step kernel (0: n/8 threads per
+        instance; 1: half of them, n >= 512).  Same results."""
+        _check(self._lib.tdse_set_shape_1d(self._ctx, int(shape)), self._ctx)
+
+    @property
+    def shape_1d(self) -> int:
+        return int(self._lib.tdse_shape_1d(self._ctx))
+
     def describe_steps(self) -> dict:
         """Launch shape of the 2D mixed Adams steps (path, clusters, ...)."""
         import json

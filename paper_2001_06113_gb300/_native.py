@@ -30,6 +30,7 @@ EXPORTS = [
     "tdse_free_choose_H", "tdse_free_choose_H_prec", "tdse_potential_times", "tdse_set_potential_table", "tdse_batch_create", "tdse_batch_tune", "tdse_batch_set_mode", "tdse_batch_step", "tdse_batch_describe",
     "tdse_batch_last_error", "tdse_batch_destroy", "tdse_set_residual_check", "tdse_residual_report",
     "tdse_save", "tdse_load", "tdse_set_step_path", "tdse_step_path", "tdse_describe_steps", "tdse_set_step_groups", "tdse_free_cheb_terms",
+    "tdse_set_shape_1d", "tdse_shape_1d",
 ]
 NOALLOC_MAX_POINTS = 524288
 
@@ -111,6 +112,8 @@ def load(path: str = _LIB_PATH) -> ctypes.CDLL:
         "tdse_step_path": ([vp], ip),
         "tdse_describe_steps": ([vp, ctypes.c_char_p, ctypes.c_size_t], ip),
         "tdse_set_step_groups": ([vp, ip], ip),
+        "tdse_set_shape_1d": ([vp, ip], ip),
+        "tdse_shape_1d": ([vp], ip),
         "tdse_free_cheb_terms": ([vp, ip], ip),
     }
     for name, (args, res) in sig.items():

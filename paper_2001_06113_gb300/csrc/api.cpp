@@ -218,6 +218,7 @@ static KArgs base_args(const tdse_ctx* c) {
     a.tn0 = c->n0;
     a.tn1 = c->d >= 2 ? c->n1 : 1;
     a.tn2 = c->d == 3 ? c->n2 : 0;
+    a.shape1d = c->shape1d;
     a.uhat = c->P<void>(c->off.uhat);
     a.ring = c->P<void>(c->off.ring);
     a.ring_slots = c->RS;
@@ -1445,6 +1446,17 @@ static tdse_status batch_check(tdse_batch* b, int nsteps) {
 
 extern "C" {
 
+tdse_status tdse_set_shape_1d(tdse_ctx* c, int shape) {
+    if (!c) return TDSE_EINVAL;
+    if (shape != 0 && shape != 1) return c->fail(TDSE_EINVAL, "shape must be 0 or 1");
+    if (c->fs || c->d != 1 || !c->mixed || c->four1d || periodic1d_f32_threads(c->n0, shape) == 0)
+        return c->fail(TDSE_EUNSUPPORTED, "launch shapes: 1D periodic TDSE_MIXED, shape 1 for n >= 512");
+    c->shape1d = shape;
+    return TDSE_OK;
+}
+
+int tdse_shape_1d(const tdse_ctx* c) { return c ? c->shape1d : -1; }
+
 tdse_status tdse_batch_create(tdse_ctx* const* members, int count, tdse_batch** out) {
     if (!members || !out || count < 1) return TDSE_EINVAL;
     *out = nullptr;
@@ -1608,6 +1620,29 @@ tdse_status tdse_batch_tune(tdse_batch* b, int trial_steps, void* stream) {
         b->grid = default_grid(b);
         st = timed(best);
     }
+    // launch shape per member: threads per instance (the FFT's points per
+    // thread) among the variants built for its n, the default N / 8 first
+    for (size_t g = 0; g < b->m.size() && st == TDSE_OK; ++g) {
+        for (int v = 0; v < MULTI_NVAR && st == TDSE_OK; ++v) {
+            if (multi_variant_n(v) != b->m[g]->n0 || v == b->var[g]) continue;
+            const int keep_v = b->var[g], keep_p = b->per[g], keep_grid = b->grid;
+            b->var[g] = v;
+            b->per[g] = MULTI_CTA / multi_variant_t(v);
+            st = build_items(b);
+            if (st != TDSE_OK) break;
+            b->grid = default_grid(b);
+            float ms = 0;
+            st = timed(ms);
+            if (st != TDSE_OK) break;
+            if (ms < best) {
+                best = ms;
+            } else {
+                b->var[g] = keep_v;
+                b->per[g] = keep_p;
+                b->grid = keep_grid;
+            }
+        }
+    }
     // instances per work item, member by member (fewer: more, smaller items)
     for (size_t g = 0; g < b->m.size() && st == TDSE_OK; ++g) {
         const int full = MULTI_CTA / multi_variant_t(b->var[g]);
@@ -1669,6 +1704,16 @@ tdse_status tdse_batch_tune(tdse_batch* b, int trial_steps, void* stream) {
         };
         float ms = 0;
         st = timed_streams(ms);
+        // the same choice of launch shape for each member's own kernel
+        for (size_t g = 0; g < b->m.size() && st == TDSE_OK; ++g) {
+            tdse_ctx* c = b->m[g];
+            if (periodic1d_f32_threads(c->n0, 1 - c->shape1d) == 0) continue;
+            c->shape1d = 1 - c->shape1d;
+            float ms2 = 0;
+            st = timed_streams(ms2);
+            if (st == TDSE_OK && ms2 < ms) ms = ms2;
+            else c->shape1d = 1 - c->shape1d;
+        }
         b->stream_ms = ms / trial_steps;
         b->fused_ms = best / trial_steps;
         if (st == TDSE_OK && ms < best) b->mode = 1;
@@ -1698,7 +1743,8 @@ tdse_status tdse_batch_describe(const tdse_batch* b, char* buf, size_t len) {
         const int t = multi_variant_t(b->var[g]);
         js += std::string(g ? ", " : "") + "{\"n\": " + std::to_string(b->m[g]->n0) + ", \"batch\": " +
               std::to_string(b->m[g]->B) + ", \"threads\": " + std::to_string(t) + ", \"per_item\": " +
-              std::to_string(b->per[g]) + "}";
+              std::to_string(b->per[g]) + ", \"stream_threads\": " +
+              std::to_string(periodic1d_f32_threads(b->m[g]->n0, b->m[g]->shape1d)) + "}";
     }
     js += "]}";
     if (js.size() + 1 > len) return TDSE_EINVAL;

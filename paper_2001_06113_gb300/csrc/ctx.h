@@ -56,6 +56,7 @@ struct tdse_ctx {
     // 1D grids beyond one CTA: N = n0 points through the 2D passes as fs0 x fs1
     // (four-step transform, grid stored transposed in the workspace)
     bool four1d = false;
+    int shape1d = 0;            // 1D FP32 steps: launch shape chosen by the batch tuner (KArgs::shape1d)
     int fs0 = 0, fs1 = 0;
     size_t NP = 0;
     int B = 1, m = 8, L = 4, S = 7, S_eff = 7, RS = 7, ntf = 0, n_int = 0, n_int_startup = 0, nhi = 1;

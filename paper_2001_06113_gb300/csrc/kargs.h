@@ -37,6 +37,8 @@ struct KArgs {
     // twiddle e^{-+2 pi i r c / N} between its transform and the column pass's.
     // tn0 = N and the 1D phase tables apply to the flattened mode index.
     int flat1d;
+    int shape1d;              // 1D one-CTA-per-instance kernels: 1 = the alternative launch shape
+                              // (half the threads per instance, twice the points per thread)
     const double2* tw1d64;    // e^{-2 pi i m / N}, m < N
     const float2* tw1d32;
     // ---- step description
@@ -119,6 +121,9 @@ bool periodic1d_supported(int n);
 bool periodic2d_supported(int n0, int n1);
 // One-time kernel attributes of the 1D step for n and combo (before stream capture).
 cudaError_t periodic1d_prepare(int n, int combo);
+// Threads per instance of the FP32 one-CTA-per-instance 1D kernel of n in
+// launch shape `shape` (0 default, 1 alternative); 0 if that shape is not built.
+int periodic1d_f32_threads(int n, int shape);
 
 // ---- uneven 1D batches: one persistent launch for many contexts (mixed steps)
 // A CTA of MULTI_CTA threads takes the next item from a global counter; an
@@ -139,7 +144,7 @@ struct MultiArgs1D {
     KArgs args[MULTI_MAX_GROUPS];
     MultiItem items[MULTI_MAX_ITEMS];
 };
-constexpr int MULTI_NVAR = 12;
+constexpr int MULTI_NVAR = 15;
 int multi_variant_n(int var);
 int multi_variant_t(int var);
 int multi_variant(int n, int t);            // -1 if not built

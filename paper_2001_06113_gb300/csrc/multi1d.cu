@@ -9,8 +9,12 @@ namespace {
 struct Variant {
     int n, t;
 };
-constexpr Variant kVariants[MULTI_NVAR] = {{256, 32},  {512, 64},  {1024, 128}, {2048, 256}, {4096, 512}, {8192, 512},
-                                           {16384, 512}, {128, 32}, {64, 32},    {32, 32},    {16, 32},    {8, 32}};
+// Variants 0..11: the default threads per instance (N / 8, 32..512); 12..14:
+// half of it (twice the points per thread), a launch shape the batch tuner
+// may pick per member.
+constexpr Variant kVariants[MULTI_NVAR] = {{256, 32},  {512, 64},  {1024, 128}, {2048, 256}, {4096, 512},
+                                           {8192, 512}, {16384, 512}, {128, 32}, {64, 32},    {32, 32},
+                                           {16, 32},   {8, 32},    {2048, 128}, {4096, 256}, {8192, 256}};
 
 // `count` instances b0.. of one context, each by a group of T threads with
 // its own N-element slice of shared memory.  Each variant is a separate
@@ -52,6 +56,9 @@ __global__ void __launch_bounds__(MULTI_CTA, 1) k_periodic1d_multi(const __grid_
             case 9: run_group<32, 32>(a, it.b0, it.count, smem); break;
             case 10: run_group<16, 32>(a, it.b0, it.count, smem); break;
             case 11: run_group<8, 32>(a, it.b0, it.count, smem); break;
+            case 12: run_group<2048, 128>(a, it.b0, it.count, smem); break;
+            case 13: run_group<4096, 256>(a, it.b0, it.count, smem); break;
+            case 14: run_group<8192, 256>(a, it.b0, it.count, smem); break;
             default: break;
         }
         __syncthreads();   // shared memory and `take` free for the next item

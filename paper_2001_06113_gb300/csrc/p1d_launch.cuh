@@ -30,36 +30,55 @@ constexpr int p1d_min_blocks() {
     return b < 1 ? 1 : (b > 32 ? 32 : b);
 }
 
-template <class C, class RT, int N>
-__global__ void __launch_bounds__(threads_1d(N), p1d_min_blocks<C, N, threads_1d(N)>()) k_periodic1d(const KArgs a) {
+// Threads per instance of the alternative launch shape the batch tuner may
+// pick (KArgs::shape1d = 1): half the default, so twice the points per
+// thread (0: none built for this n).
+constexpr int alt_threads_1d(int N) { return N >= 512 && threads_1d(N) / 2 >= 32 ? threads_1d(N) / 2 : 0; }
+
+template <class C, class RT, int N, int T = threads_1d(N)>
+__global__ void __launch_bounds__(T, p1d_min_blocks<C, N, T>()) k_periodic1d(const KArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    step1d<C, RT, N, threads_1d(N)>(a, blockIdx.x, threadIdx.x, CtaSync{}, reinterpret_cast<C*>(smem_raw));
+    step1d<C, RT, N, T>(a, blockIdx.x, threadIdx.x, CtaSync{}, reinterpret_cast<C*>(smem_raw));
 }
 
 // One-time kernel attributes (shared memory above 48 KB); done before the
 // first launch and, for stream capture, by periodic1d_prepare beforehand.
-template <class C, class RT, int N>
+template <class C, class RT, int N, int T = threads_1d(N)>
 static cudaError_t prepare_n() {
     static bool configured = false;
     if (configured) return cudaSuccess;
     const size_t smem = (size_t)N * sizeof(C);
-    cudaError_t e = cudaFuncSetAttribute(k_periodic1d<C, RT, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_periodic1d<C, RT, N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_periodic1d<C, RT, N>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(k_periodic1d<C, RT, N, T>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
     if (e == cudaSuccess) configured = true;
     return e;
 }
 
-template <class C, class RT, int N>
+template <class C, class RT, int N, int T = threads_1d(N)>
 static cudaError_t launch_n(const KArgs& a, cudaStream_t s) {
-    constexpr int T = threads_1d(N);
     const size_t smem = (size_t)N * sizeof(C);
-    cudaError_t e = prepare_n<C, RT, N>();
+    cudaError_t e = prepare_n<C, RT, N, T>();
     if (e != cudaSuccess) return e;
-    k_periodic1d<C, RT, N><<<a.B, T, smem, s>>>(a);
+    k_periodic1d<C, RT, N, T><<<a.B, T, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// The default launch shape, or the alternative one where built and selected.
+template <class C, class RT, int N>
+static cudaError_t launch_shape(const KArgs& a, cudaStream_t s) {
+    if constexpr (alt_threads_1d(N) > 0)
+        if (a.shape1d) return launch_n<C, RT, N, alt_threads_1d(N)>(a, s);
+    return launch_n<C, RT, N>(a, s);
+}
+template <class C, class RT, int N>
+static cudaError_t prepare_shapes() {
+    cudaError_t e = prepare_n<C, RT, N>();
+    if constexpr (alt_threads_1d(N) > 0)
+        if (e == cudaSuccess) e = prepare_n<C, RT, N, alt_threads_1d(N)>();
+    return e;
 }
 
 }  // namespace tdse

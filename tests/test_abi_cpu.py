@@ -116,6 +116,26 @@ def test_create_validates(native, kw, status):
         lib.tdse_destroy(ctx)
 
 
+def test_shape_1d_validation(native):
+    """The alternative 1D launch shape exists for mixed 1D contexts of n >= 512
+    (one CTA per instance) and nowhere else; no CUDA call is made."""
+    lib = native.lib()
+    # (config, status of shape 1, status of shape 0)
+    cases = [(dict(n=(512, 1), precision=1), 0, 0), (dict(n=(16384, 1), precision=1), 0, 0),
+             (dict(n=(256, 1), precision=1), -7, 0), (dict(n=(512, 1)), -7, -7),
+             (dict(n=(32768, 1), precision=1), -7, -7), (dict(dim=2, n=(64, 64), precision=1), -7, -7)]
+    for kw, want, want0 in cases:
+        ctx = ctypes.c_void_p()
+        assert lib.tdse_create(ctypes.byref(_cfg(native, **kw)), ctypes.byref(ctx)) == 0
+        assert lib.tdse_shape_1d(ctx) == 0
+        assert lib.tdse_set_shape_1d(ctx, 1) == want, kw
+        assert lib.tdse_shape_1d(ctx) == (1 if want == 0 else 0)
+        assert lib.tdse_set_shape_1d(ctx, 2) == -1
+        assert lib.tdse_set_shape_1d(ctx, 0) == want0
+        lib.tdse_destroy(ctx)
+    assert lib.tdse_shape_1d(None) == -1
+
+
 def test_workspace_size_scales_with_batch(native):
     lib = native.lib()
     sizes = []

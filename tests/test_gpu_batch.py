@@ -207,6 +207,24 @@ def test_batch_modes_give_the_same_bits(mode):
             solo.close()
 
 
+@pytest.mark.parametrize("n", [512, 2048, 8192, 16384])
+def test_launch_shapes_give_the_same_bits(n):
+    """The alternative launch shape of the one-CTA-per-instance kernel (half
+    the threads, twice the points per thread of every transform pass) gives
+    the bits of the default shape, through the start-up and the Adams steps."""
+    data = members_data([(n, 2)], seed=13)
+    insts = data[n]
+    out = []
+    for shape in (0, 1):
+        pr = make_problem(insts)
+        pr.set_shape_1d(shape)
+        assert pr.shape_1d == shape
+        pr.step(NSTEPS - 5)
+        out.append(pr.read_u())
+        pr.close()
+    assert np.array_equal(out[0], out[1])
+
+
 def test_set_initial_batch_equals_per_instance():
     """One copy of all instances' u0 gives the bits of per-instance uploads
     (periodic and free space)."""
