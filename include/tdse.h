@@ -68,6 +68,7 @@ enum { TDSE_V_SEPARABLE = 0, TDSE_V_TABLE = 1, TDSE_V_TABLE_SHARED = 2 };
 enum { TDSE_BATCH_FUSED = 0, TDSE_BATCH_STREAMS = 1 };
 enum { TDSE_PATH_AUTO = 0, TDSE_PATH_PASSES = 1, TDSE_PATH_CLUSTER = 2 };
 enum { TDSE_CT_AUTO = 0, TDSE_CT_DIRECT = 1, TDSE_CT_CHEBYSHEV = 2 };
+enum { TDSE_LAYOUT_AUTO = 0, TDSE_LAYOUT_CTA = 1, TDSE_LAYOUT_PASSES = 2 };
 
 /*
  * Problem configuration.
@@ -153,6 +154,15 @@ typedef struct {
     int c_transform;
     /* free space, dim = 3: nu of axis 2 (as nu[2] above).  Appended last. */
     int nu_z;
+    /* periodic dim = 1: how a step transforms an instance.  TDSE_LAYOUT_CTA:
+     * one CTA per instance, the whole n-point FFT in its shared memory (n up
+     * to 8192 in TDSE_FP64, 16384 in TDSE_MIXED).  TDSE_LAYOUT_PASSES: the
+     * four-step form of the same DFT (n = n0 n1, the 2D row and column pass
+     * kernels with the twiddle between them, the grid stored transposed in
+     * the workspace), so an instance spreads over many CTAs; n = 64..2^20.
+     * TDSE_LAYOUT_AUTO (0): one CTA where it is built, the passes beyond.
+     * Appended last. */
+    int layout_1d;
 } tdse_config;
 
 /* Vector potential callback: writes A(t) (dim components) to A_out. */
@@ -384,9 +394,11 @@ int tdse_shape_1d(const tdse_ctx* ctx);
  * tdse_bind_workspace). */
 int tdse_step_path(const tdse_ctx* ctx);
 
-/* The launch shape of the 2D mixed Adams steps as a JSON object ("path",
- * and for the cluster path "clusters" resident at once, "ctas_per_cluster",
- * "threads", "smem_bytes") into buf (len bytes, NUL-terminated).
+/* The launch shape of the Adams steps as a JSON object into buf (len bytes,
+ * NUL-terminated): "path" = "passes" (2D/3D pass kernels, 1D in the
+ * four-step layout: "groups", and "four_step" = [n0, n1] for 1D), "cluster"
+ * ("clusters" resident at once, "ctas_per_cluster", "threads",
+ * "smem_bytes") or "cta" (1D, one CTA per instance: "shape", "threads").
  * TDSE_EINVAL for NULL arguments or a buffer too small. */
 tdse_status tdse_describe_steps(const tdse_ctx* ctx, char* buf, size_t len);
 
@@ -426,12 +438,14 @@ tdse_status tdse_modes_to_grid_2d_noalloc(const double* uhat, double* u, int n0,
 
 /*
  * Uneven batches (1D periodic, TDSE_MIXED).  Several contexts, each with its
- * own n (8..16384) and its own batch of instances, but identical dt, nsteps,
+ * own n and its own batch of instances, but identical dt, nsteps,
  * order and startup_steps, are stepped together:
  *   - every Adams step of all of them is ONE persistent launch: a CTA of 512
  *     threads takes work items, an item being `count` instances of one
  *     context side by side, each transformed by a group of T threads (T and
- *     the CTA count are the launch shape);
+ *     the CTA count are the launch shape); members created with
+ *     TDSE_LAYOUT_PASSES (or beyond n = 16384) instead run their four-step
+ *     pass chain on their own stream beside that launch;
  *   - the start (init, Richardson start-up, change of frame) of each member
  *     runs with the member's own kernels;
  *   - with a capturable stream (not the legacy NULL stream) the whole launch

@@ -47,9 +47,10 @@ def free_choose_H(eps: float, vnorm: float, phimax: float, dim: int, precision: 
 
 
 def _config(shape, dt, nsteps, order, batch, precision, startup_steps, bc, nu, H, alpert_p, gauss_q, n_r,
-            potential="separable", c_transform="auto"):
+            potential="separable", c_transform="auto", layout_1d="auto"):
     cfg = _native.TdseConfig()
     cfg.c_transform = {"auto": 0, "direct": 1, "chebyshev": 2}[c_transform]
+    cfg.layout_1d = {"auto": 0, "cta": 1, "passes": 2}[layout_1d]
     cfg.potential = {"separable": _native.TDSE_V_SEPARABLE, "table": _native.TDSE_V_TABLE,
                      "shared_table": _native.TDSE_V_TABLE_SHARED}[potential]
     cfg.dim = len(shape)
@@ -107,7 +108,9 @@ class Problem:
     ``batch``; ``precision`` ("fp64" or "mixed"); ``startup_steps`` (-1 =
     order-1); ``bc`` ("periodic" or "free").  Free space also takes ``nu``
     (FFT length per dimension), ``H`` (contour offset), ``alpert_p``,
-    ``gauss_q`` and ``n_r``.  ``potential``: "separable" (V = f(t) V0(x),
+    ``gauss_q`` and ``n_r``.  ``layout_1d`` (1D periodic): "cta" (one CTA per
+    instance), "passes" (the four-step form through the 2D pass kernels) or
+    "auto" (one CTA where built).  ``potential``: "separable" (V = f(t) V0(x),
     ``set_potential``), "table" (general V(x, t) per instance, given at
     ``potential_times()``, ``set_potential_table`` / ``set_potential_fn``) or
     "shared_table" (one such table for every instance, instance = -1).
@@ -117,7 +120,7 @@ class Problem:
     def __init__(self, shape: Sequence[int], dt: float, nsteps: int, order: int = 8, batch: int = 1,
                  precision: str = "fp64", startup_steps: int = -1, device=None, stream=None, bc: str = "periodic",
                  nu: Optional[Sequence[int]] = None, H: float = 0.0, alpert_p: int = 8, gauss_q: int = 10,
-                 n_r: int = 1, potential: str = "separable", c_transform: str = "auto"):
+                 n_r: int = 1, potential: str = "separable", c_transform: str = "auto", layout_1d: str = "auto"):
         import torch
         self._lib = _native.lib()
         self.shape = tuple(int(s) for s in shape)
@@ -128,7 +131,7 @@ class Problem:
         self.precision = precision
         self.potential = potential
         cfg = _config(self.shape, dt, nsteps, order, batch, precision, startup_steps, bc, nu, H, alpert_p, gauss_q,
-                      n_r, potential, c_transform)
+                      n_r, potential, c_transform, layout_1d)
         self._ctx = ctypes.c_void_p()
         _check(self._lib.tdse_create(ctypes.byref(cfg), ctypes.byref(self._ctx)))
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
@@ -145,11 +148,12 @@ class Problem:
     def workspace_bytes_for(shape: Sequence[int], dt: float, nsteps: int, order: int = 8, batch: int = 1,
                             precision: str = "fp64", startup_steps: int = -1, bc: str = "periodic",
                             nu: Optional[Sequence[int]] = None, H: float = 0.0, alpert_p: int = 8, gauss_q: int = 10,
-                            n_r: int = 1, potential: str = "separable", c_transform: str = "auto") -> int:
+                            n_r: int = 1, potential: str = "separable", c_transform: str = "auto",
+                            layout_1d: str = "auto") -> int:
         """Device workspace a Problem of this configuration needs (host-only query)."""
         lib = _native.lib()
         cfg = _config(tuple(int(s) for s in shape), dt, nsteps, order, batch, precision, startup_steps, bc, nu, H,
-                      alpert_p, gauss_q, n_r, potential, c_transform)
+                      alpert_p, gauss_q, n_r, potential, c_transform, layout_1d)
         ctx = ctypes.c_void_p()
         _check(lib.tdse_create(ctypes.byref(cfg), ctypes.byref(ctx)))
         n = int(lib.tdse_workspace_bytes(ctx))

@@ -55,6 +55,7 @@ class TdseConfig(ctypes.Structure):
         ("n_z", ctypes.c_int),
         ("c_transform", ctypes.c_int),
         ("nu_z", ctypes.c_int),
+        ("layout_1d", ctypes.c_int),
     ]
 
 

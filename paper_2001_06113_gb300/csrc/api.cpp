@@ -350,10 +350,13 @@ tdse_status tdse_create(const tdse_config* cfg, tdse_ctx** out) {
     const int n0 = cfg->n[0], n1 = cfg->dim >= 2 ? cfg->n[1] : 1, n2 = cfg->dim == 3 ? cfg->n_z : 1;
     if (!is_pow2(n0) || (cfg->dim >= 2 && !is_pow2(n1)) || (cfg->dim == 3 && !is_pow2(n2))) return TDSE_EINVAL;
     if (cfg->dim == 3 && !fs && !periodic3d_supported(n0, n1, n2)) return TDSE_EUNSUPPORTED;
+    if (cfg->layout_1d < TDSE_LAYOUT_AUTO || cfg->layout_1d > TDSE_LAYOUT_PASSES) return TDSE_EINVAL;
     const bool big1d = !fs && cfg->dim == 1 && cfg->precision == TDSE_MIXED && n0 == four_step_n();
-    // larger 1D grids: the four-step transform through the 2D passes, up to 2^20 points
-    const bool four1d = !fs && cfg->dim == 1 && !periodic1d_supported(n0) && !big1d && n0 >= 64 && n0 <= (1 << 20);
-    if (!fs && cfg->dim == 1 && !periodic1d_supported(n0) && !big1d && !four1d) return TDSE_EUNSUPPORTED;
+    const bool cta1d = periodic1d_supported(n0) || big1d;   // one CTA per instance is built
+    // the four-step transform through the 2D passes (larger 1D grids, or by choice), 64..2^20 points
+    const bool four1d = !fs && cfg->dim == 1 && n0 >= 64 && n0 <= (1 << 20) &&
+                        (cfg->layout_1d == TDSE_LAYOUT_PASSES || (cfg->layout_1d == TDSE_LAYOUT_AUTO && !cta1d));
+    if (!fs && cfg->dim == 1 && !four1d && !(cta1d && cfg->layout_1d != TDSE_LAYOUT_PASSES)) return TDSE_EUNSUPPORTED;
     if (!fs && cfg->dim == 2 && !periodic2d_supported(n0, n1)) return TDSE_EUNSUPPORTED;
     if ((long long)cfg->nsteps * SUB + 1 > (1LL << 30)) return TDSE_EINVAL;
     if (cfg->potential != TDSE_V_SEPARABLE && cfg->potential != TDSE_V_TABLE &&
@@ -1256,9 +1259,15 @@ tdse_status tdse_describe_steps(const tdse_ctx* c, char* buf, size_t len) {
                           "{\"path\": \"cluster\", \"clusters\": %d, \"ctas_per_cluster\": %d, \"threads\": %d, "
                           "\"smem_bytes\": %d}",
                           c->cl.clusters, CL_Q, step2d_cluster_threads(), step2d_cluster_smem());
+    else if (!c->fs && c->d == 1 && !c->four1d)   // one CTA per instance
+        n = std::snprintf(buf, len, "{\"path\": \"cta\", \"shape\": %d, \"threads\": %d}", c->shape1d,
+                          c->mixed ? periodic1d_f32_threads(c->n0, c->shape1d) : 0);
+    else if (c->four1d)
+        n = std::snprintf(buf, len, "{\"path\": \"passes\", \"groups\": %d, \"four_step\": [%d, %d]}",
+                          c->step_groups < c->B ? c->step_groups : c->B, c->fs0, c->fs1);
     else
         n = std::snprintf(buf, len, "{\"path\": \"passes\", \"groups\": %d}",
-                          (c->d >= 2 || c->four1d) && !c->fs ? (c->step_groups < c->B ? c->step_groups : c->B) : 1);
+                          c->d >= 2 && !c->fs ? (c->step_groups < c->B ? c->step_groups : c->B) : 1);
     return (n < 0 || (size_t)n >= len) ? TDSE_EINVAL : TDSE_OK;
 }
 
@@ -1325,6 +1334,7 @@ static tdse_status build_items(tdse_batch* b) {
         const tdse_ctx* c = b->m[g];
         const int var = b->var[g];
         const int per = b->per[g];
+        if (var < 0) continue;              // four-step layout: its own pass chain beside the launch
         for (int b0 = 0; b0 < c->B; b0 += per) {
             MultiItem it{};
             it.g = (unsigned char)g;
@@ -1368,12 +1378,50 @@ static tdse_status member_status(tdse_batch* b, tdse_ctx* c, tdse_status st) {
     return TDSE_OK;
 }
 
-// One Adams step n of every member as one launch.
-static tdse_status batch_adams(tdse_batch* b, int n, int grid, cudaStream_t s) {
-    for (size_t g = 0; g < b->m.size(); ++g) b->args.args[g] = adams_args(b->m[g], n);
-    cudaError_t e = launch_periodic1d_multi(b->args, grid, b->smem, s);
-    if (e != cudaSuccess) return b->fail(TDSE_ECUDA, std::string("multi launch: ") + cudaGetErrorString(e));
-    for (tdse_ctx* c : b->m) c->step = n;
+// Launches of Adams step n of the run n0+1 .. n0+k of a member in the
+// four-step layout: the step's part of the 2D pass chain (adams_chain_2d).
+static cudaError_t four1d_chain_step(const tdse_ctx* c, int n0, int k, int n, cudaStream_t s) {
+    const int combo = step_combo(c);
+    auto A = [&](int m) { return group_args(c, adams_args(c, m), 0, c->B); };
+    cudaError_t e = cudaSuccess;
+    if (n == n0 + 1) e = step_part(c, A(n), combo, PART_COL_BEGIN, s);
+    if (e == cudaSuccess) e = step_part(c, A(n), combo, PART_ROW_MID, s);
+    if (e != cudaSuccess) return e;
+    if (n < n0 + k) {
+        KArgs f = A(n + 1);                 // as in adams_chain_2d
+        f.out_slot = slot_of(c, n);
+        f.e_step = n;
+        f.e_next = n + 1;
+        if (c->mixed) set_dither(c, f, n + 1, n);
+        return step_part(c, f, combo, PART_COL_FUSED, s);
+    }
+    return step_part(c, A(n), combo, PART_COL_END, s);
+}
+
+// Adams steps n0+1 .. n0+k: each step one persistent launch for the members
+// of one CTA per instance; members in the four-step layout run their pass
+// chains on their own streams beside it (forked from and joined to s).
+static tdse_status batch_adams(tdse_batch* b, int n0, int k, int grid, cudaStream_t s) {
+    bool side = false;
+    for (tdse_ctx* c : b->m) side = side || c->four1d;
+    cudaError_t e = side ? cudaEventRecord(b->fork, s) : cudaSuccess;
+    for (size_t g = 0; g < b->m.size() && e == cudaSuccess; ++g)
+        if (b->m[g]->four1d) e = cudaStreamWaitEvent(b->streams[g], b->fork, 0);
+    for (int n = n0 + 1; n <= n0 + k && e == cudaSuccess; ++n) {
+        for (size_t g = 0; g < b->m.size() && e == cudaSuccess; ++g) {
+            if (b->m[g]->four1d) e = four1d_chain_step(b->m[g], n0, k, n, b->streams[g]);
+            else b->args.args[g] = adams_args(b->m[g], n);
+        }
+        if (e == cudaSuccess) e = launch_periodic1d_multi(b->args, grid, b->smem, s);
+    }
+    for (size_t g = 0; g < b->m.size() && side; ++g) {   // always join, so that a capture can end
+        if (!b->m[g]->four1d) continue;
+        cudaError_t j = cudaEventRecord(b->join[g], b->streams[g]);
+        if (j == cudaSuccess) j = cudaStreamWaitEvent(s, b->join[g], 0);
+        if (e == cudaSuccess) e = j;
+    }
+    if (e != cudaSuccess) return b->fail(TDSE_ECUDA, std::string("fused step: ") + cudaGetErrorString(e));
+    for (tdse_ctx* c : b->m) c->step = n0 + k;
     return TDSE_OK;
 }
 
@@ -1383,7 +1431,8 @@ static tdse_status batch_adams_streams(tdse_batch* b, int n0, int k, cudaStream_
     for (size_t g = 0; g < b->m.size() && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(b->streams[g], b->fork, 0);
     for (int n = n0 + 1; n <= n0 + k && e == cudaSuccess; ++n)
         for (size_t g = 0; g < b->m.size() && e == cudaSuccess; ++g)
-            e = run(b->m[g], adams_args(b->m[g], n), step_combo(b->m[g]), b->streams[g]);
+            e = b->m[g]->four1d ? four1d_chain_step(b->m[g], n0, k, n, b->streams[g])
+                                : run(b->m[g], adams_args(b->m[g], n), step_combo(b->m[g]), b->streams[g]);
     for (size_t g = 0; g < b->m.size(); ++g) {   // always join, so that a capture can end
         cudaError_t j = cudaEventRecord(b->join[g], b->streams[g]);
         if (j == cudaSuccess) j = cudaStreamWaitEvent(s, b->join[g], 0);
@@ -1424,9 +1473,9 @@ static tdse_status batch_run(tdse_batch* b, int nsteps, cudaStream_t s) {
             k = nsteps;
             continue;
         }
-        tdse_status st = batch_adams(b, n, b->grid, s);
+        tdse_status st = batch_adams(b, n - 1, nsteps - k, b->grid, s);
         if (st != TDSE_OK) return st;
-        ++k;
+        k = nsteps;
     }
     return TDSE_OK;
 }
@@ -1468,18 +1517,18 @@ tdse_status tdse_batch_create(tdse_ctx* const* members, int count, tdse_batch** 
         if (!c || !c->ws) return TDSE_EINVAL;
         for (int h = 0; h < g; ++h)
             if (members[h] == c) return TDSE_EINVAL;
-        if (c->fs || c->d != 1 || !c->mixed || c->four1d) return TDSE_EUNSUPPORTED;
+        if (c->fs || c->d != 1 || !c->mixed) return TDSE_EUNSUPPORTED;
         if (c->cfg.dt != c0->cfg.dt || c->cfg.nsteps != c0->cfg.nsteps || c->cfg.order != c0->cfg.order ||
             c->S != c0->S)
             return TDSE_EINVAL;
-        if (multi_variant(c->n0, default_threads_1d(c->n0)) < 0) return TDSE_EUNSUPPORTED;
+        if (!c->four1d && multi_variant(c->n0, default_threads_1d(c->n0)) < 0) return TDSE_EUNSUPPORTED;
     }
     tdse_batch* b = new (std::nothrow) tdse_batch();
     if (!b) return TDSE_ENOMEM;
     b->m.assign(members, members + count);
     for (tdse_ctx* c : b->m) {
-        b->var.push_back(multi_variant(c->n0, default_threads_1d(c->n0)));
-        b->per.push_back(MULTI_CTA / default_threads_1d(c->n0));
+        b->var.push_back(c->four1d ? -1 : multi_variant(c->n0, default_threads_1d(c->n0)));
+        b->per.push_back(c->four1d ? 0 : MULTI_CTA / default_threads_1d(c->n0));
     }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -1600,11 +1649,11 @@ tdse_status tdse_batch_tune(tdse_batch* b, int trial_steps, void* stream) {
         if (r != TDSE_OK) return r;
         r = batch_prepare(b);
         if (r != TDSE_OK) return r;
-        r = batch_adams(b, n, b->grid, s);
+        r = batch_adams(b, n - 1, 1, b->grid, s);
         if (r != TDSE_OK) return r;
         cudaEventRecord(e0, s);
         for (int i = 0; i < trial_steps; ++i) {
-            r = batch_adams(b, n, b->grid, s);
+            r = batch_adams(b, n - 1, 1, b->grid, s);
             if (r != TDSE_OK) return r;
         }
         cudaEventRecord(e1, s);
@@ -1623,7 +1672,7 @@ tdse_status tdse_batch_tune(tdse_batch* b, int trial_steps, void* stream) {
     // launch shape per member: threads per instance (the FFT's points per
     // thread) among the variants built for its n, the default N / 8 first
     for (size_t g = 0; g < b->m.size() && st == TDSE_OK; ++g) {
-        for (int v = 0; v < MULTI_NVAR && st == TDSE_OK; ++v) {
+        for (int v = 0; v < MULTI_NVAR && st == TDSE_OK && b->var[g] >= 0; ++v) {
             if (multi_variant_n(v) != b->m[g]->n0 || v == b->var[g]) continue;
             const int keep_v = b->var[g], keep_p = b->per[g], keep_grid = b->grid;
             b->var[g] = v;
@@ -1645,6 +1694,7 @@ tdse_status tdse_batch_tune(tdse_batch* b, int trial_steps, void* stream) {
     }
     // instances per work item, member by member (fewer: more, smaller items)
     for (size_t g = 0; g < b->m.size() && st == TDSE_OK; ++g) {
+        if (b->var[g] < 0) continue;
         const int full = MULTI_CTA / multi_variant_t(b->var[g]);
         for (int per : {full / 2, full / 4}) {
             if (per < 1 || per == b->per[g]) continue;
@@ -1707,7 +1757,7 @@ tdse_status tdse_batch_tune(tdse_batch* b, int trial_steps, void* stream) {
         // the same choice of launch shape for each member's own kernel
         for (size_t g = 0; g < b->m.size() && st == TDSE_OK; ++g) {
             tdse_ctx* c = b->m[g];
-            if (periodic1d_f32_threads(c->n0, 1 - c->shape1d) == 0) continue;
+            if (c->four1d || periodic1d_f32_threads(c->n0, 1 - c->shape1d) == 0) continue;
             c->shape1d = 1 - c->shape1d;
             float ms2 = 0;
             st = timed_streams(ms2);
@@ -1744,7 +1794,8 @@ tdse_status tdse_batch_describe(const tdse_batch* b, char* buf, size_t len) {
         js += std::string(g ? ", " : "") + "{\"n\": " + std::to_string(b->m[g]->n0) + ", \"batch\": " +
               std::to_string(b->m[g]->B) + ", \"threads\": " + std::to_string(t) + ", \"per_item\": " +
               std::to_string(b->per[g]) + ", \"stream_threads\": " +
-              std::to_string(periodic1d_f32_threads(b->m[g]->n0, b->m[g]->shape1d)) + "}";
+              std::to_string(b->m[g]->four1d ? 0 : periodic1d_f32_threads(b->m[g]->n0, b->m[g]->shape1d)) +
+              ", \"layout\": \"" + (b->m[g]->four1d ? "passes" : "cta") + "\"}";
     }
     js += "]}";
     if (js.size() + 1 > len) return TDSE_EINVAL;

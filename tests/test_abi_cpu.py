@@ -80,6 +80,11 @@ def _cfg(native, **kw):
     (dict(n=(32768, 1), precision=1), 0),
     (dict(n=(65536, 1), precision=1), 0),
     (dict(n=(1 << 21, 1), precision=1), -7),
+    (dict(n=(16384, 1), precision=1, layout_1d=2), 0),   # the four-step passes by choice
+    (dict(n=(512, 1), layout_1d=2), 0),
+    (dict(n=(32768, 1), precision=1, layout_1d=1), -7),  # one CTA per instance not built there
+    (dict(n=(32, 1), layout_1d=2), -7),                  # the passes need n >= 64
+    (dict(n=(512, 1), layout_1d=3), -1),
     (dict(order=7), -1),
     (dict(order=10), -1),
     (dict(dt=0.0), -1),

@@ -55,10 +55,11 @@ def _golden(name, inst):
     return g
 
 
-def _solve(insts, precision, keep, stream=None):
+def _solve(insts, precision, keep, stream=None, layout_1d="auto"):
     from paper_2001_06113_gb300 import Problem
     it0 = insts[0]
-    prob = Problem(it0.shape, it0.dt, it0.nsteps, precision=precision, batch=len(insts), stream=stream)
+    prob = Problem(it0.shape, it0.dt, it0.nsteps, precision=precision, batch=len(insts), stream=stream,
+                   layout_1d=layout_1d)
     for b, it in enumerate(insts):
         prob.set_potential(it.V0, None, instance=b)
         p = it.pulse
@@ -107,16 +108,22 @@ def _member_16384():
     return inst, _golden("periodic_1d_16384.npz", inst)
 
 
-def test_1d_16384_solo():
+@pytest.mark.parametrize("layout", ["cta", "passes"])
+def test_1d_16384_solo(layout):
+    """One CTA per instance, and the four-step form through the 2D passes."""
     inst, g = _member_16384()
-    got = _solve([inst], "mixed", [10, 20])
+    got = _solve([inst], "mixed", [10, 20], layout_1d=layout)
     errs = {n: _err(got[n], g, n) for n in (10, 20)}
-    print("1D 16384 vs oracle", errs)
+    print("1D 16384", layout, "vs oracle", errs)
     assert max(errs.values()) <= 2e-6, errs
 
 
-@pytest.mark.parametrize("mode", ["fused", "streams"])
-def test_1d_16384_in_uneven_batch(mode):
+@pytest.mark.parametrize("mode,layout", [("fused", "cta"), ("streams", "cta"), ("fused", "passes"),
+                                         ("streams", "passes")])
+def test_1d_16384_in_uneven_batch(mode, layout):
+    """The n = 16384 member in the fused launch or on its own stream (one CTA
+    per instance), or in the four-step layout beside the launch / on its
+    stream; every member equals the same instance alone, bit for bit."""
     import torch
     from paper_2001_06113_gb300 import Batch, Problem
     big, g = _member_16384()
@@ -125,7 +132,8 @@ def test_1d_16384_in_uneven_batch(mode):
     stream = torch.cuda.Stream()
     probs = []
     for it in [big] + small:
-        pr = Problem(it.shape, it.dt, it.nsteps, precision="mixed", stream=stream)
+        pr = Problem(it.shape, it.dt, it.nsteps, precision="mixed", stream=stream,
+                     layout_1d=layout if it is big else "auto")
         pr.set_potential(it.V0, None)
         p = it.pulse
         pr.set_pulse(p.A0, p.omega, p.T_pulse, p.direction)
@@ -136,8 +144,11 @@ def test_1d_16384_in_uneven_batch(mode):
     batch.step(20)
     stream.synchronize()
     err = _err(probs[0].read_u(0), g, 20)
-    print(mode, "batch member 16384 vs oracle", err)
+    print(mode, layout, "batch member 16384 vs oracle", err)
     assert err <= 2e-6, err
+    assert batch.describe()["members"][0]["layout"] == layout
+    solo = _solve([big], "mixed", [20], layout_1d=layout)[20]
+    assert np.array_equal(probs[0].read_u(0), solo)
     for pr, it in zip(probs[1:], small):
         ref = PeriodicOracle(it.shape, it.dt, it.V0, it.vfac, fields.phi_callable(it.pulse, 1)).solve(it.u0, 20)
         e = rel_l2(pr.read_u(0), ref)
