@@ -87,6 +87,9 @@ def parse():
     ap.add_argument("--workload", default="periodic2d",
                     choices=["periodic2d", "free2d", "batch1d", "serve", "example1", "periodic3d", "free_ctype",
                              "free3d"])
+    ap.add_argument("--passes-from", type=int, default=16384,
+                    help="batch1d: members of n >= this use the four-step layout (0: one CTA per instance for "
+                         "all; whole solve 146.4 ms with 0, 140.9 with 8192, 140.6 with 16384)")
     ap.add_argument("--profile-adams", type=int, default=0,
                     help="profiling run: start-up + this many Adams steps of the batch, then exit")
     return ap.parse_args()
@@ -884,7 +887,9 @@ def run_batch1d(args, ws, rank, local):
     for it in insts:
         groups.setdefault(it.shape[0], []).append(it)
     sizes = sorted(groups)
-    probs = [Problem((N,), B1_DT, B1_NSTEPS, batch=len(groups[N]), precision="mixed", stream=stream) for N in sizes]
+    pf = args.passes_from
+    probs = [Problem((N,), B1_DT, B1_NSTEPS, batch=len(groups[N]), precision="mixed", stream=stream,
+                     layout_1d="passes" if pf and N >= pf else "auto") for N in sizes]
     pinned = {N: [(torch.from_numpy(it.V0).pin_memory(), None) for it in groups[N]] for N in sizes}
     pinned_u = {N: torch.from_numpy(np.stack([it.u0 for it in groups[N]])).pin_memory() for N in sizes}
 
@@ -1116,6 +1121,7 @@ def main_batch1d(args, ws, rank, local):
                                    "whole solve replayed from a CUDA graph",
                        "points_per_gpu": res["points"], "nsteps": B1_NSTEPS, "dt": B1_DT, "order": ORDER,
                        "launch_shape_tuned": res["shape"], "launch_shape_default": res["default_shape"],
+                       "four_step_layout_from_n": args.passes_from or None,
                        "l2": "flushed (256 MB write) before each timed solve; per-step working set "
                              f"{res['points'] * 100 / 1e6:.0f} MB > L2",
                        "step": "one whole solve (init, 7 Richardson start-up steps, 993 Adams steps)",

@@ -1366,6 +1366,7 @@ static int default_grid(tdse_batch* b) {
 static tdse_status batch_prepare(tdse_batch* b) {
     cudaError_t e = multi_prepare(b->smem);
     for (tdse_ctx* c : b->m) {
+        if (c->four1d) continue;            // the 2D pass kernels set their attributes at first launch
         if (e == cudaSuccess) e = periodic1d_prepare(c->n0, COMBO_F32);
         if (e == cudaSuccess && !c->off.tw128) e = periodic1d_prepare(c->n0, COMBO_F64_R32);
     }

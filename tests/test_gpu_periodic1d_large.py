@@ -6,7 +6,8 @@ grid stored transposed), FP64 from N = 16384 and mixed from N = 32768, up to
 Against the FP64 oracle (Sec. 2): at N = 16384 the stored direct-sum oracle
 solution (tests/golden), at larger N the oracle with its DFT pair through
 numpy's FFT (pinned against the direct sums in the CPU suite).  FP64 1e-12,
-mixed 2e-6; V = 0 against the exact solution.
+mixed 2e-6; V = 0 against the exact solution.  Such contexts (and any 1D
+context created with the four-step layout) join uneven batches.
 """
 import os
 
@@ -122,15 +123,49 @@ def test_potential_table_32768():
     assert err <= 1e-12, err
 
 
-def test_not_in_uneven_batches():
+@pytest.mark.parametrize("mode", ["fused", "streams"])
+def test_in_an_uneven_batch(mode):
+    """A 32768-point member (four-step layout) in an uneven batch with members
+    of one CTA per instance: its pass chain runs on its own stream beside the
+    fused launch (or all members on their streams); every member equals the
+    same instances run alone, bit for bit, and the large one stays within the
+    mixed bound of the oracle.  The FP64 residual check is not built for the
+    four-step layout."""
+    import torch
     from paper_2001_06113_gb300 import Batch, Problem, TdseError
-    a = Problem((32768,), 1e-3, 10, precision="mixed")
-    b = Problem((256,), 1e-3, 10, precision="mixed")
-    with pytest.raises(TdseError) as e:
-        Batch([a, b])
-    assert e.value.status == -7
-    with pytest.raises(TdseError) as e:
-        a.set_residual_check(2, 1e-6)
-    assert e.value.status == -7
-    a.close()
-    b.close()
+    big = [member(32768, i, nsteps=12) for i in range(2)]
+    small = [synth.periodic_1d_batch_member(40 + i, seed=4, nsteps=12, sizes=(n,)) for i, n in enumerate((512, 2048))]
+    stream = torch.cuda.Stream()
+
+    def make(insts):
+        it0 = insts[0]
+        pr = Problem(it0.shape, it0.dt, it0.nsteps, batch=len(insts), precision="mixed", stream=stream)
+        for b, it in enumerate(insts):
+            pr.set_potential(it.V0, None, instance=b)
+            p = it.pulse
+            pr.set_pulse(p.A0, p.omega, p.T_pulse, p.direction, instance=b)
+            pr.set_initial(it.u0, instance=b)
+        return pr
+
+    groups = [big, [small[0]], [small[1]]]
+    probs = [make(g) for g in groups]
+    batch = Batch(probs, stream=stream)
+    batch.set_mode(mode)
+    assert [m["layout"] for m in batch.describe()["members"]] == ["passes", "cta", "cta"]
+    batch.step(12)
+    stream.synchronize()
+    for pr, g in zip(probs, groups):
+        solo = make(g)
+        solo.step(12)
+        stream.synchronize()
+        assert np.array_equal(pr.read_u(), solo.read_u()), g[0].shape
+        solo.close()
+    ref = oracle_for(big[1], transform="fft").solve(big[1].u0, 12)
+    e = rel_l2(probs[0].read_u(1), ref)
+    assert e <= 2e-6, e
+    with pytest.raises(TdseError) as err:
+        probs[0].set_residual_check(2, 1e-6)
+    assert err.value.status == -7
+    batch.close()
+    for pr in probs:
+        pr.close()
