@@ -378,8 +378,9 @@ tdse_status tdse_set_step_groups(tdse_ctx* ctx, int groups);
 
 /* 1D periodic TDSE_MIXED contexts of n <= 16384 (one CTA per instance):
  * launch shape of the step kernel.  Shape 0 (default): n/8 threads per
- * instance (32..1024); shape 1: half of them, each thread taking twice the
- * points of every transform pass (built for n >= 512).  The transform's
+ * instance (32..1024); shape 1: for n = 8192 1024 threads (8 points each),
+ * for the other n >= 512 half the default threads, each thread taking twice
+ * the points of every transform pass.  The transform's
  * butterflies and the step's arithmetic are the same in both (Sec. 2.1-2.2),
  * so the results are the same bits; tdse_batch_tune sets the faster shape
  * per member.  Errors: TDSE_EUNSUPPORTED for another context or where shape 1

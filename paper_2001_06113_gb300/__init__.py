@@ -338,7 +338,8 @@ class Problem:
 
     def set_shape_1d(self, shape: int):
         """1D mixed contexts: launch shape of the step kernel (0: n/8 threads per
-        instance; 1: half of them, n >= 512).  Same results."""
+        instance, at most 512 below n = 16384; 1: 1024 threads for n = 8192, half
+        the default for the other n >= 512).  Same results."""
         _check(self._lib.tdse_set_shape_1d(self._ctx, int(shape)), self._ctx)
 
     @property

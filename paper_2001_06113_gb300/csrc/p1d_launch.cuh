@@ -24,16 +24,20 @@ namespace tdse {
 #endif
 template <class C, int N, int T>
 constexpr int p1d_min_blocks() {
-    if (!std::is_same<C, float2>::value || N > 8192) return 1;
+    if (!std::is_same<C, float2>::value || N > 8192 || T > 512) return 1;
     if (T > 256) return P1D_MINB512;
     const int b = P1D_MINW32 * 32 / T;
     return b < 1 ? 1 : (b > 32 ? 32 : b);
 }
 
 // Threads per instance of the alternative launch shape the batch tuner may
-// pick (KArgs::shape1d = 1): half the default, so twice the points per
-// thread (0: none built for this n).
-constexpr int alt_threads_1d(int N) { return N >= 512 && threads_1d(N) / 2 >= 32 ? threads_1d(N) / 2 : 0; }
+// pick (KArgs::shape1d = 1): n = 8192 with 1024 threads (8 points each, one
+// radix-8 butterfly per thread and pass, against 16 points for the default
+// 512), the other n >= 512 with half the default threads (twice the points
+// per thread); 0: none built for this n.
+constexpr int alt_threads_1d(int N) {
+    return N == 8192 ? 1024 : (N >= 512 && threads_1d(N) / 2 >= 32 ? threads_1d(N) / 2 : 0);
+}
 
 template <class C, class RT, int N, int T = threads_1d(N)>
 __global__ void __launch_bounds__(T, p1d_min_blocks<C, N, T>()) k_periodic1d(const KArgs a) {
