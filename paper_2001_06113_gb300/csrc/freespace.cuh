@@ -67,12 +67,19 @@ template <> struct FsThreads<float2> { static constexpr int value = FS_T32; };
 // dense-row and the grid phases of such a line keep only 64 threads busy and
 // the CTA's barriers then stall the rest.  Per 64^3 Adams step (nu = 256):
 // 256 / 128 / 64 threads 4.99 / 3.19 / 2.30 ms with FP32 transforms,
-// 18.1 / 14.3 / 13.7 ms in FP64 (same results).
+// 18.1 / 14.3 / 13.7 ms in FP64 (same results).  Not for longer lines: the
+// 256-point lines of the 2D 256^2 step (nu = 2048) with 128 / 64 threads
+// 0.634 / 1.204 ms against 0.438 ms (FP32 transforms), 2.26 / 3.24 against
+// 2.25 ms (FP64).
 #ifndef FS_T_SMALL
 #define FS_T_SMALL 64
 #endif
+#ifndef FS_SMALL_M
+#define FS_SMALL_M 64
+#endif
 template <class C, int M> struct FsThr {
-    static constexpr int value = M <= 64 && FS_T_SMALL < FsThreads<C>::value ? FS_T_SMALL : FsThreads<C>::value;
+    static constexpr int value =
+        M <= FS_SMALL_M && FS_T_SMALL < FsThreads<C>::value ? FS_T_SMALL : FsThreads<C>::value;
 };
 template <class C, int M> struct FsMinB {
     static constexpr int value = MinBlocks<C>::value * FsThreads<C>::value / FsThr<C, M>::value;
