@@ -47,10 +47,15 @@ namespace fs {
 // kernels keep the FP64 pipe busy at two CTAs (left to itself the compiler
 // takes 152 registers for the row pass: one CTA per SM, 2.46 against 2.26 ms
 // per 256^2 step); the FP32 ones wait on memory latency and need more warps in
-// flight (4 CTAs: 64 registers, a few words spilled; 0.41 ms against 0.45 ms
-// per 256^2 step at 2 or 3 CTAs).
+// flight (per 256^2 step: 2 or 3 CTAs 0.45 ms, 4 CTAs (64 registers) 0.430,
+// 5 CTAs (51 registers, more spilled) 0.400, 6 CTAs 0.426 ms).
 #ifndef FS_MINB32
-#define FS_MINB32 4
+#define FS_MINB32 5
+#endif
+// The same budget for the short-line kernels (FsThr below), in 256-thread
+// CTA equivalents: measured at 4.
+#ifndef FS_MINB32_SMALL
+#define FS_MINB32_SMALL 4
 #endif
 template <class C> struct MinBlocks { static constexpr int value = 2; };   // FP64: 128 registers, 2 CTAs/SM
 template <> struct MinBlocks<float2> { static constexpr int value = FS_MINB32; };
@@ -82,7 +87,9 @@ template <class C, int M> struct FsThr {
         M <= FS_SMALL_M && FS_T_SMALL < FsThreads<C>::value ? FS_T_SMALL : FsThreads<C>::value;
 };
 template <class C, int M> struct FsMinB {
-    static constexpr int value = MinBlocks<C>::value * FsThreads<C>::value / FsThr<C, M>::value;
+    static constexpr bool SMALL = FsThr<C, M>::value < FsThreads<C>::value;
+    static constexpr int base = (SMALL && std::is_same<C, float2>::value) ? FS_MINB32_SMALL : MinBlocks<C>::value;
+    static constexpr int value = base * FsThreads<C>::value / FsThr<C, M>::value;
 };
 
 __device__ __forceinline__ double2 zero2() { return make_double2(0.0, 0.0); }
