@@ -202,7 +202,7 @@ def launches_per_solve(dim: int, mixed: bool, path: str = "passes") -> int:
 TRAFFIC_BYTES_PER_POINT_STEP = {("mixed", "passes"): 72.143 + 16.105}
 TRAFFIC_NOTE = {("mixed", "passes"): "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_col_fused_ip<512> + "
                 "k_row_mid<float2,512>, batch 8 in 4 groups (2 instances per launch), scaled by points: reads "
-                "72.1 + 16.1 B per point-step; the state, history and intermediate writes (40 B) stayed in L2 "
+                "72.1 + 16.1 B per point-step (re-taken on the current kernels); the state, history and intermediate writes (40 B) stayed in L2 "
                 "within that capture (profiles/step2d_512x512_mixed_fused.md)"}
 
 
@@ -418,7 +418,7 @@ FS_METRICS = {"fp64": "point-steps/s (2D free space 256^2, nu=2048, 8th-order, T
 # DRAM bytes of one fused k_fs_row launch (end + begin) of one 256^2 instance,
 # from the ncu capture summarised in profiles/step2d_free_256x256_fp64.md.
 # FP32-transform variant: profiles/step2d_free_256x256_mixed.md (4 CTAs per SM).
-FS_ROW_TRAFFIC = {"fp64": 484.806912e6 + 123.36256e6, "mixed": 277.45024e6 + 114.500352e6}
+FS_ROW_TRAFFIC = {"fp64": 484.806912e6 + 123.36256e6, "mixed": 277.87e6 + 122.29e6}
 # FP32 FMA rate: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
