@@ -398,9 +398,13 @@ __global__ void __launch_bounds__(T2D, min_blocks_2d<C>()) k_col_end(const KArgs
 #ifndef TDSE_PF_ROWS
 #define TDSE_PF_ROWS 32
 #endif
+// 3D mixed chains use this kernel for their fused column pass as well
+#ifndef TDSE_COL_IP_3D
+#define TDSE_COL_IP_3D 1
+#endif
 constexpr int PF_ROWS = TDSE_PF_ROWS;
 
-template <int N0>
+template <int N0, bool D3>
 __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_fused_ip(const KArgs a) {
     constexpr int L = LANES2D;
     constexpr int RC = PF_ROWS < N0 ? PF_ROWS : N0;     // rows per chunk
@@ -461,6 +465,16 @@ __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_fused_ip(const KArgs a
     const int lane_t = threadIdx.x % L;
     const float2 en_1 = __ldg(&en[a.tn0 + c0 + lane_t]);
     const float2 en1_1 = __ldg(&en1[a.tn0 + c0 + lane_t]);
+    // D3 (3D column blocks, column index i1 n2 + i2): E_n = (e[m0] e[n0 + i1]) e[n0 + n1 + i2] as in e_2d
+    float2 e3_1 = en_1, e3_2 = en_1, e31_1 = en1_1, e31_2 = en1_1;
+    if constexpr (D3) {
+        int i1, i2;
+        split12(a, c0 + lane_t, i1, i2);
+        e3_1 = __ldg(&en[a.tn0 + i1]);
+        e3_2 = __ldg(&en[a.tn0 + a.tn1 + i2]);
+        e31_1 = __ldg(&en1[a.tn0 + i1]);
+        e31_2 = __ldg(&en1[a.tn0 + a.tn1 + i2]);
+    }
     float2* ring_out = ringb + (size_t)a.out_slot * NP;
 
 #pragma unroll 1
@@ -473,11 +487,23 @@ __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_fused_ip(const KArgs a
             const int m0 = c * RC + r, m1 = c0 + lane;
             const int pos = m0 * L + lane;
             const size_t idx = (size_t)m0 * n1 + m1;
-            const float2 e1n = ONE_COL ? en_1 : __ldg(&en[a.tn0 + m1]);
-            const float2 e1n1 = ONE_COL ? en1_1 : __ldg(&en1[a.tn0 + m1]);
             // end of step n: r~ = z_n R / E_n into the ring, v^_n
             const float2 R = cscale(buf[pos], scale);
-            const float2 rv = cmul(z, cmul(conjf2(cmul(__ldg(&en[m0]), e1n)), R));
+            float2 rv;
+            if constexpr (D3) {
+                if constexpr (!ONE_COL) {   // column factors of this element's column
+                    int i1, i2;
+                    split12(a, m1, i1, i2);
+                    e3_1 = __ldg(&en[a.tn0 + i1]);
+                    e3_2 = __ldg(&en[a.tn0 + a.tn1 + i2]);
+                    e31_1 = __ldg(&en1[a.tn0 + i1]);
+                    e31_2 = __ldg(&en1[a.tn0 + a.tn1 + i2]);
+                }
+                rv = cmul(z, cmul(conjf2(cmul(cmul(__ldg(&en[m0]), e3_1), e3_2)), R));
+            } else {
+                const float2 e1n = ONE_COL ? en_1 : __ldg(&en[a.tn0 + m1]);
+                rv = cmul(z, cmul(conjf2(cmul(__ldg(&en[m0]), e1n)), R));
+            }
             ring_out[idx] = rv;
             const float4 v = ip_update(a, ch.st[it], rv);
             // begin of step n+1: X = v^_n - i h sum_j c_j r~_{n+1-j}
@@ -493,7 +519,12 @@ __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_fused_ip(const KArgs a
             }
             const float4 X = ff_minus_i_times(v, a.h_hi, a.h_lo, S);
             st[idx] = X;
-            buf[pos] = cmul(cmul(__ldg(&en1[m0]), e1n1), make_float2(X.x, X.y));
+            if constexpr (D3) {
+                buf[pos] = cmul(cmul(cmul(__ldg(&en1[m0]), e31_1), e31_2), make_float2(X.x, X.y));
+            } else {
+                const float2 e1n1 = ONE_COL ? en1_1 : __ldg(&en1[a.tn0 + m1]);
+                buf[pos] = cmul(cmul(__ldg(&en1[m0]), e1n1), make_float2(X.x, X.y));
+            }
         }
         __syncthreads();                               // buffer c & 1 free
         if (c + 2 < NCH) stage(c + 2);
@@ -537,15 +568,15 @@ static cudaError_t col_end_n(const KArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int N0>
+template <int N0, bool D3 = false>
 static cudaError_t col_fused_ip_n(const KArgs& a, cudaStream_t s) {
     constexpr int RC = PF_ROWS < N0 ? PF_ROWS : N0;
     const size_t smem = (size_t)N0 * LANES2D * sizeof(float2) +
                         2 * (size_t)RC * LANES2D * (sizeof(float4) + (MAX_HIST - 1) * sizeof(float2));
     static bool done = false;
-    cudaError_t e = set_smem(k_col_fused_ip<N0>, smem, done);
+    cudaError_t e = set_smem(k_col_fused_ip<N0, D3>, smem, done);
     if (e != cudaSuccess) return e;
-    k_col_fused_ip<N0><<<dim3(a.n1 / LANES2D, a.B), T2D, smem, s>>>(a);
+    k_col_fused_ip<N0, D3><<<dim3(a.n1 / LANES2D, a.B), T2D, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -689,6 +720,20 @@ static KArgs row3(const KArgs& a) {
     return r;
 }
 
+// The fused column pass of a 3D chain: the staged interaction-picture kernel
+// for mixed steps (3D column blocks), the generic one otherwise.
+template <class C, class RT>
+static cudaError_t col_fused_3d(const KArgs& a, cudaStream_t s) {
+    if constexpr (std::is_same<C, float2>::value && std::is_same<RT, float2>::value) {
+        if (TDSE_COL_IP_3D && a.mode == MODE_STEP && a.ip) {
+#define TDSE_CFI3(n) col_fused_ip_n<n, true>
+            TDSE_SWITCH_N(a.n0, TDSE_CFI3)
+#undef TDSE_CFI3
+        }
+    }
+    return col_fused<C, RT>(a, s);
+}
+
 template <class C, class RT>
 static cudaError_t part3d(const KArgs& a, int part, cudaStream_t s) {
     const KArgs c = col3(a), r = row3(a);
@@ -703,7 +748,7 @@ static cudaError_t part3d(const KArgs& a, int part, cudaStream_t s) {
             return col_end<C, RT>(c, s);
         case PART_COL_FUSED:
             if ((e = axis1<C>(a, false, a.aux2, s)) != cudaSuccess) return e;
-            if ((e = col_fused<C, RT>(c, s)) != cudaSuccess) return e;
+            if ((e = col_fused_3d<C, RT>(c, s)) != cudaSuccess) return e;
             return axis1<C>(a, true, a.aux, s);
         default: return cudaErrorInvalidValue;
     }

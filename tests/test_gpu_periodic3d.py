@@ -101,6 +101,19 @@ def test_3d_mixed_within_tolerance():
     assert err <= 2e-6, err
 
 
+@pytest.mark.parametrize("shape", [(16, 16, 32), (64, 8, 64), (8, 16, 16)])
+def test_3d_mixed_single_steps_equal_the_fused_chain(shape):
+    """A run of Adams steps (the column pass of one step fused with the next,
+    the mode work staged in shared memory) gives the bits of the same steps
+    taken one at a time (separate begin / end column passes), for column
+    blocks of one column per thread (n0 >= 32) and of several (n0 = 8)."""
+    inst = _inst(shape, 31, nsteps=16, vamp=6.0)
+    fused = gpu_solve([inst], "mixed", keep=(8,))
+    single = gpu_solve([inst], "mixed", keep=tuple(range(1, 17)))
+    for n in (8, 16):
+        assert np.array_equal(fused[n], single[n]), n
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_3d_batch_members_and_groups_equal_solo_runs(precision):
     insts = [_inst((8, 8, 16), 20 + i, nsteps=11) for i in range(3)]
