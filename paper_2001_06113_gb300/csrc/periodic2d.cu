@@ -402,10 +402,17 @@ __global__ void __launch_bounds__(T2D, min_blocks_2d<C>()) k_col_end(const KArgs
 #ifndef TDSE_COL_IP_3D
 #define TDSE_COL_IP_3D 1
 #endif
+// ... and 1D grids in the four-step layout
+#ifndef TDSE_COL_IP_1D
+#define TDSE_COL_IP_1D 1
+#endif
 constexpr int PF_ROWS = TDSE_PF_ROWS;
 
-template <int N0, bool D3>
+// VAR 0: 2D column blocks; 1: 3D (column index i1 n2 + i2); 2: a 1D grid in
+// the four-step layout (flat1d: E_n of the flattened mode index).
+template <int N0, int VAR>
 __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_fused_ip(const KArgs a) {
+    constexpr bool D3 = VAR == 1, FLAT = VAR == 2;
     constexpr int L = LANES2D;
     constexpr int RC = PF_ROWS < N0 ? PF_ROWS : N0;     // rows per chunk
     constexpr int NCH = N0 / RC;
@@ -459,12 +466,15 @@ __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_fused_ip(const KArgs a
     // E_n(m0, m1) = e_n[m0] e_n[n0 + m1] (e_2d): the axis-1 factors of the
     // column a thread keeps (RC * L == T2D: one column per thread) are loaded once
     const size_t erow = (size_t)(a.tn0 + a.tn1 + a.tn2);
-    const float2* en = a.e2d + ((size_t)b * (a.ntf / 8 + 1) + a.e_step) * erow;
-    const float2* en1 = a.e2d + ((size_t)b * (a.ntf / 8 + 1) + a.e_next) * erow;
+    const float2* en = FLAT ? nullptr : a.e2d + ((size_t)b * (a.ntf / 8 + 1) + a.e_step) * erow;
+    const float2* en1 = FLAT ? nullptr : a.e2d + ((size_t)b * (a.ntf / 8 + 1) + a.e_next) * erow;
     constexpr bool ONE_COL = (RC * L == T2D);
     const int lane_t = threadIdx.x % L;
-    const float2 en_1 = __ldg(&en[a.tn0 + c0 + lane_t]);
-    const float2 en1_1 = __ldg(&en1[a.tn0 + c0 + lane_t]);
+    float2 en_1 = make_float2(0.f, 0.f), en1_1 = en_1;
+    if constexpr (!FLAT) {
+        en_1 = __ldg(&en[a.tn0 + c0 + lane_t]);
+        en1_1 = __ldg(&en1[a.tn0 + c0 + lane_t]);
+    }
     // D3 (3D column blocks, column index i1 n2 + i2): E_n = (e[m0] e[n0 + i1]) e[n0 + n1 + i2] as in e_2d
     float2 e3_1 = en_1, e3_2 = en_1, e31_1 = en1_1, e31_2 = en1_1;
     if constexpr (D3) {
@@ -490,7 +500,9 @@ __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_fused_ip(const KArgs a
             // end of step n: r~ = z_n R / E_n into the ring, v^_n
             const float2 R = cscale(buf[pos], scale);
             float2 rv;
-            if constexpr (D3) {
+            if constexpr (FLAT) {
+                rv = cmul(z, cmul(conjf2(e_1d(a, b, a.e_step, m0 * n1 + m1)), R));
+            } else if constexpr (D3) {
                 if constexpr (!ONE_COL) {   // column factors of this element's column
                     int i1, i2;
                     split12(a, m1, i1, i2);
@@ -519,7 +531,9 @@ __global__ void __launch_bounds__(T2D, TDSE_MINB2D) k_col_fused_ip(const KArgs a
             }
             const float4 X = ff_minus_i_times(v, a.h_hi, a.h_lo, S);
             st[idx] = X;
-            if constexpr (D3) {
+            if constexpr (FLAT) {
+                buf[pos] = cmul(e_1d(a, b, a.e_next, m0 * n1 + m1), make_float2(X.x, X.y));
+            } else if constexpr (D3) {
                 buf[pos] = cmul(cmul(cmul(__ldg(&en1[m0]), e31_1), e31_2), make_float2(X.x, X.y));
             } else {
                 const float2 e1n1 = ONE_COL ? en1_1 : __ldg(&en1[a.tn0 + m1]);
@@ -568,15 +582,15 @@ static cudaError_t col_end_n(const KArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int N0, bool D3 = false>
+template <int N0, int VAR = 0>
 static cudaError_t col_fused_ip_n(const KArgs& a, cudaStream_t s) {
     constexpr int RC = PF_ROWS < N0 ? PF_ROWS : N0;
     const size_t smem = (size_t)N0 * LANES2D * sizeof(float2) +
                         2 * (size_t)RC * LANES2D * (sizeof(float4) + (MAX_HIST - 1) * sizeof(float2));
     static bool done = false;
-    cudaError_t e = set_smem(k_col_fused_ip<N0, D3>, smem, done);
+    cudaError_t e = set_smem(k_col_fused_ip<N0, VAR>, smem, done);
     if (e != cudaSuccess) return e;
-    k_col_fused_ip<N0, D3><<<dim3(a.n1 / LANES2D, a.B), T2D, smem, s>>>(a);
+    k_col_fused_ip<N0, VAR><<<dim3(a.n1 / LANES2D, a.B), T2D, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -644,6 +658,11 @@ static cudaError_t part2d(const KArgs& a, int part, cudaStream_t s) {
 #define TDSE_CFI(n) col_fused_ip_n<n>
                     TDSE_SWITCH_N(a.n0, TDSE_CFI)
 #undef TDSE_CFI
+                }
+                if (TDSE_COL_IP_1D && a.mode == MODE_STEP && a.ip && a.flat1d) {
+#define TDSE_CFI1(n) col_fused_ip_n<n, 2>
+                    TDSE_SWITCH_N(a.n0, TDSE_CFI1)
+#undef TDSE_CFI1
                 }
             }
             return col_fused<C, RT>(a, s);
@@ -726,7 +745,7 @@ template <class C, class RT>
 static cudaError_t col_fused_3d(const KArgs& a, cudaStream_t s) {
     if constexpr (std::is_same<C, float2>::value && std::is_same<RT, float2>::value) {
         if (TDSE_COL_IP_3D && a.mode == MODE_STEP && a.ip) {
-#define TDSE_CFI3(n) col_fused_ip_n<n, true>
+#define TDSE_CFI3(n) col_fused_ip_n<n, 1>
             TDSE_SWITCH_N(a.n0, TDSE_CFI3)
 #undef TDSE_CFI3
         }

@@ -107,6 +107,32 @@ def test_batch_and_groups_equal_solo_runs(precision):
         assert np.array_equal(batched[b], gpu_solve([it], precision)[10][0]), b
 
 
+@pytest.mark.parametrize("N", [16384, 32768])
+def test_mixed_single_steps_equal_the_fused_chain(N):
+    """Mixed runs of Adams steps in the four-step layout (the staged column
+    kernel fusing the end of a step with the begin of the next) give the bits
+    of the same steps taken one at a time through the generic column passes."""
+    from paper_2001_06113_gb300 import Problem
+    inst = member(N, i=30, nsteps=16)
+
+    def run(chunks):
+        prob = Problem((N,), inst.dt, inst.nsteps, precision="mixed", layout_1d="passes")
+        prob.set_potential(inst.V0, inst.vfac_table())
+        p = inst.pulse
+        prob.set_pulse(p.A0, p.omega, p.T_pulse, p.direction)
+        prob.set_initial(inst.u0)
+        out = []
+        for k in chunks:
+            prob.step(k)
+            out.append(prob.read_u(0))
+        prob.close()
+        return out
+
+    fused = run([8, 8])
+    single = run([1] * 16)
+    assert np.array_equal(fused[0], single[7]) and np.array_equal(fused[1], single[15])
+
+
 def test_potential_table_32768():
     inst = member(32768, i=20, nsteps=10)
     x = synth.periodic_grid(32768)
