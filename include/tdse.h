@@ -154,7 +154,8 @@ typedef struct {
     int c_transform;
     /* free space, dim = 3: nu of axis 2 (as nu[2] above).  Appended last. */
     int nu_z;
-    /* periodic dim = 1: how a step transforms an instance.  TDSE_LAYOUT_CTA:
+    /* periodic dim = 1: how a step transforms an instance (the DFT pair of
+     * Sec. 2.1, eq. ftperdisc; the step is the same).  TDSE_LAYOUT_CTA:
      * one CTA per instance, the whole n-point FFT in its shared memory (n up
      * to 8192 in TDSE_FP64, 16384 in TDSE_MIXED).  TDSE_LAYOUT_PASSES: the
      * four-step form of the same DFT (n = n0 n1, the 2D row and column pass
