@@ -33,8 +33,15 @@ from typing import Callable, Dict, List, Optional, Sequence
 
 import numpy as np
 
+# 1D requests of at least this many points run in the four-step layout: one
+# instance of n = 16384 in one CTA holds a single SM for each step, the
+# four-step passes spread it over 2 n0 / 8 CTAs (the layout beyond 16384
+# anyway).
+FOUR_STEP_FROM = 16384
+
 
 @dataclasses.dataclass
+
 class Request:
     """One solve: `inst` carries grid shape, V0 and its time factor, the pulse,
     u0, dt and the step count; `bc`/`precision` and the free-space contour
@@ -103,6 +110,8 @@ class TorchBackend(Backend):
         if req.bc == "free":
             kw = dict(bc="free", nu=req.free["nu"], H=req.free["H"], gauss_q=req.free.get("gauss_q", 10),
                       n_r=req.free.get("n_r", 1))
+        elif len(it.shape) == 1 and it.shape[0] >= FOUR_STEP_FROM:
+            kw = dict(layout_1d="passes")
         # sized on the host before any device memory is taken
         return {"req": req, "stream": None, "kw": kw, "prob": None, "event": None,
                 "bytes": Problem.workspace_bytes_for(it.shape, it.dt, it.nsteps, precision=req.precision, **kw)}
